@@ -1,0 +1,258 @@
+"""Pins of the FP64 CPU oracle against what the mathematics and physics fix (no GPU).
+
+Each test states the invariant it checks. Together they are chosen so that a dropped term, a wrong sign, a
+wrong index or a transposed operand anywhere in the oracle breaks at least one of them.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import rafem_oracle as O
+from paper_2409_13036_b300 import meshgen as mg
+
+L = 0.04  # half side of the cube, metres
+
+
+def _slab_mesh(n, V0=10.0, T_D=37.0, jitter=0.0):
+    """Cube with Dirichlet data on the two x faces only (Neumann elsewhere), for 1-D reductions."""
+    m = mg.cube_mesh(n, jitter=jitter, seed=7)
+    fx = (m.lattice[:, 0] == 0) | (m.lattice[:, 0] == n)
+    return dataclasses.replace(m, bc_V=fx.astype(np.uint8), g_V=np.where(m.lattice[:, 0] == n, V0, 0.0),
+                               bc_T=fx.astype(np.uint8), g_T=np.where(fx, T_D, 0.0))
+
+
+def test_patch_test_linear_potential_reproduced():
+    """P1 patch test: with Dirichlet data from a linear field on all faces, the FE solution equals the field
+    at every node, on a jittered mesh with uniform conductivity."""
+    m = mg.cube_mesh(6, jitter=0.1, seed=11)
+    x, y, z = m.coords.T
+    lin = 3.0 + 200.0 * x - 500.0 * y + 700.0 * z
+    vol, grad = O.element_geometry(m.coords, m.tets)
+    K = O.assemble(O.element_stiffness(np.full(m.n_tets, 0.4), vol, grad), m.tets, m.n_nodes)
+    face = m.bc_T.astype(bool)
+    A, b = O.dirichlet_lift(K, np.zeros(m.n_nodes), face, np.where(face, lin, 0.0))
+    u = O.solve(A, b)
+    assert (~face).sum() > 50
+    np.testing.assert_allclose(u, lin, rtol=0, atol=1e-12 * np.abs(lin).max())
+
+
+def test_stiffness_rows_sum_to_zero_and_symmetric():
+    """K 1 = 0 (constants are in the kernel of the Laplacian) and K = K^T, with per-element conductivity."""
+    m = mg.cube_mesh(5, jitter=0.1, seed=3, sigma0="lognormal")
+    vol, grad = O.element_geometry(m.coords, m.tets)
+    K = O.assemble(O.element_stiffness(m.sigma0, vol, grad), m.tets, m.n_nodes)
+    scale = np.abs(K).max()
+    assert np.abs(K @ np.ones(m.n_nodes)).max() < 1e-13 * scale
+    assert abs(K - K.T).max() < 1e-15 * scale
+
+
+def test_element_stiffness_psd_rank3():
+    """Each element stiffness is symmetric positive semidefinite with a one-dimensional kernel (constants)."""
+    m = mg.cube_mesh(3, jitter=0.1, seed=5)
+    vol, grad = O.element_geometry(m.coords, m.tets)
+    Ke = O.element_stiffness(np.ones(m.n_tets), vol, grad)
+    w = np.linalg.eigvalsh(Ke)
+    assert np.all(np.abs(w[:, 0]) < 1e-12 * w[:, -1])
+    assert np.all(w[:, 1] > 1e-6 * w[:, -1])
+
+
+def test_element_matrices_brute_force():
+    """Independent route: shape functions from the 4x4 system [1 x y z] c = e_a, stiffness from their
+    gradients, mass by the 4-point degree-2 tetrahedral quadrature (exact for products of linears)."""
+    m = mg.cube_mesh(2, jitter=0.15, seed=9)
+    vol, grad = O.element_geometry(m.coords, m.tets)
+    Ke = O.element_stiffness(np.full(m.n_tets, 2.0), vol, grad)
+    Me = O.element_mass(vol)
+    a_, b_ = 0.5854101966249685, 0.1381966011250105
+    bary = np.full((4, 4), b_) + np.eye(4) * (a_ - b_)          # quadrature points in barycentric coords
+    for e in range(m.n_tets):
+        X = m.coords[m.tets[e]]
+        P = np.hstack([np.ones((4, 1)), X])
+        C = np.linalg.solve(P, np.eye(4))                        # column a: coefficients of phi_a
+        g = C[1:, :].T                                            # [4, 3]
+        v = abs(np.linalg.det(X[1:] - X[0])) / 6.0
+        np.testing.assert_allclose(vol[e], v, rtol=1e-13)
+        np.testing.assert_allclose(Ke[e], 2.0 * v * g @ g.T, rtol=1e-11, atol=1e-12 * np.abs(Ke[e]).max())
+        pts = bary @ X                                            # physical quadrature points
+        phi = np.hstack([np.ones((4, 1)), pts]) @ C               # phi[q, a]
+        Mq = v / 4.0 * phi.T @ phi
+        np.testing.assert_allclose(Me[e], Mq, rtol=1e-12)
+
+
+def test_mass_matrix_totals():
+    """sum(M) equals the cube volume (80 mm)^3 and M 1 equals each node's share sum_e vol_e / 4."""
+    m = mg.cube_mesh(5, jitter=0.1, seed=2)
+    vol, _ = O.element_geometry(m.coords, m.tets)
+    M = O.assemble(O.element_mass(vol), m.tets, m.n_nodes)
+    np.testing.assert_allclose(M.sum(), 0.08 ** 3, rtol=1e-13)
+    share = np.zeros(m.n_nodes)
+    np.add.at(share, m.tets.ravel(), np.repeat(vol / 4.0, 4))
+    np.testing.assert_allclose(M @ np.ones(m.n_nodes), share, rtol=1e-13)
+
+
+def test_sigma_uses_element_mean_temperature():
+    """For a linear temperature field the element mean equals the field at the centroid, so
+    sigma_e = sigma0_e (1 + alpha (T(centroid) - 37)) exactly; a uniform +10 degC raises K by 15%."""
+    m = mg.cube_mesh(4, jitter=0.1, seed=4, sigma0="lognormal")
+    x, y, z = m.coords.T
+    T = 37.0 + 100.0 * x + 50.0 * y - 80.0 * z
+    cen = m.coords[m.tets].mean(axis=1)
+    Tc = 37.0 + 100.0 * cen[:, 0] + 50.0 * cen[:, 1] - 80.0 * cen[:, 2]
+    np.testing.assert_allclose(O.sigma_of_T(m.sigma0, T, m.tets, 0.015), m.sigma0 * (1 + 0.015 * (Tc - 37.0)),
+                               rtol=1e-14)
+    model = O.Model(m)
+    A37, _ = model.system_V(np.full(m.n_nodes, 37.0))
+    A47, _ = model.system_V(np.full(m.n_nodes, 47.0))
+    free = ~m.bc_V.astype(bool)
+    rows = np.repeat(np.arange(m.n_nodes), np.diff(A37.indptr))
+    sel = free[rows] & free[A37.indices]
+    np.testing.assert_allclose(A47.data[sel], 1.15 * A37.data[sel], rtol=1e-13)
+
+
+def test_joule_uniform_field():
+    """A potential linear in x (E = V0 / 2L) gives Q_e = sigma E^2 on every element, exactly."""
+    m = mg.cube_mesh(4, jitter=0.12, seed=6)
+    V0 = 10.0
+    V = V0 * (m.coords[:, 0] + L) / (2 * L)
+    _, grad = O.element_geometry(m.coords, m.tets)
+    Q = O.joule(np.full(m.n_tets, 0.333), V, m.tets, grad)
+    np.testing.assert_allclose(Q, 0.333 * (V0 / (2 * L)) ** 2, rtol=1e-12)
+
+
+def test_joule_power_balance():
+    """Total Joule power sum_e Q_e vol_e equals V^T K V, and for the discrete solution it equals the
+    electrode voltage times the net current sum_{i in electrode} (K V)_i (outer faces are at 0 V)."""
+    m = mg.cube_mesh(6, jitter=0.1, seed=8, sigma0="lognormal")
+    model = O.Model(m)
+    T0 = np.full(m.n_nodes, 37.0)
+    A, b = model.system_V(T0)
+    V = O.solve(A, b)
+    sig = model.sigma(T0)
+    Q = O.joule(sig, V, model.tets, model.grad)
+    P = np.sum(Q * model.vol)
+    K = O.assemble(O.element_stiffness(sig, model.vol, model.grad), m.tets, m.n_nodes)
+    np.testing.assert_allclose(P, V @ (K @ V), rtol=1e-12)
+    el = m.electrode.astype(bool) & ~m.bc_T.astype(bool)
+    I_el = (K @ V)[m.electrode.astype(bool)]
+    np.testing.assert_allclose(P, m.V_electrode * I_el.sum(), rtol=1e-9)
+    assert el.sum() > 0
+    F = O.load_vector(Q, model.vol, m.tets, m.n_nodes)
+    np.testing.assert_allclose(F.sum(), P, rtol=1e-13)
+
+
+def test_uniform_temperature_decay_closed_form():
+    """All-Neumann thermal problem, no source, uniform T^n: the step gives
+    T^{n+1} = ((rho_c/dt) T^n + perf T_a) / (rho_c/dt + perf) at every node (K 1 = 0; M preserves constants)."""
+    m = mg.cube_mesh(4, jitter=0.1, seed=12)
+    m = dataclasses.replace(m, bc_T=np.zeros(m.n_nodes, np.uint8))
+    for dt in (1.0, 30.0):
+        p = O.Params(dt=dt)
+        model = O.Model(m, p)
+        A, b = model.system_T(np.full(m.n_nodes, 50.0), np.zeros(m.n_tets))
+        T1 = O.solve(A, b)
+        expect = (p.rho_c / dt * 50.0 + p.perf * p.T_a) / (p.rho_c / dt + p.perf)
+        np.testing.assert_allclose(T1, expect, rtol=1e-12)
+
+
+def test_body_temperature_is_a_fixed_point():
+    """With the electrode at 0 V there is no heating; T = 37 everywhere stays 37 through full steps
+    (checks the sign of the perfusion term against T_a = 37 and the lifted outer faces)."""
+    m = dataclasses.replace(mg.cube_mesh(5, jitter=0.1, seed=13), V_electrode=0.0)
+    m = dataclasses.replace(m, g_V=np.zeros(m.n_nodes))
+    model = O.Model(m)
+    T = np.full(m.n_nodes, 37.0)
+    for _ in range(2):
+        T, V, _ = model.step(T)
+    np.testing.assert_allclose(T, 37.0, rtol=0, atol=1e-11)
+    assert np.abs(V).max() == 0.0
+
+
+def test_slab_steady_joule_quadratic_exact():
+    """1-D reduction through the full step: plates at 0 and V0 on the x faces give uniform Q = sigma E^2;
+    with perfusion off and dt -> infinity the temperature solves -k T'' = Q, T(+-L) = 37, whose P1 nodal
+    values on the unjittered Kuhn slab are exactly 37 + Q/(2k) (L^2 - x^2)."""
+    n, V0 = 8, 10.0
+    m = _slab_mesh(n, V0=V0)
+    model = O.Model(m, O.Params(dt=1e18, perf=0.0))
+    T, V, _ = model.step(np.full(m.n_nodes, 37.0))
+    x = m.coords[:, 0]
+    np.testing.assert_allclose(V, V0 * (x + L) / (2 * L), rtol=0, atol=1e-12 * V0)
+    Q = 0.333 * (V0 / (2 * L)) ** 2
+    Tex = 37.0 + Q / (2 * 0.512) * (L * L - x * x)
+    np.testing.assert_allclose(T, Tex, rtol=0, atol=1e-11 * (Tex.max() - 37.0) + 1e-12)
+
+
+def test_slab_bioheat_perfusion_converges_second_order():
+    """Steady -k T'' + perf (T - T_a) = 0 on the slab, T(+-L) = 47: the exact solution is
+    T_a + 10 cosh(m x) / cosh(m L), m = sqrt(perf / k); P1 nodal errors fall by ~4x per halving of h."""
+    k, perf = 0.512, 2.4e4 / 64.0
+    mm = np.sqrt(perf / k)
+    errs = []
+    for n in (6, 12, 24):
+        m = _slab_mesh(n, V0=0.0, T_D=47.0)
+        model = O.Model(m, O.Params(dt=1e18, perf=perf))
+        T, _, _ = model.step(np.full(m.n_nodes, 37.0))
+        x = m.coords[:, 0]
+        Tex = 37.0 + 10.0 * np.cosh(mm * x) / np.cosh(mm * L)
+        errs.append(np.abs(T - Tex).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.8 < r2 < 4.3, (errs, r1, r2)
+
+
+def test_lift_equals_reduced_system():
+    """The symmetrically lifted full system has the same solution as the reduced free-node system
+    A_ff x_f = -A_fD g_D, and stays symmetric."""
+    m = mg.cube_mesh(5, jitter=0.1, seed=14, sigma0="lognormal")
+    model = O.Model(m)
+    T = 37.0 + np.linspace(0, 5, m.n_nodes)
+    A, b = model.system_V(T)
+    x = O.solve(A, b)
+    assert abs(A - A.T).max() <= 1e-15 * abs(A).max()
+    K = O.assemble(O.element_stiffness(model.sigma(T), model.vol, model.grad), m.tets, m.n_nodes).toarray()
+    D = m.bc_V.astype(bool)
+    f = ~D
+    xf = np.linalg.solve(K[np.ix_(f, f)], -K[np.ix_(f, D)] @ m.g_V[D])
+    np.testing.assert_allclose(x[f], xf, rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(x[D], m.g_V[D])
+
+
+def test_sparse_lu_matches_dense_lu():
+    """Above the dense limit the oracle uses SuperLU; on a 16^3 system it agrees with dense LU and leaves a
+    residual below 1e-13 ||b||."""
+    m = mg.cube_mesh(16, jitter=0.1, seed=15)
+    assert m.n_nodes > O.DENSE_LIMIT
+    model = O.Model(m)
+    A, b = model.system_V(np.full(m.n_nodes, 37.0))
+    xs = O.solve(A, b)
+    xd = np.linalg.solve(A.toarray(), b)
+    np.testing.assert_allclose(xs, xd, rtol=0, atol=1e-12 * np.abs(xd).max())
+    assert np.linalg.norm(A @ xs - b) <= 1e-13 * np.linalg.norm(b)
+
+
+def test_psnr_noise_calibration():
+    """Sec. IV control lines: adding noise of magnitude d (random sign) at every node gives MSE = d^2, so
+    PSNR = 20 log10(MAX / d) exactly; identical fields give +inf."""
+    rng = np.random.default_rng(0)
+    A = 37.0 + 60.0 * rng.random((5, 1000))
+    # adding 1e-12 to values near 100 is exact only to half an ulp (7e-15), i.e. within 0.07 dB
+    for d, tol_db in ((1e-5, 1e-6), (1e-12, 0.07)):
+        B = A + d * rng.choice([-1.0, 1.0], size=A.shape)
+        np.testing.assert_allclose(O.psnr(A, B), 20 * np.log10(A.max() / d), rtol=0, atol=tol_db)
+    assert np.all(np.isinf(O.psnr(A, A)))
+
+
+def test_corrector_converges_to_fixed_point():
+    """With fixed-point passes on, the returned pair satisfies the step equations with sigma evaluated at
+    the returned temperature (to the corrector tolerance), unlike the lagged single pass."""
+    m = mg.cube_mesh(6, jitter=0.1, seed=16)
+    p = O.Params(dt=60.0, n_corrector=50, corrector_tol=1e-10)
+    model = O.Model(m, p)
+    T0 = np.full(m.n_nodes, 37.0)
+    T1, V1, passes = model.step(T0)
+    assert 1 < passes < 50
+    A, b = model.system_V(T1)
+    np.testing.assert_allclose(A @ V1, b, rtol=0, atol=1e-8 * np.abs(b).max())
+    lag = O.Model(m, dataclasses.replace(p, n_corrector=1))
+    T1l, _, _ = lag.step(T0)
+    assert np.abs(T1l - T1).max() > 1e-6
