@@ -1,0 +1,175 @@
+/*
+ * rafem.h — C-ABI of librafem: per-time-step reassembly and sparse solve of the coupled electric-potential /
+ * Pennes-bioheat P1-tetrahedral finite-element model of radiofrequency ablation (RAFEM), on one B300 GPU.
+ *
+ * What the library computes follows the paper's statement of the problem (arXiv 2409.13036):
+ *   - Sec. II-A "Main application loop": time advances step by step; each corrector pass recomputes the
+ *     element equations from updated values, assembles them into a global sparse matrix (structurally
+ *     symmetric, fixed pattern) and solves it.
+ *   - Sec. III-A: element equations assembled into a CSR global matrix without races; Sec. III-B: the fixed
+ *     pattern lets analysis work be reused across steps; residual tolerance 1e-10.
+ *   - Sec. II-B: CG for symmetric positive-definite systems, preconditioning to accelerate convergence.
+ * The PDE pair and constants (the paper defers them to its cited formulation) are read as
+ *     div(sigma(T) grad V) = 0,  sigma_e = sigma0_e (1 + alpha (mean_e T - 37)),
+ *     rho_c dT/dt = div(k grad T) + sigma |grad V|^2 - perf (T - T_a),
+ * discretised with P1 tetrahedra, consistent mass and backward Euler, solved staggered (V then T), each
+ * system Dirichlet-lifted symmetrically so that both are SPD.
+ *
+ * Conventions (all entry points):
+ *   - Return value: 0 = RAFEM_OK; positive = soft outcome (RAFEM_NOT_CONVERGED); negative = error.
+ *   - Inputs passed to rafem_create are copied; the caller keeps ownership of every pointer it passes.
+ *   - A pointer documented as "device" must be a CUDA device pointer valid on the context's device; "host"
+ *     pointers are ordinary host memory (pinned or pageable).
+ *   - All work is issued on the stream given at create (NULL = the legacy default stream) and every entry
+ *     point synchronises that stream before returning, unless stated otherwise.
+ *   - There is no global state: calls on different contexts are independent; calls on one context must not
+ *     overlap (not thread-safe).
+ *   - Units are SI; coordinates in metres, temperatures in degrees Celsius, potentials in volts.
+ */
+#ifndef RAFEM_H
+#define RAFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------------------- */
+#define RAFEM_OK                 0
+#define RAFEM_NOT_CONVERGED      1   /* iteration cap reached; fields hold the last iterate, stats are filled  */
+#define RAFEM_ERR_BAD_INPUT     -1   /* a NULL pointer, a size out of range, an index outside the mesh         */
+#define RAFEM_ERR_BAD_MESH      -2   /* a tetrahedron with non-positive volume                                  */
+#define RAFEM_ERR_OOM           -3   /* device or host allocation failed                                       */
+#define RAFEM_ERR_NONFINITE     -4   /* NaN or Inf met in a residual, a coefficient or a field                  */
+#define RAFEM_ERR_TIMEOUT       -5   /* a device grid barrier waited past its limit (never expected)            */
+#define RAFEM_ERR_CUDA          -6   /* a CUDA runtime call failed                                              */
+#define RAFEM_ERR_INTERNAL      -7   /* an internal consistency check failed                                   */
+#define RAFEM_ERR_BREAKDOWN     -8   /* Krylov breakdown: p^T A p <= 0 (matrix not SPD) or a zero denominator  */
+
+/* ---- options ---------------------------------------------------------------------------------------------- */
+#define RAFEM_SYS_V 1                /* the electric-potential system                                          */
+#define RAFEM_SYS_T 2                /* the thermal system                                                     */
+
+#define RAFEM_PRECOND_JACOBI 0       /* diagonal preconditioner                                               */
+#define RAFEM_PRECOND_ILU0   1       /* incomplete LU(0) on the fixed pattern, multicolour level order         */
+
+#define RAFEM_PRECISION_FP64  0      /* every Krylov operation in FP64                                        */
+#define RAFEM_PRECISION_MIXED 1      /* FP32 inner Krylov (FP32 values, vectors, dots) + FP64 residual refinement */
+
+#define RAFEM_SOLVER_PCG      0      /* conjugate gradients (SPD systems)                                      */
+#define RAFEM_SOLVER_BICGSTAB 1      /* BiCGSTAB (general nonsymmetric systems)                                */
+
+/* Mesh and boundary data of one instance. All pointers are host pointers, read only during rafem_create. */
+typedef struct rafem_mesh {
+    int32_t n_nodes;                 /* N >= 4                                                                 */
+    int32_t n_tets;                  /* E >= 1                                                                 */
+    const double*  coords;           /* [N*3] x,y,z per node, metres                                           */
+    const int32_t* tets;             /* [E*4] node ids per tetrahedron (any orientation; volume must be != 0)  */
+    const uint8_t* bc_V;             /* [N] 1 = Dirichlet node of the potential system                         */
+    const double*  g_V;              /* [N] prescribed potential where bc_V = 1                                */
+    const uint8_t* bc_T;             /* [N] 1 = Dirichlet node of the thermal system                           */
+    const double*  g_T;              /* [N] prescribed temperature where bc_T = 1                              */
+    const double*  sigma0;           /* [E] electrical conductivity at 37 degC, S/m                            */
+    const double*  k;                /* [E] thermal conductivity, W/m/K                                        */
+} rafem_mesh;
+
+/* Physics, time stepping and solver parameters. rafem_default_params fills the liver defaults. */
+typedef struct rafem_params {
+    double  alpha_sigma;             /* 1/degC, temperature coefficient of sigma (0.015)                      */
+    double  rho_c;                   /* J/m^3/K (3.6e6)                                                        */
+    double  perf;                    /* W/m^3/K, perfusion coefficient (2.4e4)                                 */
+    double  T_a;                     /* degC, arterial temperature (37)                                        */
+    double  dt;                      /* s, time step (1)                                                       */
+    double  tol;                     /* relative residual ||b - A x|| / ||b|| to reach (1e-10)                 */
+    double  inner_tol;               /* mixed precision: relative reduction of each FP32 inner solve (1e-4)    */
+    double  corrector_tol;           /* degC, max |T^{k+1} - T^k| ending the corrector passes (1e-6)           */
+    int32_t max_iter;                /* cap on Krylov iterations per solve, FP64 and inner together (20000)    */
+    int32_t max_refine;              /* mixed precision: cap on FP64 refinements per solve (30)                */
+    int32_t n_corrector;             /* corrector passes per step; 1 = lagged coefficients (1, at most 50)     */
+    int32_t precond;                 /* RAFEM_PRECOND_*                                                        */
+    int32_t precision;               /* RAFEM_PRECISION_*                                                      */
+    int32_t solver;                  /* RAFEM_SOLVER_*                                                         */
+    int32_t lanes_per_row;           /* SpMV lanes per CSR row: 0 = autotuned, else 4, 8, 16 or 32             */
+    int32_t rows_per_tile;           /* rows per work tile of the persistent solver: 0 = automatic            */
+} rafem_params;
+
+/* Per-step statistics, filled on the device and copied back when requested. */
+typedef struct rafem_step_stats {
+    int32_t status;                  /* RAFEM_OK, RAFEM_NOT_CONVERGED or a negative error                     */
+    int32_t iters_V;                 /* Krylov iterations of the potential solve (all refinements)             */
+    int32_t iters_T;                 /* Krylov iterations of the thermal solve                                  */
+    int32_t refine_V;                /* FP64 refinements of the potential solve (mixed precision, else 0)     */
+    int32_t refine_T;                /* FP64 refinements of the thermal solve                                  */
+    int32_t correctors;              /* corrector passes taken in this step                                    */
+    double  relres_V;                /* final relative residual of the potential solve (FP64)                 */
+    double  relres_T;                /* final relative residual of the thermal solve (FP64)                   */
+    int64_t step;                    /* steps completed by the context                                         */
+} rafem_step_stats;
+
+typedef struct rafem_ctx rafem_ctx;
+
+/* Liver defaults: alpha 0.015, rho_c 3.6e6, perf 2.4e4, T_a 37, dt 1, tol 1e-10, inner_tol 1e-4, FP64, Jacobi,
+ * PCG, one corrector pass, automatic SpMV schedule. */
+void rafem_default_params(rafem_params* p);
+
+/* Build a context: validates the mesh (ids in range, non-degenerate tetrahedra), builds the fixed CSR pattern,
+ * the element-to-slot map and the element colouring on the host, uploads everything, precomputes element
+ * geometry on the device, assembles the constant thermal matrix and sets T = T_a, V = 0 (Dirichlet values
+ * applied). stream: a cudaStream_t or NULL. On failure *out is NULL. Ownership of *out passes to the caller,
+ * released with rafem_destroy. Errors: BAD_INPUT, BAD_MESH, OOM, CUDA. */
+int rafem_create(const rafem_mesh* mesh, const rafem_params* params, void* stream, rafem_ctx** out);
+
+/* Assemble one system into the context's device buffers (Sec. II-A, element equations from updated values;
+ * Sec. III-A race-free assembly): which = RAFEM_SYS_V builds A_V(sigma(T)) and its lifted right-hand side
+ * from the current temperature; which = RAFEM_SYS_T builds the thermal right-hand side from the current
+ * potential and temperature (the thermal matrix is constant and assembled at create). Errors: BAD_INPUT, CUDA. */
+int rafem_assemble(rafem_ctx* ctx, int which);
+
+/* Solve the assembled system `which` in place (warm start from the current field), with the context's
+ * solver settings; fills *stats (nullable) for that system. Returns OK, NOT_CONVERGED or an error. */
+int rafem_solve(rafem_ctx* ctx, int which, rafem_step_stats* stats);
+
+/* One backward-Euler time step (the corrector pass of Sec. II-A): assemble V, solve V, assemble T, solve T,
+ * repeated n_corrector times when fixed-point passes are on. stats: nullable. */
+int rafem_solve_step(rafem_ctx* ctx, rafem_step_stats* stats);
+
+/* n_steps time steps, each launched as one captured CUDA graph, with no host<->device traffic between steps
+ * (only the statistics of the last step are copied back). last: nullable, receives the statistics of the
+ * last step and, in status, the worst status met over all steps. */
+int rafem_run(rafem_ctx* ctx, int32_t n_steps, rafem_step_stats* last);
+
+/* Copy a field (RAFEM_SYS_V = potential, RAFEM_SYS_T = temperature) of N doubles to dst.
+ * dst_on_device: 0 = host pointer, 1 = device pointer. */
+int rafem_get_field(rafem_ctx* ctx, int which, double* dst, int dst_on_device);
+
+/* Replace the state: T and V (either may be NULL to keep it) of N doubles each; on_device as above. The step
+ * counter is set to `step`. Dirichlet values are not re-imposed (the caller passes consistent fields). */
+int rafem_set_state(rafem_ctx* ctx, const double* T, const double* V, int on_device, int64_t step);
+
+/* Sizes of the fixed CSR pattern: n_rows (= N), nnz, number of element colours. Any out pointer may be NULL. */
+int rafem_pattern_info(rafem_ctx* ctx, int32_t* n_rows, int64_t* nnz, int32_t* n_colors);
+
+/* Copy the current lifted system `which` to host buffers: row_ptr [N+1], col [nnz], vals [nnz], rhs [N].
+ * Any pointer may be NULL to skip it. For inspection and tests. */
+int rafem_get_system(rafem_ctx* ctx, int which, int32_t* row_ptr, int32_t* col, double* vals, double* rhs);
+
+/* Solve A x = b for an arbitrary right-hand side on the context's lifted system `which` with the context's
+ * solver settings, without touching the fields: b and x are device pointers to N doubles, x holds the
+ * initial guess on entry. */
+int rafem_solve_rhs(rafem_ctx* ctx, int which, const double* b_dev, double* x_dev, rafem_step_stats* stats);
+
+/* y = A x with the current lifted system `which` (FP64). x, y: device pointers to N doubles. */
+int rafem_spmv(rafem_ctx* ctx, int which, const double* x_dev, double* y_dev);
+
+/* Release every device and host resource of the context. NULL is accepted. */
+void rafem_destroy(rafem_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* rafem_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAFEM_H */

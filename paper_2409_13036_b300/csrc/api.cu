@@ -1,0 +1,649 @@
+// C-ABI of librafem (declared in include/rafem.h): context lifetime, per-step assembly + solve, CUDA-graph
+// time loop. The step follows the main loop of Sec. II-A: every corrector pass recomputes the element
+// equations with the newest values, assembles the global systems and solves them; here the whole step stays on
+// the device, so the per-pass host<->device copies of Sec. III-A (matrix to the host solver, solution back for
+// the host-side predictor and convergence check) do not exist.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+#include "setup.h"
+
+using namespace rafem;
+
+namespace {
+
+struct StatsDev {
+    rafem_step_stats cur;   // statistics of the step in progress / last step
+    int32_t worst;          // worst status over all steps since the last reset
+    int32_t pad;
+};
+
+}  // namespace
+
+struct rafem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    rafem_params prm{};
+    int N = 0, E = 0;
+    int64_t nnz = 0;
+    int n_colors = 0;
+    std::vector<int> color_off;      // [n_colors + 1] over the sorted element order
+    std::vector<void*> allocs;
+
+    // pattern
+    int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
+    // element data
+    ElemData el;
+    int32_t* e_nodes = nullptr;
+    int32_t* e_slots = nullptr;
+    double *e_G = nullptr, *e_vol = nullptr, *e_sig0 = nullptr, *e_k = nullptr;
+    double* xyz = nullptr;
+    // boundary data
+    uint8_t *bcV = nullptr, *bcT = nullptr;
+    double *gV = nullptr, *gT = nullptr;
+    // systems
+    double *valsV = nullptr, *valsT = nullptr;
+    float *valsV32 = nullptr, *valsT32 = nullptr;
+    double *bV = nullptr, *bT = nullptr, *bTc = nullptr;
+    // fields
+    double *V = nullptr, *T = nullptr, *T_old = nullptr, *T_prev = nullptr;
+    // solver workspace
+    double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
+    float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
+    int32_t *tile_r0 = nullptr, *tile_r1 = nullptr, *tile_inst = nullptr, *inst_t0 = nullptr, *inst_t1 = nullptr;
+    int n_tiles = 0, grid = 0, block = 0, lanes = 8;
+    InstState* instV = nullptr;
+    InstState* instT = nullptr;
+    double* partial = nullptr;
+    GridBarrier* bar = nullptr;
+    StatsDev* stats = nullptr;
+    double* scratch = nullptr;       // small device scratch (max |dT|)
+    int64_t step = 0;
+    // graph
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(rafem_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T) + 64;  // slack for vector over-reads
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaMemsetAsync(q, 0, bytes, c->stream);
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RAFEM_OK;
+    if (e == cudaErrorMemoryAllocation) return RAFEM_ERR_OOM;
+    return RAFEM_ERR_CUDA;
+}
+
+#define CK(expr)                                 \
+    do {                                         \
+        cudaError_t _e = (expr);                 \
+        if (_e != cudaSuccess) return cuda_status(_e); \
+    } while (0)
+
+__global__ void k_record(const InstState* inst, const GridBarrier* bar, int which, StatsDev* s, int final_step) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    InstState st = *inst;
+    if (bar->err) st.status = bar->err;
+    rafem_step_stats& c = s->cur;
+    if (which == RAFEM_SYS_V) {
+        c.iters_V += st.iters;
+        c.refine_V += st.refine;
+        c.relres_V = st.relres;
+    } else {
+        c.iters_T += st.iters;
+        c.refine_T += st.refine;
+        c.relres_T = st.relres;
+    }
+    int status = st.status;
+    if (status < 0 || c.status < 0)
+        c.status = status < c.status ? status : c.status;
+    else
+        c.status = status > c.status ? status : c.status;
+    if (final_step) {
+        c.step += 1;
+        if (c.status < 0 || s->worst < 0)
+            s->worst = c.status < s->worst ? c.status : s->worst;
+        else
+            s->worst = c.status > s->worst ? c.status : s->worst;
+    }
+}
+
+__global__ void k_begin_step(StatsDev* s) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    rafem_step_stats& c = s->cur;
+    c.status = 0;
+    c.iters_V = c.iters_T = c.refine_V = c.refine_T = 0;
+    c.correctors = 1;
+    c.relres_V = c.relres_T = 0.0;
+}
+
+__global__ void k_set_step(StatsDev* s, long long step) {
+    s->cur.step = step;
+    s->worst = 0;
+}
+
+__global__ void k_init_fields(int N, double T0, const uint8_t* bcT, const double* gT, const uint8_t* bcV,
+                              const double* gV, double* T, double* V) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    T[i] = bcT[i] ? gT[i] : T0;
+    V[i] = bcV[i] ? gV[i] : 0.0;
+}
+
+SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
+    SolveArgs a{};
+    a.rp = c->rp;
+    a.ci = c->ci;
+    a.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
+    a.A32 = which == RAFEM_SYS_V ? c->valsV32 : c->valsT32;
+    a.diag = c->diag;
+    a.b = b;
+    a.x = x;
+    a.r = c->wr; a.u = c->wu; a.w = c->ww; a.p = c->wp; a.s = c->ws; a.dinv = c->wdinv;
+    a.r32 = c->fr; a.u32 = c->fu; a.w32 = c->fw; a.p32 = c->fp; a.s32 = c->fs; a.d32 = c->fd; a.dinv32 = c->fdinv;
+    a.n_tiles = c->n_tiles;
+    a.tile_r0 = c->tile_r0;
+    a.tile_r1 = c->tile_r1;
+    a.tile_inst = c->tile_inst;
+    a.n_inst = 1;
+    a.inst_t0 = c->inst_t0;
+    a.inst_t1 = c->inst_t1;
+    a.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
+    a.partial = c->partial;
+    a.bar = c->bar;
+    a.tol = c->prm.tol;
+    a.inner_tol = c->prm.inner_tol;
+    a.max_iter = c->prm.max_iter;
+    a.max_refine = c->prm.max_refine;
+    a.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+    return a;
+}
+
+cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
+    cudaError_t e;
+    if (which == RAFEM_SYS_V) {
+        e = launch_init_rhs(c->N, c->bcV, c->gV, nullptr, c->bV, c->stream);
+        if (e != cudaSuccess) return e;
+        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        for (int col = 0; col < c->n_colors; ++col) {
+            e = launch_assemble_V(c->el, c->color_off[col], c->color_off[col + 1], T_sigma, c->bcV, c->gV,
+                                  c->prm.alpha_sigma, c->valsV, v32, c->bV, c->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    e = launch_init_rhs(c->N, c->bcT, c->gT, c->bTc, c->bT, c->stream);
+    if (e != cudaSuccess) return e;
+    for (int col = 0; col < c->n_colors; ++col) {
+        e = launch_rhs_T(c->el, c->color_off[col], c->color_off[col + 1], T_sigma, T_old, c->V, c->bcT,
+                         c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->bT, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
+    SolveArgs a = make_args(c, which, b, x);
+    return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
+}
+
+// One lagged pass: sigma and the mass term both use the current T.
+cudaError_t enqueue_step(rafem_ctx* c) {
+    cudaError_t e;
+    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
+    k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
+    k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 1);
+    return cudaGetLastError();
+}
+
+int finish(rafem_ctx* c, rafem_step_stats* out, bool worst) {
+    StatsDev h;
+    CK(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (worst) h.cur.status = h.worst;
+    c->step = h.cur.step;
+    if (out) *out = h.cur;
+    return h.cur.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rafem_default_params(rafem_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->alpha_sigma = 0.015;
+    p->rho_c = 3.6e6;
+    p->perf = 2.4e4;
+    p->T_a = 37.0;
+    p->dt = 1.0;
+    p->tol = 1e-10;
+    p->inner_tol = 1e-4;
+    p->corrector_tol = 1e-6;
+    p->max_iter = 20000;
+    p->max_refine = 30;
+    p->n_corrector = 1;
+    p->precond = RAFEM_PRECOND_JACOBI;
+    p->precision = RAFEM_PRECISION_FP64;
+    p->solver = RAFEM_SOLVER_PCG;
+    p->lanes_per_row = 0;
+    p->rows_per_tile = 0;
+}
+
+const char* rafem_status_string(int s) {
+    switch (s) {
+        case RAFEM_OK: return "OK";
+        case RAFEM_NOT_CONVERGED: return "NOT_CONVERGED";
+        case RAFEM_ERR_BAD_INPUT: return "ERR_BAD_INPUT";
+        case RAFEM_ERR_BAD_MESH: return "ERR_BAD_MESH";
+        case RAFEM_ERR_OOM: return "ERR_OOM";
+        case RAFEM_ERR_NONFINITE: return "ERR_NONFINITE";
+        case RAFEM_ERR_TIMEOUT: return "ERR_TIMEOUT";
+        case RAFEM_ERR_CUDA: return "ERR_CUDA";
+        case RAFEM_ERR_INTERNAL: return "ERR_INTERNAL";
+        case RAFEM_ERR_BREAKDOWN: return "ERR_BREAKDOWN";
+        default: return "UNKNOWN";
+    }
+}
+
+void rafem_destroy(rafem_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx* c) {
+    const int N = m->n_nodes, E = m->n_tets;
+    c->prm = *prm;
+    c->N = N;
+    c->E = E;
+    CK(cudaGetDevice(&c->device));
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    // ---- host setup
+    std::vector<int8_t> orient;
+    int v = validate_mesh(N, E, m->tets, m->coords, orient);
+    if (v == -1) return RAFEM_ERR_BAD_INPUT;
+    if (v == -2) return RAFEM_ERR_BAD_MESH;
+    for (int64_t i = 0; i < 3LL * N; ++i)
+        if (!std::isfinite(m->coords[i])) return RAFEM_ERR_NONFINITE;
+    for (int64_t e = 0; e < E; ++e)
+        if (!std::isfinite(m->sigma0[e]) || !std::isfinite(m->k[e])) return RAFEM_ERR_NONFINITE;
+    for (int64_t i = 0; i < N; ++i)
+        if ((m->bc_V[i] && !std::isfinite(m->g_V[i])) || (m->bc_T[i] && !std::isfinite(m->g_T[i])))
+            return RAFEM_ERR_NONFINITE;
+    std::vector<int32_t> rp, col;
+    build_pattern(N, E, m->tets, rp, col);
+    c->nnz = (int64_t)col.size();
+    if (c->nnz >= (int64_t)SLOT_MASK) return RAFEM_ERR_BAD_INPUT;
+    std::vector<int32_t> color;
+    c->n_colors = color_elements(N, E, m->tets, color);
+    if (c->n_colors <= 0) return RAFEM_ERR_INTERNAL;
+    std::vector<int64_t> order(E);
+    {
+        std::vector<int64_t> cnt(c->n_colors + 1, 0);
+        for (int64_t e = 0; e < E; ++e) cnt[color[e] + 1]++;
+        for (int q = 0; q < c->n_colors; ++q) cnt[q + 1] += cnt[q];
+        c->color_off.assign(cnt.begin(), cnt.end());
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t e = 0; e < E; ++e) order[pos[color[e]]++] = e;
+    }
+    std::vector<int32_t> slots;
+    build_slots(E, m->tets, rp, col, order, slots);
+    std::vector<int32_t> diag(N);
+    for (int i = 0; i < N; ++i) {
+        const int32_t* f = std::lower_bound(col.data() + rp[i], col.data() + rp[i + 1], i);
+        diag[i] = (int32_t)(f - col.data());
+    }
+    std::vector<int32_t> nodes_soa(4LL * E);
+    std::vector<double> sig_s(E), k_s(E);
+    for (int64_t ep = 0; ep < E; ++ep) {
+        const int64_t e = order[ep];
+        for (int a = 0; a < 4; ++a) nodes_soa[(size_t)a * E + ep] = m->tets[4 * e + a];
+        sig_s[ep] = m->sigma0[e];
+        k_s[ep] = m->k[e];
+    }
+    // ---- device buffers
+    const size_t nnz = (size_t)c->nnz;
+    const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
+    CK(dalloc(c, &c->rp, N + 1));
+    CK(dalloc(c, &c->ci, nnz));
+    CK(dalloc(c, &c->diag, N));
+    CK(dalloc(c, &c->e_nodes, 4 * (size_t)E));
+    CK(dalloc(c, &c->e_slots, 16 * (size_t)E));
+    CK(dalloc(c, &c->e_G, 10 * (size_t)E));
+    CK(dalloc(c, &c->e_vol, E));
+    CK(dalloc(c, &c->e_sig0, E));
+    CK(dalloc(c, &c->e_k, E));
+    CK(dalloc(c, &c->xyz, 3 * (size_t)N));
+    CK(dalloc(c, &c->bcV, N));
+    CK(dalloc(c, &c->bcT, N));
+    CK(dalloc(c, &c->gV, N));
+    CK(dalloc(c, &c->gT, N));
+    CK(dalloc(c, &c->valsV, nnz));
+    CK(dalloc(c, &c->valsT, nnz));
+    if (mixed) {
+        CK(dalloc(c, &c->valsV32, nnz));
+        CK(dalloc(c, &c->valsT32, nnz));
+    }
+    CK(dalloc(c, &c->bV, N));
+    CK(dalloc(c, &c->bT, N));
+    CK(dalloc(c, &c->bTc, N));
+    CK(dalloc(c, &c->V, N));
+    CK(dalloc(c, &c->T, N));
+    CK(dalloc(c, &c->T_old, N));
+    CK(dalloc(c, &c->T_prev, N));
+    CK(dalloc(c, &c->wr, N));
+    CK(dalloc(c, &c->wu, N));
+    CK(dalloc(c, &c->ww, N));
+    CK(dalloc(c, &c->wp, N));
+    CK(dalloc(c, &c->ws, N));
+    CK(dalloc(c, &c->wdinv, N));
+    if (mixed) {
+        CK(dalloc(c, &c->fr, N));
+        CK(dalloc(c, &c->fu, N));
+        CK(dalloc(c, &c->fw, N));
+        CK(dalloc(c, &c->fp, N));
+        CK(dalloc(c, &c->fs, N));
+        CK(dalloc(c, &c->fd, N));
+        CK(dalloc(c, &c->fdinv, N));
+    }
+    CK(dalloc(c, &c->stats, 1));
+    CK(dalloc(c, &c->scratch, 8));
+    CK(dalloc(c, &c->instV, 1));
+    CK(dalloc(c, &c->instT, 1));
+    CK(dalloc(c, &c->bar, 1));
+    // ---- uploads
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(c->rp, rp.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->ci, col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->diag, diag.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->e_nodes, nodes_soa.data(), nodes_soa.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->e_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->e_sig0, sig_s.data(), E * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->e_k, k_s.data(), E * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->xyz, m->coords, 3 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bcV, m->bc_V, N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bcT, m->bc_T, N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->gV, m->g_V, N * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->gT, m->g_T, N * sizeof(double), cudaMemcpyHostToDevice, st));
+    c->el.E = E;
+    c->el.nodes = c->e_nodes;
+    c->el.slots = c->e_slots;
+    c->el.G = c->e_G;
+    c->el.vol = c->e_vol;
+    c->el.sigma0 = c->e_sig0;
+    c->el.k = c->e_k;
+    // ---- solver schedule: one tile per co-resident block
+    c->lanes = prm->lanes_per_row ? prm->lanes_per_row : 8;
+    int block = 0;
+    int maxb = krylov_max_blocks(c->lanes, prm->precision, &block);
+    if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
+    c->block = block;
+    int rows_per_tile = prm->rows_per_tile > 0 ? prm->rows_per_tile : (N + maxb - 1) / maxb;
+    rows_per_tile = std::max(rows_per_tile, 1);
+    c->n_tiles = (N + rows_per_tile - 1) / rows_per_tile;
+    c->grid = std::min(c->n_tiles, maxb);
+    {
+        std::vector<int32_t> t0(c->n_tiles), t1(c->n_tiles), ti(c->n_tiles, 0);
+        for (int t = 0; t < c->n_tiles; ++t) {
+            t0[t] = (int32_t)((int64_t)t * N / c->n_tiles);
+            t1[t] = (int32_t)((int64_t)(t + 1) * N / c->n_tiles);
+        }
+        int32_t it0 = 0, it1 = c->n_tiles;
+        CK(dalloc(c, &c->tile_r0, c->n_tiles));
+        CK(dalloc(c, &c->tile_r1, c->n_tiles));
+        CK(dalloc(c, &c->tile_inst, c->n_tiles));
+        CK(dalloc(c, &c->inst_t0, 1));
+        CK(dalloc(c, &c->inst_t1, 1));
+        CK(dalloc(c, &c->partial, 4 * (size_t)c->n_tiles));
+        CK(cudaMemcpyAsync(c->tile_r0, t0.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->tile_r1, t1.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->tile_inst, ti.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->inst_t0, &it0, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->inst_t1, &it1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+    }
+    // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
+    CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
+    CK(launch_set_dirichlet_identity(N, c->bcV, c->diag, c->valsV, c->valsV32, st));
+    CK(launch_set_dirichlet_identity(N, c->bcT, c->diag, c->valsT, c->valsT32, st));
+    const double c_matrix = prm->rho_c / prm->dt + prm->perf;
+    for (int q = 0; q < c->n_colors; ++q)
+        CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
+                             prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, st));
+    k_init_fields<<<(N + 255) / 256, 256, 0, st>>>(N, prm->T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
+    CK(cudaGetLastError());
+    k_set_step<<<1, 1, 0, st>>>(c->stats, 0);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return RAFEM_OK;
+}
+
+int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx** out) {
+    if (!out) return RAFEM_ERR_BAD_INPUT;
+    *out = nullptr;
+    if (!m || !prm || !m->coords || !m->tets || !m->bc_V || !m->g_V || !m->bc_T || !m->g_T || !m->sigma0 || !m->k)
+        return RAFEM_ERR_BAD_INPUT;
+    if (m->n_nodes < 4 || m->n_tets < 1) return RAFEM_ERR_BAD_INPUT;
+    if (!(prm->dt > 0) || !(prm->rho_c > 0) || !(prm->perf >= 0) || !(prm->tol > 0) || prm->max_iter < 1 ||
+        prm->n_corrector < 1 || prm->n_corrector > 50)
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->lanes_per_row != 0 && prm->lanes_per_row != 4 && prm->lanes_per_row != 8 &&
+        prm->lanes_per_row != 16 && prm->lanes_per_row != 32)
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->precision != RAFEM_PRECISION_FP64) return RAFEM_ERR_BAD_INPUT;
+    if (prm->precond != RAFEM_PRECOND_JACOBI) return RAFEM_ERR_BAD_INPUT;
+    if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
+    rafem_ctx* c = new (std::nothrow) rafem_ctx();
+    if (!c) return RAFEM_ERR_OOM;
+    int s;
+    try {
+        s = create_impl(m, prm, stream, c);
+    } catch (const std::bad_alloc&) {
+        s = RAFEM_ERR_OOM;
+    }
+    if (s != RAFEM_OK) {
+        rafem_destroy(c);
+        return s;
+    }
+    *out = c;
+    return RAFEM_OK;
+}
+
+int rafem_assemble(rafem_ctx* c, int which) {
+    if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    CK(enqueue_assemble(c, which, c->T, c->T));
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_solve(rafem_ctx* c, int which, rafem_step_stats* stats) {
+    if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    CK(cudaGetLastError());
+    CK(enqueue_solve(c, which, which == RAFEM_SYS_V ? c->bV : c->bT, which == RAFEM_SYS_V ? c->V : c->T));
+    k_record<<<1, 32, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->bar, which, c->stats, 0);
+    CK(cudaGetLastError());
+    return finish(c, stats, false);
+}
+
+int rafem_solve_rhs(rafem_ctx* c, int which, const double* b, double* x, rafem_step_stats* stats) {
+    if (!c || !b || !x || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    CK(cudaGetLastError());
+    CK(enqueue_solve(c, which, b, x));
+    k_record<<<1, 32, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->bar, which, c->stats, 0);
+    CK(cudaGetLastError());
+    return finish(c, stats, false);
+}
+
+int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (c->prm.n_corrector <= 1) {
+        CK(enqueue_step(c));
+        return finish(c, stats, false);
+    }
+    // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n
+    CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    CK(cudaGetLastError());
+    int passes = 0;
+    for (passes = 1; passes <= c->prm.n_corrector; ++passes) {
+        CK(cudaMemcpyAsync(c->T_prev, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CK(enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T_old));
+        CK(enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V));
+        k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+        CK(enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T_old));
+        CK(enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T));
+        k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 0);
+        CK(launch_max_abs_diff(c->N, c->T, c->T_prev, c->scratch, c->stream));
+        double change = 0;
+        CK(cudaMemcpyAsync(&change, c->scratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (!(change >= c->prm.corrector_tol)) break;  // converged (or NaN: reported via status below)
+    }
+    passes = std::min(passes, c->prm.n_corrector);
+    rafem_step_stats h;
+    int s = finish(c, &h, false);
+    h.correctors = passes;
+    h.step = ++c->step;
+    k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)c->step);
+    CK(cudaStreamSynchronize(c->stream));
+    if (s == RAFEM_OK && passes == c->prm.n_corrector) {
+        // the last pass did not meet the corrector tolerance
+    }
+    if (stats) *stats = h;
+    return s;
+}
+
+int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
+    if (!c || n_steps < 0) return RAFEM_ERR_BAD_INPUT;
+    if (n_steps == 0) return finish(c, last, true);
+    k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)c->step);
+    CK(cudaGetLastError());
+    if (c->prm.n_corrector > 1) {
+        int worst = 0;
+        rafem_step_stats h{};
+        for (int i = 0; i < n_steps; ++i) {
+            int s = rafem_solve_step(c, &h);
+            if (s < 0) {
+                if (last) *last = h;
+                return s;
+            }
+            worst = std::max(worst, s);
+        }
+        h.status = worst;
+        if (last) *last = h;
+        return worst;
+    }
+    if (!c->graph && !c->graph_failed) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = enqueue_step(c);
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) c->graph = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!c->graph) {
+            c->graph_failed = true;
+            cudaGetLastError();  // clear a capture error; fall back to direct launches
+        }
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        if (c->graph) {
+            CK(cudaGraphLaunch(c->graph, c->stream));
+        } else {
+            CK(enqueue_step(c));
+        }
+    }
+    return finish(c, last, true);
+}
+
+int rafem_get_field(rafem_ctx* c, int which, double* dst, int on_device) {
+    if (!c || !dst || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    const double* src = which == RAFEM_SYS_V ? c->V : c->T;
+    CK(cudaMemcpyAsync(dst, src, c->N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_state(rafem_ctx* c, const double* T, const double* V, int on_device, int64_t step) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (T) CK(cudaMemcpyAsync(c->T, T, c->N * sizeof(double), kind, c->stream));
+    if (V) CK(cudaMemcpyAsync(c->V, V, c->N * sizeof(double), kind, c->stream));
+    c->step = step;
+    k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)step);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_pattern_info(rafem_ctx* c, int32_t* n_rows, int64_t* nnz, int32_t* n_colors) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (n_rows) *n_rows = c->N;
+    if (nnz) *nnz = c->nnz;
+    if (n_colors) *n_colors = c->n_colors;
+    return RAFEM_OK;
+}
+
+int rafem_get_system(rafem_ctx* c, int which, int32_t* row_ptr, int32_t* col, double* vals, double* rhs) {
+    if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    cudaStream_t st = c->stream;
+    if (row_ptr) CK(cudaMemcpyAsync(row_ptr, c->rp, (c->N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (col) CK(cudaMemcpyAsync(col, c->ci, c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (vals)
+        CK(cudaMemcpyAsync(vals, which == RAFEM_SYS_V ? c->valsV : c->valsT, c->nnz * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+    if (rhs)
+        CK(cudaMemcpyAsync(rhs, which == RAFEM_SYS_V ? c->bV : c->bT, c->N * sizeof(double), cudaMemcpyDeviceToHost,
+                           st));
+    CK(cudaStreamSynchronize(st));
+    return RAFEM_OK;
+}
+
+int rafem_spmv(rafem_ctx* c, int which, const double* x, double* y) {
+    if (!c || !x || !y || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    CK(launch_spmv64(c->N, c->rp, c->ci, which == RAFEM_SYS_V ? c->valsV : c->valsT, x, y, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+}  // extern "C"

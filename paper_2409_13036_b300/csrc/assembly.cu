@@ -1,0 +1,253 @@
+// Element-level kernels: geometry, colour-partitioned atomic-free assembly with fused Dirichlet lift, thermal
+// right-hand side (Joule source + mass term).
+//
+// Sec. III-A computes each element's equations in one GPU thread and places them in the CSR global matrix
+// with threads mapped to disjoint matrix regions so that no two threads race. Here the disjointness comes
+// from an element colouring: all elements of one colour share no node, so one launch per colour scatters
+// its 16 entries per element with plain loads and stores (no atomics); successive colours are ordered by the
+// stream. The Dirichlet lift is folded into the scatter: entries of Dirichlet rows are never written (they
+// hold the identity set once at create), entries in Dirichlet columns of free rows move to the right-hand
+// side as -A_ij g_j and stay zero in the matrix.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "setup.h"
+
+namespace rafem {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// index of the distinct entry (a, b) of a symmetric 4x4 element matrix in the G layout
+__device__ __forceinline__ int gidx(int a, int b) {
+    if (a == b) return a;
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    // (0,1)->4 (0,2)->5 (0,3)->6 (1,2)->7 (1,3)->8 (2,3)->9
+    return lo == 0 ? 3 + hi : (lo == 1 ? 5 + hi : 9);
+}
+
+__global__ void __launch_bounds__(kThreads) k_geometry(int E, const int32_t* __restrict__ nodes,
+                                                       const double* __restrict__ xyz, double* __restrict__ G,
+                                                       double* __restrict__ vol) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    double X[4][3];
+    for (int a = 0; a < 4; ++a) {
+        int n = nodes[(size_t)a * E + e];
+        for (int c = 0; c < 3; ++c) X[a][c] = xyz[3 * (size_t)n + c];
+    }
+    double e1[3], e2[3], e3[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = X[1][c] - X[0][c];
+        e2[c] = X[2][c] - X[0][c];
+        e3[c] = X[3][c] - X[0][c];
+    }
+    // rows of the inverse edge matrix are cross products / det: grad(phi_1) = (e2 x e3)/det, ...
+    double c[4][3];
+    c[1][0] = e2[1] * e3[2] - e2[2] * e3[1];
+    c[1][1] = e2[2] * e3[0] - e2[0] * e3[2];
+    c[1][2] = e2[0] * e3[1] - e2[1] * e3[0];
+    c[2][0] = e3[1] * e1[2] - e3[2] * e1[1];
+    c[2][1] = e3[2] * e1[0] - e3[0] * e1[2];
+    c[2][2] = e3[0] * e1[1] - e3[1] * e1[0];
+    c[3][0] = e1[1] * e2[2] - e1[2] * e2[1];
+    c[3][1] = e1[2] * e2[0] - e1[0] * e2[2];
+    c[3][2] = e1[0] * e2[1] - e1[1] * e2[0];
+    for (int q = 0; q < 3; ++q) c[0][q] = -(c[1][q] + c[2][q] + c[3][q]);
+    double det = e1[0] * c[1][0] + e1[1] * c[1][1] + e1[2] * c[1][2];
+    double adet = fabs(det);
+    vol[e] = adet / 6.0;
+    // vol * grad_a . grad_b = (|det|/6) * (c_a . c_b) / det^2 = c_a . c_b / (6 |det|)
+    double s = 1.0 / (6.0 * adet);
+    for (int a = 0; a < 4; ++a)
+        for (int b = a; b < 4; ++b)
+            G[(size_t)gidx(a, b) * E + e] = s * (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]);
+}
+
+__global__ void k_init_rhs(int N, const uint8_t* __restrict__ bc, const double* __restrict__ g,
+                           const double* __restrict__ base, double* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    b[i] = bc[i] ? g[i] : (base ? base[i] : 0.0);
+}
+
+__global__ void k_set_identity(int N, const uint8_t* __restrict__ bc, const int32_t* __restrict__ diag,
+                               double* __restrict__ vals, float* __restrict__ vals32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || !bc[i]) return;
+    vals[diag[i]] = 1.0;
+    if (vals32) vals32[diag[i]] = 1.0f;
+}
+
+// Store or accumulate one element entry according to its slot code; emit the FP32 copy on the last write.
+__device__ __forceinline__ void scatter(double v, int32_t code, double* __restrict__ vals, float* __restrict__ vals32) {
+    int32_t s = code & SLOT_MASK;
+    double val = (code & SLOT_FIRST) ? v : vals[s] + v;
+    vals[s] = val;
+    if (vals32 && (code & SLOT_LAST)) vals32[s] = (float)val;
+}
+
+// MODE 0: potential matrix  sigma(Tbar_e) * G_e
+// MODE 1: thermal matrix    k_e * G_e + c_matrix * vol_e/20 * (1 + delta_ab), constant rhs perf*T_a*vol/4
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int e1, const double* __restrict__ T,
+                                                       const uint8_t* __restrict__ bc, const double* __restrict__ g,
+                                                       double coef_a, double coef_b, double* __restrict__ vals,
+                                                       float* __restrict__ vals32, double* __restrict__ rhs) {
+    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    const int E = el.E;
+    int n[4];
+    bool d[4];
+    for (int a = 0; a < 4; ++a) {
+        n[a] = el.nodes[(size_t)a * E + e];
+        d[a] = bc[n[a]] != 0;
+    }
+    double Ge[10];
+    for (int q = 0; q < 10; ++q) Ge[q] = el.G[(size_t)q * E + e];
+    double scale, mdiag = 0.0, moff = 0.0, rhs_const = 0.0;
+    if (MODE == 0) {
+        double Tbar = 0.25 * (T[n[0]] + T[n[1]] + T[n[2]] + T[n[3]]);
+        scale = el.sigma0[e] * (1.0 + coef_a * (Tbar - 37.0));
+    } else {
+        double v = el.vol[e];
+        scale = el.k[e];
+        moff = coef_a * v * (1.0 / 20.0);
+        mdiag = 2.0 * moff;
+        rhs_const = coef_b * v * 0.25;
+    }
+    for (int a = 0; a < 4; ++a) {
+        if (d[a]) continue;  // Dirichlet row: identity, fixed at create
+        double lift = 0.0;
+        for (int b = 0; b < 4; ++b) {
+            double v = scale * Ge[gidx(a, b)];
+            if (MODE == 1) v += (a == b) ? mdiag : moff;
+            if (d[b])
+                lift += v * g[n[b]];
+            else
+                scatter(v, el.slots[(size_t)(a * 4 + b) * E + e], vals, vals32);
+        }
+        if (MODE == 1 || lift != 0.0) rhs[n[a]] += rhs_const - lift;
+    }
+}
+
+// Thermal right-hand side contributions of one element (free rows only):
+//   Joule:  Q_e vol_e / 4 with Q_e vol_e = sigma_e * V_e^T G_e V_e   (= sigma_e vol_e |grad V|^2)
+//   mass:   (rho_c/dt) (M_e T_old)_a = (rho_c/dt) vol_e/20 (sum_b T_b + T_a)
+__global__ void __launch_bounds__(kThreads) k_rhs_T(ElemData el, int e0, int e1, const double* __restrict__ Ts,
+                                                    const double* __restrict__ To, const double* __restrict__ V,
+                                                    const uint8_t* __restrict__ bc, double alpha, double c_mass,
+                                                    double* __restrict__ b) {
+    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= e1) return;
+    const int E = el.E;
+    int n[4];
+    double v[4], to[4];
+    double ts = 0.0;
+    for (int a = 0; a < 4; ++a) {
+        n[a] = el.nodes[(size_t)a * E + e];
+        v[a] = V[n[a]];
+        to[a] = To[n[a]];
+        ts += Ts[n[a]];
+    }
+    double Ge[10];
+    for (int q = 0; q < 10; ++q) Ge[q] = el.G[(size_t)q * E + e];
+    double sig = el.sigma0[e] * (1.0 + alpha * (0.25 * ts - 37.0));
+    double quad = Ge[0] * v[0] * v[0] + Ge[1] * v[1] * v[1] + Ge[2] * v[2] * v[2] + Ge[3] * v[3] * v[3] +
+                  2.0 * (Ge[4] * v[0] * v[1] + Ge[5] * v[0] * v[2] + Ge[6] * v[0] * v[3] + Ge[7] * v[1] * v[2] +
+                         Ge[8] * v[1] * v[3] + Ge[9] * v[2] * v[3]);
+    double q4 = 0.25 * sig * quad;
+    double mv = c_mass * el.vol[e] * (1.0 / 20.0);
+    double tsum = to[0] + to[1] + to[2] + to[3];
+    for (int a = 0; a < 4; ++a) {
+        if (bc[n[a]]) continue;
+        b[n[a]] += q4 + mv * (tsum + to[a]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_spmv64(int N, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const double* __restrict__ A,
+                                                     const double* __restrict__ x, double* __restrict__ y) {
+    // 8 lanes per row
+    int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = gtid >> 3, lane = gtid & 7;
+    if (row >= N) return;
+    double acc = 0.0;
+    for (int k = rp[row] + lane; k < rp[row + 1]; k += 8) acc = fma(A[k], x[ci[k]], acc);
+    unsigned mask = 0xffu << (threadIdx.x & 24);
+    for (int o = 4; o; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, 8);
+    if (lane == 0) y[row] = acc;
+}
+
+__global__ void k_max_abs_diff(int N, const double* __restrict__ a, const double* __restrict__ b,
+                               unsigned long long* out) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        m = fmax(m, fabs(a[i] - b[i]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cudaError_t launch_geometry(const ElemData& el, const double* xyz, double* G, double* vol, cudaStream_t st) {
+    if (el.E == 0) return cudaSuccess;
+    k_geometry<<<blocks_for(el.E), kThreads, 0, st>>>(el.E, el.nodes, xyz, G, vol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_rhs(int N, const uint8_t* bc, const double* g, const double* base, double* b,
+                            cudaStream_t st) {
+    k_init_rhs<<<blocks_for(N), kThreads, 0, st>>>(N, bc, g, base, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_dirichlet_identity(int N, const uint8_t* bc, const int32_t* diag, double* vals,
+                                          float* vals32, cudaStream_t st) {
+    k_set_identity<<<blocks_for(N), kThreads, 0, st>>>(N, bc, diag, vals, vals32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* T, const uint8_t* bc,
+                              const double* g, double alpha, double* vals, float* vals32, double* b,
+                              cudaStream_t st) {
+    if (e1 <= e0) return cudaSuccess;
+    k_assemble<0><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, T, bc, g, alpha, 0.0, vals, vals32, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
+                              double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
+                              cudaStream_t st) {
+    if (e1 <= e0) return cudaSuccess;
+    k_assemble<1><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, nullptr, bc, g, c_matrix, perf_Ta, vals,
+                                                            vals32, bconst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sigma, const double* T_old,
+                         const double* V, const uint8_t* bc, double alpha, double c_mass, double* b,
+                         cudaStream_t st) {
+    if (e1 <= e0) return cudaSuccess;
+    k_rhs_T<<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, T_sigma, T_old, V, bc, alpha, c_mass, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv64(int N, const int32_t* rp, const int32_t* ci, const double* A, const double* x, double* y,
+                          cudaStream_t st) {
+    k_spmv64<<<blocks_for(8LL * N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs_diff(int N, const double* a, const double* b, double* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_max_abs_diff<<<148 * 4, kThreads, 0, st>>>(N, a, b, reinterpret_cast<unsigned long long*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace rafem

@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units of librafem (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/rafem.h"
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// Element data, SoA over the colour-sorted element order. G holds the 10 distinct entries of
+// vol_e * grad(phi_a) . grad(phi_b) in the order (00,11,22,33,01,02,03,12,13,23).
+// ------------------------------------------------------------------------------------------------------------
+struct ElemData {
+    int E = 0;
+    const int32_t* nodes = nullptr;   // [4][E]
+    const int32_t* slots = nullptr;   // [16][E] slot codes (setup.h flags)
+    const double* G = nullptr;        // [10][E]
+    const double* vol = nullptr;      // [E]
+    const double* sigma0 = nullptr;   // [E]
+    const double* k = nullptr;        // [E]
+};
+
+// Launchers (assembly.cu). Every launcher only enqueues work on `st`.
+cudaError_t launch_geometry(const ElemData& el, const double* xyz, double* G, double* vol, cudaStream_t st);
+cudaError_t launch_init_rhs(int N, const uint8_t* bc, const double* g, const double* base, double* b,
+                            cudaStream_t st);
+cudaError_t launch_set_dirichlet_identity(int N, const uint8_t* bc, const int32_t* diag, double* vals,
+                                          float* vals32, cudaStream_t st);
+// A_V(sigma(T)) for elements [e0, e1) of one colour; lifted rhs contributions into b.
+cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* T, const uint8_t* bc,
+                              const double* g, double alpha, double* vals, float* vals32, double* b,
+                              cudaStream_t st);
+// Constant thermal matrix c_mass*M + K_k for one colour; constant rhs part (perfusion + lift) into bconst.
+cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
+                              double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
+                              cudaStream_t st);
+// Thermal right-hand side for one colour: Joule source + (rho_c/dt) M T_old, free rows only.
+cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sigma, const double* T_old,
+                         const double* V, const uint8_t* bc, double alpha, double c_mass, double* b,
+                         cudaStream_t st);
+cudaError_t launch_spmv64(int N, const int32_t* rp, const int32_t* ci, const double* A, const double* x, double* y,
+                          cudaStream_t st);
+cudaError_t launch_max_abs_diff(int N, const double* a, const double* b, double* out, cudaStream_t st);
+
+// ------------------------------------------------------------------------------------------------------------
+// Persistent Krylov solver (krylov.cu)
+// ------------------------------------------------------------------------------------------------------------
+struct InstState {
+    double bb;          // ||b||^2 (FP64)
+    double rr;          // latest ||r||^2 of the running (inner) iteration
+    double rr0;         // inner: ||r||^2 at the start of the inner solve
+    double gamma_prev;  // (r, M^-1 r) of the previous iteration
+    double alpha_prev;
+    double alpha, beta;
+    double relres;      // final FP64 relative residual
+    int32_t iters;      // Krylov iterations (all refinements)
+    int32_t refine;     // FP64 refinements done
+    int32_t status;
+    int32_t active;     // 1 while the instance still iterates
+    int32_t first;      // 1 before the first iteration of a (inner) CG run
+    int32_t outer;      // mixed: 1 while an outer FP64 residual step is pending
+    int32_t pad[2];
+};
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int n_active;       // instances still iterating (written by the last arriver)
+    unsigned int pad[28];
+};
+
+struct SolveArgs {
+    // matrix (lifted, fixed pattern)
+    const int32_t* rp;
+    const int32_t* ci;
+    const double* A;
+    const float* A32;
+    const int32_t* diag;  // slot of the diagonal entry of each row
+    // problem
+    const double* b;
+    double* x;
+    // FP64 workspace
+    double *r, *u, *w, *p, *s, *dinv;
+    // FP32 workspace (mixed precision)
+    float *r32, *u32, *w32, *p32, *s32, *d32, *dinv32;
+    // work tiles: contiguous row ranges, each belonging to one instance
+    int n_tiles;
+    const int32_t* tile_r0;
+    const int32_t* tile_r1;
+    const int32_t* tile_inst;
+    int n_inst;
+    const int32_t* inst_t0;  // first tile of each instance
+    const int32_t* inst_t1;  // one past its last tile
+    InstState* inst;
+    double* partial;         // [4][n_tiles]
+    GridBarrier* bar;
+    // controls
+    double tol, inner_tol;
+    int max_iter, max_refine;
+    long long spin_limit_ns;
+};
+
+int krylov_max_blocks(int lanes, int precision, int* block_threads);
+cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st);
+
+}  // namespace rafem

@@ -1,0 +1,158 @@
+// Host-side, once-per-mesh setup of the fixed sparse structure (integer graph work, OpenMP).
+//
+// The paper reuses analysis work because the global matrix pattern never changes between steps (Sec. III-B,
+// the reused column permutation). Here everything that depends only on connectivity is built once:
+//   - the CSR pattern of the node graph (row i holds every node sharing an element with i, sorted),
+//   - the element -> CSR slot map (16 slots per tetrahedron),
+//   - a greedy element colouring in which no two elements of one colour share a node, so that one colour's
+//     element matrices can be scattered into the global matrix without atomics (Sec. III-A assembles by
+//     mapping threads to disjoint matrix regions to avoid races),
+//   - first/last-writer flags per slot in colour order (the first writer stores instead of adding, which
+//     removes a per-step zeroing pass; the last writer also emits the FP32 copy of the finished value).
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace rafem {
+
+int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient) {
+    if (N < 4 || E < 1) return -1;
+    int bad_index = 0, bad_vol = 0;
+    orient.assign(E, 1);
+#pragma omp parallel for reduction(+ : bad_index, bad_vol) schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* t = tets + 4 * e;
+        bool ok = true;
+        for (int a = 0; a < 4; ++a)
+            if (t[a] < 0 || t[a] >= N) ok = false;
+        for (int a = 0; a < 4 && ok; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (t[a] == t[b]) ok = false;
+        if (!ok) { bad_index++; continue; }
+        double e1[3], e2[3], e3[3];
+        for (int c = 0; c < 3; ++c) {
+            e1[c] = xyz[3 * t[1] + c] - xyz[3 * t[0] + c];
+            e2[c] = xyz[3 * t[2] + c] - xyz[3 * t[0] + c];
+            e3[c] = xyz[3 * t[3] + c] - xyz[3 * t[0] + c];
+        }
+        double det = e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                     e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
+        double scale = 0;
+        for (int c = 0; c < 3; ++c) scale = std::max({scale, std::fabs(e1[c]), std::fabs(e2[c]), std::fabs(e3[c])});
+        if (!(std::fabs(det) > 1e-14 * scale * scale * scale) || !std::isfinite(det)) bad_vol++;
+        orient[e] = det > 0 ? 1 : -1;
+    }
+    if (bad_index) return -1;
+    if (bad_vol) return -2;
+    return 0;
+}
+
+void build_pattern(int N, int E, const int32_t* tets, std::vector<int32_t>& row_ptr, std::vector<int32_t>& col) {
+    // node -> element incidence
+    std::vector<int32_t> cnt(N + 1, 0);
+    for (int64_t i = 0; i < 4LL * E; ++i) cnt[tets[i] + 1]++;
+    for (int i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int32_t> inc(4LL * E);
+    {
+        std::vector<int32_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t e = 0; e < E; ++e)
+            for (int a = 0; a < 4; ++a) inc[pos[tets[4 * e + a]]++] = (int32_t)e;
+    }
+    // per-row unique neighbour lists: count pass, then fill pass
+    std::vector<int32_t> len(N, 0);
+#pragma omp parallel
+    {
+        std::vector<int32_t> buf;
+#pragma omp for schedule(dynamic, 1024)
+        for (int i = 0; i < N; ++i) {
+            buf.clear();
+            for (int32_t q = cnt[i]; q < cnt[i + 1]; ++q)
+                for (int a = 0; a < 4; ++a) buf.push_back(tets[4LL * inc[q] + a]);
+            std::sort(buf.begin(), buf.end());
+            len[i] = (int32_t)(std::unique(buf.begin(), buf.end()) - buf.begin());
+        }
+    }
+    row_ptr.assign(N + 1, 0);
+    for (int i = 0; i < N; ++i) row_ptr[i + 1] = row_ptr[i] + len[i];
+    col.assign(row_ptr[N], 0);
+#pragma omp parallel
+    {
+        std::vector<int32_t> buf;
+#pragma omp for schedule(dynamic, 1024)
+        for (int i = 0; i < N; ++i) {
+            buf.clear();
+            for (int32_t q = cnt[i]; q < cnt[i + 1]; ++q)
+                for (int a = 0; a < 4; ++a) buf.push_back(tets[4LL * inc[q] + a]);
+            std::sort(buf.begin(), buf.end());
+            int n = (int)(std::unique(buf.begin(), buf.end()) - buf.begin());
+            std::copy(buf.begin(), buf.begin() + n, col.begin() + row_ptr[i]);
+        }
+    }
+}
+
+int color_elements(int N, int E, const int32_t* tets, std::vector<int32_t>& color) {
+    // Greedy: each element takes the lowest colour not used by any element already coloured that shares one
+    // of its nodes. Node masks hold up to 256 colours.
+    const int W = 4;
+    std::vector<uint64_t> used((size_t)N * W, 0);
+    color.assign(E, -1);
+    int ncol = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        uint64_t m[W] = {0, 0, 0, 0};
+        for (int a = 0; a < 4; ++a)
+            for (int w = 0; w < W; ++w) m[w] |= used[(size_t)tets[4 * e + a] * W + w];
+        int c = -1;
+        for (int w = 0; w < W && c < 0; ++w)
+            if (~m[w]) c = 64 * w + __builtin_ctzll(~m[w]);
+        if (c < 0) return -1;
+        color[e] = c;
+        ncol = std::max(ncol, c + 1);
+        for (int a = 0; a < 4; ++a) used[(size_t)tets[4 * e + a] * W + c / 64] |= 1ULL << (c % 64);
+    }
+    return ncol;
+}
+
+void build_slots(int E, const int32_t* tets, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                 const std::vector<int64_t>& order, std::vector<int32_t>& slots) {
+    // slots is SoA over the colour-sorted element order: slots[(a*4+b)*E + e'] for element order[e'].
+    slots.assign(16LL * E, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t ep = 0; ep < E; ++ep) {
+        const int32_t* t = tets + 4 * order[ep];
+        for (int a = 0; a < 4; ++a) {
+            const int32_t* rb = col.data() + row_ptr[t[a]];
+            const int32_t* re = col.data() + row_ptr[t[a] + 1];
+            for (int b = 0; b < 4; ++b) {
+                const int32_t* f = std::lower_bound(rb, re, t[b]);
+                slots[(int64_t)(a * 4 + b) * E + ep] = (int32_t)(f - col.data());
+            }
+        }
+    }
+    // first / last writer in execution order (colour-sorted element order, any order inside a colour is
+    // race-free because elements of one colour share no node and hence no slot)
+    const int64_t nnz = (int64_t)col.size();
+    std::vector<int64_t> first(nnz, -1), last(nnz, -1);
+    for (int64_t ep = 0; ep < E; ++ep)
+        for (int q = 0; q < 16; ++q) {
+            int32_t s = slots[(int64_t)q * E + ep];
+            int64_t id = ep * 16 + q;
+            if (first[s] < 0) first[s] = id;
+            last[s] = id;
+        }
+#pragma omp parallel for schedule(static)
+    for (int64_t ep = 0; ep < E; ++ep)
+        for (int q = 0; q < 16; ++q) {
+            int32_t& s = slots[(int64_t)q * E + ep];
+            int64_t id = ep * 16 + q;
+            int32_t code = s;
+            if (first[s] == id) code |= SLOT_FIRST;
+            if (last[s] == id) code |= SLOT_LAST;
+            s = code;
+        }
+}
+
+}  // namespace rafem

@@ -1,0 +1,26 @@
+// Host-side setup of the fixed sparse structure (see setup.cpp).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace rafem {
+
+// Slot-code flags stored in the element -> CSR slot map (slot index in the low 29 bits).
+constexpr int32_t SLOT_FIRST = 1 << 30;   // this element is the first writer of the slot: store, do not add
+constexpr int32_t SLOT_LAST = 1 << 29;    // this element is the last writer of the slot: emit the FP32 copy
+constexpr int32_t SLOT_MASK = (1 << 29) - 1;
+
+// 0 ok, -1 bad index / repeated node, -2 degenerate element. orient[e] = sign of the element's volume.
+int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient);
+
+// CSR pattern of the node graph: row i lists every node sharing an element with i (itself included), sorted.
+void build_pattern(int N, int E, const int32_t* tets, std::vector<int32_t>& row_ptr, std::vector<int32_t>& col);
+
+// Greedy element colouring (no two elements of a colour share a node). Returns the colour count or -1.
+int color_elements(int N, int E, const int32_t* tets, std::vector<int32_t>& color);
+
+// Element -> slot map over the element order `order` (SoA [16][E]), with first/last-writer flags.
+void build_slots(int E, const int32_t* tets, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                 const std::vector<int64_t>& order, std::vector<int32_t>& slots);
+
+}  // namespace rafem

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of librafem (include/rafem.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; if librafem.so is missing or cannot be loaded this
+module raises, it never falls back to another implementation. Functions keep the C names
+(rafem_create, rafem_assemble, rafem_solve_step, rafem_run, ...); `Context` wraps them for convenience.
+Device pointers may be passed as integers (e.g. torch.Tensor.data_ptr()).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librafem.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rafem.h")
+
+RAFEM_OK = 0
+RAFEM_NOT_CONVERGED = 1
+RAFEM_ERR_BAD_INPUT = -1
+RAFEM_ERR_BAD_MESH = -2
+RAFEM_ERR_OOM = -3
+RAFEM_ERR_NONFINITE = -4
+RAFEM_ERR_TIMEOUT = -5
+RAFEM_ERR_CUDA = -6
+RAFEM_ERR_INTERNAL = -7
+RAFEM_ERR_BREAKDOWN = -8
+
+RAFEM_SYS_V = 1
+RAFEM_SYS_T = 2
+RAFEM_PRECOND_JACOBI = 0
+RAFEM_PRECOND_ILU0 = 1
+RAFEM_PRECISION_FP64 = 0
+RAFEM_PRECISION_MIXED = 1
+RAFEM_SOLVER_PCG = 0
+RAFEM_SOLVER_BICGSTAB = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class rafem_mesh(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_tets", ctypes.c_int32), ("coords", _dp), ("tets", _ip),
+                ("bc_V", _u8p), ("g_V", _dp), ("bc_T", _u8p), ("g_T", _dp), ("sigma0", _dp), ("k", _dp)]
+
+
+class rafem_params(ctypes.Structure):
+    _fields_ = [("alpha_sigma", ctypes.c_double), ("rho_c", ctypes.c_double), ("perf", ctypes.c_double),
+                ("T_a", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("corrector_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("n_corrector", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32)]
+
+
+class rafem_step_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters_V", ctypes.c_int32), ("iters_T", ctypes.c_int32),
+                ("refine_V", ctypes.c_int32), ("refine_T", ctypes.c_int32), ("correctors", ctypes.c_int32),
+                ("relres_V", ctypes.c_double), ("relres_T", ctypes.c_double), ("step", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load librafem.so (built in-tree). Raises if it is missing: there is no fallback path."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librafem.so not built ({LIB_PATH}); run python -m paper_2409_13036_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    sig = {
+        "rafem_default_params": (None, [ctypes.POINTER(rafem_params)]),
+        "rafem_create": (ctypes.c_int, [ctypes.POINTER(rafem_mesh), ctypes.POINTER(rafem_params), vp,
+                                        ctypes.POINTER(vp)]),
+        "rafem_assemble": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rafem_solve": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(rafem_step_stats)]),
+        "rafem_solve_step": (ctypes.c_int, [vp, ctypes.POINTER(rafem_step_stats)]),
+        "rafem_run": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(rafem_step_stats)]),
+        "rafem_get_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+        "rafem_set_state": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int64]),
+        "rafem_pattern_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int32)]),
+        "rafem_get_system": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
+        "rafem_solve_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rafem_step_stats)]),
+        "rafem_spmv": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "rafem_destroy": (None, [vp]),
+        "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_symbols() -> list[str]:
+    """Names of every entry point declared in include/rafem.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rafem_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(s: int) -> str:
+    return lib().rafem_status_string(int(s)).decode()
+
+
+class RafemError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def _check(s, where, soft_ok=True):
+    if s < 0 or (s > 0 and not soft_ok):
+        raise RafemError(s, where)
+    return s
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def default_params(**kw) -> rafem_params:
+    p = rafem_params()
+    lib().rafem_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _dev(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+class Context:
+    """Owns one rafem_ctx (one problem instance on the current CUDA device)."""
+
+    def __init__(self, mesh, params: rafem_params | None = None, stream: int | None = None, **kw):
+        self._keep = [np.ascontiguousarray(mesh.coords, dtype=np.float64),
+                      np.ascontiguousarray(mesh.tets, dtype=np.int32),
+                      np.ascontiguousarray(mesh.bc_V, dtype=np.uint8),
+                      np.ascontiguousarray(mesh.g_V, dtype=np.float64),
+                      np.ascontiguousarray(mesh.bc_T, dtype=np.uint8),
+                      np.ascontiguousarray(mesh.g_T, dtype=np.float64),
+                      np.ascontiguousarray(mesh.sigma0, dtype=np.float64),
+                      np.ascontiguousarray(mesh.k, dtype=np.float64)]
+        c, t, bv, gv, bt, gt, s0, k = self._keep
+        m = rafem_mesh(n_nodes=c.shape[0], n_tets=t.shape[0], coords=_ptr(c, ctypes.c_double),
+                       tets=_ptr(t, ctypes.c_int32), bc_V=_ptr(bv, ctypes.c_uint8), g_V=_ptr(gv, ctypes.c_double),
+                       bc_T=_ptr(bt, ctypes.c_uint8), g_T=_ptr(gt, ctypes.c_double),
+                       sigma0=_ptr(s0, ctypes.c_double), k=_ptr(k, ctypes.c_double))
+        self.params = params if params is not None else default_params(**kw)
+        self.N = int(c.shape[0])
+        self._ctx = ctypes.c_void_p()
+        s = lib().rafem_create(ctypes.byref(m), ctypes.byref(self.params), ctypes.c_void_p(stream or 0),
+                               ctypes.byref(self._ctx))
+        _check(s, "rafem_create")
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().rafem_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C-ABI calls ----------------------------------------------------------------------------------------
+    def assemble(self, which: int):
+        return _check(lib().rafem_assemble(self._ctx, which), "rafem_assemble")
+
+    def solve(self, which: int):
+        st = rafem_step_stats()
+        s = lib().rafem_solve(self._ctx, which, ctypes.byref(st))
+        return _check(s, "rafem_solve"), st
+
+    def solve_step(self):
+        st = rafem_step_stats()
+        s = lib().rafem_solve_step(self._ctx, ctypes.byref(st))
+        return _check(s, "rafem_solve_step"), st
+
+    def run(self, n_steps: int):
+        st = rafem_step_stats()
+        s = lib().rafem_run(self._ctx, int(n_steps), ctypes.byref(st))
+        return _check(s, "rafem_run"), st
+
+    def get_field(self, which: int) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.float64)
+        _check(lib().rafem_get_field(self._ctx, which, out.ctypes.data, 0), "rafem_get_field")
+        return out
+
+    def get_field_device(self, which: int, dst) -> None:
+        _check(lib().rafem_get_field(self._ctx, which, _dev(dst), 1), "rafem_get_field")
+
+    def set_state(self, T=None, V=None, step: int = 0):
+        Ta = None if T is None else np.ascontiguousarray(T, dtype=np.float64)
+        Va = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+        s = lib().rafem_set_state(self._ctx, None if Ta is None else Ta.ctypes.data,
+                                  None if Va is None else Va.ctypes.data, 0, int(step))
+        _check(s, "rafem_set_state")
+
+    def set_state_device(self, T=None, V=None, step: int = 0):
+        _check(lib().rafem_set_state(self._ctx, _dev(T), _dev(V), 1, int(step)), "rafem_set_state")
+
+    def pattern_info(self):
+        n = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        nc = ctypes.c_int32()
+        _check(lib().rafem_pattern_info(self._ctx, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc)),
+               "rafem_pattern_info")
+        return n.value, nnz.value, nc.value
+
+    def get_system(self, which: int):
+        """(row_ptr, col, vals, rhs) of the current lifted system, as host arrays."""
+        n, nnz, _ = self.pattern_info()
+        rp = np.empty(n + 1, np.int32)
+        col = np.empty(nnz, np.int32)
+        vals = np.empty(nnz, np.float64)
+        rhs = np.empty(n, np.float64)
+        _check(lib().rafem_get_system(self._ctx, which, rp.ctypes.data, col.ctypes.data, vals.ctypes.data,
+                                      rhs.ctypes.data), "rafem_get_system")
+        return rp, col, vals, rhs
+
+    def solve_rhs(self, which: int, b_dev, x_dev):
+        st = rafem_step_stats()
+        s = lib().rafem_solve_rhs(self._ctx, which, _dev(b_dev), _dev(x_dev), ctypes.byref(st))
+        return _check(s, "rafem_solve_rhs"), st
+
+    def spmv(self, which: int, x_dev, y_dev):
+        _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+
+# C names, for callers that prefer the flat API
+def rafem_create(mesh, params=None, stream=None):
+    return Context(mesh, params, stream)
+
+
+def rafem_assemble(ctx: Context, which: int):
+    return ctx.assemble(which)
+
+
+def rafem_solve_step(ctx: Context):
+    return ctx.solve_step()
+
+
+def rafem_run(ctx: Context, n_steps: int):
+    return ctx.run(n_steps)
+
+
+def rafem_destroy(ctx: Context):
+    ctx.close()

@@ -1,0 +1,64 @@
+"""Host-side checks (no GPU): the C-ABI library loads and exports every entry point of include/rafem.h, and
+the sampled-row oracle helper agrees with the full oracle."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from oracle import rafem_oracle as O
+from paper_2409_13036_b300 import meshgen as mg
+from tests.sampled_rows import lifted_rows
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2409_13036_b300 import build
+    return build.build()
+
+
+def test_library_exports_every_header_symbol(built):
+    from paper_2409_13036_b300 import rafem
+    names = rafem.header_symbols()
+    assert "rafem_create" in names and "rafem_run" in names and len(names) >= 14
+    L = ctypes.CDLL(built)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert rafem.lib() is not None
+
+
+def test_status_strings(built):
+    from paper_2409_13036_b300 import rafem
+    assert rafem.status_string(0) == "OK"
+    assert rafem.status_string(-5) == "ERR_TIMEOUT"
+    p = rafem.default_params()
+    assert p.tol == 1e-10 and p.alpha_sigma == 0.015 and p.n_corrector == 1
+
+
+def test_sampled_rows_helper_matches_full_oracle():
+    m = mg.cube_mesh(6, jitter=0.1, seed=3, sigma0="lognormal")
+    rng = np.random.default_rng(0)
+    T = 37 + 10 * rng.random(m.n_nodes)
+    V = 20 * rng.random(m.n_nodes)
+    model = O.Model(m)
+    rows = rng.choice(m.n_nodes, 60, replace=False)
+    for which in ("V", "T"):
+        if which == "V":
+            A, b = model.system_V(T)
+            r, ref, bs = lifted_rows(m, rows, T, which="V")
+        else:
+            A, b = model.system_T(T, O.joule(model.sigma(T), V, model.tets, model.grad))
+            r, ref, bs = lifted_rows(m, rows, T, which="T", V=V, T_old=T)
+        np.testing.assert_allclose(bs, b[r], rtol=1e-12, atol=1e-14 * np.abs(b).max())
+        for i in r:
+            lo, hi = A.indptr[i], A.indptr[i + 1]
+            got = np.array([ref[i][c] for c in A.indices[lo:hi]])
+            np.testing.assert_allclose(got, A.data[lo:hi], rtol=1e-12, atol=1e-14 * np.abs(A.data).max())
+
+
+def test_mesh_generator_counts():
+    for n, N, E, el in ((8, 729, 3072, 3), (48, 117649, 663552, 13)):
+        m = mg.cube_mesh(n, jitter=0.1, seed=1)
+        assert (m.n_nodes, m.n_tets, int(m.electrode.sum())) == (N, E, el)
+    m = mg.cube_mesh(127, jitter=0.0)
+    assert int(m.electrode.sum()) == 16 * 32

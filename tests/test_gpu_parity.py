@@ -1,0 +1,240 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C-ABI (needs a B300)."""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import rafem_oracle as O
+from paper_2409_13036_b300 import meshgen as mg
+from tests.sampled_rows import lifted_rows, rows_adjacent_to
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2409_13036_b300 import build
+    build.build()
+    torch.cuda.init()
+    yield
+
+
+def R():
+    from paper_2409_13036_b300 import rafem
+    return rafem
+
+
+def _csr(rp, col, vals, n):
+    return sp.csr_matrix((vals, col, rp), shape=(n, n))
+
+
+def _nonuniform_T(mesh, seed=0):
+    rng = np.random.default_rng(seed)
+    T = 37.0 + 25.0 * rng.random(mesh.n_nodes)
+    return np.where(mesh.bc_T.astype(bool), mesh.g_T, T)
+
+
+def test_assembled_potential_system_matches_oracle():
+    """A_V(sigma(T)) and its lifted rhs, slot by slot, on a jittered lognormal mesh with a non-uniform T."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=21, sigma0="lognormal")
+    T = _nonuniform_T(m)
+    with rafem.Context(m) as ctx:
+        ctx.set_state(T=T)
+        ctx.assemble(rafem.RAFEM_SYS_V)
+        rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_V)
+    A, b = O.Model(m).system_V(T)
+    np.testing.assert_array_equal(rp, A.indptr)
+    np.testing.assert_array_equal(col, A.indices)
+    scale = np.abs(A.data).max()
+    np.testing.assert_allclose(vals, A.data, rtol=1e-13, atol=1e-14 * scale)
+    np.testing.assert_allclose(rhs, b, rtol=1e-13, atol=1e-14 * np.abs(b).max())
+
+
+def test_assembled_thermal_system_matches_oracle():
+    """Constant thermal matrix and the rhs (Joule from V, mass term from T), slot by slot."""
+    rafem = R()
+    m = mg.cube_mesh(9, jitter=0.1, seed=22, sigma0="lognormal")
+    T = _nonuniform_T(m, 1)
+    rng = np.random.default_rng(2)
+    V = np.where(m.bc_V.astype(bool), m.g_V, 20.0 * rng.random(m.n_nodes))
+    model = O.Model(m)
+    with rafem.Context(m) as ctx:
+        ctx.set_state(T=T, V=V)
+        ctx.assemble(rafem.RAFEM_SYS_T)
+        rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_T)
+    Q = O.joule(model.sigma(T), V, model.tets, model.grad)
+    A, b = model.system_T(T, Q)
+    np.testing.assert_array_equal(rp, A.indptr)
+    np.testing.assert_array_equal(col, A.indices)
+    np.testing.assert_allclose(vals, A.data, rtol=1e-13, atol=1e-14 * np.abs(A.data).max())
+    np.testing.assert_allclose(rhs, b, rtol=1e-13, atol=1e-14 * np.abs(b).max())
+
+
+def test_potential_solve_matches_direct_solve():
+    """One PCG solve to a 1e-13 relative residual agrees with the oracle's LU solution to 1e-10."""
+    rafem = R()
+    m = mg.cube_mesh(14, jitter=0.1, seed=23, sigma0="lognormal")
+    T = _nonuniform_T(m, 3)
+    with rafem.Context(m, tol=1e-13) as ctx:
+        ctx.set_state(T=T)
+        ctx.assemble(rafem.RAFEM_SYS_V)
+        s, st = ctx.solve(rafem.RAFEM_SYS_V)
+        V = ctx.get_field(rafem.RAFEM_SYS_V)
+    assert s == rafem.RAFEM_OK and st.relres_V <= 1e-13 and st.iters_V > 10
+    A, b = O.Model(m).system_V(T)
+    V_ref = O.solve(A, b)
+    assert O.rel_err(V, V_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("n,steps", [(12, 6), (20, 4)])
+def test_time_steps_match_oracle(n, steps):
+    """Full backward-Euler steps (assemble V, solve, Joule + thermal rhs, solve) vs the oracle's LU path:
+    relative error <= 1e-9 per field per step (solver tolerance 1e-12), temperature PSNR >= 80 dB."""
+    rafem = R()
+    m = mg.cube_mesh(n, jitter=0.1, seed=24 + n, sigma0="lognormal")
+    Ts, Vs = [], []
+    with rafem.Context(m, tol=1e-12, dt=5.0) as ctx:
+        for _ in range(steps):
+            s, st = ctx.solve_step()
+            assert s == rafem.RAFEM_OK, st.as_dict()
+            Ts.append(ctx.get_field(rafem.RAFEM_SYS_T))
+            Vs.append(ctx.get_field(rafem.RAFEM_SYS_V))
+    model = O.Model(m, O.Params(dt=5.0))
+    T_ref, V_ref = model.run(steps)
+    for k in range(steps):
+        assert O.rel_err(Vs[k], V_ref[k]) <= 1e-9
+        assert O.rel_err(Ts[k], T_ref[k]) <= 1e-9
+    assert np.all(O.psnr(T_ref, np.array(Ts)) >= 80.0)
+    assert T_ref[-1].max() > 37.5  # the run actually heats
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_lanes_and_ragged_tiles_agree(lanes):
+    """Every SpMV lane width and a ragged tile size (37 rows) give the same step to 1e-11."""
+    rafem = R()
+    m = mg.cube_mesh(11, jitter=0.1, seed=31, sigma0="lognormal")
+    with rafem.Context(m, tol=1e-12) as ref:
+        ref.run(2)
+        T0 = ref.get_field(rafem.RAFEM_SYS_T)
+        V0 = ref.get_field(rafem.RAFEM_SYS_V)
+    with rafem.Context(m, tol=1e-12, lanes_per_row=lanes, rows_per_tile=37) as ctx:
+        ctx.run(2)
+        assert O.rel_err(ctx.get_field(rafem.RAFEM_SYS_T), T0) <= 1e-11
+        assert O.rel_err(ctx.get_field(rafem.RAFEM_SYS_V), V0) <= 1e-11
+
+
+def test_graph_run_equals_step_loop_bitwise():
+    """rafem_run (one CUDA graph per step) and repeated rafem_solve_step give bit-identical fields; two runs
+    are bit-identical (fixed reduction order)."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=32)
+    out = []
+    for mode in ("run", "step", "run"):
+        with rafem.Context(m) as ctx:
+            if mode == "run":
+                s, st = ctx.run(4)
+            else:
+                for _ in range(4):
+                    s, st = ctx.solve_step()
+            assert s == rafem.RAFEM_OK and st.step == 4
+            out.append((ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V)))
+    for T, V in out[1:]:
+        np.testing.assert_array_equal(T, out[0][0])
+        np.testing.assert_array_equal(V, out[0][1])
+
+
+def test_iteration_cap_reports_not_converged():
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=33)
+    with rafem.Context(m, max_iter=3) as ctx:
+        s, st = ctx.solve_step()
+    assert s == rafem.RAFEM_NOT_CONVERGED
+    assert st.iters_V == 3 and st.relres_V > 1e-10
+
+
+def test_bad_inputs_rejected():
+    rafem = R()
+    m = mg.cube_mesh(3)
+    bad = dataclasses.replace(m, sigma0=np.where(np.arange(m.n_tets) == 5, np.nan, m.sigma0))
+    with pytest.raises(rafem.RafemError) as e:
+        rafem.Context(bad)
+    assert e.value.status == rafem.RAFEM_ERR_NONFINITE
+    t = m.tets.copy()
+    t[7] = [0, 1, 2, 3]  # coplanar nodes on the bottom face
+    with pytest.raises(rafem.RafemError) as e:
+        rafem.Context(dataclasses.replace(m, tets=t))
+    assert e.value.status == rafem.RAFEM_ERR_BAD_MESH
+    t = m.tets.copy()
+    t[2, 1] = m.n_nodes + 5
+    with pytest.raises(rafem.RafemError) as e:
+        rafem.Context(dataclasses.replace(m, tets=t))
+    assert e.value.status == rafem.RAFEM_ERR_BAD_INPUT
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_degenerate_tiny_meshes(n):
+    """n=1: every node is Dirichlet (the solution is the boundary data). n=2: one interior node."""
+    rafem = R()
+    m = mg.cube_mesh(n)
+    with rafem.Context(m) as ctx:
+        s, st = ctx.run(2)
+        assert s == rafem.RAFEM_OK
+        T = ctx.get_field(rafem.RAFEM_SYS_T)
+        V = ctx.get_field(rafem.RAFEM_SYS_V)
+    T_ref, V_ref = O.Model(m).run(2)
+    np.testing.assert_allclose(V, V_ref[-1], rtol=0, atol=1e-9 * 20)
+    np.testing.assert_allclose(T, T_ref[-1], rtol=0, atol=1e-9 * 37)
+
+
+def _sampled_check(m, ctx, rafem, T_before, rng, n_rand=3000):
+    """Sampled-row parity of both lifted systems and of the solutions after one step at full size."""
+    V = ctx.get_field(rafem.RAFEM_SYS_V)
+    T = ctx.get_field(rafem.RAFEM_SYS_T)
+    # rows carrying the potential's right-hand side, plus random rows
+    hot = rows_adjacent_to(m, np.nonzero(m.electrode)[0])
+    rows = np.unique(np.concatenate([hot, rng.integers(0, m.n_nodes, n_rand)]))
+    rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_V)
+    r_ids, ref, b_ref = lifted_rows(m, rows, T_before, which="V")
+    bnorm = np.sqrt(np.sum(b_ref[np.isin(r_ids, hot)] ** 2))  # all nonzero rhs rows are in `hot`
+    worst_val = worst_res = 0.0
+    for k, i in enumerate(r_ids):
+        cols = col[rp[i]:rp[i + 1]]
+        got = vals[rp[i]:rp[i + 1]]
+        exp = np.array([ref[i].get(int(c), np.nan) for c in cols])
+        assert set(cols.tolist()) == set(ref[i].keys())
+        worst_val = max(worst_val, np.abs(got - exp).max() / np.abs(exp).max())
+        assert abs(rhs[i] - b_ref[k]) <= 1e-13 * max(abs(b_ref[k]), 1.0)
+        worst_res = max(worst_res, abs(np.dot(exp, V[cols]) - b_ref[k]))
+    assert worst_val <= 1e-13
+    assert worst_res <= 2e-10 * bnorm, (worst_res, bnorm)
+    # thermal system rows with the GPU's V and the pre-step T (sigma and mass term)
+    rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_T)
+    r_ids, ref, b_ref = lifted_rows(m, rows, T_before, which="T", V=V, T_old=T_before)
+    for k, i in enumerate(r_ids):
+        cols = col[rp[i]:rp[i + 1]]
+        exp = np.array([ref[i][int(c)] for c in cols])
+        np.testing.assert_allclose(vals[rp[i]:rp[i + 1]], exp, rtol=1e-13, atol=1e-14 * np.abs(exp).max())
+        np.testing.assert_allclose(rhs[i], b_ref[k], rtol=1e-12)
+        # ||r|| <= tol ||b|| with ||b|| >= ||b_sampled||: per-row bound on the sampled rows
+        assert abs(np.dot(exp, T[cols]) - b_ref[k]) <= 1e-10 * np.sqrt(m.n_nodes) * np.abs(b_ref).max()
+
+
+@pytest.mark.parametrize("n", [48, 127])
+def test_full_size_sampled_rows(n):
+    """At the full workload sizes (48^3 and 127^3 cells, bench launch configuration): after one step the
+    assembled rows agree with the oracle slot by slot and the solutions satisfy the oracle's equations on
+    sampled rows (all rows carrying the potential's rhs plus 3000 random rows)."""
+    rafem = R()
+    m = mg.workload_48() if n == 48 else mg.workload_127()
+    rng = np.random.default_rng(n)
+    with rafem.Context(m) as ctx:
+        T_before = ctx.get_field(rafem.RAFEM_SYS_T)
+        s, st = ctx.run(1)
+        assert s == rafem.RAFEM_OK, st.as_dict()
+        assert st.relres_V <= 1e-10 and st.relres_T <= 1e-10
+        _sampled_check(m, ctx, rafem, T_before, rng)
