@@ -1,0 +1,375 @@
+"""Benchmark of the RAFEM time step on one B300: time-steps/s at 2.1M DoF per system, FP64 and mixed.
+
+Workload: the 127^3-cell cube (2,097,152 nodes, 12,290,298 P1 tetrahedra, 31,065,598 nonzeros per system),
+interior jitter +-10% of the cell width, lognormal sigma0 (mean 0.333 S/m, 10% CV), dt = 1 s, relative
+residual 1e-10, Jacobi preconditioning. A step is one backward-Euler step: assemble A_V(sigma(T)) and its
+lifted rhs, solve V, assemble the thermal rhs (Joule + mass term), solve T, all in one CUDA graph.
+Inputs are synthetic (seeded) and resident in HBM before the timed region; each step streams both
+matrices (373 MB each in FP64) and the element data, far more than the 126 MB L2.
+
+The headline `value` is the mixed-precision form (FP32 inner Krylov, FP64 refinement to the same 1e-10 FP64
+residual); the FP64 path is reported beside it in `fp64`, with the mixed-vs-FP64 field error and PSNR.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rafem|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/s at 2.1M DoF (FP64 vs mixed vs oracle); SpMV HBM GB/s vs peak"
+UNIT = "time-steps/s"
+WORKLOAD = ("RAFEM cube 127^3 cells, 2,097,152 nodes, 12,290,298 P1 tets, 31,065,598 nnz per system; jitter 10%, "
+            "lognormal sigma0; dt=1 s; Jacobi-PCG to FP64 relative residual 1e-10; steps W+1..W+K of the 900-step "
+            "run")
+ORACLE_SAMPLE_N = 24          # oracle sample: the same workload family on a 24^3-cell cube (15,625 nodes)
+ORACLE_SAMPLE_STEPS = 5
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def _oracle_sample(n: int, steps: int) -> dict:
+    """Time the FP64 oracle (dense/sparse direct LU, one thread) on steps of an n^3 instance."""
+    from oracle import rafem_oracle as O
+    from paper_2409_13036_b300 import meshgen as mg
+    import numpy as np
+    m = mg.cube_mesh(n, jitter=0.10, seed=mg.SEED_BASE + 2, sigma0="lognormal")
+    model = O.Model(m)
+    T = np.full(m.n_nodes, 37.0)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        T, V, _ = model.step(T)
+        times.append(time.perf_counter() - t0)
+    return {"n": n, "nodes": m.n_nodes, "times": times}
+
+
+def run_oracle_subprocess(n: int, steps: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_sample(%d, %d)))" % (ROOT, n, steps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = ""
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3]) if v.lower().startswith("active")})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def _source_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per iteration of `kernel` from the committed ncu summary, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        e = json.load(f).get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2409_13036_b300", "csrc", e["source"])
+    if _source_hash(src) != e["source_sha256"]:
+        return None
+    return e
+
+
+def alg_bytes_cg64(N: int, nnz: int, iters: float) -> float:
+    """Algorithmic HBM bytes of one FP64 Chronopoulos-Gear Jacobi-PCG solve launch.
+    Per iteration: SpMV w = A u streams 12 B per nonzero (value + column index), reads u once and writes w
+    (16N); the vector phase reads u, w, p, s, x, r, dinv and writes p, s, x, r, u (96N). Start-up (r = b - Ax,
+    u, w = Au) and the final true-residual SpMV add two more iterations' worth."""
+    per_iter = 12 * nnz + 16 * N + 96 * N
+    return (iters + 2) * per_iter
+
+
+def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float) -> float:
+    """Algorithmic HBM bytes of one mixed-precision solve launch.
+    Inner FP32 iteration: SpMV 8 B per nonzero + 8N (u read, w written); vector phase 12 x 4N.
+    Each FP64 refinement: x64 += d32 (8N read + 4N read + 8N write) and the FP64 residual SpMV
+    (12 B per nonzero + 8N x + 8N b) writing r32, u32, d32 (12N) and reading dinv32 (4N); plus one start SpMV
+    in FP32 (8 B per nonzero + 8N)."""
+    inner = 8 * nnz + 8 * N + 48 * N
+    outer = (20 * N) + (12 * nnz + 16 * N + 16 * N) + (8 * nnz + 8 * N)
+    return iters * inner + (refinements + 1) * outer
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = ORACLE_SAMPLE_N
+    res = run_oracle_subprocess(n, args.warmup + args.steps)
+    t = res["times"][args.warmup:]
+    value = len(t) / sum(t)
+    sample = (f"FP64 oracle (own assembly + SuperLU direct solve, 1 thread) on the same workload family at "
+              f"{n}^3 cells ({res['nodes']} nodes): {len(t)} timed steps after {args.warmup} warm-up; "
+              f"the direct LU does not finish at 127^3")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle_sample_cells": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks):
+    """Warm up, time K steps with CUDA events on the context's stream, then a few traced steps."""
+    stream = torch.cuda.Stream()
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision)
+    N, nnz, n_colors = ctx.pattern_info()
+    s, st = ctx.run(args.warmup)
+    if s < 0:
+        raise RuntimeError(f"warm-up failed: {rafem.status_string(s)}")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local) if want_clocks else None
+    if clk:
+        clk.__enter__()
+    ev0.record(stream)
+    s, st = ctx.run(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fields = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
+    ctx.set_tracing(True)
+    ctx.run(3)
+    tr = ctx.get_trace()
+    ctx.set_tracing(False)
+    return {"ctx": ctx, "ms": ms, "status": rafem.status_string(s), "last": st.as_dict(), "trace": tr,
+            "fields": fields, "N": N, "nnz": nnz, "n_colors": n_colors, "clocks": clk.summary() if clk else None}
+
+
+def roofline(res, mixed, peaks, peak_kind):
+    tr = res["trace"]
+    N, nnz = res["N"], res["nnz"]
+    steps = tr["steps"]
+    solve_ms = tr["ms_solve_V"] / steps
+    iters = tr["iters_V"] / steps
+    if mixed:
+        ref = tr["refine_V"] / steps
+        alg = alg_bytes_mixed(N, nnz, iters, ref)
+        kern = "k_cg_mixed<1>"
+    else:
+        ref = 0.0
+        alg = alg_bytes_cg64(N, nnz, iters)
+        kern = "k_cg64<1>"
+    achieved = alg / (solve_ms * 1e-3) / 1e9
+    nc = _ncu_traffic(kern)
+    traffic = None
+    if nc:
+        traffic = nc["dram_bytes_per_iteration"] * (iters + 2)
+    return {"bound": "hbm", "kernel": f"{kern} (potential-system persistent solver, one launch per step)",
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_kind": ("measured copy bandwidth, MEASURED_PEAKS.json hbm_gbs (of measured)"
+                          if peak_kind == "measured" else "fallback 6.4 TB/s (of fallback)"),
+            "traffic": traffic, "launch_ms": solve_ms, "iters_per_launch": iters, "refinements_per_launch": ref,
+            "alg_bytes_per_launch": alg}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rafem", choices=["rafem", "reference"])
+    ap.add_argument("--cells", type=int, default=127)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="run one precision only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline first, in a child process (no CUDA context in this process yet)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        res = run_oracle_subprocess(ORACLE_SAMPLE_N, ORACLE_SAMPLE_STEPS)
+        t = res["times"][1:]  # the first step also factors the constant thermal matrix
+        cpu = {"value": len(t) / sum(t), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"{len(t)} time steps of the FP64 oracle (own assembly + SuperLU, 1 thread) on the "
+                          f"{ORACLE_SAMPLE_N}^3-cell instance ({res['nodes']} nodes) of the same workload; "
+                          f"not extrapolated (direct LU cost grows superlinearly)")}
+
+    import numpy as np
+    import torch
+    from paper_2409_13036_b300 import build, meshgen as mg, rafem
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+
+    mesh = mg.workload_127() if args.cells == 127 else mg.cube_mesh(args.cells, jitter=0.1,
+                                                                     seed=mg.SEED_BASE + 2, sigma0="lognormal")
+    peaks, peak_kind = _measured_peaks()
+    runs = {}
+    for name, prec in (("fp64", rafem.RAFEM_PRECISION_FP64), ("mixed", rafem.RAFEM_PRECISION_MIXED)):
+        if args.only and args.only != name:
+            continue
+        r = measure(rafem, torch, mesh, prec, args, local, dist, want_clocks=(name == "mixed" or args.only == name))
+        r["roofline"] = roofline(r, prec == rafem.RAFEM_PRECISION_MIXED, peaks, peak_kind)
+        runs[name] = r
+        if name == "fp64" and args.only is None:
+            r["ctx"].close()
+            r["ctx"] = None
+    head_name = "mixed" if "mixed" in runs else "fp64"
+    head = runs[head_name]
+    ctx = head["ctx"]
+    N, nnz, n_colors = head["N"], head["nnz"], head["n_colors"]
+
+    # end to end through the C-ABI with host buffers: H2D of the state, one step, D2H of both fields
+    hT = torch.empty(N, dtype=torch.float64).pin_memory()
+    hV = torch.empty(N, dtype=torch.float64).pin_memory()
+    ctx.get_field_ptr(rafem.RAFEM_SYS_T, hT.data_ptr(), 0)
+    ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.set_state_ptr(hT.data_ptr(), hV.data_ptr(), 0, 0)
+        ctx.run(1)
+        ctx.get_field_ptr(rafem.RAFEM_SYS_T, hT.data_ptr(), 0)
+        ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)
+    t_e2e = time.perf_counter() - t0
+    ctx.close()
+
+    def summary(r):
+        tr = r["trace"]
+        return {"value": world * args.steps / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / args.steps,
+                "status": r["status"], "last_step": r["last"],
+                "iters_V_per_step": tr["iters_V"] / tr["steps"], "iters_T_per_step": tr["iters_T"] / tr["steps"],
+                "refine_V_per_step": tr["refine_V"] / tr["steps"],
+                "regions_ms_per_step": {k: tr[k] / tr["steps"] for k in ("ms_assemble_V", "ms_solve_V",
+                                                                          "ms_assemble_T", "ms_solve_T")},
+                "roofline": r["roofline"]}
+
+    per_step_launches = 1 + (1 + n_colors + 2 + 1) + (1 + n_colors + 2 + 1)
+    head_sum = summary(head)
+    line = {"metric": METRIC, "value": head_sum["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head_sum["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head_name == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": N, "nnz_per_system": nnz, "colours": n_colors,
+                       "precision": head_name, "layout": "SELL-32",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (two 373 MB FP64 matrices + element data per step)"},
+            "status": head_sum["status"],
+            "iters_V_per_step": head_sum["iters_V_per_step"], "iters_T_per_step": head_sum["iters_T_per_step"],
+            "refine_V_per_step": head_sum["refine_V_per_step"],
+            "regions_ms_per_step": head_sum["regions_ms_per_step"],
+            "roofline": head["roofline"],
+            "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+                    "d2h_bytes_per_step": 16 * N},
+            "gpu_launches": per_step_launches * args.steps,
+            "clocks": head["clocks"]}
+    if "fp64" in runs and head_name != "fp64":
+        line["fp64"] = summary(runs["fp64"])
+        # the mixed form's accuracy against the FP64 GPU path after the same W+K steps (Sec. IV PSNR, Eq. 1-2)
+        Tf, Vf = runs["fp64"]["fields"]
+        Tm, Vm = head["fields"]
+        mse_T = float(np.mean((Tm - Tf) ** 2))
+        line["mixed_vs_fp64"] = {
+            "rel_err_T": float(np.linalg.norm(Tm - Tf) / np.linalg.norm(Tf)),
+            "rel_err_V": float(np.linalg.norm(Vm - Vf) / np.linalg.norm(Vf)),
+            "psnr_T_db": float("inf") if mse_T == 0 else float(20 * np.log10(Tf.max() / np.sqrt(mse_T))),
+            "speedup": head_sum["value"] / line["fp64"]["value"]}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -20,8 +20,8 @@
  *   - Inputs passed to rafem_create are copied; the caller keeps ownership of every pointer it passes.
  *   - A pointer documented as "device" must be a CUDA device pointer valid on the context's device; "host"
  *     pointers are ordinary host memory (pinned or pageable).
- *   - All work is issued on the stream given at create (NULL = the legacy default stream) and every entry
- *     point synchronises that stream before returning, unless stated otherwise.
+ *   - All work is issued on the stream given at create (NULL = a non-blocking stream the context creates and
+ *     owns) and every entry point synchronises that stream before returning, unless stated otherwise.
  *   - There is no global state: calls on different contexts are independent; calls on one context must not
  *     overlap (not thread-safe).
  *   - Units are SI; coordinates in metres, temperatures in degrees Celsius, potentials in volts.
@@ -90,7 +90,8 @@ typedef struct rafem_params {
     int32_t precond;                 /* RAFEM_PRECOND_*                                                        */
     int32_t precision;               /* RAFEM_PRECISION_*                                                      */
     int32_t solver;                  /* RAFEM_SOLVER_*                                                         */
-    int32_t lanes_per_row;           /* SpMV lanes per CSR row: 0 = autotuned, else 4, 8, 16 or 32             */
+    int32_t lanes_per_row;           /* matrix layout: 0 or 1 = SELL-32 (one thread per row), 4/8/16/32 = CSR
+                                        with that many lanes per row                                          */
     int32_t rows_per_tile;           /* rows per work tile of the persistent solver: 0 = automatic            */
 } rafem_params;
 
@@ -161,6 +162,27 @@ int rafem_solve_rhs(rafem_ctx* ctx, int which, const double* b_dev, double* x_de
 
 /* y = A x with the current lifted system `which` (FP64). x, y: device pointers to N doubles. */
 int rafem_spmv(rafem_ctx* ctx, int which, const double* x_dev, double* y_dev);
+
+/* Region timing (the paper's trace regions of Sec. III-C: Assembly, Solve, memcpyH2D, memcpyD2H), measured
+ * with CUDA events on the context's stream. While tracing is on, rafem_solve_step and rafem_run launch each
+ * region directly (no graph) with an event on each side and NVTX ranges of the same names. */
+typedef struct rafem_trace {
+    int64_t steps;                   /* traced steps accumulated                                              */
+    int64_t iters_V, iters_T;        /* Krylov iterations over the traced steps                              */
+    int64_t solves;                  /* traced solves of each system                                          */
+    int64_t refine_V;                /* FP64 refinements of the potential solves (mixed precision)           */
+    double  ms_assemble_V;           /* "Assembly" of the potential system (matrix + lifted rhs)             */
+    double  ms_solve_V;              /* "Solve" of the potential system (one persistent solver launch)       */
+    double  ms_assemble_T;           /* "Assembly" of the thermal rhs (Joule + mass term)                     */
+    double  ms_solve_T;              /* "Solve" of the thermal system                                         */
+    double  ms_memcpy_h2d;           /* rafem_set_state copies                                                */
+    double  ms_memcpy_d2h;           /* rafem_get_field copies                                                */
+} rafem_trace;
+
+/* enable: 1 = on (accumulators cleared), 0 = off. */
+int rafem_set_tracing(rafem_ctx* ctx, int enable);
+/* Copy the accumulated region timings to *out. */
+int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
 
 /* Release every device and host resource of the context. NULL is accepted. */
 void rafem_destroy(rafem_ctx* ctx);

@@ -13,6 +13,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "setup.h"
 
@@ -39,8 +41,12 @@ struct rafem_ctx {
     std::vector<int> color_off;      // [n_colors + 1] over the sorted element order
     std::vector<void*> allocs;
 
-    // pattern
+    // pattern: CSR (rp, ci) or SELL-32 (rp = slice pointers, ci = slice columns) on the device; the CSR
+    // pattern and the CSR -> storage map stay on the host for inspection
     int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
+    bool sell = true;
+    int64_t nnz_store = 0;
+    std::vector<int32_t> h_rp, h_col, h_map;
     // element data
     ElemData el;
     int32_t* e_nodes = nullptr;
@@ -71,6 +77,10 @@ struct rafem_ctx {
     // graph
     cudaGraphExec_t graph = nullptr;
     bool graph_failed = false;
+    // tracing
+    bool tracing = false;
+    rafem_trace trace{};
+    cudaEvent_t ev[6] = {};
 };
 
 namespace {
@@ -150,6 +160,7 @@ __global__ void k_init_fields(int N, double T0, const uint8_t* bcT, const double
 
 SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     SolveArgs a{};
+    a.N = c->N;
     a.rp = c->rp;
     a.ci = c->ci;
     a.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
@@ -220,6 +231,55 @@ cudaError_t enqueue_step(rafem_ctx* c) {
     return cudaGetLastError();
 }
 
+// Traced step: the same launches as enqueue_step with an event between regions.
+cudaError_t enqueue_step_traced(rafem_ctx* c) {
+    cudaError_t e;
+    for (int i = 0; i < 6; ++i)
+        if (!c->ev[i] && (e = cudaEventCreate(&c->ev[i])) != cudaSuccess) return e;
+    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    nvtxRangePushA("Assembly");
+    cudaEventRecord(c->ev[0], c->stream);
+    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[1], c->stream);
+    nvtxRangePop();
+    nvtxRangePushA("Solve");
+    if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[2], c->stream);
+    nvtxRangePop();
+    k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+    nvtxRangePushA("Assembly");
+    cudaEventRecord(c->ev[3], c->stream);
+    if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[4], c->stream);
+    nvtxRangePop();
+    nvtxRangePushA("Solve");
+    if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[5], c->stream);
+    nvtxRangePop();
+    k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    float ms[4];
+    cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&ms[2], c->ev[3], c->ev[4]);
+    cudaEventElapsedTime(&ms[3], c->ev[4], c->ev[5]);
+    c->trace.ms_assemble_V += ms[0];
+    c->trace.ms_solve_V += ms[1];
+    c->trace.ms_assemble_T += ms[2];
+    c->trace.ms_solve_T += ms[3];
+    c->trace.steps += 1;
+    c->trace.solves += 1;
+    InstState iv, it;
+    if ((e = cudaMemcpy(&iv, c->instV, sizeof(iv), cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(&it, c->instT, sizeof(it), cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    c->trace.iters_V += iv.iters;
+    c->trace.iters_T += it.iters;
+    c->trace.refine_V += iv.refine;
+    return cudaSuccess;
+}
+
 int finish(rafem_ctx* c, rafem_step_stats* out, bool worst) {
     StatsDev h;
     CK(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -275,6 +335,8 @@ void rafem_destroy(rafem_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -327,6 +389,27 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         const int32_t* f = std::lower_bound(col.data() + rp[i], col.data() + rp[i + 1], i);
         diag[i] = (int32_t)(f - col.data());
     }
+    // storage layout of the matrix values: SELL-32 (lanes_per_row 0 or 1) or CSR
+    c->lanes = prm->lanes_per_row ? prm->lanes_per_row : 1;
+    c->sell = c->lanes == 1;
+    std::vector<int32_t> dev_rp, dev_ci;
+    if (c->sell) {
+        std::vector<int32_t> map;
+        build_sell(N, rp, col, dev_rp, dev_ci, map);
+        c->nnz_store = (int64_t)dev_ci.size();
+        if (c->nnz_store >= (int64_t)SLOT_MASK) return RAFEM_ERR_BAD_INPUT;
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < (int64_t)slots.size(); ++q) {
+            const int32_t code = slots[q];
+            slots[q] = map[code & SLOT_MASK] | (code & ~SLOT_MASK);
+        }
+        for (int i = 0; i < N; ++i) diag[i] = map[diag[i]];
+        c->h_map = std::move(map);
+    } else {
+        dev_rp = rp;
+        dev_ci = col;
+        c->nnz_store = c->nnz;
+    }
     std::vector<int32_t> nodes_soa(4LL * E);
     std::vector<double> sig_s(E), k_s(E);
     for (int64_t ep = 0; ep < E; ++ep) {
@@ -336,9 +419,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         k_s[ep] = m->k[e];
     }
     // ---- device buffers
-    const size_t nnz = (size_t)c->nnz;
+    const size_t nnz = (size_t)c->nnz_store;
     const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
-    CK(dalloc(c, &c->rp, N + 1));
+    CK(dalloc(c, &c->rp, dev_rp.size()));
     CK(dalloc(c, &c->ci, nnz));
     CK(dalloc(c, &c->diag, N));
     CK(dalloc(c, &c->e_nodes, 4 * (size_t)E));
@@ -387,8 +470,8 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->bar, 1));
     // ---- uploads
     cudaStream_t st = c->stream;
-    CK(cudaMemcpyAsync(c->rp, rp.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->ci, col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->rp, dev_rp.data(), dev_rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->ci, dev_ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->diag, diag.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_nodes, nodes_soa.data(), nodes_soa.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -406,21 +489,21 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     c->el.vol = c->e_vol;
     c->el.sigma0 = c->e_sig0;
     c->el.k = c->e_k;
-    // ---- solver schedule: one tile per co-resident block
-    c->lanes = prm->lanes_per_row ? prm->lanes_per_row : 8;
+    // ---- solver schedule: one tile per co-resident block (SELL tiles start on a slice boundary)
     int block = 0;
     int maxb = krylov_max_blocks(c->lanes, prm->precision, &block);
     if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
     c->block = block;
     int rows_per_tile = prm->rows_per_tile > 0 ? prm->rows_per_tile : (N + maxb - 1) / maxb;
     rows_per_tile = std::max(rows_per_tile, 1);
+    if (c->sell) rows_per_tile = (rows_per_tile + SELL_C - 1) / SELL_C * SELL_C;
     c->n_tiles = (N + rows_per_tile - 1) / rows_per_tile;
     c->grid = std::min(c->n_tiles, maxb);
     {
         std::vector<int32_t> t0(c->n_tiles), t1(c->n_tiles), ti(c->n_tiles, 0);
         for (int t = 0; t < c->n_tiles; ++t) {
-            t0[t] = (int32_t)((int64_t)t * N / c->n_tiles);
-            t1[t] = (int32_t)((int64_t)(t + 1) * N / c->n_tiles);
+            t0[t] = (int32_t)std::min<int64_t>((int64_t)t * rows_per_tile, N);
+            t1[t] = (int32_t)std::min<int64_t>((int64_t)(t + 1) * rows_per_tile, N);
         }
         int32_t it0 = 0, it1 = c->n_tiles;
         CK(dalloc(c, &c->tile_r0, c->n_tiles));
@@ -449,6 +532,8 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     k_set_step<<<1, 1, 0, st>>>(c->stats, 0);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
+    c->h_rp = std::move(rp);
+    c->h_col = std::move(col);
     return RAFEM_OK;
 }
 
@@ -461,10 +546,11 @@ int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, raf
     if (!(prm->dt > 0) || !(prm->rho_c > 0) || !(prm->perf >= 0) || !(prm->tol > 0) || prm->max_iter < 1 ||
         prm->n_corrector < 1 || prm->n_corrector > 50)
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->lanes_per_row != 0 && prm->lanes_per_row != 4 && prm->lanes_per_row != 8 &&
+    if (prm->lanes_per_row != 0 && prm->lanes_per_row != 1 && prm->lanes_per_row != 4 && prm->lanes_per_row != 8 &&
         prm->lanes_per_row != 16 && prm->lanes_per_row != 32)
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->precision != RAFEM_PRECISION_FP64) return RAFEM_ERR_BAD_INPUT;
+    if (prm->precision != RAFEM_PRECISION_FP64 && prm->precision != RAFEM_PRECISION_MIXED) return RAFEM_ERR_BAD_INPUT;
+    if (prm->precision == RAFEM_PRECISION_MIXED && !(prm->inner_tol > 0 && prm->inner_tol < 1)) return RAFEM_ERR_BAD_INPUT;
     if (prm->precond != RAFEM_PRECOND_JACOBI) return RAFEM_ERR_BAD_INPUT;
     if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     rafem_ctx* c = new (std::nothrow) rafem_ctx();
@@ -513,7 +599,7 @@ int rafem_solve_rhs(rafem_ctx* c, int which, const double* b, double* x, rafem_s
 int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     if (c->prm.n_corrector <= 1) {
-        CK(enqueue_step(c));
+        CK(c->tracing ? enqueue_step_traced(c) : enqueue_step(c));
         return finish(c, stats, false);
     }
     // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n
@@ -586,7 +672,9 @@ int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
         }
     }
     for (int i = 0; i < n_steps; ++i) {
-        if (c->graph) {
+        if (c->tracing) {
+            CK(enqueue_step_traced(c));
+        } else if (c->graph) {
             CK(cudaGraphLaunch(c->graph, c->stream));
         } else {
             CK(enqueue_step(c));
@@ -598,17 +686,44 @@ int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
 int rafem_get_field(rafem_ctx* c, int which, double* dst, int on_device) {
     if (!c || !dst || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
     const double* src = which == RAFEM_SYS_V ? c->V : c->T;
+    if (c->tracing) {
+        for (int i = 0; i < 2; ++i)
+            if (!c->ev[i]) CK(cudaEventCreate(&c->ev[i]));
+        nvtxRangePushA("memcpyD2H");
+        CK(cudaEventRecord(c->ev[0], c->stream));
+    }
     CK(cudaMemcpyAsync(dst, src, c->N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->stream));
+    if (c->tracing) CK(cudaEventRecord(c->ev[1], c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->tracing) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        c->trace.ms_memcpy_d2h += ms;
+        nvtxRangePop();
+    }
     return RAFEM_OK;
 }
 
 int rafem_set_state(rafem_ctx* c, const double* T, const double* V, int on_device, int64_t step) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->tracing) {
+        for (int i = 0; i < 2; ++i)
+            if (!c->ev[i]) CK(cudaEventCreate(&c->ev[i]));
+        nvtxRangePushA("memcpyH2D");
+        CK(cudaEventRecord(c->ev[0], c->stream));
+    }
     if (T) CK(cudaMemcpyAsync(c->T, T, c->N * sizeof(double), kind, c->stream));
     if (V) CK(cudaMemcpyAsync(c->V, V, c->N * sizeof(double), kind, c->stream));
+    if (c->tracing) {
+        CK(cudaEventRecord(c->ev[1], c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        c->trace.ms_memcpy_h2d += ms;
+        nvtxRangePop();
+    }
     c->step = step;
     k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)step);
     CK(cudaGetLastError());
@@ -627,22 +742,45 @@ int rafem_pattern_info(rafem_ctx* c, int32_t* n_rows, int64_t* nnz, int32_t* n_c
 int rafem_get_system(rafem_ctx* c, int which, int32_t* row_ptr, int32_t* col, double* vals, double* rhs) {
     if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
     cudaStream_t st = c->stream;
-    if (row_ptr) CK(cudaMemcpyAsync(row_ptr, c->rp, (c->N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (col) CK(cudaMemcpyAsync(col, c->ci, c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (vals)
-        CK(cudaMemcpyAsync(vals, which == RAFEM_SYS_V ? c->valsV : c->valsT, c->nnz * sizeof(double),
+    if (row_ptr) std::copy(c->h_rp.begin(), c->h_rp.end(), row_ptr);
+    if (col) std::copy(c->h_col.begin(), c->h_col.end(), col);
+    std::vector<double> store;
+    if (vals) {
+        store.resize(c->nnz_store);
+        CK(cudaMemcpyAsync(store.data(), which == RAFEM_SYS_V ? c->valsV : c->valsT, c->nnz_store * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
+    }
     if (rhs)
         CK(cudaMemcpyAsync(rhs, which == RAFEM_SYS_V ? c->bV : c->bT, c->N * sizeof(double), cudaMemcpyDeviceToHost,
                            st));
     CK(cudaStreamSynchronize(st));
+    if (vals) {
+        if (c->sell)
+            for (int64_t k = 0; k < c->nnz; ++k) vals[k] = store[c->h_map[k]];
+        else
+            std::copy(store.begin(), store.end(), vals);
+    }
     return RAFEM_OK;
 }
 
 int rafem_spmv(rafem_ctx* c, int which, const double* x, double* y) {
     if (!c || !x || !y || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
-    CK(launch_spmv64(c->N, c->rp, c->ci, which == RAFEM_SYS_V ? c->valsV : c->valsT, x, y, c->stream));
+    CK(launch_spmv64(c->N, c->sell ? 1 : 0, c->rp, c->ci, which == RAFEM_SYS_V ? c->valsV : c->valsT, x, y,
+                     c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_tracing(rafem_ctx* c, int enable) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    c->tracing = enable != 0;
+    c->trace = rafem_trace{};
+    return RAFEM_OK;
+}
+
+int rafem_get_trace(rafem_ctx* c, rafem_trace* out) {
+    if (!c || !out) return RAFEM_ERR_BAD_INPUT;
+    *out = c->trace;
     return RAFEM_OK;
 }
 

@@ -180,6 +180,19 @@ __global__ void __launch_bounds__(kThreads) k_spmv64(int N, const int32_t* __res
     if (lane == 0) y[row] = acc;
 }
 
+__global__ void __launch_bounds__(kThreads) k_spmv64_sell(int N, const int32_t* __restrict__ sp,
+                                                          const int32_t* __restrict__ sc,
+                                                          const double* __restrict__ A, const double* __restrict__ x,
+                                                          double* __restrict__ y) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    int s = row >> 5, lane = row & 31;
+    int base = sp[s], w = (sp[s + 1] - base) >> 5;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(A[base + 32 * k + lane], x[sc[base + 32 * k + lane]], acc);
+    y[row] = acc;
+}
+
 __global__ void k_max_abs_diff(int N, const double* __restrict__ a, const double* __restrict__ b,
                                unsigned long long* out) {
     double m = 0.0;
@@ -237,9 +250,12 @@ cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sig
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmv64(int N, const int32_t* rp, const int32_t* ci, const double* A, const double* x, double* y,
-                          cudaStream_t st) {
-    k_spmv64<<<blocks_for(8LL * N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
+cudaError_t launch_spmv64(int N, int sell, const int32_t* rp, const int32_t* ci, const double* A, const double* x,
+                          double* y, cudaStream_t st) {
+    if (sell)
+        k_spmv64_sell<<<blocks_for(N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
+    else
+        k_spmv64<<<blocks_for(8LL * N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
     return cudaGetLastError();
 }
 

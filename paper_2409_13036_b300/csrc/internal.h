@@ -40,8 +40,9 @@ cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t*
 cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sigma, const double* T_old,
                          const double* V, const uint8_t* bc, double alpha, double c_mass, double* b,
                          cudaStream_t st);
-cudaError_t launch_spmv64(int N, const int32_t* rp, const int32_t* ci, const double* A, const double* x, double* y,
-                          cudaStream_t st);
+// y = A x in FP64 for either storage layout (sell = 1: SELL-32 slices sp/sc; sell = 0: CSR rp/ci).
+cudaError_t launch_spmv64(int N, int sell, const int32_t* rp_or_sp, const int32_t* ci_or_sc, const double* A,
+                          const double* x, double* y, cudaStream_t st);
 cudaError_t launch_max_abs_diff(int N, const double* a, const double* b, double* out, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------------------------
@@ -50,7 +51,9 @@ cudaError_t launch_max_abs_diff(int N, const double* a, const double* b, double*
 struct InstState {
     double bb;          // ||b||^2 (FP64)
     double rr;          // latest ||r||^2 of the running (inner) iteration
-    double rr0;         // inner: ||r||^2 at the start of the inner solve
+    double rr0;         // mixed: FP64 ||r||^2 at the start of the current refinement
+    double rr_in0;      // mixed: inner ||r32||^2 at the start of the current inner solve
+    double gamma;       // mixed: inner gamma of the start vector
     double gamma_prev;  // (r, M^-1 r) of the previous iteration
     double alpha_prev;
     double alpha, beta;
@@ -60,8 +63,7 @@ struct InstState {
     int32_t status;
     int32_t active;     // 1 while the instance still iterates
     int32_t first;      // 1 before the first iteration of a (inner) CG run
-    int32_t outer;      // mixed: 1 while an outer FP64 residual step is pending
-    int32_t pad[2];
+    int32_t outer;      // mixed: state of the refinement state machine
 };
 
 struct GridBarrier {
@@ -73,7 +75,8 @@ struct GridBarrier {
 };
 
 struct SolveArgs {
-    // matrix (lifted, fixed pattern)
+    // matrix (lifted, fixed pattern): CSR (rp, ci) or SELL-32 (rp = slice pointers, ci = slice columns)
+    int N;
     const int32_t* rp;
     const int32_t* ci;
     const double* A;
@@ -103,6 +106,7 @@ struct SolveArgs {
     long long spin_limit_ns;
 };
 
+// lanes = 1 selects the SELL-32 thread-per-row kernels, 4/8/16/32 the CSR sub-warp kernels.
 int krylov_max_blocks(int lanes, int precision, int* block_threads);
 cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st);
 

@@ -155,4 +155,34 @@ void build_slots(int E, const int32_t* tets, const std::vector<int32_t>& row_ptr
         }
 }
 
+void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col, std::vector<int32_t>& csr_to_sell) {
+    const int S = (N + SELL_C - 1) / SELL_C;
+    slice_ptr.assign(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        int w = 0;
+        for (int r = s * SELL_C; r < std::min(N, (s + 1) * SELL_C); ++r) w = std::max(w, row_ptr[r + 1] - row_ptr[r]);
+        slice_ptr[s + 1] = slice_ptr[s] + w * SELL_C;
+    }
+    sell_col.assign(slice_ptr[S], 0);
+    csr_to_sell.assign(col.size(), 0);
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < S; ++s) {
+        const int w = (slice_ptr[s + 1] - slice_ptr[s]) / SELL_C;
+        for (int l = 0; l < SELL_C; ++l) {
+            const int r = s * SELL_C + l;
+            const int len = r < N ? row_ptr[r + 1] - row_ptr[r] : 0;
+            for (int k = 0; k < w; ++k) {
+                const int pos = slice_ptr[s] + k * SELL_C + l;
+                if (k < len) {
+                    sell_col[pos] = col[row_ptr[r] + k];
+                    csr_to_sell[row_ptr[r] + k] = pos;
+                } else {
+                    sell_col[pos] = std::min(r, N - 1);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace rafem

@@ -23,4 +23,11 @@ int color_elements(int N, int E, const int32_t* tets, std::vector<int32_t>& colo
 void build_slots(int E, const int32_t* tets, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                  const std::vector<int64_t>& order, std::vector<int32_t>& slots);
 
+// SELL-C layout (C = 32, no sorting) of a CSR pattern: slice s holds rows [32s, 32s+32), padded to the longest
+// row of the slice and stored column-major (entry k of lane l at slice_ptr[s] + 32k + l). Padding entries get
+// column min(row, N-1) and are never written. csr_to_sell maps each CSR position to its SELL position.
+constexpr int SELL_C = 32;
+void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col, std::vector<int32_t>& csr_to_sell);
+
 }  // namespace rafem

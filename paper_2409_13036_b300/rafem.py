@@ -65,6 +65,16 @@ class rafem_step_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rafem_trace(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("iters_V", ctypes.c_int64), ("iters_T", ctypes.c_int64),
+                ("solves", ctypes.c_int64), ("refine_V", ctypes.c_int64), ("ms_assemble_V", ctypes.c_double),
+                ("ms_solve_V", ctypes.c_double), ("ms_assemble_T", ctypes.c_double), ("ms_solve_T", ctypes.c_double),
+                ("ms_memcpy_h2d", ctypes.c_double), ("ms_memcpy_d2h", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -92,6 +102,8 @@ def lib() -> ctypes.CDLL:
         "rafem_get_system": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
         "rafem_solve_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rafem_step_stats)]),
         "rafem_spmv": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "rafem_set_tracing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rafem_get_trace": (ctypes.c_int, [vp, ctypes.POINTER(rafem_trace)]),
         "rafem_destroy": (None, [vp]),
         "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -250,6 +262,20 @@ class Context:
         st = rafem_step_stats()
         s = lib().rafem_solve_rhs(self._ctx, which, _dev(b_dev), _dev(x_dev), ctypes.byref(st))
         return _check(s, "rafem_solve_rhs"), st
+
+    def set_tracing(self, on: bool):
+        _check(lib().rafem_set_tracing(self._ctx, 1 if on else 0), "rafem_set_tracing")
+
+    def get_trace(self) -> dict:
+        t = rafem_trace()
+        _check(lib().rafem_get_trace(self._ctx, ctypes.byref(t)), "rafem_get_trace")
+        return t.as_dict()
+
+    def set_state_ptr(self, T_ptr=None, V_ptr=None, on_device=0, step=0):
+        _check(lib().rafem_set_state(self._ctx, T_ptr, V_ptr, int(on_device), int(step)), "rafem_set_state")
+
+    def get_field_ptr(self, which: int, dst_ptr: int, on_device=0):
+        _check(lib().rafem_get_field(self._ctx, which, dst_ptr, int(on_device)), "rafem_get_field")
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
