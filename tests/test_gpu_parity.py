@@ -154,13 +154,14 @@ def test_mixed_precision_matches_oracle(n, steps):
 
 @pytest.mark.parametrize("lanes", [1, 8])
 def test_mixed_matches_fp64_gpu_at_48(lanes):
-    """At 48^3 (117,649 nodes) over 5 steps, mixed and FP64 GPU fields (both to a 1e-11 residual) agree to
-    1e-8 relative."""
+    """At 48^3 (117,649 nodes) over 5 steps, mixed and FP64 GPU fields agree to 1e-8 relative. The field
+    error is bounded by cond(A) x residual and cond(A_V) is ~1e3 at this size (a 1e-11 residual left a 2.4e-8
+    difference), so both run to a 1e-12 FP64 residual."""
     rafem = R()
     m = mg.workload_48()
     out = {}
     for prec in (rafem.RAFEM_PRECISION_FP64, rafem.RAFEM_PRECISION_MIXED):
-        with rafem.Context(m, precision=prec, lanes_per_row=lanes, tol=1e-11) as ctx:
+        with rafem.Context(m, precision=prec, lanes_per_row=lanes, tol=1e-12) as ctx:
             s, st = ctx.run(5)
             assert s == rafem.RAFEM_OK, st.as_dict()
             out[prec] = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
