@@ -184,6 +184,34 @@ int rafem_set_tracing(rafem_ctx* ctx, int enable);
 /* Copy the accumulated region timings to *out. */
 int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
 
+/* Solve A x = b with the library's persistent FP64 Jacobi-PCG for a CSR system the caller already holds on the
+ * device, without allocating any memory. The paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc when they need a solve, such as code running under CUDA stream capture (allocation is not allowed
+ * there), code inside a framework whose caching allocator already owns the device memory, or a latency-bound
+ * loop that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree. It calls no allocation
+ * routine; the caller passes only its inputs and outputs.
+ *
+ * Working memory comes from one fixed device array of RAFEM_NOALLOC_SCRATCH_BYTES (7 MiB) inside the library,
+ * present on every device that loads the library until the process exits. Hence:
+ *   - n_rows must be in [1, RAFEM_NOALLOC_MAX_ROWS]; larger systems are rejected with RAFEM_ERR_BAD_INPUT
+ *     before any device work.
+ *   - Every call on a device shares that array and leaves its contents behind; the entry point clears what must
+ *     start at zero itself. Calls whose GPU work overlaps in time (different streams, or different host threads
+ *     on the same device) race on the array and give wrong results: serialise them.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that device
+ *     current) and keeps it; make that first call before any stream capture begins.
+ * Arguments (device pointers unless stated): row_ptr [n_rows+1] and col [row_ptr[n_rows]] int32 CSR pattern,
+ * every row storing its diagonal entry (else RAFEM_ERR_BAD_INPUT); vals [row_ptr[n_rows]] FP64 values of a
+ * symmetric positive-definite matrix; b [n_rows]; x [n_rows] initial guess on entry, solution on exit. tol:
+ * relative residual ||b - A x|| / ||b||; max_iter: iteration cap. stream: cudaStream_t or NULL (legacy default
+ * stream); the call synchronises it. stats (host, nullable): status, iters_V = iterations, relres_V = final
+ * relative residual, other fields 0. Returns OK, NOT_CONVERGED, BAD_INPUT, BREAKDOWN, NONFINITE, TIMEOUT or CUDA. */
+#define RAFEM_NOALLOC_MAX_ROWS 131072
+#define RAFEM_NOALLOC_SCRATCH_BYTES 7340032
+int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* vals,
+                          const double* b, double* x, double tol, int32_t max_iter, void* stream,
+                          rafem_step_stats* stats);
+
 /* Release every device and host resource of the context. NULL is accepted. */
 void rafem_destroy(rafem_ctx* ctx);
 

@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "rafem_spmv": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_tracing": (ctypes.c_int, [vp, ctypes.c_int]),
         "rafem_get_trace": (ctypes.c_int, [vp, ctypes.POINTER(rafem_trace)]),
+        "rafem_pcg_csr_noalloc": (ctypes.c_int, [ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_double,
+                                                 ctypes.c_int32, vp, ctypes.POINTER(rafem_step_stats)]),
         "rafem_destroy": (None, [vp]),
         "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -279,6 +281,15 @@ class Context:
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+
+def pcg_csr_noalloc(n_rows, row_ptr, col, vals, b, x, tol=1e-10, max_iter=20000, stream=None):
+    """rafem_pcg_csr_noalloc: Jacobi-PCG on a caller-held device CSR system using only the library's fixed
+    scratch array (no allocation). Arguments are device pointers (ints) or tensors; returns (status, stats)."""
+    st = rafem_step_stats()
+    s = lib().rafem_pcg_csr_noalloc(int(n_rows), _dev(row_ptr), _dev(col), _dev(vals), _dev(b), _dev(x), float(tol),
+                                    int(max_iter), ctypes.c_void_p(stream or 0), ctypes.byref(st))
+    return s, st
 
 
 # C names, for callers that prefer the flat API
