@@ -65,6 +65,7 @@ struct rafem_ctx {
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
+    float *fz = nullptr, *fq = nullptr, *fm0 = nullptr, *fm1 = nullptr;
     int32_t *tile_r0 = nullptr, *tile_r1 = nullptr, *tile_inst = nullptr, *inst_t0 = nullptr, *inst_t1 = nullptr;
     int n_tiles = 0, grid = 0, block = 0, lanes = 8;
     InstState* instV = nullptr;
@@ -170,6 +171,7 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.x = x;
     a.r = c->wr; a.u = c->wu; a.w = c->ww; a.p = c->wp; a.s = c->ws; a.dinv = c->wdinv;
     a.r32 = c->fr; a.u32 = c->fu; a.w32 = c->fw; a.p32 = c->fp; a.s32 = c->fs; a.d32 = c->fd; a.dinv32 = c->fdinv;
+    a.z32 = c->fz; a.q32 = c->fq; a.m32a = c->fm0; a.m32b = c->fm1;
     a.n_tiles = c->n_tiles;
     a.tile_r0 = c->tile_r0;
     a.tile_r1 = c->tile_r1;
@@ -462,6 +464,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         CK(dalloc(c, &c->fs, N));
         CK(dalloc(c, &c->fd, N));
         CK(dalloc(c, &c->fdinv, N));
+        CK(dalloc(c, &c->fz, N));
+        CK(dalloc(c, &c->fq, N));
+        CK(dalloc(c, &c->fm0, N));
+        CK(dalloc(c, &c->fm1, N));
     }
     CK(dalloc(c, &c->stats, 1));
     CK(dalloc(c, &c->scratch, 8));

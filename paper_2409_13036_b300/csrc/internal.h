@@ -64,6 +64,8 @@ struct InstState {
     int32_t active;     // 1 while the instance still iterates
     int32_t first;      // 1 before the first iteration of a (inner) CG run
     int32_t outer;      // mixed: state of the refinement state machine
+    int32_t mbuf;       // mixed: which m buffer holds M^-1 w of the current iteration
+    int32_t breakdowns; // mixed: inner solves ended early by an FP32 curvature breakdown
 };
 
 struct GridBarrier {
@@ -89,6 +91,7 @@ struct SolveArgs {
     double *r, *u, *w, *p, *s, *dinv;
     // FP32 workspace (mixed precision)
     float *r32, *u32, *w32, *p32, *s32, *d32, *dinv32;
+    float *z32, *q32, *m32a, *m32b;  // pipelined inner CG: z = A q, q = M^-1 s, m = M^-1 w (double-buffered)
     // work tiles: contiguous row ranges, each belonging to one instance
     int n_tiles;
     const int32_t* tile_r0;

@@ -25,8 +25,12 @@
 // tiles, and instances that have converged are skipped, so many independent systems of different sizes run
 // in one launch (the batching form) with per-instance convergence.
 //
-// Storage: SELL-32 (slices of 32 rows, column-major, one thread per row: coalesced loads, every entry of a row
-// an independent load) or CSR with 4..32 lanes per row.
+// Storage: SELL-32 (slices of 32 rows, column-major, one thread per row) or CSR with 4..32 lanes per row.
+// For SELL-32 the matrix stream is staged into shared memory by the Tensor Memory Accelerator: a producer
+// warp issues bulk copies (cp.async.bulk, completion on mbarriers) of groups of slices into an 8-slot ring
+// while 16 consumer warps compute on earlier groups, so the HBM stream keeps ~200 KB in flight per SM no
+// matter how the consumers' gathers stall; the x gathers and the vector phases read L2, where the Krylov
+// vectors stay because the matrix stream is loaded with an evict-first policy.
 //
 // Every grid barrier waits with a bounded spin (wall-clock limit); on expiry the kernel records
 // RAFEM_ERR_TIMEOUT and returns instead of waiting forever.
@@ -40,8 +44,18 @@ namespace rafem {
 
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kConsumerWarps = 16;
+constexpr int kBlock = (kConsumerWarps + 1) * 32;  // + one producer warp that issues the bulk copies
 constexpr int kWarps = kBlock / 32;
+
+// TMA staging of SELL-32 slices: groups of kGroup consecutive slices are copied into a ring of kSlots
+// shared-memory slots (full/empty mbarrier pair per slot); a group holds up to kGroupCap entries.
+constexpr int kGroup = 4;
+constexpr int kSlots = 8;
+constexpr int kGroupCap = kGroup * 32 * 16;
+constexpr int kSlotBytes = kGroupCap * (int)(sizeof(double) + sizeof(int32_t));
+constexpr int kRingBytes = kSlots * kSlotBytes;
+constexpr int kTeams = kConsumerWarps / kGroup;
 
 enum { Q_GAMMA = 0, Q_RR = 1, Q_DELTA = 2, Q_BB = 3, Q_RR64 = 4, NQ_ALL = 5 };
 enum { ST_OUTER = 1, ST_START = 2, ST_ITER = 3 };
@@ -50,9 +64,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -63,7 +74,57 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // Loads of data written by other blocks during the kernel go through L2 (L1 is not coherent).
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+
+// The matrix is streamed once per SpMV: loaded with an L2 evict-first policy (and no L1 allocation) so that
+// the Krylov vectors, which every phase touches again, stay resident in L2.
+__device__ __forceinline__ unsigned long long policy_stream() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ldm(const double* p, unsigned long long pol) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldm(const float* p, unsigned long long pol) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ldm(const int* p, unsigned long long pol) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// ---- mbarrier + bulk-copy primitives (shared memory addresses are 32-bit shared-window offsets) ----------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Bulk copy global -> shared; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                          unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
 
 // W consecutive values loaded/stored as one vector access (W = 1, 2 for double; 1, 4 for float).
 template <typename T, int W>
@@ -134,34 +195,19 @@ __device__ __forceinline__ void block_sum(T (&v)[NQ], T* sm /* [NQ*32] */) {
     __syncthreads();
 }
 
-// Grid barrier. The last block to arrive runs `last` (whole block) before releasing the others.
-// Returns true when the solve must stop because an error was recorded.
-template <class F>
-__device__ __forceinline__ bool grid_sync(const SolveArgs& a, F&& last) {
-    __shared__ unsigned s_gen;
-    __shared__ int s_last, s_err;
+// Grid barrier on a counter that only grows during a launch: every block adds 1 and waits until the counter
+// reaches its own running target (gridDim.x per barrier). No block has a special role, so the release is one
+// atomic plus one poll latency. Returns true when the solve must stop because an error was recorded.
+__device__ __forceinline__ bool grid_wait(const SolveArgs& a, unsigned& target) {
+    __shared__ int s_err;
     __syncthreads();
+    target += gridDim.x;
     if (threadIdx.x == 0) {
-        unsigned g = ld_acquire_u32(&a.bar->gen);
         __threadfence();
-        unsigned t = atomicAdd(&a.bar->count, 1u);
-        s_gen = g;
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        last();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            a.bar->count = 0;
-            __threadfence();
-            st_release_u32(&a.bar->gen, s_gen + 1);
-        }
-    } else if (threadIdx.x == 0) {
+        atomicAdd(&a.bar->count, 1u);
         const unsigned long long t0 = globaltimer();
         long long spins = 0;
-        while (ld_acquire_u32(&a.bar->gen) == s_gen) {
+        while ((int)(ld_acquire_u32(&a.bar->count) - target) < 0) {
             ++spins;
             if ((spins & 255) == 0 &&
                 ((long long)(globaltimer() - t0) > a.spin_limit_ns || spins > (1LL << 40))) {
@@ -169,98 +215,234 @@ __device__ __forceinline__ bool grid_sync(const SolveArgs& a, F&& last) {
                 break;
             }
         }
+        __threadfence();
+        s_err = *(volatile int*)&a.bar->err;
     }
-    if (threadIdx.x == 0) s_err = *(volatile int*)&a.bar->err;
     __syncthreads();
     return s_err != 0;
 }
 
-struct NoOp {
-    __device__ void operator()() const {}
+// ---- SpMV over the rows of one tile -------------------------------------------------------------------------
+// An emitter provides pre(row) -> P (row-local loads issued before the row's products, so they overlap the
+// gathers) and fin(row, value, P) (consumes y_row = sum_k A_rk x_k).
+
+// Ring of shared-memory slots receiving bulk copies of SELL-32 slice groups. Group J (counted over the whole
+// kernel) lives in slot J % kSlots; full[slot] completes when its bytes have landed, empty[slot] when the
+// kGroup consumer warps of the group are done with it.
+struct Ring {
+    unsigned char* data;        // kSlots x kSlotBytes: values (kGroupCap x sizeof(VT)), then columns
+    unsigned long long* full;   // [kSlots], arrival count 1 + transaction bytes
+    unsigned long long* empty;  // [kSlots], arrival count kGroup
+    int* st_n;                  // [kSlots] slices in the group; negative = group too large, read directly
+    int* abort;                 // shared flag: a wait gave up, stop waiting
+    unsigned base;              // groups issued before the current SpMV (identical in every thread)
 };
 
-// InstState is rewritten by whichever block arrives last at a barrier, so every read of it bypasses L1.
-__device__ __forceinline__ InstState load_state(const InstState* p) {
-    static_assert(sizeof(InstState) % 8 == 0, "InstState layout");
-    InstState s;
-    const long long* src = reinterpret_cast<const long long*>(p);
-    long long* dst = reinterpret_cast<long long*>(&s);
-#pragma unroll
-    for (int k = 0; k < (int)(sizeof(InstState) / 8); ++k) dst[k] = __ldcg(src + k);
-    return s;
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// ---- SpMV over the rows of one tile -------------------------------------------------------------------------
-// emit(row, value) receives y_row = sum_k A_rk x_k for every row of [r0, r1).
-// L == 1: SELL-32, one thread per row (r0 is a multiple of 32). L >= 4: CSR with L lanes per row; emit runs
-// on lane 0 of the row's group.
-template <int L, typename VT, typename AT, typename Emit>
-__device__ __forceinline__ void spmv_tile(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                          const VT* __restrict__ A, const VT* xin, int r0, int r1, Emit&& emit) {
-    if constexpr (L == 1) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
-        for (int s = s0 + warp; s < s1; s += kWarps) {
-            const int base = __ldg(rp + s);
-            const int w = (__ldg(rp + s + 1) - base) >> 5;
-            const VT* av = A + base + lane;
-            const int32_t* cv = ci + base + lane;
-            AT acc = AT(0);
-            int k = 0;
-            for (; k + 8 <= w; k += 8) {
-                VT v[8];
-                int c[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    v[q] = __ldg(av + 32 * (k + q));
-                    c[q] = __ldg(cv + 32 * (k + q));
-                }
-                VT x[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + c[q]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc = fma((AT)v[q], (AT)x[q], acc);
+// Bounded wait; gives up (recording RAFEM_ERR_TIMEOUT and raising the block's abort flag) after the spin
+// limit, and returns at once while the abort flag is up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, const SolveArgs& a,
+                                                  int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    long long spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 63) == 0) {
+            if (*(volatile int*)abort) return false;
+            if ((long long)(globaltimer() - t0) > a.spin_limit_ns || spins > (1LL << 34)) {
+                atomicExch(&a.bar->err, RAFEM_ERR_TIMEOUT);
+                atomicExch(abort, 1);
+                return false;
             }
-            for (; k < w; ++k) acc = fma((AT)__ldg(av + 32 * k), (AT)ldcg(xin + __ldg(cv + 32 * k)), acc);
-            const int row = (s << 5) + lane;
-            if (row < r1) emit(row, acc);
+        }
+    }
+    return true;
+}
+
+template <typename VT, typename AT, class Emit>
+__device__ __forceinline__ void slice_direct(const int32_t* sp, const int32_t* sc, const VT* A, const VT* xin,
+                                             int slice, int r1, const Emit& em, unsigned long long pol) {
+    const int lane = threadIdx.x & 31;
+    const int row = (slice << 5) + lane;
+    const int base = __ldg(sp + slice), w = (__ldg(sp + slice + 1) - base) >> 5;
+    AT acc = AT(0);
+    for (int k = 0; k < w; ++k)
+        acc = fma((AT)ldm(A + base + 32 * k + lane, pol), (AT)ldcg(xin + ldm(sc + base + 32 * k + lane, pol)), acc);
+    if (row < r1) em.fin(row, acc, em.pre(row));
+}
+
+// SELL-32 SpMV over rows [r0, r1) of one tile (r0 a multiple of 32). The producer warp streams slice groups
+// into the ring; consumer warps take one slice each, team by team, and never synchronise the whole block.
+// Returns false when a wait gave up (the error is recorded in the barrier word).
+template <typename VT, typename AT, class Emit>
+__device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int32_t* __restrict__ sp,
+                                          const int32_t* __restrict__ sc, const VT* __restrict__ A, const VT* xin,
+                                          int r0, int r1, const Emit& em) {
+    const unsigned long long pol = policy_stream();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s_begin = r0 >> 5, s_end = (r1 + 31) >> 5;
+    const int ngroups = (s_end - s_begin + kGroup - 1) / kGroup;
+    bool ok = true;
+    if (warp == kConsumerWarps) {
+        if (lane == 0) {
+            for (int j = 0; j < ngroups && ok; ++j) {
+                const unsigned J = g.base + j;
+                const int slot = (int)(J % kSlots);
+                if (J >= (unsigned)kSlots) ok = mbar_wait_bounded(&g.empty[slot], ((J / kSlots) - 1) & 1, a, g.abort);
+                if (!ok) break;
+                const int s = s_begin + j * kGroup;
+                const int ns = min(kGroup, s_end - s);
+                const int base = __ldg(sp + s), endp = __ldg(sp + s + ns);
+                const unsigned nb = (unsigned)(endp - base);
+                if (nb > (unsigned)kGroupCap) {
+                    g.st_n[slot] = -ns;
+                    mbar_arrive(&g.full[slot]);
+                } else {
+                    g.st_n[slot] = ns;
+                    unsigned char* dst = g.data + (size_t)slot * kSlotBytes;
+                    fence_proxy_async();
+                    mbar_arrive_tx(&g.full[slot], nb * (unsigned)(sizeof(VT) + sizeof(int32_t)));
+                    bulk_copy(dst, A + base, nb * (unsigned)sizeof(VT), &g.full[slot], pol);
+                    bulk_copy(dst + (size_t)kGroupCap * sizeof(VT), sc + base, nb * 4u, &g.full[slot], pol);
+                }
+            }
         }
     } else {
-        const int lane = threadIdx.x & (L - 1);
-        const int grp = threadIdx.x / L, ngrp = kBlock / L;
-        const unsigned mask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
-        for (int row = r0 + grp; row < r1; row += ngrp) {
-            const int s = __ldg(rp + row), e = __ldg(rp + row + 1);
-            AT acc = AT(0);
-            for (int k = s + lane; k < e; k += L) acc = fma((AT)__ldg(A + k), (AT)ldcg(xin + __ldg(ci + k)), acc);
+        const int team = warp / kGroup, member = warp % kGroup;
+        for (int j = team; j < ngroups; j += kTeams) {
+            const unsigned J = g.base + j;
+            const int slot = (int)(J % kSlots);
+            if (!mbar_wait_bounded(&g.full[slot], (J / kSlots) & 1, a, g.abort)) {
+                ok = false;
+                break;
+            }
+            const int n = g.st_n[slot];
+            const int slice = s_begin + j * kGroup + member;
+            if (n > 0 && member < n) {
+                const int row = (slice << 5) + lane;
+                const bool valid = row < r1;
+                const int gb = __ldg(sp + s_begin + j * kGroup);
+                const int off = __ldg(sp + slice) - gb;
+                const int w = (__ldg(sp + slice + 1) - __ldg(sp + slice)) >> 5;
+                const unsigned char* base = g.data + (size_t)slot * kSlotBytes;
+                const VT* av = reinterpret_cast<const VT*>(base) + off + lane;
+                const int32_t* cv = reinterpret_cast<const int32_t*>(base + (size_t)kGroupCap * sizeof(VT)) + off + lane;
+                const auto pre = em.pre(valid ? row : r0);
+                AT acc = AT(0);
+                int k = 0;
+                for (; k + 8 <= w; k += 8) {
+                    VT x[8];
 #pragma unroll
-            for (int o = L / 2; o; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, L);
-            if (lane == 0) emit(row, acc);
+                    for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + cv[32 * (k + q)]);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc = fma((AT)av[32 * (k + q)], (AT)x[q], acc);
+                }
+                for (; k < w; ++k) acc = fma((AT)av[32 * k], (AT)ldcg(xin + cv[32 * k]), acc);
+                if (valid) em.fin(row, acc, pre);
+            } else if (n < 0 && member < -n) {
+                slice_direct<VT, AT>(sp, sc, A, xin, slice, r1, em, pol);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&g.empty[slot]);
         }
+    }
+    g.base += (unsigned)ngroups;
+    // On a failed wait the producer lane waits (bounded) for the copies it issued before the kernel exits.
+    if (!ok && warp == kConsumerWarps && lane == 0) {
+        const unsigned J0 = g.base - ngroups;
+        for (int j = 0; j < ngroups; ++j) {
+            const unsigned J = J0 + j;
+            if (!mbar_try_wait(&g.full[J % kSlots], (J / kSlots) & 1)) {
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try_wait(&g.full[J % kSlots], (J / kSlots) & 1) &&
+                       (long long)(globaltimer() - t0) < a.spin_limit_ns) {
+                }
+            }
+        }
+    }
+    return __syncthreads_and(ok);
+}
+
+// CSR SpMV with L lanes per row; pre/fin run on lane 0 of the row's group.
+template <int L, typename VT, typename AT, class Emit>
+__device__ __forceinline__ void csr_tile(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const VT* __restrict__ A, const VT* xin, int r0, int r1, const Emit& em) {
+    const unsigned long long pol = policy_stream();
+    const int lane = threadIdx.x & (L - 1);
+    const int grp = threadIdx.x / L, ngrp = kBlock / L;
+    const unsigned mask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+    for (int row = r0 + grp; row < r1; row += ngrp) {
+        const int s = __ldg(rp + row), e = __ldg(rp + row + 1);
+        AT acc = AT(0);
+        for (int k = s + lane; k < e; k += L) acc = fma((AT)ldm(A + k, pol), (AT)ldcg(xin + ldm(ci + k, pol)), acc);
+#pragma unroll
+        for (int o = L / 2; o; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, L);
+        if (lane == 0) em.fin(row, acc, em.pre(row));
     }
 }
 
+template <int L, typename VT, typename AT, class Emit>
+__device__ __forceinline__ bool spmv_tile(const SolveArgs& a, Ring& g, const VT* A, const VT* xin, int r0, int r1,
+                                          const Emit& em) {
+    if constexpr (L == 1) {
+        return sell_tile<VT, AT>(a, g, a.rp, a.ci, A, xin, r0, r1, em);
+    } else {
+        csr_tile<L, VT, AT>(a.rp, a.ci, A, xin, r0, r1, em);
+        return true;
+    }
+}
+
+// Block-uniform ring set-up at kernel start (SELL-32 kernels).
+#define RAFEM_RING_SETUP(L_)                                                           \
+    extern __shared__ __align__(128) unsigned char ring_data[];                       \
+    __shared__ unsigned long long ring_full[kSlots], ring_empty[kSlots];              \
+    __shared__ int ring_n[kSlots], ring_abort;                                        \
+    Ring ring{ring_data, ring_full, ring_empty, ring_n, &ring_abort, 0u};             \
+    if constexpr ((L_) == 1) {                                                        \
+        if (threadIdx.x == 0) {                                                       \
+            for (int q = 0; q < kSlots; ++q) {                                        \
+                mbar_init(&ring_full[q], 1);                                          \
+                mbar_init(&ring_empty[q], kGroup);                                    \
+            }                                                                         \
+            ring_abort = 0;                                                           \
+            fence_proxy_async();                                                      \
+        }                                                                             \
+        __syncthreads();                                                              \
+    }
+
 // ---- last-arriver reductions ---------------------------------------------------------------------------------
 
-// Sum partial[q][t] over the tiles of every active instance for q in [0, NQ): the whole block when there is
-// one instance, one warp per instance otherwise. Calls fn(i, sums) on one thread per instance.
+// After a barrier every block reduces the per-tile partial sums itself (fixed order: every block gets the same
+// bits) and updates its own shared-memory copy of the per-instance solver state with fn(i, sums, state). Only
+// active instances are visited. Returns the number of instances still active (block-uniform).
+constexpr int kMaxInst = 128;
+
 template <int NQ, class Fn>
-__device__ __forceinline__ void reduce_instances(const SolveArgs& a, Fn&& fn) {
+__device__ __forceinline__ int reduce_shared(const SolveArgs& a, InstState* sst, Fn&& fn) {
     __shared__ double sm[NQ_ALL * 32];
+    __shared__ int s_active;
     if (a.n_inst == 1) {
         double v[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-        for (int t = threadIdx.x; t < a.n_tiles; t += kBlock)
+        if (sst[0].active)
+            for (int t = threadIdx.x; t < a.n_tiles; t += kBlock)
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) v[q] += ldcg(a.partial + (size_t)q * a.n_tiles + t);
+                for (int q = 0; q < NQ; ++q) v[q] += ldcg(a.partial + (size_t)q * a.n_tiles + t);
         block_sum<NQ>(v, sm);
-        if (threadIdx.x == 0) fn(0, v);
-        return;
+        if (threadIdx.x == 0) {
+            if (sst[0].active) fn(0, v, sst[0]);
+            s_active = sst[0].active;
+        }
+        __syncthreads();
+        return s_active;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < a.n_inst; i += kWarps) {
-        if (!ldcg(&a.inst[i].active)) continue;
+        if (!sst[i].active) continue;
         double v[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) v[q] = 0.0;
@@ -272,21 +454,33 @@ __device__ __forceinline__ void reduce_instances(const SolveArgs& a, Fn&& fn) {
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-        if (lane == 0) fn(i, v);
+        if (lane == 0) fn(i, v, sst[i]);
     }
-}
-
-// Count active instances into bar->n_active (after the per-instance updates of this barrier).
-__device__ __forceinline__ void count_active(const SolveArgs& a) {
-    __syncthreads();
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
+    if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
     int c = 0;
-    for (int i = threadIdx.x; i < a.n_inst; i += kBlock) c += ldcg(&a.inst[i].active);
-    if (c) atomicAdd(&cnt, c);
+    for (int i = threadIdx.x; i < a.n_inst; i += kBlock) c += sst[i].active;
+    if (c) atomicAdd(&s_active, c);
     __syncthreads();
-    if (threadIdx.x == 0) a.bar->n_active = cnt;
+    return s_active;
+}
+
+// Shared-memory solver state at kernel start: every instance active, first CG iteration pending.
+__device__ __forceinline__ void init_shared_state(const SolveArgs& a, InstState* sst) {
+    for (int i = threadIdx.x; i < a.n_inst; i += kBlock) {
+        InstState z = {};
+        z.active = 1;
+        z.first = 1;
+        z.outer = ST_OUTER;
+        sst[i] = z;
+    }
+    __syncthreads();
+}
+
+// Block 0 publishes the final per-instance state (statistics) after the last barrier.
+__device__ __forceinline__ void publish_state(const SolveArgs& a, const InstState* sst) {
+    if (blockIdx.x != 0) return;
+    for (int i = threadIdx.x; i < a.n_inst; i += kBlock) a.inst[i] = sst[i];
 }
 
 __device__ __forceinline__ void stop(InstState& st, int status) {
@@ -387,24 +581,62 @@ struct CgRows {
     }
 };
 
+// ---- emitters (row-local work fused into the SpMV) ----------------------------------------------------------
+
+// r = b - A x, dinv = 1 / a_ii, partial bb += b^2
+struct EmInitResidual {
+    const SolveArgs& a;
+    double* v;
+    __device__ __forceinline__ double pre(int row) const { return a.b[row]; }
+    __device__ __forceinline__ void fin(int row, double ax, double bi) const {
+        a.r[row] = bi - ax;
+        a.dinv[row] = 1.0 / a.A[a.diag[row]];
+        v[0] = fma(bi, bi, v[0]);
+    }
+};
+
+// w = A u, partial delta += w u
+template <typename T>
+struct EmAu {
+    T* w;
+    const T* u;
+    T* v;
+    __device__ __forceinline__ T pre(int row) const { return ldcg(u + row); }
+    __device__ __forceinline__ void fin(int row, T wu, T ui) const {
+        w[row] = wu;
+        v[0] = fma(wu, ui, v[0]);
+    }
+};
+
+// partial ||b - A x||^2
+struct EmTrueResidual {
+    const double* b;
+    double* v;
+    __device__ __forceinline__ double pre(int row) const { return b[row]; }
+    __device__ __forceinline__ void fin(int, double ax, double bi) const {
+        const double r = bi - ax;
+        v[0] = fma(r, r, v[0]);
+    }
+};
+
 // ---- FP64 Chronopoulos-Gear Jacobi-PCG ----------------------------------------------------------------------
 
 template <int L>
-__global__ void __launch_bounds__(kBlock) k_cg64(SolveArgs a) {
+__global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
+    RAFEM_RING_SETUP(L)
     __shared__ double sm[NQ_ALL * 32];
+    __shared__ InstState sst[kMaxInst];
+    init_shared_state(a, sst);
     const int nt = a.n_tiles;
     const double tol2 = a.tol * a.tol;
+    unsigned target = 0;
+    bool ok = true;
 
     // init 1: r = b - A x, dinv, bb
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
         double v[1] = {0.0};
-        spmv_tile<L, double, double>(a.rp, a.ci, a.A, a.x, r0, r1, [&](int row, double ax) {
-            const double bi = a.b[row];
-            a.r[row] = bi - ax;
-            a.dinv[row] = 1.0 / a.A[a.diag[row]];
-            v[0] += bi * bi;
-        });
+        ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmInitResidual{a, v}) && ok;
         block_sum<1>(v, sm);
         if (threadIdx.x == 0) a.partial[(size_t)Q_BB * nt + t] = v[0];
     }
@@ -426,39 +658,30 @@ __global__ void __launch_bounds__(kBlock) k_cg64(SolveArgs a) {
             a.partial[(size_t)Q_RR * nt + t] = v[1];
         }
     }
-    if (grid_sync(a, NoOp{})) return;
+    if (grid_wait(a, target) || !ok) return;
     // init 3: w = A u; delta
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
         double v[1] = {0.0};
-        spmv_tile<L, double, double>(a.rp, a.ci, a.A, a.u, r0, r1, [&](int row, double wu) {
-            a.w[row] = wu;
-            v[0] += wu * ldcg(a.u + row);
-        });
+        ok = spmv_tile<L, double, double>(a, ring, a.A, a.u, r0, r1, EmAu<double>{a.w, a.u, v}) && ok;
         block_sum<1>(v, sm);
         if (threadIdx.x == 0) a.partial[(size_t)Q_DELTA * nt + t] = v[0];
     }
-    if (grid_sync(a, [&] {
-            reduce_instances<4>(a, [&](int i, double* s) {
-                InstState st = load_state(a.inst + i);
-                st.bb = s[Q_BB];
-                st.first = 1;
-                cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, false);
-                a.inst[i] = st;
-            });
-            count_active(a);
-        }))
-        return;
+    if (grid_wait(a, target) || !ok) return;
+    int n_active = reduce_shared<4>(a, sst, [&](int, const double* s, InstState& st) {
+        st.bb = s[Q_BB];
+        st.first = 1;
+        cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, false);
+    });
 
-    while (ldcg(&a.bar->n_active) > 0) {
+    while (n_active > 0) {
         // phase A
         for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-            const InstState* st = a.inst + a.tile_inst[t];
-            if (!ldcg(&st->active)) continue;
+            const InstState& st = sst[a.tile_inst[t]];
+            if (!st.active) continue;
             const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
             double v[2] = {0.0, 0.0};
-            CgRows<double> f{a.x,  a.r, a.u, a.w, a.p, a.s, a.dinv, ldcg(&st->alpha), ldcg(&st->beta),
-                             ldcg(&st->first) != 0, v};
+            CgRows<double> f{a.x, a.r, a.u, a.w, a.p, a.s, a.dinv, st.alpha, st.beta, st.first != 0, v};
             for_rows<2>(r0, r1, f);
             block_sum<2>(v, sm);
             if (threadIdx.x == 0) {
@@ -466,44 +689,34 @@ __global__ void __launch_bounds__(kBlock) k_cg64(SolveArgs a) {
                 a.partial[(size_t)Q_RR * nt + t] = v[1];
             }
         }
-        if (grid_sync(a, NoOp{})) return;
+        if (grid_wait(a, target)) return;
         // phase B
         for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-            const InstState* st = a.inst + a.tile_inst[t];
-            if (!ldcg(&st->active)) continue;
+            const InstState& st = sst[a.tile_inst[t]];
+            if (!st.active) continue;
             const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
             double v[1] = {0.0};
-            spmv_tile<L, double, double>(a.rp, a.ci, a.A, a.u, r0, r1, [&](int row, double wu) {
-                a.w[row] = wu;
-                v[0] = fma(wu, ldcg(a.u + row), v[0]);
-            });
+            ok = spmv_tile<L, double, double>(a, ring, a.A, a.u, r0, r1, EmAu<double>{a.w, a.u, v}) && ok;
             block_sum<1>(v, sm);
             if (threadIdx.x == 0) a.partial[(size_t)Q_DELTA * nt + t] = v[0];
         }
-        if (grid_sync(a, [&] {
-                reduce_instances<3>(a, [&](int i, double* s) {
-                    InstState st = load_state(a.inst + i);
-                    st.first = 0;
-                    cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, true);
-                    a.inst[i] = st;
-                });
-                count_active(a);
-            }))
-            return;
+        if (grid_wait(a, target) || !ok) return;
+        n_active = reduce_shared<3>(a, sst, [&](int, const double* s, InstState& st) {
+            st.first = 0;
+            cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, true);
+        });
     }
 
     // final: true residual ||b - A x|| for the reported relative residual
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
         double v[1] = {0.0};
-        spmv_tile<L, double, double>(a.rp, a.ci, a.A, a.x, r0, r1, [&](int row, double ax) {
-            const double ri = a.b[row] - ax;
-            v[0] += ri * ri;
-        });
+        ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmTrueResidual{a.b, v}) && ok;
         block_sum<1>(v, sm);
         if (threadIdx.x == 0) a.partial[(size_t)Q_RR * nt + t] = v[0];
     }
-    grid_sync(a, [&] {
+    if (grid_wait(a, target) || !ok) return;
+    if (blockIdx.x == 0) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int i = warp; i < a.n_inst; i += kWarps) {
             double v = 0.0;
@@ -511,32 +724,43 @@ __global__ void __launch_bounds__(kBlock) k_cg64(SolveArgs a) {
 #pragma unroll
             for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) {
-                InstState st = load_state(a.inst + i);
+                InstState& st = sst[i];
                 const double bb = st.bb > 0.0 ? st.bb : 1.0;
                 st.relres = sqrt(v / bb);
                 if (!isfinite(v) && st.status >= 0) st.status = RAFEM_ERR_NONFINITE;
-                a.inst[i] = st;
             }
         }
-    });
+        __syncthreads();
+        publish_state(a, sst);
+    }
 }
 
 // ---- mixed precision: FP32 Chronopoulos-Gear inner iterations, FP64 residual refinement ---------------------
+// Each instance runs a state machine over rounds of [phase A, barrier, phase B, barrier + reduce]:
+//   OUTER: A: x64 += d32 (after an inner solve)   B: r64 = b - A64 x64 (FP64 SpMV), r32 = (float) r64, d32 = 0,
+//                                                    u32 = M^-1 r32; sums bb, rr64, gamma, rr32
+//   START: A: -                                   B: w32 = A32 u32; sum delta
+//   ITER:  A: FP32 CG vector update                B: w32 = A32 u32; sum delta
+// An inner solve ends at inner_tol, at the predicted outer target, or when its FP32 recurrence loses positive
+// curvature; the FP64 residual then starts the next one.
 
-// Outer step of one row: r64 = b - A64 x; start the inner solve from d = 0 with r32 = r64.
-struct OuterRow {
+struct EmOuter {
     const SolveArgs& a;
     double* v;  // [bb, rr64]
     float* f;   // [gamma, rr32]
-    __device__ __forceinline__ void operator()(int row, double ax) const {
-        const double bi = a.b[row];
-        const double r64 = bi - ax;
+    struct P {
+        double b;
+        float dinv;
+    };
+    __device__ __forceinline__ P pre(int row) const { return P{a.b[row], ldcg(a.dinv32 + row)}; }
+    __device__ __forceinline__ void fin(int row, double ax, const P& p) const {
+        const double r64 = p.b - ax;
         const float r32 = (float)r64;
-        const float u32 = ldcg(a.dinv32 + row) * r32;
+        const float u32 = p.dinv * r32;
         a.r32[row] = r32;
         a.u32[row] = u32;
         a.d32[row] = 0.0f;
-        v[0] = fma(bi, bi, v[0]);
+        v[0] = fma(p.b, p.b, v[0]);
         v[1] = fma(r64, r64, v[1]);
         f[0] = fmaf(r32, u32, f[0]);
         f[1] = fmaf(r32, r32, f[1]);
@@ -565,32 +789,37 @@ struct AddCorrection {
 };
 
 template <int L>
-__global__ void __launch_bounds__(kBlock) k_cg_mixed(SolveArgs a) {
+__global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
+    RAFEM_RING_SETUP(L)
     __shared__ double sm[NQ_ALL * 32];
     __shared__ float smf[NQ_ALL * 32];
+    __shared__ InstState sst[kMaxInst];
+    init_shared_state(a, sst);
     const int nt = a.n_tiles;
     const double tol2 = a.tol * a.tol;
     const double itol2 = a.inner_tol * a.inner_tol;
+    unsigned target = 0;
+    bool ok = true;
 
     // init: dinv32 from the FP32 diagonal (row-local; read again only by the same block after a barrier)
     for (int t = blockIdx.x; t < nt; t += gridDim.x)
         for (int i = a.tile_r0[t] + threadIdx.x; i < a.tile_r1[t]; i += kBlock) a.dinv32[i] = 1.0f / a.A32[a.diag[i]];
     __syncthreads();
     bool first_round = true;
-    for (;;) {
+    int n_active = a.n_inst;
+    while (n_active > 0) {
         // ---------------- phase A ----------------
         if (!first_round) {
             for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-                const InstState* sp = a.inst + a.tile_inst[t];
-                if (!ldcg(&sp->active)) continue;
-                const int state = ldcg(&sp->outer);
+                const InstState& st = sst[a.tile_inst[t]];
+                if (!st.active) continue;
                 const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
-                if (state == ST_OUTER) {
+                if (st.outer == ST_OUTER) {
                     for_rows<4>(r0, r1, AddCorrection{a.x, a.d32});
-                } else if (state == ST_ITER) {
+                } else if (st.outer == ST_ITER) {
                     float v[2] = {0.0f, 0.0f};
-                    CgRows<float> f{a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, a.dinv32, (float)ldcg(&sp->alpha),
-                                    (float)ldcg(&sp->beta), ldcg(&sp->first) != 0, v};
+                    CgRows<float> f{a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, a.dinv32, (float)st.alpha,
+                                    (float)st.beta, st.first != 0, v};
                     for_rows<4>(r0, r1, f);
                     block_sum<2>(v, smf);
                     if (threadIdx.x == 0) {
@@ -599,18 +828,17 @@ __global__ void __launch_bounds__(kBlock) k_cg_mixed(SolveArgs a) {
                     }
                 }
             }
-            if (grid_sync(a, NoOp{})) return;
+            if (grid_wait(a, target)) return;
         }
         // ---------------- phase B ----------------
         for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-            const InstState* sp = a.inst + a.tile_inst[t];
-            if (!ldcg(&sp->active)) continue;
-            const int state = ldcg(&sp->outer);
+            const InstState& st = sst[a.tile_inst[t]];
+            if (!st.active) continue;
             const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
-            if (state == ST_OUTER) {
+            if (st.outer == ST_OUTER) {
                 double v[2] = {0.0, 0.0};
                 float f[2] = {0.0f, 0.0f};
-                spmv_tile<L, double, double>(a.rp, a.ci, a.A, a.x, r0, r1, OuterRow{a, v, f});
+                ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmOuter{a, v, f}) && ok;
                 block_sum<2>(v, sm);
                 block_sum<2>(f, smf);
                 if (threadIdx.x == 0) {
@@ -621,71 +849,67 @@ __global__ void __launch_bounds__(kBlock) k_cg_mixed(SolveArgs a) {
                 }
             } else {
                 float v[1] = {0.0f};
-                spmv_tile<L, float, float>(a.rp, a.ci, a.A32, a.u32, r0, r1, [&](int row, float wu) {
-                    a.w32[row] = wu;
-                    v[0] = fmaf(wu, ldcg(a.u32 + row), v[0]);
-                });
+                ok = spmv_tile<L, float, float>(a, ring, a.A32, a.u32, r0, r1, EmAu<float>{a.w32, a.u32, v}) && ok;
                 block_sum<1>(v, smf);
                 if (threadIdx.x == 0) a.partial[(size_t)Q_DELTA * nt + t] = (double)v[0];
             }
         }
         first_round = false;
-        if (grid_sync(a, [&] {
-                reduce_instances<NQ_ALL>(a, [&](int i, double* s) {
-                    InstState st = load_state(a.inst + i);
-                    if (st.outer == ST_OUTER) {
-                        // FP64 residual of the current x: converged, capped, or start an inner solve
-                        st.bb = s[Q_BB];
-                        const double bb = st.bb > 0.0 ? st.bb : 1.0;
-                        const double rr64 = s[Q_RR64];
-                        st.relres = sqrt(rr64 / bb);
-                        st.rr0 = rr64;  // outer residual at the start of this refinement
-                        if (!isfinite(rr64)) {
-                            stop(st, RAFEM_ERR_NONFINITE);
-                        } else if (rr64 <= tol2 * bb) {
-                            stop(st, RAFEM_OK);
-                        } else if (st.refine >= a.max_refine || st.iters >= a.max_iter) {
-                            stop(st, RAFEM_NOT_CONVERGED);
-                        } else {
-                            st.refine += 1;
-                            st.outer = ST_START;
-                            st.gamma = s[Q_GAMMA];  // inner gamma of the start vector
-                            st.rr = s[Q_RR];        // inner ||r32||^2 at the start
-                            st.first = 1;
-                        }
-                    } else if (st.outer == ST_START) {
-                        st.first = 1;
-                        if (!isfinite(s[Q_DELTA])) {
-                            stop(st, RAFEM_ERR_NONFINITE);
-                        } else if (cg_coefficients(st, st.gamma, s[Q_DELTA])) {
-                            st.outer = ST_ITER;
-                            st.rr_in0 = st.rr;
-                        }
-                    } else {
-                        // ST_ITER: one inner FP32 iteration done
-                        st.iters += 1;
-                        st.first = 0;
-                        const double rr = s[Q_RR];
-                        st.rr = rr;
-                        // stop the inner solve at inner_tol, or once the predicted outer residual
-                        // ||r64|| * ||r32|| / ||r32_0|| is a quarter of the outer tolerance
-                        const double bb = st.bb > 0.0 ? st.bb : 1.0;
-                        const double target = fmax(itol2, 0.0625 * tol2 * bb / fmax(st.rr0, 1e-300));
-                        if (!isfinite(rr) || !isfinite(s[Q_GAMMA]) || !isfinite(s[Q_DELTA])) {
-                            stop(st, RAFEM_ERR_NONFINITE);
-                        } else if (rr <= target * st.rr_in0 || st.iters >= a.max_iter) {
-                            st.outer = ST_OUTER;
-                        } else {
-                            cg_coefficients(st, s[Q_GAMMA], s[Q_DELTA]);
-                        }
-                    }
-                    a.inst[i] = st;
-                });
-                count_active(a);
-            }))
-            return;
-        if (ldcg(&a.bar->n_active) == 0) break;
+        if (grid_wait(a, target) || !ok) return;
+        n_active = reduce_shared<NQ_ALL>(a, sst, [&](int, const double* s, InstState& st) {
+            if (st.outer == ST_OUTER) {
+                // FP64 residual of the current x: converged, capped, or start an inner solve
+                st.bb = s[Q_BB];
+                const double bb = st.bb > 0.0 ? st.bb : 1.0;
+                const double rr64 = s[Q_RR64];
+                st.relres = sqrt(rr64 / bb);
+                st.rr0 = rr64;
+                if (!isfinite(rr64)) {
+                    stop(st, RAFEM_ERR_NONFINITE);
+                } else if (rr64 <= tol2 * bb) {
+                    stop(st, RAFEM_OK);
+                } else if (st.refine >= a.max_refine || st.iters >= a.max_iter) {
+                    stop(st, RAFEM_NOT_CONVERGED);
+                } else {
+                    st.refine += 1;
+                    st.outer = ST_START;
+                    st.gamma = s[Q_GAMMA];
+                    st.rr_in0 = s[Q_RR];
+                    st.first = 1;
+                }
+            } else if (st.outer == ST_START) {
+                st.first = 1;
+                if (!isfinite(s[Q_DELTA])) {
+                    stop(st, RAFEM_ERR_NONFINITE);
+                } else if (cg_coefficients(st, st.gamma, s[Q_DELTA])) {
+                    st.outer = ST_ITER;
+                }
+            } else {
+                // ST_ITER: one inner FP32 iteration done
+                st.iters += 1;
+                st.first = 0;
+                const double rr = s[Q_RR];
+                st.rr = rr;
+                // stop the inner solve at inner_tol, or once the predicted outer residual
+                // ||r64|| * ||r32|| / ||r32_0|| is a quarter of the outer tolerance
+                const double bb = st.bb > 0.0 ? st.bb : 1.0;
+                const double target_rr = fmax(itol2, 0.0625 * tol2 * bb / fmax(st.rr0, 1e-300));
+                if (!isfinite(rr) || !isfinite(s[Q_GAMMA]) || !isfinite(s[Q_DELTA])) {
+                    stop(st, RAFEM_ERR_NONFINITE);
+                } else if (rr <= target_rr * st.rr_in0 || st.iters >= a.max_iter) {
+                    st.outer = ST_OUTER;
+                } else if (!cg_coefficients(st, s[Q_GAMMA], s[Q_DELTA])) {
+                    // FP32 recurrence lost positive curvature: keep the correction found so far and let
+                    // the FP64 residual start the next inner solve
+                    st.status = RAFEM_OK;
+                    st.active = 1;
+                    st.outer = ST_OUTER;
+                    st.breakdowns += 1;
+                }
+            }
+        });
     }
+    publish_state(a, sst);
 }
 
 __global__ void k_reset(InstState* inst, int n_inst, GridBarrier* bar) {
@@ -721,13 +945,18 @@ void* select_kernel(int lanes, int precision) {
 
 }  // namespace
 
+// Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32, none for CSR.
+static int dyn_smem(int lanes) { return lanes == 1 ? kRingBytes : 0; }
+
 int krylov_max_blocks(int lanes, int precision, int* block_threads) {
     void* k = select_kernel(lanes, precision);
     if (!k) return 0;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, 0) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem(lanes)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, dyn_smem(lanes)) != cudaSuccess) return 0;
     if (block_threads) *block_threads = kBlock;
     return per_sm * sms;
 }
@@ -741,7 +970,7 @@ cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn_smem(lanes);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
