@@ -66,6 +66,8 @@ struct InstState {
     int32_t outer;      // mixed: state of the refinement state machine
     int32_t mbuf;       // mixed: which m buffer holds M^-1 w of the current iteration
     int32_t breakdowns; // mixed: inner solves ended early by an FP32 curvature breakdown
+    // mixed: FP32 coefficients of the inner iteration and its stopping threshold on ||r32||^2
+    float alpha32, beta32, gprev32, aprev32, thr32, pad32;
 };
 
 struct GridBarrier {

@@ -173,25 +173,31 @@ __device__ __forceinline__ void for_rows(int r0, int r1, const F& f) {
     for (int i = a1 + threadIdx.x; i < r1; i += kBlock) f.template operator()<1>(i);
 }
 
-// Block-wide sum of NQ values with a fixed reduction tree; result valid in thread 0.
+// Block-wide sum of NQ (<= 2) values with a fixed order; result valid in thread 0. Every thread stages its
+// values in shared memory and one warp per quantity adds them up: the block issues ~kWarps + 5 add
+// instructions per quantity instead of 5 per warp, which matters for FP64 (B300 retires ~2 FP64 FMAs per
+// clock per SM).
+constexpr int kSumMax = 2;
 template <int NQ, typename T>
-__device__ __forceinline__ void block_sum(T (&v)[NQ], T* sm /* [NQ*32] */) {
+__device__ __forceinline__ void block_sum(T (&v)[NQ], T* sm /* [kSumMax * kBlock] */) {
+    static_assert(NQ <= kSumMax, "block_sum handles at most kSumMax values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
+    for (int q = 0; q < NQ; ++q) sm[q * kBlock + threadIdx.x] = v[q];
+    __syncthreads();
+    if (warp < NQ) {
+        T acc = sm[warp * kBlock + lane];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-        if (lane == 0) sm[q * 32 + warp] = v[q];
+        for (int k = 1; k < kWarps; ++k) acc += sm[warp * kBlock + 32 * k + lane];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __syncwarp();
+        if (lane == 0) sm[warp * kBlock] = acc;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            v[q] = lane < kWarps ? sm[q * 32 + lane] : T(0);
-#pragma unroll
-            for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-        }
-    }
+        for (int q = 0; q < NQ; ++q) v[q] = sm[q * kBlock];
     __syncthreads();
 }
 
@@ -418,23 +424,24 @@ __device__ __forceinline__ bool spmv_tile(const SolveArgs& a, Ring& g, const VT*
 // After a barrier every block reduces the per-tile partial sums itself (fixed order: every block gets the same
 // bits) and updates its own shared-memory copy of the per-instance solver state with fn(i, sums, state). Only
 // active instances are visited. Returns the number of instances still active (block-uniform).
-constexpr int kMaxInst = 128;
+constexpr int kMaxInst = 96;
 
 template <int NQ, class Fn>
 __device__ __forceinline__ int reduce_shared(const SolveArgs& a, InstState* sst, Fn&& fn) {
-    __shared__ double sm[NQ_ALL * 32];
+    __shared__ double s_tot[NQ_ALL];
     __shared__ int s_active;
     if (a.n_inst == 1) {
-        double v[NQ];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (sst[0].active && warp < NQ) {
+            double acc = 0.0;
+            for (int t = lane; t < a.n_tiles; t += 32) acc += ldcg(a.partial + (size_t)warp * a.n_tiles + t);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-        if (sst[0].active)
-            for (int t = threadIdx.x; t < a.n_tiles; t += kBlock)
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) v[q] += ldcg(a.partial + (size_t)q * a.n_tiles + t);
-        block_sum<NQ>(v, sm);
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) s_tot[warp] = acc;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            if (sst[0].active) fn(0, v, sst[0]);
+            if (sst[0].active) fn(0, s_tot, sst[0]);
             s_active = sst[0].active;
         }
         __syncthreads();
@@ -514,12 +521,24 @@ __device__ __forceinline__ bool cg_coefficients(InstState& st, double gamma, dou
     return true;
 }
 
+// FP32 coefficients of the inner iteration of the mixed solver (the inner solve runs in FP32 throughout).
+__device__ __forceinline__ bool cg_coefficients32(InstState& st, float gamma, float delta) {
+    const float beta = gamma / st.gprev32;
+    const float den = delta - beta * gamma / st.aprev32;
+    if (!(den > 0.0f) || !(gamma > 0.0f)) return false;
+    const float alpha = gamma / den;
+    st.alpha32 = alpha;
+    st.beta32 = beta;
+    st.gprev32 = gamma;
+    st.aprev32 = alpha;
+    return true;
+}
+
 // FP64 CG update of one instance at a reduce point.
 __device__ __forceinline__ void cg_update(InstState& st, double gamma, double rr, double delta, double tol2,
                                           int max_iter, bool count_iter) {
     const double bb = st.bb > 0.0 ? st.bb : 1.0;
     if (count_iter) st.iters += 1;
-    st.relres = sqrt(rr / bb);
     st.rr = rr;
     if (!isfinite(gamma) || !isfinite(rr) || !isfinite(delta)) return stop(st, RAFEM_ERR_NONFINITE);
     if (rr <= tol2 * bb) return stop(st, RAFEM_OK);
@@ -624,7 +643,7 @@ struct EmTrueResidual {
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
     RAFEM_RING_SETUP(L)
-    __shared__ double sm[NQ_ALL * 32];
+    __shared__ double sm[kSumMax * kBlock];
     __shared__ InstState sst[kMaxInst];
     init_shared_state(a, sst);
     const int nt = a.n_tiles;
@@ -791,8 +810,8 @@ struct AddCorrection {
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
     RAFEM_RING_SETUP(L)
-    __shared__ double sm[NQ_ALL * 32];
-    __shared__ float smf[NQ_ALL * 32];
+    __shared__ double sm[kSumMax * kBlock];
+    float* smf = reinterpret_cast<float*>(sm);
     __shared__ InstState sst[kMaxInst];
     init_shared_state(a, sst);
     const int nt = a.n_tiles;
@@ -818,8 +837,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
                     for_rows<4>(r0, r1, AddCorrection{a.x, a.d32});
                 } else if (st.outer == ST_ITER) {
                     float v[2] = {0.0f, 0.0f};
-                    CgRows<float> f{a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, a.dinv32, (float)st.alpha,
-                                    (float)st.beta, st.first != 0, v};
+                    CgRows<float> f{a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, a.dinv32, st.alpha32, st.beta32,
+                                    st.first != 0, v};
                     for_rows<4>(r0, r1, f);
                     block_sum<2>(v, smf);
                     if (threadIdx.x == 0) {
@@ -879,30 +898,34 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
                 }
             } else if (st.outer == ST_START) {
                 st.first = 1;
+                const float gamma = (float)st.gamma, delta = (float)s[Q_DELTA];
                 if (!isfinite(s[Q_DELTA])) {
                     stop(st, RAFEM_ERR_NONFINITE);
-                } else if (cg_coefficients(st, st.gamma, s[Q_DELTA])) {
+                } else if (!(delta > 0.0f) || !(gamma > 0.0f)) {
+                    stop(st, RAFEM_ERR_BREAKDOWN);
+                } else {
+                    st.alpha32 = gamma / delta;
+                    st.beta32 = 0.0f;
+                    st.gprev32 = gamma;
+                    st.aprev32 = st.alpha32;
+                    // the inner solve stops at inner_tol, or once the predicted outer residual
+                    // ||r64|| * ||r32|| / ||r32_0|| is a quarter of the outer tolerance
+                    const double bb = st.bb > 0.0 ? st.bb : 1.0;
+                    st.thr32 = (float)(fmax(itol2, 0.0625 * tol2 * bb / fmax(st.rr0, 1e-300)) * st.rr_in0);
                     st.outer = ST_ITER;
                 }
             } else {
                 // ST_ITER: one inner FP32 iteration done
                 st.iters += 1;
                 st.first = 0;
-                const double rr = s[Q_RR];
-                st.rr = rr;
-                // stop the inner solve at inner_tol, or once the predicted outer residual
-                // ||r64|| * ||r32|| / ||r32_0|| is a quarter of the outer tolerance
-                const double bb = st.bb > 0.0 ? st.bb : 1.0;
-                const double target_rr = fmax(itol2, 0.0625 * tol2 * bb / fmax(st.rr0, 1e-300));
-                if (!isfinite(rr) || !isfinite(s[Q_GAMMA]) || !isfinite(s[Q_DELTA])) {
+                const float rr = (float)s[Q_RR], gamma = (float)s[Q_GAMMA], delta = (float)s[Q_DELTA];
+                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) {
                     stop(st, RAFEM_ERR_NONFINITE);
-                } else if (rr <= target_rr * st.rr_in0 || st.iters >= a.max_iter) {
+                } else if (rr <= st.thr32 || st.iters >= a.max_iter) {
                     st.outer = ST_OUTER;
-                } else if (!cg_coefficients(st, s[Q_GAMMA], s[Q_DELTA])) {
+                } else if (!cg_coefficients32(st, gamma, delta)) {
                     // FP32 recurrence lost positive curvature: keep the correction found so far and let
                     // the FP64 residual start the next inner solve
-                    st.status = RAFEM_OK;
-                    st.active = 1;
                     st.outer = ST_OUTER;
                     st.breakdowns += 1;
                 }
