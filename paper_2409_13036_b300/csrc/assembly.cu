@@ -80,55 +80,80 @@ __global__ void k_set_identity(int N, const uint8_t* __restrict__ bc, const int3
     if (vals32) vals32[diag[i]] = 1.0f;
 }
 
-// Store or accumulate one element entry according to its slot code; emit the FP32 copy on the last write.
-__device__ __forceinline__ void scatter(double v, int32_t code, double* __restrict__ vals, float* __restrict__ vals32) {
-    int32_t s = code & SLOT_MASK;
-    double val = (code & SLOT_FIRST) ? v : vals[s] + v;
-    vals[s] = val;
-    if (vals32 && (code & SLOT_LAST)) vals32[s] = (float)val;
-}
-
 // MODE 0: potential matrix  sigma(Tbar_e) * G_e
 // MODE 1: thermal matrix    k_e * G_e + c_matrix * vol_e/20 * (1 + delta_ab), constant rhs perf*T_a*vol/4
+// Memory accesses are batched into three dependent rounds (element data; nodal gathers; previous values of the
+// slots to accumulate into) followed by the stores, instead of one read-modify-write chain per entry.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int e1, const double* __restrict__ T,
                                                        const uint8_t* __restrict__ bc, const double* __restrict__ g,
                                                        double coef_a, double coef_b, double* __restrict__ vals,
                                                        float* __restrict__ vals32, double* __restrict__ rhs) {
-    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= e1) return;
-    const int E = el.E;
+    const size_t E = (size_t)el.E;
+    // round 1: element data
     int n[4];
-    bool d[4];
-    for (int a = 0; a < 4; ++a) {
-        n[a] = el.nodes[(size_t)a * E + e];
-        d[a] = bc[n[a]] != 0;
-    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) n[a] = __ldg(el.nodes + a * E + e);
+    int32_t code[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) code[q] = __ldg(el.slots + q * E + e);
     double Ge[10];
-    for (int q = 0; q < 10; ++q) Ge[q] = el.G[(size_t)q * E + e];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) Ge[q] = __ldg(el.G + q * E + e);
+    const double own = MODE == 0 ? __ldg(el.sigma0 + e) : __ldg(el.k + e);
+    const double vol = MODE == 1 ? __ldg(el.vol + e) : 0.0;
+    // round 2: nodal gathers
+    bool d[4];
+    double tn[4] = {0.0, 0.0, 0.0, 0.0}, gn[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        d[a] = bc[n[a]] != 0;
+        gn[a] = g[n[a]];
+        if (MODE == 0) tn[a] = T[n[a]];
+    }
     double scale, mdiag = 0.0, moff = 0.0, rhs_const = 0.0;
     if (MODE == 0) {
-        double Tbar = 0.25 * (T[n[0]] + T[n[1]] + T[n[2]] + T[n[3]]);
-        scale = el.sigma0[e] * (1.0 + coef_a * (Tbar - 37.0));
+        const double Tbar = 0.25 * (tn[0] + tn[1] + tn[2] + tn[3]);
+        scale = own * (1.0 + coef_a * (Tbar - 37.0));
     } else {
-        double v = el.vol[e];
-        scale = el.k[e];
-        moff = coef_a * v * (1.0 / 20.0);
+        scale = own;
+        moff = coef_a * vol * (1.0 / 20.0);
         mdiag = 2.0 * moff;
-        rhs_const = coef_b * v * 0.25;
+        rhs_const = coef_b * vol * 0.25;
     }
+    // round 3: previous values of the slots this element accumulates into
+    double old[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int a = q >> 2, b = q & 3;
+        const bool acc = !d[a] && !d[b] && !(code[q] & SLOT_FIRST);
+        old[q] = acc ? vals[code[q] & SLOT_MASK] : 0.0;
+    }
+    double rold[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rold[a] = d[a] ? 0.0 : rhs[n[a]];
+    // stores
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
         if (d[a]) continue;  // Dirichlet row: identity, fixed at create
         double lift = 0.0;
+#pragma unroll
         for (int b = 0; b < 4; ++b) {
+            const int q = a * 4 + b;
             double v = scale * Ge[gidx(a, b)];
             if (MODE == 1) v += (a == b) ? mdiag : moff;
-            if (d[b])
-                lift += v * g[n[b]];
-            else
-                scatter(v, el.slots[(size_t)(a * 4 + b) * E + e], vals, vals32);
+            if (d[b]) {
+                lift += v * gn[b];
+            } else {
+                const int32_t c = code[q];
+                const double val = old[q] + v;
+                vals[c & SLOT_MASK] = val;
+                if (vals32 && (c & SLOT_LAST)) vals32[c & SLOT_MASK] = (float)val;
+            }
         }
-        if (MODE == 1 || lift != 0.0) rhs[n[a]] += rhs_const - lift;
+        if (MODE == 1 || lift != 0.0) rhs[n[a]] = rold[a] + (rhs_const - lift);
     }
 }
 
@@ -139,31 +164,38 @@ __global__ void __launch_bounds__(kThreads) k_rhs_T(ElemData el, int e0, int e1,
                                                     const double* __restrict__ To, const double* __restrict__ V,
                                                     const uint8_t* __restrict__ bc, double alpha, double c_mass,
                                                     double* __restrict__ b) {
-    int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= e1) return;
-    const int E = el.E;
+    const size_t E = (size_t)el.E;
     int n[4];
-    double v[4], to[4];
-    double ts = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) n[a] = __ldg(el.nodes + a * E + e);
+    double Ge[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) Ge[q] = __ldg(el.G + q * E + e);
+    const double sig0 = __ldg(el.sigma0 + e), vol = __ldg(el.vol + e);
+    double v[4], to[4], ts = 0.0;
+    bool d[4];
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
-        n[a] = el.nodes[(size_t)a * E + e];
         v[a] = V[n[a]];
         to[a] = To[n[a]];
         ts += Ts[n[a]];
+        d[a] = bc[n[a]] != 0;
     }
-    double Ge[10];
-    for (int q = 0; q < 10; ++q) Ge[q] = el.G[(size_t)q * E + e];
-    double sig = el.sigma0[e] * (1.0 + alpha * (0.25 * ts - 37.0));
-    double quad = Ge[0] * v[0] * v[0] + Ge[1] * v[1] * v[1] + Ge[2] * v[2] * v[2] + Ge[3] * v[3] * v[3] +
-                  2.0 * (Ge[4] * v[0] * v[1] + Ge[5] * v[0] * v[2] + Ge[6] * v[0] * v[3] + Ge[7] * v[1] * v[2] +
-                         Ge[8] * v[1] * v[3] + Ge[9] * v[2] * v[3]);
-    double q4 = 0.25 * sig * quad;
-    double mv = c_mass * el.vol[e] * (1.0 / 20.0);
-    double tsum = to[0] + to[1] + to[2] + to[3];
-    for (int a = 0; a < 4; ++a) {
-        if (bc[n[a]]) continue;
-        b[n[a]] += q4 + mv * (tsum + to[a]);
-    }
+    double bold[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) bold[a] = d[a] ? 0.0 : b[n[a]];
+    const double sig = sig0 * (1.0 + alpha * (0.25 * ts - 37.0));
+    const double quad = Ge[0] * v[0] * v[0] + Ge[1] * v[1] * v[1] + Ge[2] * v[2] * v[2] + Ge[3] * v[3] * v[3] +
+                        2.0 * (Ge[4] * v[0] * v[1] + Ge[5] * v[0] * v[2] + Ge[6] * v[0] * v[3] + Ge[7] * v[1] * v[2] +
+                               Ge[8] * v[1] * v[3] + Ge[9] * v[2] * v[3]);
+    const double q4 = 0.25 * sig * quad;
+    const double mv = c_mass * vol * (1.0 / 20.0);
+    const double tsum = to[0] + to[1] + to[2] + to[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        if (!d[a]) b[n[a]] = bold[a] + (q4 + mv * (tsum + to[a]));
 }
 
 __global__ void __launch_bounds__(kThreads) k_spmv64(int N, const int32_t* __restrict__ rp,
