@@ -60,6 +60,10 @@ extern "C" {
 #define RAFEM_SOLVER_PCG      0      /* conjugate gradients (SPD systems)                                      */
 #define RAFEM_SOLVER_BICGSTAB 1      /* BiCGSTAB (general nonsymmetric systems)                                */
 
+#define RAFEM_ASSEMBLY_GATHER 0      /* row-owner assembly: one thread per matrix row sums the element
+                                        contributions of its entries (SELL-32 layout only)                    */
+#define RAFEM_ASSEMBLY_COLOR  1      /* element-owner scatter, one launch per element colour, no atomics     */
+
 /* Mesh and boundary data of one instance. All pointers are host pointers, read only during rafem_create. */
 typedef struct rafem_mesh {
     int32_t n_nodes;                 /* N >= 4                                                                 */
@@ -93,6 +97,7 @@ typedef struct rafem_params {
     int32_t lanes_per_row;           /* matrix layout: 0 or 1 = SELL-32 (one thread per row), 4/8/16/32 = CSR
                                         with that many lanes per row                                          */
     int32_t rows_per_tile;           /* rows per work tile of the persistent solver: 0 = automatic            */
+    int32_t assembly;                /* RAFEM_ASSEMBLY_GATHER (default with SELL-32) or RAFEM_ASSEMBLY_COLOR      */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */

@@ -75,6 +75,11 @@ struct rafem_ctx {
     StatsDev* stats = nullptr;
     double* scratch = nullptr;       // small device scratch (max |dT|)
     int64_t step = 0;
+    // row-owner assembly
+    bool gather = false;
+    GatherData gd;
+    uint8_t* gather_cg = nullptr;
+    long long gather_nc = 0;
     // graph
     cudaGraphExec_t graph = nullptr;
     bool graph_failed = false;
@@ -192,6 +197,14 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
 
 cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
     cudaError_t e;
+    if (c->gather) {
+        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        if (which == RAFEM_SYS_V)
+            return launch_assemble_V_gather(c->gd, c->N, c->rp, c->ci, c->diag, c->el, T_sigma, c->prm.alpha_sigma,
+                                            c->bcV, c->gV, c->valsV, v32, c->bV, c->stream);
+        return launch_rhs_T_gather(c->gd, c->N, c->el, T_sigma, T_old, c->V, c->bcT, c->gT, c->bTc,
+                                   c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->bT, c->stream);
+    }
     if (which == RAFEM_SYS_V) {
         e = launch_init_rhs(c->N, c->bcV, c->gV, nullptr, c->bV, c->stream);
         if (e != cudaSuccess) return e;
@@ -315,6 +328,7 @@ void rafem_default_params(rafem_params* p) {
     p->solver = RAFEM_SOLVER_PCG;
     p->lanes_per_row = 0;
     p->rows_per_tile = 0;
+    p->assembly = RAFEM_ASSEMBLY_GATHER;
 }
 
 const char* rafem_status_string(int s) {
@@ -394,10 +408,14 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     // storage layout of the matrix values: SELL-32 (lanes_per_row 0 or 1) or CSR
     c->lanes = prm->lanes_per_row ? prm->lanes_per_row : 1;
     c->sell = c->lanes == 1;
+    c->gather = c->sell && prm->assembly == RAFEM_ASSEMBLY_GATHER;
     std::vector<int32_t> dev_rp, dev_ci;
+    std::vector<int32_t> g_off, g_cnt, g_elem, i_off, i_cnt, i_elem;
+    std::vector<uint8_t> g_idx;
     if (c->sell) {
         std::vector<int32_t> map;
         build_sell(N, rp, col, dev_rp, dev_ci, map);
+        if (c->gather) build_gather(N, E, rp, col, slots, dev_rp, g_off, g_cnt, g_elem, g_idx);
         c->nnz_store = (int64_t)dev_ci.size();
         if (c->nnz_store >= (int64_t)SLOT_MASK) return RAFEM_ERR_BAD_INPUT;
 #pragma omp parallel for schedule(static)
@@ -420,6 +438,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         sig_s[ep] = m->sigma0[e];
         k_s[ep] = m->k[e];
     }
+    if (c->gather) build_incidence(N, E, nodes_soa, i_off, i_cnt, i_elem);
     // ---- device buffers
     const size_t nnz = (size_t)c->nnz_store;
     const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
@@ -488,6 +507,39 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(cudaMemcpyAsync(c->bcT, m->bc_T, N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->gV, m->g_V, N * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->gT, m->g_T, N * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (c->gather) {
+        int32_t *goff, *gcnt, *celem, *ioff, *icnt, *ielem;
+        uint8_t* cg;
+        double *cval, *ework, *mT;
+        CK(dalloc(c, &goff, g_off.size()));
+        CK(dalloc(c, &gcnt, g_cnt.size()));
+        CK(dalloc(c, &celem, g_elem.size()));
+        CK(dalloc(c, &cg, g_idx.size()));
+        CK(dalloc(c, &cval, g_elem.size()));
+        CK(dalloc(c, &ioff, i_off.size()));
+        CK(dalloc(c, &icnt, i_cnt.size()));
+        CK(dalloc(c, &ielem, i_elem.size()));
+        CK(dalloc(c, &ework, E));
+        CK(dalloc(c, &mT, N));
+        CK(cudaMemcpyAsync(goff, g_off.data(), g_off.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(gcnt, g_cnt.data(), g_cnt.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(celem, g_elem.data(), g_elem.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(cg, g_idx.data(), g_idx.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ioff, i_off.data(), i_off.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(icnt, i_cnt.data(), i_cnt.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ielem, i_elem.data(), i_elem.size() * 4, cudaMemcpyHostToDevice, st));
+        c->gd.goff = goff;
+        c->gd.gcnt = gcnt;
+        c->gd.cval = cval;
+        c->gd.celem = celem;
+        c->gd.ioff = ioff;
+        c->gd.icnt = icnt;
+        c->gd.ielem = ielem;
+        c->gd.ework = ework;
+        c->gd.mT = mT;
+        c->gather_cg = cg;
+        c->gather_nc = (long long)g_elem.size();
+    }
     c->el.E = E;
     c->el.nodes = c->e_nodes;
     c->el.slots = c->e_slots;
@@ -527,6 +579,11 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
     CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
+    if (c->gather) {
+        CK(launch_fill_cval(c->gather_nc, c->gd.celem, c->gather_cg, c->e_sig0, c->e_G, E, const_cast<double*>(c->gd.cval),
+                            st));
+        CK(launch_node_mass(c->gd, N, c->e_vol, prm->rho_c / prm->dt, st));
+    }
     CK(launch_set_dirichlet_identity(N, c->bcV, c->diag, c->valsV, c->valsV32, st));
     CK(launch_set_dirichlet_identity(N, c->bcT, c->diag, c->valsT, c->valsT32, st));
     const double c_matrix = prm->rho_c / prm->dt + prm->perf;
@@ -559,6 +616,7 @@ int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, raf
     if (prm->precision == RAFEM_PRECISION_MIXED && !(prm->inner_tol > 0 && prm->inner_tol < 1)) return RAFEM_ERR_BAD_INPUT;
     if (prm->precond != RAFEM_PRECOND_JACOBI) return RAFEM_ERR_BAD_INPUT;
     if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
+    if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     rafem_ctx* c = new (std::nothrow) rafem_ctx();
     if (!c) return RAFEM_ERR_OOM;
     int s;

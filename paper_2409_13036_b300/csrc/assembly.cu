@@ -198,6 +198,144 @@ __global__ void __launch_bounds__(kThreads) k_rhs_T(ElemData el, int e0, int e1,
         if (!d[a]) b[n[a]] = bold[a] + (q4 + mv * (tsum + to[a]));
 }
 
+// ---- row-owner ("gather") assembly on the SELL-32 layout --------------------------------------------------
+// The potential matrix is K(T) = sum_e f_e (sigma0_e G_e) with f_e = 1 + alpha (Tbar_e - 37). One element pass
+// writes f_e; then one thread per row sums, for each off-diagonal entry, the precomputed products
+// c = sigma0_e G_e[a][b] of the elements sharing that edge, weighted by f_e. Because every element stiffness
+// annihilates constants, K_ii = -sum_{j != i} K_ij, so the diagonal needs no list of its own. The lift is
+// row-local: Dirichlet columns move to the right-hand side and stay zero, Dirichlet rows keep the identity.
+// Every value is written once, in the slice layout, with no colouring.
+
+__global__ void k_fill_cval(long long nc, const int32_t* __restrict__ celem, const uint8_t* __restrict__ cg,
+                            const double* __restrict__ sigma0, const double* __restrict__ G, long long E,
+                            double* __restrict__ cval) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc; i += (long long)gridDim.x * blockDim.x) {
+        const int g = cg[i];
+        const int e = celem[i];
+        cval[i] = g == 255 ? 0.0 : sigma0[e] * G[g * E + e];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sigma_factor(int E, const int32_t* __restrict__ nodes,
+                                                           const double* __restrict__ T, double alpha,
+                                                           double* __restrict__ f) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const size_t Es = (size_t)E;
+    double ts = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ts += T[__ldg(nodes + a * Es + e)];
+    f[e] = 1.0 + alpha * (0.25 * ts - 37.0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_assemble_V_gather(
+    int N, const int32_t* __restrict__ sp, const int32_t* __restrict__ sc, const int32_t* __restrict__ diag,
+    const int32_t* __restrict__ goff, const int32_t* __restrict__ gcnt, const double* __restrict__ cval,
+    const int32_t* __restrict__ celem, const double* __restrict__ f, const uint8_t* __restrict__ bc,
+    const double* __restrict__ g, double* __restrict__ vals, float* __restrict__ vals32, double* __restrict__ b) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    if (bc[row]) {
+        b[row] = g[row];
+        return;
+    }
+    const int s = row >> 5, lane = row & 31;
+    const int base = __ldg(sp + s), w = (__ldg(sp + s + 1) - base) >> 5, q0 = base >> 5;
+    const int dpos = __ldg(diag + row);
+    double dsum = 0.0, lift = 0.0;
+    for (int k = 0; k < w; ++k) {
+        const int pos = base + 32 * k + lane;
+        const int P = __ldg(gcnt + q0 + k);
+        if (P == 0 || pos == dpos) continue;
+        const int off = __ldg(goff + q0 + k) + lane;
+        double acc = 0.0;
+        for (int m = 0; m < P; ++m) acc = fma(__ldg(cval + off + 32 * m), f[__ldg(celem + off + 32 * m)], acc);
+        dsum += acc;
+        const int j = __ldg(sc + pos);
+        if (j != row && bc[j]) {
+            lift = fma(acc, g[j], lift);
+        } else {
+            vals[pos] = acc;
+            if (vals32) vals32[pos] = (float)acc;
+        }
+    }
+    vals[dpos] = -dsum;
+    if (vals32) vals32[dpos] = (float)(-dsum);
+    b[row] = -lift;
+}
+
+// Element pass of the thermal right-hand side: w_e = Q_e vol_e / 4 + (rho_c/dt) vol_e/20 * sum_b T_old,b with
+// Q_e vol_e = sigma_e V_e^T G_e V_e and sigma_e at T_sigma.
+__global__ void __launch_bounds__(kThreads) k_rhsT_elem(ElemData el, const double* __restrict__ Ts,
+                                                        const double* __restrict__ To, const double* __restrict__ V,
+                                                        double alpha, double c_mass, double* __restrict__ w) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= el.E) return;
+    const size_t E = (size_t)el.E;
+    int n[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) n[a] = __ldg(el.nodes + a * E + e);
+    double Ge[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) Ge[q] = __ldg(el.G + q * E + e);
+    const double sig0 = __ldg(el.sigma0 + e), vol = __ldg(el.vol + e);
+    double v[4], tsum = 0.0, ts = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        v[a] = V[n[a]];
+        tsum += To[n[a]];
+        ts += Ts[n[a]];
+    }
+    const double sig = sig0 * (1.0 + alpha * (0.25 * ts - 37.0));
+    const double quad = Ge[0] * v[0] * v[0] + Ge[1] * v[1] * v[1] + Ge[2] * v[2] * v[2] + Ge[3] * v[3] * v[3] +
+                        2.0 * (Ge[4] * v[0] * v[1] + Ge[5] * v[0] * v[2] + Ge[6] * v[0] * v[3] + Ge[7] * v[1] * v[2] +
+                               Ge[8] * v[1] * v[3] + Ge[9] * v[2] * v[3]);
+    w[e] = 0.25 * sig * quad + c_mass * vol * (1.0 / 20.0) * tsum;
+}
+
+// Row pass: b_i = bconst_i + mT_i T_old,i + sum_{e containing i} w_e for free rows, g_i for Dirichlet rows;
+// mT_i = (rho_c/dt) sum_e vol_e / 20 (the T_a term of (M_e T_old)_a).
+__global__ void __launch_bounds__(kThreads) k_rhsT_gather(int N, const int32_t* __restrict__ ioff,
+                                                          const int32_t* __restrict__ icnt,
+                                                          const int32_t* __restrict__ ielem,
+                                                          const double* __restrict__ w, const double* __restrict__ mT,
+                                                          const double* __restrict__ bconst,
+                                                          const double* __restrict__ To, const uint8_t* __restrict__ bc,
+                                                          const double* __restrict__ g, double* __restrict__ b) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    if (bc[row]) {
+        b[row] = g[row];
+        return;
+    }
+    const int s = row >> 5, lane = row & 31;
+    const int off = __ldg(ioff + s) + lane, P = __ldg(icnt + s);
+    double acc = 0.0;
+    for (int m = 0; m < P; ++m) {
+        const int e = __ldg(ielem + off + 32 * m);
+        if (e >= 0) acc += w[e];
+    }
+    b[row] = bconst[row] + mT[row] * To[row] + acc;
+}
+
+// mT_i = c_mass * sum_{e containing i} vol_e / 20 (once at create).
+__global__ void __launch_bounds__(kThreads) k_node_mass(int N, const int32_t* __restrict__ ioff,
+                                                        const int32_t* __restrict__ icnt,
+                                                        const int32_t* __restrict__ ielem,
+                                                        const double* __restrict__ vol, double c_mass,
+                                                        double* __restrict__ mT) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    const int s = row >> 5, lane = row & 31;
+    const int off = __ldg(ioff + s) + lane, P = __ldg(icnt + s);
+    double acc = 0.0;
+    for (int m = 0; m < P; ++m) {
+        const int e = __ldg(ielem + off + 32 * m);
+        if (e >= 0) acc += vol[e];
+    }
+    mT[row] = c_mass * acc * (1.0 / 20.0);
+}
+
 __global__ void __launch_bounds__(kThreads) k_spmv64(int N, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ ci, const double* __restrict__ A,
                                                      const double* __restrict__ x, double* __restrict__ y) {
@@ -288,6 +426,41 @@ cudaError_t launch_spmv64(int N, int sell, const int32_t* rp, const int32_t* ci,
         k_spmv64_sell<<<blocks_for(N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
     else
         k_spmv64<<<blocks_for(8LL * N), kThreads, 0, st>>>(N, rp, ci, A, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_cval(long long nc, const int32_t* celem, const uint8_t* cg, const double* sigma0,
+                             const double* G, int E, double* cval, cudaStream_t st) {
+    if (nc == 0) return cudaSuccess;
+    k_fill_cval<<<148 * 8, kThreads, 0, st>>>(nc, celem, cg, sigma0, G, (long long)E, cval);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_V_gather(const GatherData& gd, int N, const int32_t* sp, const int32_t* sc,
+                                     const int32_t* diag, const ElemData& el, const double* T, double alpha,
+                                     const uint8_t* bc, const double* g, double* vals, float* vals32, double* b,
+                                     cudaStream_t st) {
+    k_sigma_factor<<<blocks_for(el.E), kThreads, 0, st>>>(el.E, el.nodes, T, alpha, gd.ework);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assemble_V_gather<<<blocks_for(N), kThreads, 0, st>>>(N, sp, sc, diag, gd.goff, gd.gcnt, gd.cval, gd.celem,
+                                                            gd.ework, bc, g, vals, vals32, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_T_gather(const GatherData& gd, int N, const ElemData& el, const double* T_sigma,
+                                const double* T_old, const double* V, const uint8_t* bc, const double* g,
+                                const double* bconst, double alpha, double c_mass, double* b, cudaStream_t st) {
+    k_rhsT_elem<<<blocks_for(el.E), kThreads, 0, st>>>(el, T_sigma, T_old, V, alpha, c_mass, gd.ework);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_rhsT_gather<<<blocks_for(N), kThreads, 0, st>>>(N, gd.ioff, gd.icnt, gd.ielem, gd.ework, gd.mT, bconst, T_old,
+                                                      bc, g, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_mass(const GatherData& gd, int N, const double* vol, double c_mass, cudaStream_t st) {
+    k_node_mass<<<blocks_for(N), kThreads, 0, st>>>(N, gd.ioff, gd.icnt, gd.ielem, vol, c_mass, gd.mT);
     return cudaGetLastError();
 }
 

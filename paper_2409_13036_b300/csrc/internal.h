@@ -22,7 +22,30 @@ struct ElemData {
     const double* k = nullptr;        // [E]
 };
 
+// Row-owner assembly data (SELL-32 layout; see setup.h build_gather / build_incidence).
+struct GatherData {
+    const int32_t* goff = nullptr;   // [nnz_store/32] start of each (slice, column) contribution group
+    const int32_t* gcnt = nullptr;   // [nnz_store/32] contributions per lane in the group
+    const double* cval = nullptr;    // sigma0_e G_e[a][b] per contribution (0 for padding)
+    const int32_t* celem = nullptr;  // element (sorted order) per contribution
+    const int32_t* ioff = nullptr;   // [N/32] node -> element incidence, per slice
+    const int32_t* icnt = nullptr;
+    const int32_t* ielem = nullptr;  // -1 = padding
+    double* ework = nullptr;         // [E] per-element factor (f_e, then w_e)
+    double* mT = nullptr;            // [N] (rho_c/dt) sum vol/20
+};
+
 // Launchers (assembly.cu). Every launcher only enqueues work on `st`.
+cudaError_t launch_fill_cval(long long nc, const int32_t* celem, const uint8_t* cg, const double* sigma0,
+                             const double* G, int E, double* cval, cudaStream_t st);
+cudaError_t launch_assemble_V_gather(const GatherData& gd, int N, const int32_t* sp, const int32_t* sc,
+                                     const int32_t* diag, const ElemData& el, const double* T, double alpha,
+                                     const uint8_t* bc, const double* g, double* vals, float* vals32, double* b,
+                                     cudaStream_t st);
+cudaError_t launch_rhs_T_gather(const GatherData& gd, int N, const ElemData& el, const double* T_sigma,
+                                const double* T_old, const double* V, const uint8_t* bc, const double* g,
+                                const double* bconst, double alpha, double c_mass, double* b, cudaStream_t st);
+cudaError_t launch_node_mass(const GatherData& gd, int N, const double* vol, double c_mass, cudaStream_t st);
 cudaError_t launch_geometry(const ElemData& el, const double* xyz, double* G, double* vol, cudaStream_t st);
 cudaError_t launch_init_rhs(int N, const uint8_t* bc, const double* g, const double* base, double* b,
                             cudaStream_t st);

@@ -185,4 +185,85 @@ void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<in
     }
 }
 
+namespace {
+int local_gidx(int a, int b) {
+    if (a == b) return a;
+    const int lo = std::min(a, b), hi = std::max(a, b);
+    return lo == 0 ? 3 + hi : (lo == 1 ? 5 + hi : 9);
+}
+}  // namespace
+
+void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                  const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
+                  std::vector<int32_t>& gather_off, std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem,
+                  std::vector<uint8_t>& cgidx) {
+    const int64_t nnz = (int64_t)col.size();
+    std::vector<int32_t> cnt(nnz, 0);
+    for (int64_t ep = 0; ep < E; ++ep)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                if (a != b) cnt[csr_slots[(int64_t)(a * 4 + b) * E + ep] & SLOT_MASK]++;
+    const int S = (int)slice_ptr.size() - 1;
+    const int64_t Q = (int64_t)slice_ptr[S] / SELL_C;
+    gather_off.assign(Q, 0);
+    gather_cnt.assign(Q, 0);
+    std::vector<int64_t> pos(nnz, -1);  // list start of each CSR entry (lane included)
+    int64_t total = 0;
+    for (int s = 0; s < S; ++s) {
+        const int w = (slice_ptr[s + 1] - slice_ptr[s]) / SELL_C;
+        const int64_t q0 = slice_ptr[s] / SELL_C;
+        for (int k = 0; k < w; ++k) {
+            int P = 0;
+            for (int l = 0; l < SELL_C; ++l) {
+                const int r = s * SELL_C + l;
+                if (r < N && k < row_ptr[r + 1] - row_ptr[r]) P = std::max(P, cnt[row_ptr[r] + k]);
+            }
+            gather_off[q0 + k] = (int32_t)total;
+            gather_cnt[q0 + k] = P;
+            for (int l = 0; l < SELL_C; ++l) {
+                const int r = s * SELL_C + l;
+                if (r < N && k < row_ptr[r + 1] - row_ptr[r]) pos[row_ptr[r] + k] = total + l;
+            }
+            total += (int64_t)P * SELL_C;
+        }
+    }
+    celem.assign(total, 0);
+    cgidx.assign(total, 255);
+    std::vector<int32_t> fill(nnz, 0);
+    for (int64_t ep = 0; ep < E; ++ep)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                if (a == b) continue;
+                const int32_t p = csr_slots[(int64_t)(a * 4 + b) * E + ep] & SLOT_MASK;
+                const int64_t at = pos[p] + (int64_t)SELL_C * fill[p]++;
+                celem[at] = (int32_t)ep;
+                cgidx[at] = (uint8_t)local_gidx(a, b);
+            }
+}
+
+void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::vector<int32_t>& inc_off,
+                     std::vector<int32_t>& inc_cnt, std::vector<int32_t>& inc_elem) {
+    std::vector<int32_t> cnt(N, 0);
+    for (int64_t q = 0; q < 4LL * E; ++q) cnt[nodes_soa[q]]++;
+    const int S = (N + SELL_C - 1) / SELL_C;
+    inc_off.assign(S, 0);
+    inc_cnt.assign(S, 0);
+    int64_t total = 0;
+    for (int s = 0; s < S; ++s) {
+        int P = 0;
+        for (int r = s * SELL_C; r < std::min(N, (s + 1) * SELL_C); ++r) P = std::max(P, cnt[r]);
+        inc_off[s] = (int32_t)total;
+        inc_cnt[s] = P;
+        total += (int64_t)P * SELL_C;
+    }
+    inc_elem.assign(total, -1);
+    std::vector<int32_t> fill(N, 0);
+    for (int a = 0; a < 4; ++a)
+        for (int64_t ep = 0; ep < E; ++ep) {
+            const int r = nodes_soa[(int64_t)a * E + ep];
+            const int s = r / SELL_C, l = r % SELL_C;
+            inc_elem[inc_off[s] + (int64_t)SELL_C * fill[r]++ + l] = (int32_t)ep;
+        }
+}
+
 }  // namespace rafem

@@ -30,4 +30,20 @@ constexpr int SELL_C = 32;
 void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                 std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col, std::vector<int32_t>& csr_to_sell);
 
+// Row-owner ("gather") assembly of the pure stiffness matrix sigma(T)-weighted sum_e sigma0_e G_e on the SELL-32
+// layout. For every off-diagonal SELL entry the elements sharing that edge are listed with the index of
+// G_e[a][b]; entries of one (slice, column) group are stored column-major with the group padded to the longest
+// list among its 32 rows: contribution m of lane l of group q lives at gather_off[q] + 32 m + l, and the group has
+// gather_cnt[q] contributions (0 for groups holding only diagonal or padding entries). Padding contributions
+// carry gidx = 255. csr_slots are the element->CSR slot codes (flags allowed) over the sorted element order.
+void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                  const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
+                  std::vector<int32_t>& gather_off, std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem,
+                  std::vector<uint8_t>& cgidx);
+
+// Node -> element incidence (sorted element order) in the SELL-32 slice layout: element m of row 32 s + l at
+// inc_off[s] + 32 m + l for m < inc_cnt[s]; -1 marks padding.
+void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::vector<int32_t>& inc_off,
+                     std::vector<int32_t>& inc_cnt, std::vector<int32_t>& inc_elem);
+
 }  // namespace rafem

@@ -36,6 +36,8 @@ RAFEM_PRECISION_FP64 = 0
 RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
+RAFEM_ASSEMBLY_GATHER = 0
+RAFEM_ASSEMBLY_COLOR = 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -53,7 +55,7 @@ class rafem_params(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("corrector_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("n_corrector", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):

@@ -38,12 +38,14 @@ def _nonuniform_T(mesh, seed=0):
     return np.where(mesh.bc_T.astype(bool), mesh.g_T, T)
 
 
-def test_assembled_potential_system_matches_oracle():
-    """A_V(sigma(T)) and its lifted rhs, slot by slot, on a jittered lognormal mesh with a non-uniform T."""
+@pytest.mark.parametrize("assembly", [0, 1])
+def test_assembled_potential_system_matches_oracle(assembly):
+    """A_V(sigma(T)) and its lifted rhs, slot by slot, on a jittered lognormal mesh with a non-uniform T, for the
+    row-owner gather (0) and the colour-partitioned scatter (1)."""
     rafem = R()
     m = mg.cube_mesh(10, jitter=0.1, seed=21, sigma0="lognormal")
     T = _nonuniform_T(m)
-    with rafem.Context(m) as ctx:
+    with rafem.Context(m, assembly=assembly) as ctx:
         ctx.set_state(T=T)
         ctx.assemble(rafem.RAFEM_SYS_V)
         rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_V)
@@ -55,15 +57,16 @@ def test_assembled_potential_system_matches_oracle():
     np.testing.assert_allclose(rhs, b, rtol=1e-13, atol=1e-14 * np.abs(b).max())
 
 
-def test_assembled_thermal_system_matches_oracle():
-    """Constant thermal matrix and the rhs (Joule from V, mass term from T), slot by slot."""
+@pytest.mark.parametrize("assembly", [0, 1])
+def test_assembled_thermal_system_matches_oracle(assembly):
+    """Constant thermal matrix and the rhs (Joule from V, mass term from T), slot by slot, both assemblies."""
     rafem = R()
     m = mg.cube_mesh(9, jitter=0.1, seed=22, sigma0="lognormal")
     T = _nonuniform_T(m, 1)
     rng = np.random.default_rng(2)
     V = np.where(m.bc_V.astype(bool), m.g_V, 20.0 * rng.random(m.n_nodes))
     model = O.Model(m)
-    with rafem.Context(m) as ctx:
+    with rafem.Context(m, assembly=assembly) as ctx:
         ctx.set_state(T=T, V=V)
         ctx.assemble(rafem.RAFEM_SYS_T)
         rp, col, vals, rhs = ctx.get_system(rafem.RAFEM_SYS_T)
@@ -91,14 +94,14 @@ def test_potential_solve_matches_direct_solve():
     assert O.rel_err(V, V_ref) <= 1e-10
 
 
-@pytest.mark.parametrize("n,steps", [(12, 6), (20, 4)])
-def test_time_steps_match_oracle(n, steps):
+@pytest.mark.parametrize("n,steps,assembly", [(12, 6, 0), (20, 4, 0), (12, 3, 1)])
+def test_time_steps_match_oracle(n, steps, assembly):
     """Full backward-Euler steps (assemble V, solve, Joule + thermal rhs, solve) vs the oracle's LU path:
     relative error <= 1e-9 per field per step (solver tolerance 1e-12), temperature PSNR >= 80 dB."""
     rafem = R()
     m = mg.cube_mesh(n, jitter=0.1, seed=24 + n, sigma0="lognormal")
     Ts, Vs = [], []
-    with rafem.Context(m, tol=1e-12, dt=5.0) as ctx:
+    with rafem.Context(m, tol=1e-12, dt=5.0, assembly=assembly) as ctx:
         for _ in range(steps):
             s, st = ctx.solve_step()
             assert s == rafem.RAFEM_OK, st.as_dict()
