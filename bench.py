@@ -314,8 +314,9 @@ def main():
     ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ctx.set_state_ptr(hT.data_ptr(), hV.data_ptr(), 0, 0)
+    n_done = head["last"]["step"] + 3  # timed steps + the traced ones
+    for k in range(args.e2e_steps):
+        ctx.set_state_ptr(hT.data_ptr(), hV.data_ptr(), 0, n_done + k)
         ctx.run(1)
         ctx.get_field_ptr(rafem.RAFEM_SYS_T, hT.data_ptr(), 0)
         ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)

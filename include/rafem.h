@@ -98,6 +98,8 @@ typedef struct rafem_params {
                                         with that many lanes per row                                          */
     int32_t rows_per_tile;           /* rows per work tile of the persistent solver: 0 = automatic            */
     int32_t assembly;                /* RAFEM_ASSEMBLY_GATHER (default with SELL-32) or RAFEM_ASSEMBLY_COLOR      */
+    int32_t predictor;               /* 1 = start each solve from the linear extrapolation 2 x^n - x^{n-1}
+                                        (the predictor of the predictor-corrector loop), 0 = from x^n (1)    */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
@@ -150,7 +152,9 @@ int rafem_run(rafem_ctx* ctx, int32_t n_steps, rafem_step_stats* last);
 int rafem_get_field(rafem_ctx* ctx, int which, double* dst, int dst_on_device);
 
 /* Replace the state: T and V (either may be NULL to keep it) of N doubles each; on_device as above. The step
- * counter is set to `step`. Dirichlet values are not re-imposed (the caller passes consistent fields). */
+ * counter is set to `step`. Dirichlet values are not re-imposed (the caller passes consistent fields). When
+ * `step` differs from the context's current step count the predictor's history is cleared (the next step starts
+ * its solves from the given fields); when it is equal the run continues and the history is kept. */
 int rafem_set_state(rafem_ctx* ctx, const double* T, const double* V, int on_device, int64_t step);
 
 /* Sizes of the fixed CSR pattern: n_rows (= N), nnz, number of element colours. Any out pointer may be NULL. */

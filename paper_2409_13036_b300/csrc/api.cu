@@ -25,7 +25,7 @@ namespace {
 struct StatsDev {
     rafem_step_stats cur;   // statistics of the step in progress / last step
     int32_t worst;          // worst status over all steps since the last reset
-    int32_t pad;
+    int32_t hist;           // steps completed since the last state reset (predictor history)
 };
 
 }  // namespace
@@ -62,6 +62,7 @@ struct rafem_ctx {
     double *bV = nullptr, *bT = nullptr, *bTc = nullptr;
     // fields
     double *V = nullptr, *T = nullptr, *T_old = nullptr, *T_prev = nullptr;
+    double *V_hist = nullptr, *T_hist = nullptr;   // predictor history (x^{n-1})
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -135,6 +136,7 @@ __global__ void k_record(const InstState* inst, const GridBarrier* bar, int whic
         c.status = status > c.status ? status : c.status;
     if (final_step) {
         c.step += 1;
+        s->hist += 1;
         if (c.status < 0 || s->worst < 0)
             s->worst = c.status < s->worst ? c.status : s->worst;
         else
@@ -155,6 +157,18 @@ __global__ void k_set_step(StatsDev* s, long long step) {
     s->cur.step = step;
     s->worst = 0;
 }
+
+// Predictor: x <- 2 x^n - x^{n-1} on free rows once a previous step exists; the history keeps x^n.
+__global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ xprev, const uint8_t* __restrict__ bc,
+                          const StatsDev* s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double t = x[i];
+    if (s->hist >= 1 && !bc[i]) x[i] = 2.0 * t - xprev[i];
+    xprev[i] = t;
+}
+
+__global__ void k_reset_hist(StatsDev* s) { s->hist = 0; }
 
 __global__ void k_init_fields(int N, double T0, const uint8_t* bcT, const double* gT, const uint8_t* bcV,
                               const double* gV, double* T, double* V) {
@@ -231,16 +245,28 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
     return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
 }
 
+// Initial guess of a step's solve (the predictor of Sec. II-A's predictor-corrector loop).
+cudaError_t enqueue_predict(rafem_ctx* c, int which) {
+    if (!c->prm.predictor) return cudaSuccess;
+    if (which == RAFEM_SYS_V)
+        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->V, c->V_hist, c->bcV, c->stats);
+    else
+        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->T, c->T_hist, c->bcT, c->stats);
+    return cudaGetLastError();
+}
+
 // One lagged pass: sigma and the mass term both use the current T.
 cudaError_t enqueue_step(rafem_ctx* c) {
     cudaError_t e;
     k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_predict(c, RAFEM_SYS_T)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
     k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 1);
     return cudaGetLastError();
@@ -259,6 +285,7 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     cudaEventRecord(c->ev[1], c->stream);
     nvtxRangePop();
     nvtxRangePushA("Solve");
+    if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[2], c->stream);
     nvtxRangePop();
@@ -269,6 +296,7 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     cudaEventRecord(c->ev[4], c->stream);
     nvtxRangePop();
     nvtxRangePushA("Solve");
+    if ((e = enqueue_predict(c, RAFEM_SYS_T)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[5], c->stream);
     nvtxRangePop();
@@ -329,6 +357,7 @@ void rafem_default_params(rafem_params* p) {
     p->lanes_per_row = 0;
     p->rows_per_tile = 0;
     p->assembly = RAFEM_ASSEMBLY_GATHER;
+    p->predictor = 1;
 }
 
 const char* rafem_status_string(int s) {
@@ -469,6 +498,8 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->T, N));
     CK(dalloc(c, &c->T_old, N));
     CK(dalloc(c, &c->T_prev, N));
+    CK(dalloc(c, &c->V_hist, N));
+    CK(dalloc(c, &c->T_hist, N));
     CK(dalloc(c, &c->wr, N));
     CK(dalloc(c, &c->wu, N));
     CK(dalloc(c, &c->ww, N));
@@ -788,9 +819,14 @@ int rafem_set_state(rafem_ctx* c, const double* T, const double* V, int on_devic
         c->trace.ms_memcpy_h2d += ms;
         nvtxRangePop();
     }
+    const bool continuing = step == c->step;
     c->step = step;
     k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)step);
     CK(cudaGetLastError());
+    if (!continuing) {
+        k_reset_hist<<<1, 1, 0, c->stream>>>(c->stats);
+        CK(cudaGetLastError());
+    }
     CK(cudaStreamSynchronize(c->stream));
     return RAFEM_OK;
 }

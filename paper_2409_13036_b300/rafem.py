@@ -55,7 +55,8 @@ class rafem_params(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("corrector_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("n_corrector", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
+                ("predictor", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):

@@ -192,6 +192,29 @@ def test_graph_run_equals_step_loop_bitwise():
         np.testing.assert_array_equal(V, out[0][1])
 
 
+def test_state_roundtrip_continues_run_bitwise():
+    """Reading the fields back and setting them again at the same step index continues the run exactly (the
+    predictor history is kept); setting them at another index restarts the history but stays within the
+    solver tolerance of the uninterrupted run."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=34)
+    with rafem.Context(m, tol=1e-12) as a:
+        a.run(4)
+        T4, V4 = a.get_field(rafem.RAFEM_SYS_T), a.get_field(rafem.RAFEM_SYS_V)
+    with rafem.Context(m, tol=1e-12) as b:
+        b.run(2)
+        T2, V2 = b.get_field(rafem.RAFEM_SYS_T), b.get_field(rafem.RAFEM_SYS_V)
+        b.set_state(T=T2, V=V2, step=2)
+        b.run(2)
+        np.testing.assert_array_equal(b.get_field(rafem.RAFEM_SYS_T), T4)
+        np.testing.assert_array_equal(b.get_field(rafem.RAFEM_SYS_V), V4)
+    with rafem.Context(m, tol=1e-12) as c:
+        c.set_state(T=T2, V=V2, step=2)
+        c.run(2)
+        assert O.rel_err(c.get_field(rafem.RAFEM_SYS_V), V4) <= 1e-9
+        assert O.rel_err(c.get_field(rafem.RAFEM_SYS_T), T4) <= 1e-9
+
+
 def test_iteration_cap_reports_not_converged():
     rafem = R()
     m = mg.cube_mesh(10, jitter=0.1, seed=33)
