@@ -44,6 +44,7 @@ struct rafem_ctx {
     // pattern: CSR (rp, ci) or SELL-32 (rp = slice pointers, ci = slice columns) on the device; the CSR
     // pattern and the CSR -> storage map stay on the host for inspection
     int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
+    int16_t* ci16 = nullptr;  // SELL column deltas (when they fit 16 bits)
     bool sell = true;
     int64_t nnz_store = 0;
     std::vector<int32_t> h_rp, h_col, h_map;
@@ -183,6 +184,7 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.N = c->N;
     a.rp = c->rp;
     a.ci = c->ci;
+    a.ci16 = c->ci16;
     a.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
     a.A32 = which == RAFEM_SYS_V ? c->valsV32 : c->valsT32;
     a.diag = c->diag;
@@ -437,14 +439,33 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     // storage layout of the matrix values: SELL-32 (lanes_per_row 0 or 1) or CSR
     c->lanes = prm->lanes_per_row ? prm->lanes_per_row : 1;
     c->sell = c->lanes == 1;
+    const bool want16 = prm->lanes_per_row == 0;
     c->gather = c->sell && prm->assembly == RAFEM_ASSEMBLY_GATHER;
     std::vector<int32_t> dev_rp, dev_ci;
+    std::vector<int16_t> d16;
     std::vector<int32_t> g_off, g_cnt, g_elem, i_off, i_cnt, i_elem;
     std::vector<uint8_t> g_idx;
     if (c->sell) {
         std::vector<int32_t> map;
         build_sell(N, rp, col, dev_rp, dev_ci, map);
         if (c->gather) build_gather(N, E, rp, col, slots, dev_rp, g_off, g_cnt, g_elem, g_idx);
+        if (want16) {
+            bool fits = true;
+            d16.resize(dev_ci.size());
+            const int S = (int)dev_rp.size() - 1;
+            for (int sl = 0; sl < S && fits; ++sl)
+                for (int32_t q = dev_rp[sl]; q < dev_rp[sl + 1]; ++q) {
+                    const int r = sl * SELL_C + (int)((q - dev_rp[sl]) % SELL_C);
+                    const int d = dev_ci[q] - r;
+                    if (d < -32768 || d > 32767) {
+                        fits = false;
+                        break;
+                    }
+                    d16[q] = (int16_t)d;
+                }
+            if (fits) c->lanes = 2;
+            else d16.clear();
+        }
         c->nnz_store = (int64_t)dev_ci.size();
         if (c->nnz_store >= (int64_t)SLOT_MASK) return RAFEM_ERR_BAD_INPUT;
 #pragma omp parallel for schedule(static)
@@ -528,6 +549,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->rp, dev_rp.data(), dev_rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->ci, dev_ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (!d16.empty()) {
+        CK(dalloc(c, &c->ci16, d16.size()));
+        CK(cudaMemcpyAsync(c->ci16, d16.data(), d16.size() * sizeof(int16_t), cudaMemcpyHostToDevice, st));
+    }
     CK(cudaMemcpyAsync(c->diag, diag.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_nodes, nodes_soa.data(), nodes_soa.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));

@@ -106,6 +106,7 @@ struct SolveArgs {
     int N;
     const int32_t* rp;
     const int32_t* ci;
+    const int16_t* ci16;  // SELL-32 column deltas col - row (kernel code 2), when every delta fits 16 bits
     const double* A;
     const float* A32;
     const int32_t* diag;  // slot of the diagonal entry of each row
@@ -134,7 +135,8 @@ struct SolveArgs {
     long long spin_limit_ns;
 };
 
-// lanes = 1 selects the SELL-32 thread-per-row kernels, 4/8/16/32 the CSR sub-warp kernels.
+// Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 4/8/16/32 = CSR with that
+// many lanes per row.
 int krylov_max_blocks(int lanes, int precision, int* block_threads);
 cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st);
 

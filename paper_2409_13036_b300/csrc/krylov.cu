@@ -48,14 +48,16 @@ constexpr int kConsumerWarps = 16;
 constexpr int kBlock = (kConsumerWarps + 1) * 32;  // + one producer warp that issues the bulk copies
 constexpr int kWarps = kBlock / 32;
 
-// TMA staging of SELL-32 slices: groups of kGroup consecutive slices are copied into a ring of kSlots
-// shared-memory slots (full/empty mbarrier pair per slot); a group holds up to kGroupCap entries.
-constexpr int kGroup = 4;
+// TMA staging of SELL-32 slices: groups of consecutive slices are copied into a ring of kSlots shared-memory
+// slots of kSlotBytes (full/empty mbarrier pair per slot). A group holds as many slices as fit a slot at 16
+// entries per row (8 for FP32 values with 16-bit columns, 4 for FP64 values), so every slot carries ~24 KB.
 constexpr int kSlots = 8;
-constexpr int kGroupCap = kGroup * 32 * 16;
-constexpr int kSlotBytes = kGroupCap * (int)(sizeof(double) + sizeof(int32_t));
+constexpr int kSlotBytes = 24576;
 constexpr int kRingBytes = kSlots * kSlotBytes;
-constexpr int kTeams = kConsumerWarps / kGroup;
+template <typename VT, typename CT>
+constexpr int group_slices() {
+    return kSlotBytes / (32 * 16 * (int)(sizeof(VT) + sizeof(CT))) >= 8 ? 8 : 4;
+}
 
 enum { Q_GAMMA = 0, Q_RR = 1, Q_DELTA = 2, Q_BB = 3, Q_RR64 = 4, NQ_ALL = 5 };
 enum { ST_OUTER = 1, ST_START = 2, ST_ITER = 3 };
@@ -169,8 +171,10 @@ __device__ __forceinline__ void for_rows(int r0, int r1, const F& f) {
     if (a0 > r1) a0 = r1;
     const int a1 = a0 + (r1 - a0) / W * W;
     for (int i = r0 + threadIdx.x; i < a0; i += kBlock) f.template operator()<1>(i);
-    for (int i = a0 + W * threadIdx.x; i < a1; i += W * kBlock) f.template operator()<W>(i);
-    for (int i = a1 + threadIdx.x; i < r1; i += kBlock) f.template operator()<1>(i);
+    int i = a0 + W * threadIdx.x;
+    for (; i + W * kBlock < a1; i += 2 * W * kBlock) f.template pair<W>(i, i + W * kBlock);
+    if (i < a1) f.template operator()<W>(i);
+    for (int j = a1 + threadIdx.x; j < r1; j += kBlock) f.template operator()<1>(j);
 }
 
 // Block-wide sum of NQ (<= 2) values with a fixed order; result valid in thread 0. Every thread stages its
@@ -234,11 +238,11 @@ __device__ __forceinline__ bool grid_wait(const SolveArgs& a, unsigned& target) 
 
 // Ring of shared-memory slots receiving bulk copies of SELL-32 slice groups. Group J (counted over the whole
 // kernel) lives in slot J % kSlots; full[slot] completes when its bytes have landed, empty[slot] when the
-// kGroup consumer warps of the group are done with it.
+// consumer warps of the group are done with it.
 struct Ring {
-    unsigned char* data;        // kSlots x kSlotBytes: values (kGroupCap x sizeof(VT)), then columns
+    unsigned char* data;        // kSlots x kSlotBytes: values, then columns
     unsigned long long* full;   // [kSlots], arrival count 1 + transaction bytes
-    unsigned long long* empty;  // [kSlots], arrival count kGroup
+    unsigned long long* empty;  // [kSlots], arrival count kConsumerWarps
     int* st_n;                  // [kSlots] slices in the group; negative = group too large, read directly
     int* abort;                 // shared flag: a wait gave up, stop waiting
     unsigned base;              // groups issued before the current SpMV (identical in every thread)
@@ -246,6 +250,9 @@ struct Ring {
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_n(unsigned long long* bar, unsigned n) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
 }
 
 // Bounded wait; gives up (recording RAFEM_ERR_TIMEOUT and raising the block's abort flag) after the spin
@@ -268,29 +275,39 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     return true;
 }
 
-template <typename VT, typename AT, class Emit>
-__device__ __forceinline__ void slice_direct(const int32_t* sp, const int32_t* sc, const VT* A, const VT* xin,
-                                             int slice, int r1, const Emit& em, unsigned long long pol) {
+// Column of a SELL entry: stored directly (int32) or as a 16-bit delta to the row.
+__device__ __forceinline__ int col_of(int32_t c, int) { return c; }
+__device__ __forceinline__ int col_of(int16_t d, int row) { return row + (int)d; }
+__device__ __forceinline__ int32_t ldm_col(const int32_t* p, unsigned long long pol) { return ldm(p, pol); }
+__device__ __forceinline__ int16_t ldm_col(const int16_t* p, unsigned long long) { return __ldg(p); }
+
+template <typename VT, typename AT, typename CT, class Emit>
+__device__ __forceinline__ void slice_direct(const int32_t* sp, const CT* sc, const VT* A, const VT* xin, int slice,
+                                             int r1, const Emit& em, unsigned long long pol) {
     const int lane = threadIdx.x & 31;
     const int row = (slice << 5) + lane;
     const int base = __ldg(sp + slice), w = (__ldg(sp + slice + 1) - base) >> 5;
     AT acc = AT(0);
     for (int k = 0; k < w; ++k)
-        acc = fma((AT)ldm(A + base + 32 * k + lane, pol), (AT)ldcg(xin + ldm(sc + base + 32 * k + lane, pol)), acc);
+        acc = fma((AT)ldm(A + base + 32 * k + lane, pol),
+                  (AT)ldcg(xin + col_of(ldm_col(sc + base + 32 * k + lane, pol), row)), acc);
     if (row < r1) em.fin(row, acc, em.pre(row));
 }
 
 // SELL-32 SpMV over rows [r0, r1) of one tile (r0 a multiple of 32). The producer warp streams slice groups
 // into the ring; consumer warps take one slice each, team by team, and never synchronise the whole block.
 // Returns false when a wait gave up (the error is recorded in the barrier word).
-template <typename VT, typename AT, class Emit>
+template <typename VT, typename AT, typename CT, class Emit>
 __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int32_t* __restrict__ sp,
-                                          const int32_t* __restrict__ sc, const VT* __restrict__ A, const VT* xin,
+                                          const CT* __restrict__ sc, const VT* __restrict__ A, const VT* xin,
                                           int r0, int r1, const Emit& em) {
     const unsigned long long pol = policy_stream();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s_begin = r0 >> 5, s_end = (r1 + 31) >> 5;
-    const int ngroups = (s_end - s_begin + kGroup - 1) / kGroup;
+    constexpr int kG = group_slices<VT, CT>();
+    constexpr int kCap = kG * 32 * 16;                 // entries per slot
+    constexpr int kTeamsG = kConsumerWarps / kG;
+    const int ngroups = (s_end - s_begin + kG - 1) / kG;
     bool ok = true;
     if (warp == kConsumerWarps) {
         if (lane == 0) {
@@ -299,26 +316,26 @@ __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int
                 const int slot = (int)(J % kSlots);
                 if (J >= (unsigned)kSlots) ok = mbar_wait_bounded(&g.empty[slot], ((J / kSlots) - 1) & 1, a, g.abort);
                 if (!ok) break;
-                const int s = s_begin + j * kGroup;
-                const int ns = min(kGroup, s_end - s);
+                const int s = s_begin + j * kG;
+                const int ns = min(kG, s_end - s);
                 const int base = __ldg(sp + s), endp = __ldg(sp + s + ns);
                 const unsigned nb = (unsigned)(endp - base);
-                if (nb > (unsigned)kGroupCap) {
+                if (nb > (unsigned)kCap) {
                     g.st_n[slot] = -ns;
                     mbar_arrive(&g.full[slot]);
                 } else {
                     g.st_n[slot] = ns;
                     unsigned char* dst = g.data + (size_t)slot * kSlotBytes;
                     fence_proxy_async();
-                    mbar_arrive_tx(&g.full[slot], nb * (unsigned)(sizeof(VT) + sizeof(int32_t)));
+                    mbar_arrive_tx(&g.full[slot], nb * (unsigned)(sizeof(VT) + sizeof(CT)));
                     bulk_copy(dst, A + base, nb * (unsigned)sizeof(VT), &g.full[slot], pol);
-                    bulk_copy(dst + (size_t)kGroupCap * sizeof(VT), sc + base, nb * 4u, &g.full[slot], pol);
+                    bulk_copy(dst + (size_t)kCap * sizeof(VT), sc + base, nb * (unsigned)sizeof(CT), &g.full[slot], pol);
                 }
             }
         }
     } else {
-        const int team = warp / kGroup, member = warp % kGroup;
-        for (int j = team; j < ngroups; j += kTeams) {
+        const int team = warp / kG, member = warp % kG;
+        for (int j = team; j < ngroups; j += kTeamsG) {
             const unsigned J = g.base + j;
             const int slot = (int)(J % kSlots);
             if (!mbar_wait_bounded(&g.full[slot], (J / kSlots) & 1, a, g.abort)) {
@@ -326,33 +343,45 @@ __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int
                 break;
             }
             const int n = g.st_n[slot];
-            const int slice = s_begin + j * kGroup + member;
+            const int slice = s_begin + j * kG + member;
             if (n > 0 && member < n) {
                 const int row = (slice << 5) + lane;
                 const bool valid = row < r1;
-                const int gb = __ldg(sp + s_begin + j * kGroup);
+                const int gb = __ldg(sp + s_begin + j * kG);
                 const int off = __ldg(sp + slice) - gb;
                 const int w = (__ldg(sp + slice + 1) - __ldg(sp + slice)) >> 5;
                 const unsigned char* base = g.data + (size_t)slot * kSlotBytes;
                 const VT* av = reinterpret_cast<const VT*>(base) + off + lane;
-                const int32_t* cv = reinterpret_cast<const int32_t*>(base + (size_t)kGroupCap * sizeof(VT)) + off + lane;
+                const CT* cv = reinterpret_cast<const CT*>(base + (size_t)kCap * sizeof(VT)) + off + lane;
                 const auto pre = em.pre(valid ? row : r0);
                 AT acc = AT(0);
-                int k = 0;
-                for (; k + 8 <= w; k += 8) {
-                    VT x[8];
+                if (w <= 16) {
+                    // one batch of gathers for the whole row: a single L2 round trip per slice
+                    VT x[16];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + cv[32 * (k + q)]);
+                    for (int q = 0; q < 16; ++q) x[q] = q < w ? ldcg(xin + col_of(cv[32 * q], row)) : VT(0);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) acc = fma((AT)av[32 * (k + q)], (AT)x[q], acc);
+                    for (int q = 0; q < 16; ++q)
+                        if (q < w) acc = fma((AT)av[32 * q], (AT)x[q], acc);
+                } else {
+                    int k = 0;
+                    for (; k + 8 <= w; k += 8) {
+                        VT x[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + col_of(cv[32 * (k + q)], row));
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc = fma((AT)av[32 * (k + q)], (AT)x[q], acc);
+                    }
+                    for (; k < w; ++k) acc = fma((AT)av[32 * k], (AT)ldcg(xin + col_of(cv[32 * k], row)), acc);
                 }
-                for (; k < w; ++k) acc = fma((AT)av[32 * k], (AT)ldcg(xin + cv[32 * k]), acc);
                 if (valid) em.fin(row, acc, pre);
             } else if (n < 0 && member < -n) {
-                slice_direct<VT, AT>(sp, sc, A, xin, slice, r1, em, pol);
+                slice_direct<VT, AT, CT>(sp, sc, A, xin, slice, r1, em, pol);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&g.empty[slot]);
+            // the empty barrier expects kConsumerWarps arrivals per use: each of the kG warps of the team adds
+            // kConsumerWarps / kG
+            if (lane == 0) mbar_arrive_n(&g.empty[slot], kConsumerWarps / kG);
         }
     }
     g.base += (unsigned)ngroups;
@@ -394,7 +423,9 @@ template <int L, typename VT, typename AT, class Emit>
 __device__ __forceinline__ bool spmv_tile(const SolveArgs& a, Ring& g, const VT* A, const VT* xin, int r0, int r1,
                                           const Emit& em) {
     if constexpr (L == 1) {
-        return sell_tile<VT, AT>(a, g, a.rp, a.ci, A, xin, r0, r1, em);
+        return sell_tile<VT, AT, int32_t>(a, g, a.rp, a.ci, A, xin, r0, r1, em);
+    } else if constexpr (L == 2) {
+        return sell_tile<VT, AT, int16_t>(a, g, a.rp, a.ci16, A, xin, r0, r1, em);
     } else {
         csr_tile<L, VT, AT>(a.rp, a.ci, A, xin, r0, r1, em);
         return true;
@@ -407,11 +438,11 @@ __device__ __forceinline__ bool spmv_tile(const SolveArgs& a, Ring& g, const VT*
     __shared__ unsigned long long ring_full[kSlots], ring_empty[kSlots];              \
     __shared__ int ring_n[kSlots], ring_abort;                                        \
     Ring ring{ring_data, ring_full, ring_empty, ring_n, &ring_abort, 0u};             \
-    if constexpr ((L_) == 1) {                                                        \
+    if constexpr ((L_) <= 2) {                                                        \
         if (threadIdx.x == 0) {                                                       \
             for (int q = 0; q < kSlots; ++q) {                                        \
                 mbar_init(&ring_full[q], 1);                                          \
-                mbar_init(&ring_empty[q], kGroup);                                    \
+                mbar_init(&ring_empty[q], kConsumerWarps);                            \
             }                                                                         \
             ring_abort = 0;                                                           \
             fence_proxy_async();                                                      \
@@ -582,6 +613,57 @@ __device__ __forceinline__ void cg_vector_rows(int i, T alpha, T beta, bool firs
     stv<T, W>(u + i, ui);
 }
 
+template <typename T, int W>
+struct CgLoad {
+    Vec<T, W> u, w, x, r, d, p, s;
+};
+template <typename T, int W>
+__device__ __forceinline__ CgLoad<T, W> cg_load(int i, bool first, const T* x, const T* r, const T* u, const T* w,
+                                               const T* p, const T* s, const T* dinv) {
+    CgLoad<T, W> L;
+    L.u = ldv<T, W>(u + i);
+    L.w = ldv<T, W>(w + i);
+    L.x = ldv<T, W>(x + i);
+    L.r = ldv<T, W>(r + i);
+    L.d = ldv<T, W>(dinv + i);
+    if (!first) {
+        L.p = ldv<T, W>(p + i);
+        L.s = ldv<T, W>(s + i);
+    }
+    return L;
+}
+template <typename T, int W>
+__device__ __forceinline__ void cg_apply(int i, CgLoad<T, W>& L, T alpha, T beta, bool first, T* x, T* r, T* u, T* p,
+                                         T* s, T& g, T& rr) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const T pi = first ? L.u.v[k] : fma(beta, L.p.v[k], L.u.v[k]);
+        const T si = first ? L.w.v[k] : fma(beta, L.s.v[k], L.w.v[k]);
+        L.p.v[k] = pi;
+        L.s.v[k] = si;
+        L.x.v[k] = fma(alpha, pi, L.x.v[k]);
+        const T ri = fma(-alpha, si, L.r.v[k]);
+        L.r.v[k] = ri;
+        const T ui = L.d.v[k] * ri;
+        L.u.v[k] = ui;
+        g = fma(ri, ui, g);
+        rr = fma(ri, ri, rr);
+    }
+    stv<T, W>(p + i, L.p);
+    stv<T, W>(s + i, L.s);
+    stv<T, W>(x + i, L.x);
+    stv<T, W>(r + i, L.r);
+    stv<T, W>(u + i, L.u);
+}
+template <typename T, int W>
+__device__ __forceinline__ void cg_vector_rows2(int i, int j, T alpha, T beta, bool first, T* x, T* r, T* u,
+                                                const T* w, T* p, T* s, const T* dinv, T& g, T& rr) {
+    CgLoad<T, W> A = cg_load<T, W>(i, first, x, r, u, w, p, s, dinv);
+    CgLoad<T, W> B = cg_load<T, W>(j, first, x, r, u, w, p, s, dinv);
+    cg_apply<T, W>(i, A, alpha, beta, first, x, r, u, p, s, g, rr);
+    cg_apply<T, W>(j, B, alpha, beta, first, x, r, u, p, s, g, rr);
+}
+
 template <typename T>
 struct CgRows {
     T* x;
@@ -597,6 +679,11 @@ struct CgRows {
     template <int W>
     __device__ __forceinline__ void operator()(int i) const {
         cg_vector_rows<T, W>(i, alpha, beta, first, x, r, u, w, p, s, dinv, v[0], v[1]);
+    }
+    // two independent groups: every load of both is issued before the first store
+    template <int W>
+    __device__ __forceinline__ void pair(int i, int j) const {
+        cg_vector_rows2<T, W>(i, j, alpha, beta, first, x, r, u, w, p, s, dinv, v[0], v[1]);
     }
 };
 
@@ -791,6 +878,11 @@ struct AddCorrection {
     double* x;
     const float* d;
     template <int W>
+    __device__ __forceinline__ void pair(int i, int j) const {
+        operator()<W>(i);
+        operator()<W>(j);
+    }
+    template <int W>
     __device__ __forceinline__ void operator()(int i) const {
         if constexpr (W == 1) {
             x[i] = ldcg(x + i) + (double)ldcg(d + i);
@@ -811,7 +903,6 @@ template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
     RAFEM_RING_SETUP(L)
     __shared__ double sm[kSumMax * kBlock];
-    float* smf = reinterpret_cast<float*>(sm);
     __shared__ InstState sst[kMaxInst];
     init_shared_state(a, sst);
     const int nt = a.n_tiles;
@@ -840,10 +931,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
                     CgRows<float> f{a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, a.dinv32, st.alpha32, st.beta32,
                                     st.first != 0, v};
                     for_rows<4>(r0, r1, f);
-                    block_sum<2>(v, smf);
+                    double vd[2] = {(double)v[0], (double)v[1]};
+                    block_sum<2>(vd, sm);
                     if (threadIdx.x == 0) {
-                        a.partial[(size_t)Q_GAMMA * nt + t] = (double)v[0];
-                        a.partial[(size_t)Q_RR * nt + t] = (double)v[1];
+                        a.partial[(size_t)Q_GAMMA * nt + t] = vd[0];
+                        a.partial[(size_t)Q_RR * nt + t] = vd[1];
                     }
                 }
             }
@@ -859,18 +951,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
                 float f[2] = {0.0f, 0.0f};
                 ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmOuter{a, v, f}) && ok;
                 block_sum<2>(v, sm);
-                block_sum<2>(f, smf);
+                double fd[2] = {(double)f[0], (double)f[1]};
+                block_sum<2>(fd, sm);
                 if (threadIdx.x == 0) {
                     a.partial[(size_t)Q_BB * nt + t] = v[0];
                     a.partial[(size_t)Q_RR64 * nt + t] = v[1];
-                    a.partial[(size_t)Q_GAMMA * nt + t] = (double)f[0];
-                    a.partial[(size_t)Q_RR * nt + t] = (double)f[1];
+                    a.partial[(size_t)Q_GAMMA * nt + t] = fd[0];
+                    a.partial[(size_t)Q_RR * nt + t] = fd[1];
                 }
             } else {
                 float v[1] = {0.0f};
                 ok = spmv_tile<L, float, float>(a, ring, a.A32, a.u32, r0, r1, EmAu<float>{a.w32, a.u32, v}) && ok;
-                block_sum<1>(v, smf);
-                if (threadIdx.x == 0) a.partial[(size_t)Q_DELTA * nt + t] = (double)v[0];
+                double vd[1] = {(double)v[0]};
+                block_sum<1>(vd, sm);
+                if (threadIdx.x == 0) a.partial[(size_t)Q_DELTA * nt + t] = vd[0];
             }
         }
         first_round = false;
@@ -958,6 +1052,7 @@ void* kernel_ptr(int precision) {
 void* select_kernel(int lanes, int precision) {
     switch (lanes) {
         case 1: return kernel_ptr<1>(precision);
+        case 2: return kernel_ptr<2>(precision);
         case 4: return kernel_ptr<4>(precision);
         case 8: return kernel_ptr<8>(precision);
         case 16: return kernel_ptr<16>(precision);
@@ -969,7 +1064,7 @@ void* select_kernel(int lanes, int precision) {
 }  // namespace
 
 // Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32, none for CSR.
-static int dyn_smem(int lanes) { return lanes == 1 ? kRingBytes : 0; }
+static int dyn_smem(int lanes) { return lanes <= 2 ? kRingBytes : 0; }
 
 int krylov_max_blocks(int lanes, int precision, int* block_threads) {
     void* k = select_kernel(lanes, precision);
