@@ -143,23 +143,23 @@ def _ncu_traffic(kernel: str):
     return e
 
 
-def alg_bytes_cg64(N: int, nnz: int, iters: float) -> float:
-    """Algorithmic HBM bytes of one FP64 Chronopoulos-Gear Jacobi-PCG solve launch.
-    Per iteration: SpMV w = A u streams 12 B per nonzero (value + column index), reads u once and writes w
-    (16N); the vector phase reads u, w, p, s, x, r, dinv and writes p, s, x, r, u (96N). Start-up (r = b - Ax,
-    u, w = Au) and the final true-residual SpMV add two more iterations' worth."""
-    per_iter = 12 * nnz + 16 * N + 96 * N
+def alg_bytes_cg64(N: int, nnz: int, iters: float, col_bytes: int) -> float:
+    """Algorithmic HBM bytes of one FP64 Chronopoulos-Gear Jacobi-PCG solve launch (stored format).
+    Per iteration: SpMV w = A u streams (8 + col_bytes) B per nonzero (value + column index) and reads u once and
+    writes w (16N); the vector phase reads u, w, p, s, x, r, dinv and writes p, s, x, r, u (96N). Start-up
+    (r = b - Ax, u, w = Au) and the final true-residual SpMV add two more iterations' worth."""
+    per_iter = (8 + col_bytes) * nnz + 16 * N + 96 * N
     return (iters + 2) * per_iter
 
 
-def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float) -> float:
-    """Algorithmic HBM bytes of one mixed-precision solve launch.
-    Inner FP32 iteration: SpMV 8 B per nonzero + 8N (u read, w written); vector phase 12 x 4N.
-    Each FP64 refinement: x64 += d32 (8N read + 4N read + 8N write) and the FP64 residual SpMV
-    (12 B per nonzero + 8N x + 8N b) writing r32, u32, d32 (12N) and reading dinv32 (4N); plus one start SpMV
-    in FP32 (8 B per nonzero + 8N)."""
-    inner = 8 * nnz + 8 * N + 48 * N
-    outer = (20 * N) + (12 * nnz + 16 * N + 16 * N) + (8 * nnz + 8 * N)
+def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_bytes: int) -> float:
+    """Algorithmic HBM bytes of one mixed-precision solve launch (stored format).
+    Inner FP32 iteration: SpMV (4 + col_bytes) B per nonzero + 8N (u read, w written); vector phase 12 x 4N.
+    Each FP64 refinement: x64 += d32 (8N + 4N read, 8N written), the FP64 residual SpMV ((8 + col_bytes) B per
+    nonzero + 8N x + 8N b) writing r32, u32, d32 (12N) and reading dinv32 (4N), and the FP32 start SpMV
+    ((4 + col_bytes) B per nonzero + 8N)."""
+    inner = (4 + col_bytes) * nnz + 8 * N + 48 * N
+    outer = (20 * N) + ((8 + col_bytes) * nnz + 16 * N + 16 * N) + ((4 + col_bytes) * nnz + 8 * N)
     return iters * inner + (refinements + 1) * outer
 
 
@@ -189,6 +189,7 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks):
     stream = torch.cuda.Stream()
     ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision)
     N, nnz, n_colors = ctx.pattern_info()
+    layout = ctx.layout_info()
     s, st = ctx.run(args.warmup)
     if s < 0:
         raise RuntimeError(f"warm-up failed: {rafem.status_string(s)}")
@@ -218,7 +219,8 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks):
     tr = ctx.get_trace()
     ctx.set_tracing(False)
     return {"ctx": ctx, "ms": ms, "status": rafem.status_string(s), "last": st.as_dict(), "trace": tr,
-            "fields": fields, "N": N, "nnz": nnz, "n_colors": n_colors, "clocks": clk.summary() if clk else None}
+            "fields": fields, "N": N, "nnz": nnz, "n_colors": n_colors, "layout": layout,
+            "clocks": clk.summary() if clk else None}
 
 
 def roofline(res, mixed, peaks, peak_kind):
@@ -227,14 +229,16 @@ def roofline(res, mixed, peaks, peak_kind):
     steps = tr["steps"]
     solve_ms = tr["ms_solve_V"] / steps
     iters = tr["iters_V"] / steps
+    cb = res["layout"]["column_bytes"]
+    code = res["layout"]["kernel_code"]
     if mixed:
         ref = tr["refine_V"] / steps
-        alg = alg_bytes_mixed(N, nnz, iters, ref)
-        kern = "k_cg_mixed<1>"
+        alg = alg_bytes_mixed(N, nnz, iters, ref, cb)
+        kern = f"k_cg_mixed<{code}>"
     else:
         ref = 0.0
-        alg = alg_bytes_cg64(N, nnz, iters)
-        kern = "k_cg64<1>"
+        alg = alg_bytes_cg64(N, nnz, iters, cb)
+        kern = f"k_cg64<{code}>"
     achieved = alg / (solve_ms * 1e-3) / 1e9
     nc = _ncu_traffic(kern)
     traffic = None
@@ -343,7 +347,7 @@ def main():
                        "precision": head_name, "layout": "SELL-32",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (two 373 MB FP64 matrices + element data per step)"},
-            "status": head_sum["status"],
+            "status": head_sum["status"], "last_step": head_sum["last_step"],
             "iters_V_per_step": head_sum["iters_V_per_step"], "iters_T_per_step": head_sum["iters_T_per_step"],
             "refine_V_per_step": head_sum["refine_V_per_step"],
             "regions_ms_per_step": head_sum["regions_ms_per_step"],

@@ -160,6 +160,12 @@ int rafem_set_state(rafem_ctx* ctx, const double* T, const double* V, int on_dev
 /* Sizes of the fixed CSR pattern: n_rows (= N), nnz, number of element colours. Any out pointer may be NULL. */
 int rafem_pattern_info(rafem_ctx* ctx, int32_t* n_rows, int64_t* nnz, int32_t* n_colors);
 
+/* Storage actually used by the solver: kernel_code 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit
+ * column deltas, 4/8/16/32 = CSR with that many lanes per row; nnz_stored includes slice padding; column_bytes is
+ * 2 or 4; assembly is the RAFEM_ASSEMBLY_* in use. Any out pointer may be NULL. */
+int rafem_layout_info(rafem_ctx* ctx, int32_t* kernel_code, int64_t* nnz_stored, int32_t* column_bytes,
+                      int32_t* assembly);
+
 /* Copy the current lifted system `which` to host buffers: row_ptr [N+1], col [nnz], vals [nnz], rhs [N].
  * Any pointer may be NULL to skip it. For inspection and tests. */
 int rafem_get_system(rafem_ctx* ctx, int which, int32_t* row_ptr, int32_t* col, double* vals, double* rhs);

@@ -864,6 +864,16 @@ int rafem_pattern_info(rafem_ctx* c, int32_t* n_rows, int64_t* nnz, int32_t* n_c
     return RAFEM_OK;
 }
 
+int rafem_layout_info(rafem_ctx* c, int32_t* kernel_code, int64_t* nnz_stored, int32_t* column_bytes,
+                      int32_t* assembly) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (kernel_code) *kernel_code = c->lanes;
+    if (nnz_stored) *nnz_stored = c->nnz_store;
+    if (column_bytes) *column_bytes = c->ci16 ? 2 : 4;
+    if (assembly) *assembly = c->gather ? RAFEM_ASSEMBLY_GATHER : RAFEM_ASSEMBLY_COLOR;
+    return RAFEM_OK;
+}
+
 int rafem_get_system(rafem_ctx* c, int which, int32_t* row_ptr, int32_t* col, double* vals, double* rhs) {
     if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
     cudaStream_t st = c->stream;

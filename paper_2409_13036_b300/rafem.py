@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
         "rafem_pattern_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_int32)]),
         "rafem_get_system": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
+        "rafem_layout_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "rafem_solve_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rafem_step_stats)]),
         "rafem_spmv": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_tracing": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -251,6 +253,12 @@ class Context:
         _check(lib().rafem_pattern_info(self._ctx, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc)),
                "rafem_pattern_info")
         return n.value, nnz.value, nc.value
+
+    def layout_info(self) -> dict:
+        code, nst, cb, asm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rafem_layout_info(self._ctx, ctypes.byref(code), ctypes.byref(nst), ctypes.byref(cb),
+                                       ctypes.byref(asm)), "rafem_layout_info")
+        return {"kernel_code": code.value, "nnz_stored": nst.value, "column_bytes": cb.value, "assembly": asm.value}
 
     def get_system(self, which: int):
         """(row_ptr, col, vals, rhs) of the current lifted system, as host arrays."""
