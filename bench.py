@@ -243,12 +243,16 @@ def roofline(res, mixed, peaks, peak_kind):
     nc = _ncu_traffic(kern)
     traffic = None
     if nc:
-        traffic = nc["dram_bytes_per_iteration"] * (iters + 2)
+        # DRAM bytes of one ncu capture (smaller case of the same workload), scaled by algorithmic bytes
+        traffic = nc["dram_per_alg_byte"] * alg
     return {"bound": "hbm", "kernel": f"{kern} (potential-system persistent solver, one launch per step)",
             "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "peak_kind": ("measured copy bandwidth, MEASURED_PEAKS.json hbm_gbs (of measured)"
                           if peak_kind == "measured" else "fallback 6.4 TB/s (of fallback)"),
-            "traffic": traffic, "launch_ms": solve_ms, "iters_per_launch": iters, "refinements_per_launch": ref,
+            "traffic": traffic,
+            "traffic_note": ("ncu DRAM read+write of the 112^3 capture scaled by algorithmic bytes" if traffic else
+                             "no ncu capture for the current source"),
+            "launch_ms": solve_ms, "iters_per_launch": iters, "refinements_per_launch": ref,
             "alg_bytes_per_launch": alg}
 
 
