@@ -160,6 +160,26 @@ int rafem_set_state(rafem_ctx* ctx, const double* T, const double* V, int on_dev
 /* Sizes of the fixed CSR pattern: n_rows (= N), nnz, number of element colours. Any out pointer may be NULL. */
 int rafem_pattern_info(rafem_ctx* ctx, int32_t* n_rows, int64_t* nnz, int32_t* n_colors);
 
+/* ---- batching form ----------------------------------------------------------------------------------------
+ * Many independent instances (meshes of different sizes, electrode settings and tissue properties, one set of
+ * physics/solver parameters) in one context: every step assembles all instances and solves all of them in one
+ * persistent launch per system, each instance with its own Krylov scalars and convergence test (an instance
+ * that has converged stops iterating while the others continue). The paper simulates one case per run
+ * (Sec. II-A); the batch is this library's answer to evaluating many treatment cases.
+ * The instances' nodes are laid out one after the other, each starting at a multiple of 32 (the nodes in
+ * between are isolated and carry zero potential / T_a), so rafem_get_field, rafem_set_state and
+ * rafem_get_system address the concatenated fields; rafem_batch_info gives each instance's first node. */
+#define RAFEM_MAX_BATCH 96
+
+/* n in [1, RAFEM_MAX_BATCH]; meshes[i] as for rafem_create (host pointers, copied). Errors as rafem_create. */
+int rafem_batch_create(int32_t n, const rafem_mesh* const* meshes, const rafem_params* params, void* stream,
+                       rafem_ctx** out);
+/* n_inst (nullable) and node_offsets [n_inst + 1] (nullable): first node of each instance, then the total. */
+int rafem_batch_info(rafem_ctx* ctx, int32_t* n_inst, int32_t* node_offsets);
+/* Statistics of the last step per instance, per_instance [n_inst] (host). The step statistics returned by
+ * rafem_solve_step / rafem_run summarise all instances (worst status, largest iteration counts and residuals). */
+int rafem_batch_stats(rafem_ctx* ctx, rafem_step_stats* per_instance);
+
 /* Storage actually used by the solver: kernel_code 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit
  * column deltas, 4/8/16/32 = CSR with that many lanes per row; nnz_stored includes slice padding; column_bytes is
  * 2 or 4; assembly is the RAFEM_ASSEMBLY_* in use. Any out pointer may be NULL. */

@@ -70,8 +70,11 @@ struct rafem_ctx {
     float *fz = nullptr, *fq = nullptr, *fm0 = nullptr, *fm1 = nullptr;
     int32_t *tile_r0 = nullptr, *tile_r1 = nullptr, *tile_inst = nullptr, *inst_t0 = nullptr, *inst_t1 = nullptr;
     int n_tiles = 0, grid = 0, block = 0, lanes = 8;
-    InstState* instV = nullptr;
-    InstState* instT = nullptr;
+    InstState* instV = nullptr;        // [n_inst]
+    InstState* instT = nullptr;        // [n_inst]
+    int n_inst = 1;                    // independent problem instances (a batch) in this context
+    std::vector<int32_t> inst_node_off;  // [n_inst + 1] first node of each instance (multiples of 32)
+    rafem_step_stats* istats = nullptr;  // [n_inst] per-instance statistics of the current step
     double* partial = nullptr;
     GridBarrier* bar = nullptr;
     StatsDev* stats = nullptr;
@@ -116,25 +119,55 @@ int cuda_status(cudaError_t e) {
         if (_e != cudaSuccess) return cuda_status(_e); \
     } while (0)
 
-__global__ void k_record(const InstState* inst, const GridBarrier* bar, int which, StatsDev* s, int final_step) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    InstState st = *inst;
-    if (bar->err) st.status = bar->err;
-    rafem_step_stats& c = s->cur;
-    if (which == RAFEM_SYS_V) {
-        c.iters_V += st.iters;
-        c.refine_V += st.refine;
-        c.relres_V = st.relres;
-    } else {
-        c.iters_T += st.iters;
-        c.refine_T += st.refine;
-        c.relres_T = st.relres;
+// Per-instance statistics of one solve (thread i handles instance i) and the step summary over instances
+// (status: worst; iterations, refinements, relative residual: maximum).
+__global__ void k_record(const InstState* inst, int n_inst, const GridBarrier* bar, int which, StatsDev* s,
+                         rafem_step_stats* istats, int final_step) {
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        InstState st = inst[i];
+        if (bar->err) st.status = bar->err;
+        rafem_step_stats& q = istats[i];
+        if (which == RAFEM_SYS_V) {
+            q.iters_V += st.iters;
+            q.refine_V += st.refine;
+            q.relres_V = st.relres;
+        } else {
+            q.iters_T += st.iters;
+            q.refine_T += st.refine;
+            q.relres_T = st.relres;
+        }
+        const int status = st.status;
+        if (status < 0 || q.status < 0)
+            q.status = status < q.status ? status : q.status;
+        else
+            q.status = status > q.status ? status : q.status;
+        if (final_step) q.step += 1;
     }
-    int status = st.status;
-    if (status < 0 || c.status < 0)
-        c.status = status < c.status ? status : c.status;
-    else
-        c.status = status > c.status ? status : c.status;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    rafem_step_stats& c = s->cur;
+    int iV = 0, iT = 0, rV = 0, rT = 0, stat = 0;
+    double resV = 0.0, resT = 0.0;
+    for (int i = 0; i < n_inst; ++i) {
+        const rafem_step_stats& q = istats[i];
+        iV = max(iV, q.iters_V);
+        iT = max(iT, q.iters_T);
+        rV = max(rV, q.refine_V);
+        rT = max(rT, q.refine_T);
+        resV = fmax(resV, q.relres_V);
+        resT = fmax(resT, q.relres_T);
+        if (q.status < 0 || stat < 0)
+            stat = q.status < stat ? q.status : stat;
+        else
+            stat = q.status > stat ? q.status : stat;
+    }
+    c.iters_V = iV;
+    c.iters_T = iT;
+    c.refine_V = rV;
+    c.refine_T = rT;
+    c.relres_V = resV;
+    c.relres_T = resT;
+    c.status = stat;
     if (final_step) {
         c.step += 1;
         s->hist += 1;
@@ -145,7 +178,14 @@ __global__ void k_record(const InstState* inst, const GridBarrier* bar, int whic
     }
 }
 
-__global__ void k_begin_step(StatsDev* s) {
+__global__ void k_begin_step(StatsDev* s, rafem_step_stats* istats, int n_inst) {
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        rafem_step_stats& q = istats[i];
+        const int64_t step = q.step;
+        q = rafem_step_stats{};
+        q.correctors = 1;
+        q.step = step;
+    }
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     rafem_step_stats& c = s->cur;
     c.status = 0;
@@ -197,7 +237,7 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.tile_r0 = c->tile_r0;
     a.tile_r1 = c->tile_r1;
     a.tile_inst = c->tile_inst;
-    a.n_inst = 1;
+    a.n_inst = c->n_inst;
     a.inst_t0 = c->inst_t0;
     a.inst_t1 = c->inst_t1;
     a.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
@@ -260,17 +300,17 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
 // One lagged pass: sigma and the mass term both use the current T.
 cudaError_t enqueue_step(rafem_ctx* c) {
     cudaError_t e;
-    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
     if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
-    k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+    k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
     if ((e = enqueue_predict(c, RAFEM_SYS_T)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
-    k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 1);
+    k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 1);
     return cudaGetLastError();
 }
 
@@ -279,7 +319,7 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     cudaError_t e;
     for (int i = 0; i < 6; ++i)
         if (!c->ev[i] && (e = cudaEventCreate(&c->ev[i])) != cudaSuccess) return e;
-    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     nvtxRangePushA("Assembly");
     cudaEventRecord(c->ev[0], c->stream);
@@ -291,7 +331,7 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[2], c->stream);
     nvtxRangePop();
-    k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+    k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     nvtxRangePushA("Assembly");
     cudaEventRecord(c->ev[3], c->stream);
     if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
@@ -302,7 +342,7 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[5], c->stream);
     nvtxRangePop();
-    k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 1);
+    k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
     float ms[4];
@@ -316,12 +356,20 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     c->trace.ms_solve_T += ms[3];
     c->trace.steps += 1;
     c->trace.solves += 1;
-    InstState iv, it;
-    if ((e = cudaMemcpy(&iv, c->instV, sizeof(iv), cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(&it, c->instT, sizeof(it), cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
-    c->trace.iters_V += iv.iters;
-    c->trace.iters_T += it.iters;
-    c->trace.refine_V += iv.refine;
+    std::vector<InstState> iv(c->n_inst), it(c->n_inst);
+    if ((e = cudaMemcpy(iv.data(), c->instV, c->n_inst * sizeof(InstState), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(it.data(), c->instT, c->n_inst * sizeof(InstState), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    int mv = 0, mt = 0, mr = 0;
+    for (int i = 0; i < c->n_inst; ++i) {
+        mv = std::max(mv, iv[i].iters);
+        mt = std::max(mt, it[i].iters);
+        mr = std::max(mr, iv[i].refine);
+    }
+    c->trace.iters_V += mv;
+    c->trace.iters_T += mt;
+    c->trace.refine_V += mr;
     return cudaSuccess;
 }
 
@@ -389,8 +437,11 @@ void rafem_destroy(rafem_ctx* c) {
     delete c;
 }
 
-static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx* c) {
+static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx* c, int n_inst,
+                       const std::vector<int32_t>& node_off) {
     const int N = m->n_nodes, E = m->n_tets;
+    c->n_inst = n_inst;
+    c->inst_node_off = node_off;
     c->prm = *prm;
     c->N = N;
     c->E = E;
@@ -542,8 +593,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     }
     CK(dalloc(c, &c->stats, 1));
     CK(dalloc(c, &c->scratch, 8));
-    CK(dalloc(c, &c->instV, 1));
-    CK(dalloc(c, &c->instT, 1));
+    CK(dalloc(c, &c->instV, n_inst));
+    CK(dalloc(c, &c->instT, n_inst));
+    CK(dalloc(c, &c->istats, n_inst));
     CK(dalloc(c, &c->bar, 1));
     // ---- uploads
     cudaStream_t st = c->stream;
@@ -608,29 +660,35 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     int maxb = krylov_max_blocks(c->lanes, prm->precision, &block);
     if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
     c->block = block;
-    int rows_per_tile = prm->rows_per_tile > 0 ? prm->rows_per_tile : (N + maxb - 1) / maxb;
+    // one tile per block for a single instance; for a batch ~4 tiles per block, never straddling instances
+    int rows_per_tile = prm->rows_per_tile > 0 ? prm->rows_per_tile
+                                                : (n_inst == 1 ? (N + maxb - 1) / maxb : (N + 4 * maxb - 1) / (4 * maxb));
     rows_per_tile = std::max(rows_per_tile, 1);
     if (c->sell) rows_per_tile = (rows_per_tile + SELL_C - 1) / SELL_C * SELL_C;
-    c->n_tiles = (N + rows_per_tile - 1) / rows_per_tile;
-    c->grid = std::min(c->n_tiles, maxb);
     {
-        std::vector<int32_t> t0(c->n_tiles), t1(c->n_tiles), ti(c->n_tiles, 0);
-        for (int t = 0; t < c->n_tiles; ++t) {
-            t0[t] = (int32_t)std::min<int64_t>((int64_t)t * rows_per_tile, N);
-            t1[t] = (int32_t)std::min<int64_t>((int64_t)(t + 1) * rows_per_tile, N);
+        std::vector<int32_t> t0, t1, ti, it0(n_inst), it1(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            it0[i] = (int32_t)t0.size();
+            for (int64_t r = node_off[i]; r < node_off[i + 1]; r += rows_per_tile) {
+                t0.push_back((int32_t)r);
+                t1.push_back((int32_t)std::min<int64_t>(r + rows_per_tile, node_off[i + 1]));
+                ti.push_back(i);
+            }
+            it1[i] = (int32_t)t0.size();
         }
-        int32_t it0 = 0, it1 = c->n_tiles;
+        c->n_tiles = (int)t0.size();
+        c->grid = std::min(c->n_tiles, maxb);
         CK(dalloc(c, &c->tile_r0, c->n_tiles));
         CK(dalloc(c, &c->tile_r1, c->n_tiles));
         CK(dalloc(c, &c->tile_inst, c->n_tiles));
-        CK(dalloc(c, &c->inst_t0, 1));
-        CK(dalloc(c, &c->inst_t1, 1));
-        CK(dalloc(c, &c->partial, 4 * (size_t)c->n_tiles));
+        CK(dalloc(c, &c->inst_t0, n_inst));
+        CK(dalloc(c, &c->inst_t1, n_inst));
+        CK(dalloc(c, &c->partial, (size_t)kPartialQ * c->n_tiles));
         CK(cudaMemcpyAsync(c->tile_r0, t0.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(c->tile_r1, t1.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(c->tile_inst, ti.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->inst_t0, &it0, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->inst_t1, &it1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->inst_t0, it0.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->inst_t1, it1.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));  // host vectors go out of scope
     }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
@@ -656,9 +714,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     return RAFEM_OK;
 }
 
-int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx** out) {
-    if (!out) return RAFEM_ERR_BAD_INPUT;
-    *out = nullptr;
+static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
     if (!m || !prm || !m->coords || !m->tets || !m->bc_V || !m->g_V || !m->bc_T || !m->g_T || !m->sigma0 || !m->k)
         return RAFEM_ERR_BAD_INPUT;
     if (m->n_nodes < 4 || m->n_tets < 1) return RAFEM_ERR_BAD_INPUT;
@@ -673,11 +729,21 @@ int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, raf
     if (prm->precond != RAFEM_PRECOND_JACOBI) return RAFEM_ERR_BAD_INPUT;
     if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
+    return RAFEM_OK;
+}
+
+int rafem_create(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx** out) {
+    if (!out) return RAFEM_ERR_BAD_INPUT;
+    *out = nullptr;
+    {
+        const int v = validate_params(m, prm);
+        if (v != RAFEM_OK) return v;
+    }
     rafem_ctx* c = new (std::nothrow) rafem_ctx();
     if (!c) return RAFEM_ERR_OOM;
     int s;
     try {
-        s = create_impl(m, prm, stream, c);
+        s = create_impl(m, prm, stream, c, 1, std::vector<int32_t>{0, m->n_nodes});
     } catch (const std::bad_alloc&) {
         s = RAFEM_ERR_OOM;
     }
@@ -698,20 +764,20 @@ int rafem_assemble(rafem_ctx* c, int which) {
 
 int rafem_solve(rafem_ctx* c, int which, rafem_step_stats* stats) {
     if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
-    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     CK(cudaGetLastError());
     CK(enqueue_solve(c, which, which == RAFEM_SYS_V ? c->bV : c->bT, which == RAFEM_SYS_V ? c->V : c->T));
-    k_record<<<1, 32, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->bar, which, c->stats, 0);
+    k_record<<<1, 128, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->n_inst, c->bar, which, c->stats, c->istats, 0);
     CK(cudaGetLastError());
     return finish(c, stats, false);
 }
 
 int rafem_solve_rhs(rafem_ctx* c, int which, const double* b, double* x, rafem_step_stats* stats) {
     if (!c || !b || !x || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
-    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     CK(cudaGetLastError());
     CK(enqueue_solve(c, which, b, x));
-    k_record<<<1, 32, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->bar, which, c->stats, 0);
+    k_record<<<1, 128, 0, c->stream>>>(which == RAFEM_SYS_V ? c->instV : c->instT, c->n_inst, c->bar, which, c->stats, c->istats, 0);
     CK(cudaGetLastError());
     return finish(c, stats, false);
 }
@@ -724,17 +790,17 @@ int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
     }
     // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n
     CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    k_begin_step<<<1, 32, 0, c->stream>>>(c->stats);
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     CK(cudaGetLastError());
     int passes = 0;
     for (passes = 1; passes <= c->prm.n_corrector; ++passes) {
         CK(cudaMemcpyAsync(c->T_prev, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         CK(enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T_old));
         CK(enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V));
-        k_record<<<1, 32, 0, c->stream>>>(c->instV, c->bar, RAFEM_SYS_V, c->stats, 0);
+        k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
         CK(enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T_old));
         CK(enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T));
-        k_record<<<1, 32, 0, c->stream>>>(c->instT, c->bar, RAFEM_SYS_T, c->stats, 0);
+        k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 0);
         CK(launch_max_abs_diff(c->N, c->T, c->T_prev, c->scratch, c->stream));
         double change = 0;
         CK(cudaMemcpyAsync(&change, c->scratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -861,6 +927,84 @@ int rafem_pattern_info(rafem_ctx* c, int32_t* n_rows, int64_t* nnz, int32_t* n_c
     if (n_rows) *n_rows = c->N;
     if (nnz) *nnz = c->nnz;
     if (n_colors) *n_colors = c->n_colors;
+    return RAFEM_OK;
+}
+
+int rafem_batch_create(int32_t n, const rafem_mesh* const* meshes, const rafem_params* prm, void* stream,
+                       rafem_ctx** out) {
+    if (!out) return RAFEM_ERR_BAD_INPUT;
+    *out = nullptr;
+    if (!meshes || !prm || n < 1 || n > RAFEM_MAX_BATCH) return RAFEM_ERR_BAD_INPUT;
+    // the union mesh: instance i's nodes start at off[i] (a multiple of 32); the nodes between instances are
+    // isolated, Dirichlet in both systems, and touched by no element
+    std::vector<int32_t> off(n + 1, 0);
+    int64_t E = 0;
+    for (int i = 0; i < n; ++i) {
+        const rafem_mesh* m = meshes[i];
+        if (!m || !m->coords || !m->tets || !m->bc_V || !m->g_V || !m->bc_T || !m->g_T || !m->sigma0 || !m->k ||
+            m->n_nodes < 4 || m->n_tets < 1)
+            return RAFEM_ERR_BAD_INPUT;
+        const int64_t next = off[i] + ((int64_t)m->n_nodes + SELL_C - 1) / SELL_C * SELL_C;
+        if (next > INT32_MAX / 2) return RAFEM_ERR_BAD_INPUT;
+        off[i + 1] = (int32_t)next;
+        E += m->n_tets;
+    }
+    if (E > INT32_MAX / 16) return RAFEM_ERR_BAD_INPUT;
+    const int32_t N = off[n];
+    std::vector<double> xyz(3 * (size_t)N, 0.0), gV(N, 0.0), gT(N, prm->T_a), s0, kk;
+    std::vector<uint8_t> bV(N, 1), bT(N, 1);
+    std::vector<int32_t> tets;
+    tets.reserve(4 * (size_t)E);
+    s0.reserve(E);
+    kk.reserve(E);
+    for (int i = 0; i < n; ++i) {
+        const rafem_mesh* m = meshes[i];
+        const int32_t o = off[i];
+        std::copy(m->coords, m->coords + 3 * (size_t)m->n_nodes, xyz.begin() + 3 * (size_t)o);
+        std::copy(m->g_V, m->g_V + m->n_nodes, gV.begin() + o);
+        std::copy(m->g_T, m->g_T + m->n_nodes, gT.begin() + o);
+        std::copy(m->bc_V, m->bc_V + m->n_nodes, bV.begin() + o);
+        std::copy(m->bc_T, m->bc_T + m->n_nodes, bT.begin() + o);
+        for (int64_t q = 0; q < 4LL * m->n_tets; ++q) {
+            const int32_t v = m->tets[q];
+            if (v < 0 || v >= m->n_nodes) return RAFEM_ERR_BAD_INPUT;
+            tets.push_back(v + o);
+        }
+        s0.insert(s0.end(), m->sigma0, m->sigma0 + m->n_tets);
+        kk.insert(kk.end(), m->k, m->k + m->n_tets);
+    }
+    rafem_mesh u{N, (int32_t)E, xyz.data(), tets.data(), bV.data(), gV.data(), bT.data(), gT.data(), s0.data(),
+                 kk.data()};
+    rafem_ctx* c = nullptr;
+    int s = validate_params(&u, prm);
+    if (s != RAFEM_OK) return s;
+    c = new (std::nothrow) rafem_ctx();
+    if (!c) return RAFEM_ERR_OOM;
+    try {
+        s = create_impl(&u, prm, stream, c, n, off);
+    } catch (const std::bad_alloc&) {
+        s = RAFEM_ERR_OOM;
+    }
+    if (s != RAFEM_OK) {
+        rafem_destroy(c);
+        return s;
+    }
+    *out = c;
+    return RAFEM_OK;
+}
+
+int rafem_batch_info(rafem_ctx* c, int32_t* n_inst, int32_t* node_offsets) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (n_inst) *n_inst = c->n_inst;
+    if (node_offsets) std::copy(c->inst_node_off.begin(), c->inst_node_off.end(), node_offsets);
+    return RAFEM_OK;
+}
+
+int rafem_batch_stats(rafem_ctx* c, rafem_step_stats* per_instance) {
+    if (!c || !per_instance) return RAFEM_ERR_BAD_INPUT;
+    CK(cudaMemcpyAsync(per_instance, c->istats, c->n_inst * sizeof(rafem_step_stats), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return RAFEM_OK;
 }
 

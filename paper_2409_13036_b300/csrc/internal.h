@@ -93,6 +93,9 @@ struct InstState {
     float alpha32, beta32, gprev32, aprev32, thr32, pad32;
 };
 
+// Number of per-tile partial sums a solver kernel writes (gamma, rr, delta, bb, rr64).
+constexpr int kPartialQ = 5;
+
 struct GridBarrier {
     unsigned int count;
     unsigned int gen;
@@ -127,7 +130,7 @@ struct SolveArgs {
     const int32_t* inst_t0;  // first tile of each instance
     const int32_t* inst_t1;  // one past its last tile
     InstState* inst;
-    double* partial;         // [4][n_tiles]
+    double* partial;         // [kPartialQ][n_tiles]
     GridBarrier* bar;
     // controls
     double tol, inner_tol;

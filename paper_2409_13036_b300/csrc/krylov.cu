@@ -60,6 +60,7 @@ constexpr int group_slices() {
 }
 
 enum { Q_GAMMA = 0, Q_RR = 1, Q_DELTA = 2, Q_BB = 3, Q_RR64 = 4, NQ_ALL = 5 };
+static_assert(NQ_ALL == kPartialQ, "partial-sum buffer size");
 enum { ST_OUTER = 1, ST_START = 2, ST_ITER = 3 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {

@@ -33,8 +33,8 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kVecBytes = align256((size_t)kMaxRows * sizeof(double));
 constexpr size_t kOffVec = 0;                                           // r, u, w, p, s, dinv
 constexpr size_t kOffDiag = kOffVec + 6 * kVecBytes;                    // int32 [kMaxRows]
-constexpr size_t kOffPartial = kOffDiag + align256((size_t)kMaxRows * 4);  // double [4][kMaxTiles]
-constexpr size_t kOffTiles = kOffPartial + align256((size_t)4 * kMaxTiles * 8);  // int32 [3][kMaxTiles]
+constexpr size_t kOffPartial = kOffDiag + align256((size_t)kMaxRows * 4);  // double [kPartialQ][kMaxTiles]
+constexpr size_t kOffTiles = kOffPartial + align256((size_t)kPartialQ * kMaxTiles * 8);  // int32 [3][kMaxTiles]
 constexpr size_t kOffInstTiles = kOffTiles + align256((size_t)3 * kMaxTiles * 4);  // int32 [2]
 constexpr size_t kOffFlag = kOffInstTiles + 256;                        // int32 bad-input counter
 constexpr size_t kOffInst = kOffFlag + 256;                             // InstState

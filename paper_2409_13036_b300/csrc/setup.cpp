@@ -70,6 +70,7 @@ void build_pattern(int N, int E, const int32_t* tets, std::vector<int32_t>& row_
 #pragma omp for schedule(dynamic, 1024)
         for (int i = 0; i < N; ++i) {
             buf.clear();
+            buf.push_back(i);  // every row stores its diagonal, also for a node that no element touches
             for (int32_t q = cnt[i]; q < cnt[i + 1]; ++q)
                 for (int a = 0; a < 4; ++a) buf.push_back(tets[4LL * inc[q] + a]);
             std::sort(buf.begin(), buf.end());
@@ -85,6 +86,7 @@ void build_pattern(int N, int E, const int32_t* tets, std::vector<int32_t>& row_
 #pragma omp for schedule(dynamic, 1024)
         for (int i = 0; i < N; ++i) {
             buf.clear();
+            buf.push_back(i);
             for (int32_t q = cnt[i]; q < cnt[i + 1]; ++q)
                 for (int a = 0; a < 4; ++a) buf.push_back(tets[4LL * inc[q] + a]);
             std::sort(buf.begin(), buf.end());

@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
         "rafem_get_trace": (ctypes.c_int, [vp, ctypes.POINTER(rafem_trace)]),
         "rafem_pcg_csr_noalloc": (ctypes.c_int, [ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_double,
                                                  ctypes.c_int32, vp, ctypes.POINTER(rafem_step_stats)]),
+        "rafem_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(rafem_mesh)),
+                                              ctypes.POINTER(rafem_params), vp, ctypes.POINTER(vp)]),
+        "rafem_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), vp]),
+        "rafem_batch_stats": (ctypes.c_int, [vp, vp]),
         "rafem_destroy": (None, [vp]),
         "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -167,8 +171,45 @@ def _dev(x):
     return x.data_ptr()
 
 
+def _mesh_struct(mesh):
+    keep = [np.ascontiguousarray(mesh.coords, dtype=np.float64), np.ascontiguousarray(mesh.tets, dtype=np.int32),
+            np.ascontiguousarray(mesh.bc_V, dtype=np.uint8), np.ascontiguousarray(mesh.g_V, dtype=np.float64),
+            np.ascontiguousarray(mesh.bc_T, dtype=np.uint8), np.ascontiguousarray(mesh.g_T, dtype=np.float64),
+            np.ascontiguousarray(mesh.sigma0, dtype=np.float64), np.ascontiguousarray(mesh.k, dtype=np.float64)]
+    c, t, bv, gv, bt, gt, s0, k = keep
+    m = rafem_mesh(n_nodes=c.shape[0], n_tets=t.shape[0], coords=_ptr(c, ctypes.c_double),
+                   tets=_ptr(t, ctypes.c_int32), bc_V=_ptr(bv, ctypes.c_uint8), g_V=_ptr(gv, ctypes.c_double),
+                   bc_T=_ptr(bt, ctypes.c_uint8), g_T=_ptr(gt, ctypes.c_double), sigma0=_ptr(s0, ctypes.c_double),
+                   k=_ptr(k, ctypes.c_double))
+    return m, keep
+
+
 class Context:
-    """Owns one rafem_ctx (one problem instance on the current CUDA device)."""
+    """Owns one rafem_ctx (one problem instance, or a batch, on the current CUDA device)."""
+
+    @classmethod
+    def batch(cls, meshes, params: rafem_params | None = None, stream: int | None = None, **kw):
+        """rafem_batch_create over a list of meshes."""
+        self = cls.__new__(cls)
+        structs, keeps = zip(*[_mesh_struct(m) for m in meshes])
+        arr = (ctypes.POINTER(rafem_mesh) * len(structs))(*[ctypes.pointer(s) for s in structs])
+        self.params = params if params is not None else default_params(**kw)
+        self._ctx = ctypes.c_void_p()
+        s = lib().rafem_batch_create(len(structs), arr, ctypes.byref(self.params), ctypes.c_void_p(stream or 0),
+                                     ctypes.byref(self._ctx))
+        _check(s, "rafem_batch_create")
+        n = ctypes.c_int32()
+        offs = np.zeros(len(structs) + 1, np.int32)
+        _check(lib().rafem_batch_info(self._ctx, ctypes.byref(n), offs.ctypes.data), "rafem_batch_info")
+        self.offsets = offs
+        self.N = int(offs[-1])
+        self.n_inst = int(n.value)
+        return self
+
+    def batch_stats(self):
+        out = (rafem_step_stats * self.n_inst)()
+        _check(lib().rafem_batch_stats(self._ctx, ctypes.cast(out, ctypes.c_void_p)), "rafem_batch_stats")
+        return [o.as_dict() for o in out]
 
     def __init__(self, mesh, params: rafem_params | None = None, stream: int | None = None, **kw):
         self._keep = [np.ascontiguousarray(mesh.coords, dtype=np.float64),
@@ -191,6 +232,8 @@ class Context:
                                ctypes.byref(self._ctx))
         _check(s, "rafem_create")
         self._keep = None
+        self.n_inst = 1
+        self.offsets = np.array([0, self.N], np.int32)
 
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:

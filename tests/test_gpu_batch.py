@@ -1,0 +1,67 @@
+"""Batching form: many independent instances in one context and one persistent launch per system, compared
+with one context per instance and with the oracle (needs a B300)."""
+import numpy as np
+import pytest
+
+from oracle import rafem_oracle as O
+from paper_2409_13036_b300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2409_13036_b300 import build
+    build.build()
+    yield
+
+
+def _instances():
+    """Five uneven instances (sizes, electrode voltage and depth, sigma0 differ; none a multiple of 32 nodes)."""
+    draws = [(6, 12.0, 12.0, 0.27, 11), (9, 35.0, 25.0, 0.41, 12), (11, 20.0, 18.0, 0.33, 13), (13, 15.0, 29.0, 0.30, 14),
+             (8, 40.0, 10.0, 0.45, 15)]
+    return [mg.batch_mesh(d) for d in draws]
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-9), (1, 1e-11, 1e-8)])
+def test_batch_matches_single_instance_contexts(precision, tol, bound):
+    from paper_2409_13036_b300 import rafem
+    meshes = _instances()
+    steps = 3
+    with rafem.Context.batch(meshes, precision=precision, tol=tol, dt=5.0) as b:
+        s, st = b.run(steps)
+        assert s == rafem.RAFEM_OK, st.as_dict()
+        T = b.get_field(rafem.RAFEM_SYS_T)
+        V = b.get_field(rafem.RAFEM_SYS_V)
+        per = b.batch_stats()
+        off = b.offsets
+    assert len(per) == len(meshes) and all(p["status"] == 0 for p in per)
+    assert len({p["iters_V"] for p in per}) > 1  # instances converge on their own schedules
+    for i, m in enumerate(meshes):
+        Ti, Vi = T[off[i]:off[i] + m.n_nodes], V[off[i]:off[i] + m.n_nodes]
+        with rafem.Context(m, precision=0, tol=1e-12, dt=5.0) as c:
+            c.run(steps)
+            assert O.rel_err(Ti, c.get_field(rafem.RAFEM_SYS_T)) <= bound
+            assert O.rel_err(Vi, c.get_field(rafem.RAFEM_SYS_V)) <= bound
+        # the padding nodes between instances keep their boundary values
+        pad = slice(off[i] + m.n_nodes, off[i + 1])
+        assert np.all(V[pad] == 0.0)
+    # one instance against the oracle's direct solves
+    T_ref, V_ref = O.Model(meshes[2], O.Params(dt=5.0)).run(steps)
+    m = meshes[2]
+    assert O.rel_err(T[off[2]:off[2] + m.n_nodes], T_ref[-1]) <= bound
+    assert O.rel_err(V[off[2]:off[2] + m.n_nodes], V_ref[-1]) <= bound
+
+
+def test_batch_limits():
+    from paper_2409_13036_b300 import rafem
+    m = mg.cube_mesh(2)
+    with pytest.raises(rafem.RafemError) as e:
+        rafem.Context.batch([m] * 97)
+    assert e.value.status == rafem.RAFEM_ERR_BAD_INPUT
+    with rafem.Context.batch([m]) as b:
+        s, st = b.run(1)
+        assert s == rafem.RAFEM_OK and b.n_inst == 1
