@@ -256,6 +256,55 @@ def roofline(res, mixed, peaks, peak_kind):
             "alg_bytes_per_launch": alg}
 
 
+def measure_batch(rafem, torch, mg, args):
+    """Batching form: the 96-instance workload (sizes 12^3..64^3 cells, electrode 10-40 V at 10-30 mm, sigma0
+    0.25-0.45 S/m, seeded) in one context per precision, schedule from the autotuner, against one context per
+    instance run one after the other (FP64). Throughput in instance-steps per second."""
+    from paper_2409_13036_b300.autotune import autotune_schedule
+    meshes = [mg.batch_mesh(d) for d in mg.batch_draws()]
+    nodes = sum(m.n_nodes for m in meshes)
+    kb = args.batch_steps
+    out = {"instances": len(meshes), "nodes": nodes, "steps": kb, "warmup": 3}
+    stream = torch.cuda.Stream()
+    for name, prec in (("mixed", rafem.RAFEM_PRECISION_MIXED), ("fp64", rafem.RAFEM_PRECISION_FP64)):
+        ctx = rafem.Context.batch(meshes, stream=stream.cuda_stream, precision=prec)
+        T0, V0 = ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V)
+        tune = autotune_schedule(ctx, steps=2)
+        ctx.set_state(T=T0, V=V0, step=0)  # back to the initial state: same trajectory as the sequential runs
+        ctx.run(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s, st = ctx.run(kb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        per = ctx.batch_stats()
+        out[name] = {"instance_steps_per_s": len(meshes) * kb / (ms * 1e-3), "ms_per_step": ms / kb,
+                     "status": rafem.status_string(s), "rows_per_tile": tune["rows_per_tile"],
+                     "tuned_from_cache": tune["cached"],
+                     "iters_V_min_max": [min(q["iters_V"] for q in per), max(q["iters_V"] for q in per)]}
+        ctx.close()
+    # the same instances one context at a time, FP64
+    total_ms = 0.0
+    for m in meshes:
+        ctx = rafem.Context(m, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_FP64)
+        ctx.run(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.run(kb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        ctx.close()
+    out["sequential_fp64"] = {"instance_steps_per_s": len(meshes) * kb / (total_ms * 1e-3),
+                              "ms_per_step_all_instances": total_ms / kb}
+    out["speedup_mixed_batch_vs_sequential_fp64"] = (out["mixed"]["instance_steps_per_s"] /
+                                                     out["sequential_fp64"]["instance_steps_per_s"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,6 +315,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="run one precision only")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -373,6 +423,11 @@ def main():
             "speedup": head_sum["value"] / line["fp64"]["value"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if args.batch_steps > 0 and args.only is None and args.cells == 127:
+        try:
+            line["batch"] = measure_batch(rafem, torch, mg, args)
+        except Exception as exc:  # the headline line must still be printed
+            line["batch"] = {"error": repr(exc)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -180,6 +180,12 @@ int rafem_batch_info(rafem_ctx* ctx, int32_t* n_inst, int32_t* node_offsets);
  * rafem_solve_step / rafem_run summarise all instances (worst status, largest iteration counts and residuals). */
 int rafem_batch_stats(rafem_ctx* ctx, rafem_step_stats* per_instance);
 
+/* Work schedule of the persistent solvers: rows per work tile (tiles never straddle batch instances; rounded up
+ * to a multiple of 32 for SELL-32). 0 = automatic. Rebuilds only the tile arrays (cheap) and drops the captured
+ * step graph; used by the autotuner. rafem_get_schedule reports the tile size, tile count and solver grid. */
+int rafem_set_schedule(rafem_ctx* ctx, int32_t rows_per_tile);
+int rafem_get_schedule(rafem_ctx* ctx, int32_t* rows_per_tile, int32_t* n_tiles, int32_t* grid);
+
 /* Storage actually used by the solver: kernel_code 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit
  * column deltas, 4/8/16/32 = CSR with that many lanes per row; nnz_stored includes slice padding; column_bytes is
  * 2 or 4; assembly is the RAFEM_ASSEMBLY_* in use. Any out pointer may be NULL. */

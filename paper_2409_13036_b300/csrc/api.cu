@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -73,6 +74,9 @@ struct rafem_ctx {
     InstState* instV = nullptr;        // [n_inst]
     InstState* instT = nullptr;        // [n_inst]
     int n_inst = 1;                    // independent problem instances (a batch) in this context
+    int maxb = 0;                      // co-resident blocks of the solver kernel
+    int rows_per_tile = 0;
+    std::vector<void*> tile_allocs;    // tile arrays and partial sums (rebuilt by rafem_set_schedule)
     std::vector<int32_t> inst_node_off;  // [n_inst + 1] first node of each instance (multiples of 32)
     rafem_step_stats* istats = nullptr;  // [n_inst] per-instance statistics of the current step
     double* partial = nullptr;
@@ -432,9 +436,66 @@ void rafem_destroy(rafem_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (void* p : c->tile_allocs) cudaFree(p);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+// Work tiles of the persistent solvers: contiguous row ranges of at most rows_per_tile rows (a multiple of 32
+// for SELL-32), never straddling instances. rows_per_tile <= 0 picks one tile per block for a single instance
+// and about four per block for a batch. Replaces any previous tiles and drops the captured step graph.
+static int build_tiles(rafem_ctx* c, int rows_per_tile) {
+    const int N = c->N, n_inst = c->n_inst;
+    const std::vector<int32_t>& node_off = c->inst_node_off;
+    if (rows_per_tile <= 0)
+        rows_per_tile = n_inst == 1 ? (N + c->maxb - 1) / c->maxb : (N + 4 * c->maxb - 1) / (4 * c->maxb);
+    rows_per_tile = std::max(rows_per_tile, 1);
+    if (c->sell) rows_per_tile = (rows_per_tile + SELL_C - 1) / SELL_C * SELL_C;
+    std::vector<int32_t> t0, t1, ti, it0(n_inst), it1(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        it0[i] = (int32_t)t0.size();
+        for (int64_t r = node_off[i]; r < node_off[i + 1]; r += rows_per_tile) {
+            t0.push_back((int32_t)r);
+            t1.push_back((int32_t)std::min<int64_t>(r + rows_per_tile, node_off[i + 1]));
+            ti.push_back(i);
+        }
+        it1[i] = (int32_t)t0.size();
+    }
+    cudaStream_t st = c->stream;
+    CK(cudaStreamSynchronize(st));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    for (void* p : c->tile_allocs) cudaFree(p);
+    c->tile_allocs.clear();
+    const int nt = (int)t0.size();
+    auto talloc = [&](auto** ptr, size_t count) -> cudaError_t {
+        void* q = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(**ptr) + 64;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return e;
+        c->tile_allocs.push_back(q);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
+        return cudaMemsetAsync(q, 0, bytes, st);
+    };
+    CK(talloc(&c->tile_r0, nt));
+    CK(talloc(&c->tile_r1, nt));
+    CK(talloc(&c->tile_inst, nt));
+    CK(talloc(&c->inst_t0, n_inst));
+    CK(talloc(&c->inst_t1, n_inst));
+    CK(talloc(&c->partial, (size_t)kPartialQ * nt));
+    CK(cudaMemcpyAsync(c->tile_r0, t0.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->tile_r1, t1.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->tile_inst, ti.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->inst_t0, it0.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->inst_t1, it1.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+    c->n_tiles = nt;
+    c->grid = std::min(nt, c->maxb);
+    c->rows_per_tile = rows_per_tile;
+    return RAFEM_OK;
 }
 
 static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx* c, int n_inst,
@@ -660,36 +721,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     int maxb = krylov_max_blocks(c->lanes, prm->precision, &block);
     if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
     c->block = block;
-    // one tile per block for a single instance; for a batch ~4 tiles per block, never straddling instances
-    int rows_per_tile = prm->rows_per_tile > 0 ? prm->rows_per_tile
-                                                : (n_inst == 1 ? (N + maxb - 1) / maxb : (N + 4 * maxb - 1) / (4 * maxb));
-    rows_per_tile = std::max(rows_per_tile, 1);
-    if (c->sell) rows_per_tile = (rows_per_tile + SELL_C - 1) / SELL_C * SELL_C;
+    c->maxb = maxb;
     {
-        std::vector<int32_t> t0, t1, ti, it0(n_inst), it1(n_inst);
-        for (int i = 0; i < n_inst; ++i) {
-            it0[i] = (int32_t)t0.size();
-            for (int64_t r = node_off[i]; r < node_off[i + 1]; r += rows_per_tile) {
-                t0.push_back((int32_t)r);
-                t1.push_back((int32_t)std::min<int64_t>(r + rows_per_tile, node_off[i + 1]));
-                ti.push_back(i);
-            }
-            it1[i] = (int32_t)t0.size();
-        }
-        c->n_tiles = (int)t0.size();
-        c->grid = std::min(c->n_tiles, maxb);
-        CK(dalloc(c, &c->tile_r0, c->n_tiles));
-        CK(dalloc(c, &c->tile_r1, c->n_tiles));
-        CK(dalloc(c, &c->tile_inst, c->n_tiles));
-        CK(dalloc(c, &c->inst_t0, n_inst));
-        CK(dalloc(c, &c->inst_t1, n_inst));
-        CK(dalloc(c, &c->partial, (size_t)kPartialQ * c->n_tiles));
-        CK(cudaMemcpyAsync(c->tile_r0, t0.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->tile_r1, t1.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->tile_inst, ti.data(), c->n_tiles * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->inst_t0, it0.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c->inst_t1, it1.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+        const int t = build_tiles(c, prm->rows_per_tile);
+        if (t != RAFEM_OK) return t;
     }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
     CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
@@ -1005,6 +1040,19 @@ int rafem_batch_stats(rafem_ctx* c, rafem_step_stats* per_instance) {
     CK(cudaMemcpyAsync(per_instance, c->istats, c->n_inst * sizeof(rafem_step_stats), cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_schedule(rafem_ctx* c, int32_t rows_per_tile) {
+    if (!c || rows_per_tile < 0) return RAFEM_ERR_BAD_INPUT;
+    return build_tiles(c, rows_per_tile);
+}
+
+int rafem_get_schedule(rafem_ctx* c, int32_t* rows_per_tile, int32_t* n_tiles, int32_t* grid) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (rows_per_tile) *rows_per_tile = c->rows_per_tile;
+    if (n_tiles) *n_tiles = c->n_tiles;
+    if (grid) *grid = c->grid;
     return RAFEM_OK;
 }
 

@@ -115,6 +115,9 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(rafem_params), vp, ctypes.POINTER(vp)]),
         "rafem_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), vp]),
         "rafem_batch_stats": (ctypes.c_int, [vp, vp]),
+        "rafem_set_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "rafem_get_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32)]),
         "rafem_destroy": (None, [vp]),
         "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -296,6 +299,15 @@ class Context:
         _check(lib().rafem_pattern_info(self._ctx, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc)),
                "rafem_pattern_info")
         return n.value, nnz.value, nc.value
+
+    def set_schedule(self, rows_per_tile: int):
+        _check(lib().rafem_set_schedule(self._ctx, int(rows_per_tile)), "rafem_set_schedule")
+
+    def get_schedule(self) -> dict:
+        r, n, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rafem_get_schedule(self._ctx, ctypes.byref(r), ctypes.byref(n), ctypes.byref(g)),
+               "rafem_get_schedule")
+        return {"rows_per_tile": r.value, "n_tiles": n.value, "grid": g.value}
 
     def layout_info(self) -> dict:
         code, nst, cb, asm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
