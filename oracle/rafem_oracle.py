@@ -243,3 +243,144 @@ def rel_err(x, x_ref):
     """||x - x_ref||_2 / ||x_ref||_2."""
     x_ref = np.asarray(x_ref, dtype=np.float64)
     return float(np.linalg.norm(np.asarray(x, dtype=np.float64) - x_ref) / np.linalg.norm(x_ref))
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Differentiation of the time loop (gradient of a loss on the final temperature with respect to the
+# per-element conductivities sigma0_e and k_e, and to the initial temperature).
+#
+# Two independent routes, both on the lagged step (n_corrector = 1):
+#   * forward mode: the tangent-linear step, obtained by differentiating every line of Model.step, propagates
+#     directional derivatives (dT^n, dsigma0, dk) -> dT^{n+1};
+#   * central finite differences of the forward model.
+# gradient_dense_adjoint builds, for tiny meshes, the full step Jacobians column by column with the tangent step
+# and accumulates the gradient backwards with their explicit transposes (no symmetry of any matrix is used).
+# ----------------------------------------------------------------------------------------------------------
+
+def _scatter(vals_e4, tets, N):
+    """Sum per-(element, vertex) values [E, 4, m] into nodes [N, m]."""
+    out = np.zeros((N, vals_e4.shape[2]))
+    np.add.at(out, np.asarray(tets).ravel(), vals_e4.reshape(-1, vals_e4.shape[2]))
+    return out
+
+
+def _solve_many(A, B):
+    """Solve A X = B for a block of right-hand sides with a direct method."""
+    if A.shape[0] <= DENSE_LIMIT:
+        return np.linalg.solve(A.toarray(), B)
+    return spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A").solve(B)
+
+
+def model_with_params(model: "Model", sigma0=None, k=None) -> "Model":
+    """A copy of `model` with new per-element sigma0 and/or k (the thermal matrix is rebuilt)."""
+    m = Model.__new__(Model)
+    m.__dict__.update({key: val for key, val in model.__dict__.items() if key != "_lu_T"})
+    if sigma0 is not None:
+        m.sigma0 = np.asarray(sigma0, dtype=np.float64).copy()
+    if k is not None:
+        m.k = np.asarray(k, dtype=np.float64).copy()
+        m.Kk = assemble(element_stiffness(m.k, m.vol, m.grad), m.tets, m.N)
+        p = m.p
+        m.A_T = ((p.rho_c / p.dt + p.perf) * m.M + m.Kk).tocsr()
+        m.A_T.sort_indices()
+    return m
+
+
+def step_tangent(model: "Model", T_old, dT_old, dsig0, dk):
+    """One lagged step and its forward-mode derivative.
+
+    dT_old [N, m], dsig0 [E, m], dk [E, m] are m directions; returns (T_new, V_new, dT_new [N, m]). Every term
+    differentiates the corresponding line of the step:
+      sigma_e = sigma0_e f_e, f_e = 1 + alpha (Tbar_e - 37)
+          d sigma_e = dsigma0_e f_e + sigma0_e alpha dTbar_e
+      K(sigma) V = 0 (lifted)      ->  K_ff dV_f = -(dK V)_f,  dK V = sum_e dsigma_e G_e V_e
+      F_a = sum_e sigma_e V_e^T G_e V_e / 4
+          dF_a = sum_e (dsigma_e V_e^T G_e V_e + 2 sigma_e V_e^T G_e dV_e) / 4
+      A_T T^{n+1} = (rho_c/dt) M T^n + perf T_a M 1 + F (lifted)
+          A_T,ff dT_f = ((rho_c/dt) M dT^n + dF - (dA_T T^{n+1}))_f,  dA_T T = sum_e dk_e G_e T_e
+    with G_e = vol_e grad(phi) grad(phi)^T and zero derivatives on Dirichlet rows.
+    """
+    p = model.p
+    tets = model.tets
+    N = model.N
+    dT_old = np.asarray(dT_old, dtype=np.float64)
+    dsig0 = np.asarray(dsig0, dtype=np.float64)
+    dk = np.asarray(dk, dtype=np.float64)
+    f = 1.0 + p.alpha_sigma * (element_mean(T_old, tets) - 37.0)
+    sig = model.sigma0 * f
+    A_V, b_V = model.system_V(T_old)
+    V = solve(A_V, b_V)
+    Q = joule(sig, V, tets, model.grad)
+    A_T, b_T = model.system_T(T_old, Q)
+    T_new = solve(A_T, b_T)
+
+    G = element_stiffness(np.ones(len(tets)), model.vol, model.grad)       # [E, 4, 4]
+    GV = np.einsum("eab,eb->ea", G, V[tets])                                 # [E, 4]
+    dTbar = dT_old[tets].mean(axis=1)                                        # [E, m]
+    dsig = dsig0 * f[:, None] + model.sigma0[:, None] * p.alpha_sigma * dTbar
+    rhs_V = -_scatter(GV[:, :, None] * dsig[:, None, :], tets, N)
+    rhs_V[model.bc_V] = 0.0
+    dV = _solve_many(A_V, rhs_V)
+    VGV = np.einsum("ea,ea->e", V[tets], GV)
+    VGdV = np.einsum("ea,eam->em", GV, dV[tets])
+    dq = 0.25 * (dsig * VGV[:, None] + 2.0 * sig[:, None] * VGdV)          # [E, m]
+    dF = _scatter(np.repeat(dq[:, None, :], 4, axis=1), tets, N)
+    GT = np.einsum("eab,eb->ea", G, T_new[tets])
+    rhs_T = (p.rho_c / p.dt) * (model.M @ dT_old) + dF - _scatter(GT[:, :, None] * dk[:, None, :], tets, N)
+    rhs_T[model.bc_T] = 0.0
+    dT_new = _solve_many(A_T, rhs_T)
+    return T_new, V, dT_new
+
+
+def gradient_dense_adjoint(model: "Model", n_steps, dL_dT_final, T0=None):
+    """Reverse accumulation with dense step Jacobians (tiny meshes only).
+
+    For each step n the Jacobians J_T = dT^{n+1}/dT^n [N, N], J_s = dT^{n+1}/dsigma0 [N, E] and
+    J_k = dT^{n+1}/dk [N, E] are built column by column with step_tangent; then, from lam = dL/dT^N backwards,
+    g_sigma0 += J_s^T lam, g_k += J_k^T lam, lam <- J_T^T lam. Returns (g_sigma0, g_k, dL/dT^0); the last one is
+    the derivative with respect to every entry of the initial state vector (Dirichlet entries included: they
+    enter the first step through sigma(Tbar) and the mass term).
+    """
+    if model.p.n_corrector != 1:
+        raise ValueError("the gradient is defined for the lagged step (n_corrector = 1)")
+    N, E = model.N, len(model.tets)
+    T = np.full(N, 37.0) if T0 is None else np.asarray(T0, dtype=np.float64).copy()
+    states = [T]
+    for _ in range(n_steps):
+        T, _, _ = model.step(T)
+        states.append(T)
+    lam = np.asarray(dL_dT_final, dtype=np.float64).copy()
+    g_s = np.zeros(E)
+    g_k = np.zeros(E)
+    for n in reversed(range(n_steps)):
+        Tn = states[n]
+        _, _, J_T = step_tangent(model, Tn, np.eye(N), np.zeros((E, N)), np.zeros((E, N)))
+        _, _, J_s = step_tangent(model, Tn, np.zeros((N, E)), np.eye(E), np.zeros((E, E)))
+        _, _, J_k = step_tangent(model, Tn, np.zeros((N, E)), np.zeros((E, E)), np.eye(E))
+        g_s += J_s.T @ lam
+        g_k += J_k.T @ lam
+        lam = J_T.T @ lam
+    return g_s, g_k, lam
+
+
+def loss_final_T(model: "Model", n_steps, target, T0=None):
+    """L = sum_i (T^N_i - target_i)^2 after n_steps lagged steps."""
+    T, _ = model.run(n_steps, T0)
+    return float(np.sum((T[-1] - np.asarray(target, dtype=np.float64)) ** 2))
+
+
+def gradient_fd(model: "Model", n_steps, target, which, elems, eps=1e-6, T0=None):
+    """Central finite differences of loss_final_T with respect to sigma0_e or k_e (which = "sigma0" | "k") for the
+    listed elements; the step is h = eps * |p_e| (relative perturbation)."""
+    base = model.sigma0 if which == "sigma0" else model.k
+    out = np.empty(len(elems))
+    for i, e in enumerate(elems):
+        h = eps * abs(base[e])
+        vals = []
+        for sgn in (1.0, -1.0):
+            q = base.copy()
+            q[e] += sgn * h
+            m = model_with_params(model, **{which: q})
+            vals.append(loss_final_T(m, n_steps, target, T0))
+        out[i] = (vals[0] - vals[1]) / (2.0 * h)
+    return out
