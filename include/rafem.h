@@ -253,6 +253,50 @@ int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t*
                           const double* b, double* x, double tol, int32_t max_iter, void* stream,
                           rafem_step_stats* stats);
 
+/* ---- differentiation form ----------------------------------------------------------------------------------
+ * Gradients of a loss on the final fields with respect to the per-element conductivities sigma0 and k (and the
+ * initial temperature), by the discrete adjoint of the lagged time step (n_corrector = 1): back-propagating
+ * through step n solves A_T mu = dL/dT^{n+1} and K(sigma(T^n)) nu = h (both systems are symmetric, so the
+ * transposed solves use the same solver), then accumulates the element terms. The forward states the backward
+ * pass needs are recomputed segment by segment from checkpoints written every `checkpoint_every` steps. The
+ * paper runs the forward model only (Sec. II-A); this form exists for calibrating tissue properties. */
+
+/* Reset the state to the initial condition of rafem_create (T = T_a, V = 0, Dirichlet values applied), step 0,
+ * predictor history cleared; ends any tape. */
+int rafem_reset(rafem_ctx* ctx);
+
+/* Replace the per-element sigma0 [E] and/or k [E] (either may be NULL to keep it; mesh element order; for a batch
+ * the instances' elements one after the other). on_device: 0 = host pointers (checked for finite values),
+ * 1 = device pointers (not checked). The constant thermal matrix is reassembled when k changes. Ends any tape. */
+int rafem_set_params(rafem_ctx* ctx, const double* sigma0, const double* k, int on_device);
+
+/* Start recording: the current state is the tape's origin (checkpoint 0); every later time step taken by
+ * rafem_run or rafem_solve_step stores a checkpoint of the state (fields, predictor history, statistics) each time
+ * (step - origin) is a multiple of checkpoint_every (>= 1). Checkpoint memory: 4 N doubles each, kept for reuse
+ * until rafem_destroy. Requires n_corrector = 1. rafem_set_state, rafem_reset, rafem_set_params and rafem_solve end
+ * the tape. Errors: BAD_INPUT. */
+int rafem_tape_begin(rafem_ctx* ctx, int32_t checkpoint_every);
+
+typedef struct rafem_adjoint_stats {
+    int32_t status;                  /* worst status of the adjoint solves                                   */
+    int32_t forward_status;          /* worst status of the recomputed forward steps                          */
+    int32_t steps;                   /* steps back-propagated (current step - tape origin)                    */
+    int32_t segments;                /* checkpoint segments recomputed                                         */
+    int64_t iters_V, iters_T;        /* Krylov iterations of the adjoint potential / thermal solves           */
+    double  ms;                      /* wall time of the call                                                  */
+} rafem_adjoint_stats;
+
+/* Back-propagate from the current state to the tape origin. Inputs (N doubles each; in_on_device 0 = host,
+ * 1 = device): dL_dT = dL/dT at the current step (required), dL_dV = dL/dV at the current step (nullable; the
+ * potential of the last step). Outputs (nullable; out_on_device as above): dL_dsigma0 [E] and dL_dk [E] in mesh
+ * element order, dL_dT0 [N] = dL/dT at the tape origin with respect to every entry of that state vector (Dirichlet
+ * entries included: they enter the first step through sigma(mean T) and the mass term). Entries of dL_dT and dL_dV
+ * on Dirichlet nodes are ignored for steps after the origin (those values are fixed). The forward state of the
+ * context is left exactly as it was. Returns the worse of the adjoint and recomputation statuses (OK or
+ * NOT_CONVERGED), or BAD_INPUT (no tape), OOM, CUDA. stats: nullable. */
+int rafem_adjoint(rafem_ctx* ctx, const double* dL_dT, const double* dL_dV, int in_on_device, double* dL_dsigma0,
+                  double* dL_dk, double* dL_dT0, int out_on_device, rafem_adjoint_stats* stats);
+
 /* Release every device and host resource of the context. NULL is accepted. */
 void rafem_destroy(rafem_ctx* ctx);
 

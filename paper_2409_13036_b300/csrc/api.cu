@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,6 +97,21 @@ struct rafem_ctx {
     bool tracing = false;
     rafem_trace trace{};
     cudaEvent_t ev[6] = {};
+    // differentiation: element order map, tape of checkpoints, adjoint workspace
+    int32_t* e_order = nullptr;      // [E] sorted element -> mesh element
+    double* p_tmpE = nullptr;        // [E] staging of parameter uploads / gradient downloads
+    int tape_every = 0;              // 0 = not recording
+    int64_t tape_origin = 0;
+    size_t n_ckpt = 0;
+    std::vector<void*> ckpt;         // checkpoint k: the state at step tape_origin + k * tape_every
+    void* ckpt_live = nullptr;       // the live state saved during rafem_adjoint
+    size_t ckpt_bytes = 0;
+    bool adj_ready = false;
+    int seg_cap = 0;
+    double *a_segT = nullptr, *a_segV = nullptr;   // [seg_cap + 1][N], [seg_cap][N]
+    double *a_lam = nullptr, *a_mu = nullptr, *a_nu = nullptr, *a_h = nullptr, *a_dv = nullptr;
+    double *a_ew4 = nullptr, *a_w = nullptr, *a_gs = nullptr, *a_gk = nullptr;
+    int32_t* a_count = nullptr;      // [iters_V, iters_T, adjoint status, recomputation status]
 };
 
 namespace {
@@ -214,6 +230,11 @@ __global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ xp
 }
 
 __global__ void k_reset_hist(StatsDev* s) { s->hist = 0; }
+
+__global__ void k_fold_worst(const StatsDev* s, int32_t* acc) {
+    const int w = s->worst, a = *acc;
+    *acc = (w < 0 || a < 0) ? min(w, a) : max(w, a);
+}
 
 __global__ void k_init_fields(int N, double T0, const uint8_t* bcT, const double* gT, const uint8_t* bcV,
                               const double* gV, double* T, double* V) {
@@ -377,6 +398,77 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     return cudaSuccess;
 }
 
+// The step graph (captured once; direct launches if capture is not possible).
+void ensure_graph(rafem_ctx* c) {
+    if (c->graph || c->graph_failed) return;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_step(c);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
+            if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) c->graph = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    if (!c->graph) {
+        c->graph_failed = true;
+        cudaGetLastError();  // clear a capture error; fall back to direct launches
+    }
+}
+
+// One lagged step: traced, graph or direct launches (all issue the same kernels on the same data).
+cudaError_t launch_step(rafem_ctx* c) {
+    if (c->tracing) return enqueue_step_traced(c);
+    ensure_graph(c);
+    if (c->graph) return cudaGraphLaunch(c->graph, c->stream);
+    return enqueue_step(c);
+}
+
+// ---- checkpoints of the differentiation tape: [T | V | T_hist | V_hist] (N doubles each), StatsDev, istats
+size_t state_bytes(const rafem_ctx* c) {
+    return 4 * (size_t)c->N * sizeof(double) + sizeof(StatsDev) + (size_t)c->n_inst * sizeof(rafem_step_stats);
+}
+
+cudaError_t state_copy(rafem_ctx* c, void* buf, bool save) {
+    char* p = static_cast<char*>(buf);
+    const size_t nb = (size_t)c->N * sizeof(double);
+    double* f[4] = {c->T, c->V, c->T_hist, c->V_hist};
+    cudaError_t e;
+    for (int q = 0; q < 4; ++q) {
+        e = save ? cudaMemcpyAsync(p + q * nb, f[q], nb, cudaMemcpyDeviceToDevice, c->stream)
+                 : cudaMemcpyAsync(f[q], p + q * nb, nb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    p += 4 * nb;
+    e = save ? cudaMemcpyAsync(p, c->stats, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream)
+             : cudaMemcpyAsync(c->stats, p, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    p += sizeof(StatsDev);
+    const size_t ib = (size_t)c->n_inst * sizeof(rafem_step_stats);
+    return save ? cudaMemcpyAsync(p, c->istats, ib, cudaMemcpyDeviceToDevice, c->stream)
+                : cudaMemcpyAsync(c->istats, p, ib, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+int tape_save(rafem_ctx* c, size_t k) {
+    while (c->ckpt.size() <= k) {
+        char* q = nullptr;
+        CK(dalloc(c, &q, state_bytes(c)));
+        c->ckpt.push_back(q);
+    }
+    CK(state_copy(c, c->ckpt[k], true));
+    c->n_ckpt = k + 1;
+    return RAFEM_OK;
+}
+
+// After a step that brought the context to step `now`: store a checkpoint when the tape asks for one.
+int tape_record(rafem_ctx* c, int64_t now) {
+    if (c->tape_every <= 0) return RAFEM_OK;
+    const int64_t rel = now - c->tape_origin;
+    if (rel <= 0 || rel % c->tape_every) return RAFEM_OK;
+    return tape_save(c, (size_t)(rel / c->tape_every));
+}
+
 int finish(rafem_ctx* c, rafem_step_stats* out, bool worst) {
     StatsDev h;
     CK(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -501,6 +593,7 @@ static int build_tiles(rafem_ctx* c, int rows_per_tile) {
 static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* stream, rafem_ctx* c, int n_inst,
                        const std::vector<int32_t>& node_off) {
     const int N = m->n_nodes, E = m->n_tets;
+    if ((int64_t)E * 16 >= (int64_t)INT32_MAX) return RAFEM_ERR_BAD_INPUT;  // slot codes and 4 e + a incidence
     c->n_inst = n_inst;
     c->inst_node_off = node_off;
     c->prm = *prm;
@@ -601,6 +694,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         k_s[ep] = m->k[e];
     }
     if (c->gather) build_incidence(N, E, nodes_soa, i_off, i_cnt, i_elem);
+    std::vector<int32_t> order32(order.begin(), order.end());
     // ---- device buffers
     const size_t nnz = (size_t)c->nnz_store;
     const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
@@ -658,6 +752,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->instT, n_inst));
     CK(dalloc(c, &c->istats, n_inst));
     CK(dalloc(c, &c->bar, 1));
+    CK(dalloc(c, &c->e_order, E));
     // ---- uploads
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->rp, dev_rp.data(), dev_rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -669,6 +764,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(cudaMemcpyAsync(c->diag, diag.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_nodes, nodes_soa.data(), nodes_soa.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->e_order, order32.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_sig0, sig_s.data(), E * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_k, k_s.data(), E * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->xyz, m->coords, 3 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -799,6 +895,7 @@ int rafem_assemble(rafem_ctx* c, int which) {
 
 int rafem_solve(rafem_ctx* c, int which, rafem_step_stats* stats) {
     if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
     k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     CK(cudaGetLastError());
     CK(enqueue_solve(c, which, which == RAFEM_SYS_V ? c->bV : c->bT, which == RAFEM_SYS_V ? c->V : c->T));
@@ -821,7 +918,9 @@ int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     if (c->prm.n_corrector <= 1) {
         CK(c->tracing ? enqueue_step_traced(c) : enqueue_step(c));
-        return finish(c, stats, false);
+        const int s = finish(c, stats, false);
+        const int t = tape_record(c, c->step);
+        return t != RAFEM_OK ? t : s;
     }
     // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n
     CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -876,30 +975,11 @@ int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
         if (last) *last = h;
         return worst;
     }
-    if (!c->graph && !c->graph_failed) {
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e1 = enqueue_step(c);
-            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-            if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
-                if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) c->graph = nullptr;
-            }
-            if (g) cudaGraphDestroy(g);
-        }
-        if (!c->graph) {
-            c->graph_failed = true;
-            cudaGetLastError();  // clear a capture error; fall back to direct launches
-        }
-    }
+    const int64_t s0 = c->step;
     for (int i = 0; i < n_steps; ++i) {
-        if (c->tracing) {
-            CK(enqueue_step_traced(c));
-        } else if (c->graph) {
-            CK(cudaGraphLaunch(c->graph, c->stream));
-        } else {
-            CK(enqueue_step(c));
-        }
+        CK(launch_step(c));
+        const int t = tape_record(c, s0 + i + 1);
+        if (t != RAFEM_OK) return t;
     }
     return finish(c, last, true);
 }
@@ -928,6 +1008,7 @@ int rafem_get_field(rafem_ctx* c, int which, double* dst, int on_device) {
 
 int rafem_set_state(rafem_ctx* c, const double* T, const double* V, int on_device, int64_t step) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->tracing) {
         for (int i = 0; i < 2; ++i)
@@ -1041,6 +1122,226 @@ int rafem_batch_stats(rafem_ctx* c, rafem_step_stats* per_instance) {
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return RAFEM_OK;
+}
+
+int rafem_reset(rafem_ctx* c) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
+    const int N = c->N;
+    k_init_fields<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->prm.T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(c->T_hist, 0, N * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->V_hist, 0, N * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->istats, 0, c->n_inst * sizeof(rafem_step_stats), c->stream));
+    CK(cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream));
+    c->step = 0;
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on_device) {
+    if (!c || (!sigma0 && !k)) return RAFEM_ERR_BAD_INPUT;
+    const int E = c->E;
+    if (!on_device) {
+        for (const double* q : {sigma0, k})
+            if (q)
+                for (int e = 0; e < E; ++e)
+                    if (!std::isfinite(q[e])) return RAFEM_ERR_NONFINITE;
+    }
+    if (!c->p_tmpE) CK(dalloc(c, &c->p_tmpE, E));
+    c->tape_every = 0;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t st = c->stream;
+    if (sigma0) {
+        CK(cudaMemcpyAsync(c->p_tmpE, sigma0, E * sizeof(double), kind, st));
+        CK(launch_permute(E, c->e_order, c->p_tmpE, c->e_sig0, 0, st));
+        if (c->gather)
+            CK(launch_fill_cval(c->gather_nc, c->gd.celem, c->gather_cg, c->e_sig0, c->e_G, E,
+                                const_cast<double*>(c->gd.cval), st));
+    }
+    if (k) {
+        CK(cudaMemcpyAsync(c->p_tmpE, k, E * sizeof(double), kind, st));
+        CK(launch_permute(E, c->e_order, c->p_tmpE, c->e_k, 0, st));
+        // constant thermal matrix and rhs part: every free slot is stored by its first writer, Dirichlet rows
+        // keep the identity; the constant rhs accumulates and restarts from zero
+        CK(cudaMemsetAsync(c->bTc, 0, c->N * sizeof(double), st));
+        const double c_matrix = c->prm.rho_c / c->prm.dt + c->prm.perf;
+        for (int q = 0; q < c->n_colors; ++q)
+            CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
+                                 c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return RAFEM_OK;
+}
+
+int rafem_tape_begin(rafem_ctx* c, int32_t checkpoint_every) {
+    if (!c || checkpoint_every < 1 || c->prm.n_corrector != 1) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
+    c->n_ckpt = 0;
+    const int s = tape_save(c, 0);
+    if (s != RAFEM_OK) return s;
+    c->tape_every = checkpoint_every;
+    c->tape_origin = c->step;
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+namespace {
+
+// Workspace of the adjoint, and the node incidence + nodal mass when the assembly mode did not build them.
+int ensure_adjoint(rafem_ctx* c) {
+    const int N = c->N, E = c->E;
+    if (!c->gd.ioff) {
+        std::vector<int32_t> nodes_soa(4 * (size_t)E), i_off, i_cnt, i_elem;
+        CK(cudaMemcpyAsync(nodes_soa.data(), c->e_nodes, nodes_soa.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        build_incidence(N, E, nodes_soa, i_off, i_cnt, i_elem);
+        int32_t *ioff, *icnt, *ielem;
+        double* mT;
+        CK(dalloc(c, &ioff, i_off.size()));
+        CK(dalloc(c, &icnt, i_cnt.size()));
+        CK(dalloc(c, &ielem, i_elem.size()));
+        CK(dalloc(c, &mT, N));
+        CK(cudaMemcpyAsync(ioff, i_off.data(), i_off.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(icnt, i_cnt.data(), i_cnt.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(ielem, i_elem.data(), i_elem.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        c->gd.ioff = ioff;
+        c->gd.icnt = icnt;
+        c->gd.ielem = ielem;
+        c->gd.mT = mT;
+        CK(launch_node_mass(c->gd, N, c->e_vol, c->prm.rho_c / c->prm.dt, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (!c->adj_ready) {
+        CK(dalloc(c, &c->a_lam, N));
+        CK(dalloc(c, &c->a_mu, N));
+        CK(dalloc(c, &c->a_nu, N));
+        CK(dalloc(c, &c->a_h, N));
+        CK(dalloc(c, &c->a_dv, N));
+        CK(dalloc(c, &c->a_ew4, 4 * (size_t)E));
+        CK(dalloc(c, &c->a_w, E));
+        CK(dalloc(c, &c->a_gs, E));
+        CK(dalloc(c, &c->a_gk, E));
+        CK(dalloc(c, &c->a_count, 4));
+        char* live = nullptr;
+        CK(dalloc(c, &live, state_bytes(c)));
+        c->ckpt_live = live;
+        if (!c->p_tmpE) CK(dalloc(c, &c->p_tmpE, E));
+        c->adj_ready = true;
+    }
+    if (c->seg_cap < c->tape_every) {
+        CK(dalloc(c, &c->a_segT, (size_t)(c->tape_every + 1) * N));
+        CK(dalloc(c, &c->a_segV, (size_t)c->tape_every * N));
+        c->seg_cap = c->tape_every;
+    }
+    return RAFEM_OK;
+}
+
+int merge_status(int a, int b) {
+    if (a < 0 || b < 0) return std::min(a, b);
+    return std::max(a, b);
+}
+
+}  // namespace
+
+int rafem_adjoint(rafem_ctx* c, const double* dL_dT, const double* dL_dV, int in_on_device, double* dL_dsigma0,
+                  double* dL_dk, double* dL_dT0, int out_on_device, rafem_adjoint_stats* out) {
+    if (!c || !dL_dT || c->tape_every <= 0) return RAFEM_ERR_BAD_INPUT;
+    const auto t_start = std::chrono::steady_clock::now();
+    const int64_t nsteps = c->step - c->tape_origin;
+    const int every = c->tape_every;
+    const int64_t n_seg = (nsteps + every - 1) / every;
+    if (nsteps < 0 || nsteps > INT32_MAX || (size_t)n_seg > c->n_ckpt) return RAFEM_ERR_INTERNAL;
+    {
+        const int s = ensure_adjoint(c);
+        if (s != RAFEM_OK) return s;
+    }
+    const int N = c->N, E = c->E;
+    const size_t nb = (size_t)N * sizeof(double);
+    cudaStream_t st = c->stream;
+    const cudaMemcpyKind in_kind = in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double alpha = c->prm.alpha_sigma, c_mass = c->prm.rho_c / c->prm.dt;
+    CK(cudaMemsetAsync(c->a_gs, 0, E * sizeof(double), st));
+    CK(cudaMemsetAsync(c->a_gk, 0, E * sizeof(double), st));
+    CK(cudaMemsetAsync(c->a_mu, 0, nb, st));
+    CK(cudaMemsetAsync(c->a_nu, 0, nb, st));
+    CK(cudaMemsetAsync(c->a_count, 0, 4 * sizeof(int32_t), st));
+    CK(cudaMemcpyAsync(c->a_h, dL_dT, nb, in_kind, st));
+    if (dL_dV) {
+        CK(cudaMemcpyAsync(c->a_lam, dL_dV, nb, in_kind, st));
+        CK(launch_mask(N, c->bcV, c->a_lam, c->a_dv, st));
+    }
+    int fwd_status = RAFEM_OK;
+    if (nsteps == 0) {
+        CK(cudaMemcpyAsync(c->a_lam, c->a_h, nb, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(launch_mask(N, c->bcT, c->a_h, c->a_lam, st));
+        CK(state_copy(c, c->ckpt_live, true));
+        const int64_t live_step = c->step;
+        const int saved_every = c->tape_every;
+        c->tape_every = 0;  // the recomputation must not write checkpoints
+        for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
+            const int64_t b0 = seg * every, b1 = std::min<int64_t>(b0 + every, nsteps);
+            const int L = (int)(b1 - b0);
+            CK(state_copy(c, c->ckpt[seg], false));
+            CK(cudaMemcpyAsync(c->a_segT, c->T, nb, cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < L; ++j) {
+                CK(launch_step(c));
+                CK(cudaMemcpyAsync(c->a_segT + (size_t)(j + 1) * N, c->T, nb, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(c->a_segV + (size_t)j * N, c->V, nb, cudaMemcpyDeviceToDevice, st));
+            }
+            k_fold_worst<<<1, 1, 0, st>>>(c->stats, c->a_count + 3);
+            CK(cudaGetLastError());
+            for (int j = L - 1; j >= 0; --j) {
+                const int64_t n = b0 + j;
+                const double* Tn = c->a_segT + (size_t)j * N;
+                const double* T1 = c->a_segT + (size_t)(j + 1) * N;
+                const double* V1 = c->a_segV + (size_t)j * N;
+                CK(enqueue_solve(c, RAFEM_SYS_T, c->a_lam, c->a_mu));
+                CK(launch_adj_count(c->instT, c->n_inst, c->bar, c->a_count, 1, st));
+                CK(enqueue_assemble(c, RAFEM_SYS_V, Tn, Tn));
+                CK(launch_adj_h(c->el, c->gd, N, Tn, V1, c->a_mu, alpha, c->bcV,
+                                (dL_dV && n == nsteps - 1) ? c->a_dv : nullptr, c->a_ew4, c->a_h, st));
+                CK(enqueue_solve(c, RAFEM_SYS_V, c->a_h, c->a_nu));
+                CK(launch_adj_count(c->instV, c->n_inst, c->bar, c->a_count, 0, st));
+                CK(launch_adj_g(c->el, c->gd, N, Tn, V1, T1, c->a_mu, c->a_nu, alpha, c_mass, c->bcT, n != 0,
+                                c->a_gs, c->a_gk, c->a_w, c->a_lam, st));
+            }
+        }
+        CK(state_copy(c, c->ckpt_live, false));
+        c->step = live_step;
+        c->tape_every = saved_every;
+    }
+    // outputs (gradients back in mesh element order)
+    const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dL_dsigma0) {
+        double* dst = out_on_device ? dL_dsigma0 : c->p_tmpE;
+        CK(launch_permute(E, c->e_order, c->a_gs, dst, 1, st));
+        if (!out_on_device) CK(cudaMemcpyAsync(dL_dsigma0, c->p_tmpE, E * sizeof(double), out_kind, st));
+    }
+    if (dL_dk) {
+        if (!out_on_device) CK(cudaStreamSynchronize(st));  // p_tmpE is reused
+        double* dst = out_on_device ? dL_dk : c->p_tmpE;
+        CK(launch_permute(E, c->e_order, c->a_gk, dst, 1, st));
+        if (!out_on_device) CK(cudaMemcpyAsync(dL_dk, c->p_tmpE, E * sizeof(double), out_kind, st));
+    }
+    if (dL_dT0) CK(cudaMemcpyAsync(dL_dT0, c->a_lam, nb, out_kind, st));
+    int32_t cnt[4];
+    CK(cudaMemcpyAsync(cnt, c->a_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int adj_status = cnt[2];
+    fwd_status = cnt[3];
+    if (out) {
+        out->status = adj_status;
+        out->forward_status = fwd_status;
+        out->steps = (int32_t)nsteps;
+        out->segments = (int32_t)n_seg;
+        out->iters_V = cnt[0];
+        out->iters_T = cnt[1];
+        out->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return merge_status(adj_status, fwd_status);
 }
 
 int rafem_set_schedule(rafem_ctx* c, int32_t rows_per_tile) {

@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_rhsT_gather(int N, const int32_t* 
     const int off = __ldg(ioff + s) + lane, P = __ldg(icnt + s);
     double acc = 0.0;
     for (int m = 0; m < P; ++m) {
-        const int e = __ldg(ielem + off + 32 * m);
-        if (e >= 0) acc += w[e];
+        const int v = __ldg(ielem + off + 32 * m);
+        if (v >= 0) acc += w[v >> 2];
     }
     b[row] = bconst[row] + mT[row] * To[row] + acc;
 }
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(kThreads) k_node_mass(int N, const int32_t* __
     const int off = __ldg(ioff + s) + lane, P = __ldg(icnt + s);
     double acc = 0.0;
     for (int m = 0; m < P; ++m) {
-        const int e = __ldg(ielem + off + 32 * m);
-        if (e >= 0) acc += vol[e];
+        const int v = __ldg(ielem + off + 32 * m);
+        if (v >= 0) acc += vol[v >> 2];
     }
     mT[row] = c_mass * acc * (1.0 / 20.0);
 }

@@ -30,7 +30,7 @@ struct GatherData {
     const int32_t* celem = nullptr;  // element (sorted order) per contribution
     const int32_t* ioff = nullptr;   // [N/32] node -> element incidence, per slice
     const int32_t* icnt = nullptr;
-    const int32_t* ielem = nullptr;  // -1 = padding
+    const int32_t* ielem = nullptr;  // 4 e + a (element, local vertex); -1 = padding
     double* ework = nullptr;         // [E] per-element factor (f_e, then w_e)
     double* mT = nullptr;            // [N] (rho_c/dt) sum vol/20
 };
@@ -142,5 +142,27 @@ struct SolveArgs {
 // many lanes per row.
 int krylov_max_blocks(int lanes, int precision, int* block_threads);
 cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st);
+
+}  // namespace rafem
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// Differentiation form (adjoint.cu). gd must hold the node incidence (4 e + a entries) and mT.
+// ------------------------------------------------------------------------------------------------------------
+// h = sum over incident (e, a) of 2 s_e sigma_e (G_e V_e)_a (+ extra) on free rows of bcV, 0 on Dirichlet rows;
+// ew4 is [4][E] scratch.
+cudaError_t launch_adj_h(const ElemData& el, const GatherData& gd, int N, const double* Tn, const double* V,
+                         const double* mu, double alpha, const uint8_t* bcV, const double* extra, double* ew4,
+                         double* h, cudaStream_t st);
+// gs += dL/dsigma0, gk += dL/dk of one step (sorted element order); lam = dL/dT^n (w is [E] scratch).
+cudaError_t launch_adj_g(const ElemData& el, const GatherData& gd, int N, const double* Tn, const double* V,
+                         const double* T1, const double* mu, const double* nu, double alpha, double c_mass,
+                         const uint8_t* bcT, int zero_dirichlet, double* gs, double* gk, double* w, double* lam,
+                         cudaStream_t st);
+cudaError_t launch_mask(int N, const uint8_t* bc, const double* in, double* out, cudaStream_t st);
+cudaError_t launch_permute(int n, const int32_t* perm, const double* in, double* out, int scatter, cudaStream_t st);
+cudaError_t launch_adj_count(const InstState* inst, int n_inst, const GridBarrier* bar, int32_t* acc, int slot,
+                             cudaStream_t st);
 
 }  // namespace rafem

@@ -264,7 +264,7 @@ void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::v
         for (int64_t ep = 0; ep < E; ++ep) {
             const int r = nodes_soa[(int64_t)a * E + ep];
             const int s = r / SELL_C, l = r % SELL_C;
-            inc_elem[inc_off[s] + (int64_t)SELL_C * fill[r]++ + l] = (int32_t)ep;
+            inc_elem[inc_off[s] + (int64_t)SELL_C * fill[r]++ + l] = (int32_t)(4 * ep + a);
         }
 }
 

@@ -41,8 +41,9 @@ void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::
                   std::vector<int32_t>& gather_off, std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem,
                   std::vector<uint8_t>& cgidx);
 
-// Node -> element incidence (sorted element order) in the SELL-32 slice layout: element m of row 32 s + l at
-// inc_off[s] + 32 m + l for m < inc_cnt[s]; -1 marks padding.
+// Node -> element incidence (sorted element order) in the SELL-32 slice layout: entry m of row 32 s + l at
+// inc_off[s] + 32 m + l for m < inc_cnt[s] holds 4 e + a (element e, local vertex a); -1 marks padding.
+// Requires 4 E < 2^31.
 void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::vector<int32_t>& inc_off,
                      std::vector<int32_t>& inc_cnt, std::vector<int32_t>& inc_elem);
 

@@ -78,6 +78,15 @@ class rafem_trace(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rafem_adjoint_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("forward_status", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("segments", ctypes.c_int32), ("iters_V", ctypes.c_int64), ("iters_T", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -118,6 +127,11 @@ def lib() -> ctypes.CDLL:
         "rafem_set_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
         "rafem_get_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]),
+        "rafem_reset": (ctypes.c_int, [vp]),
+        "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "rafem_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_int,
+                                         ctypes.POINTER(rafem_adjoint_stats)]),
         "rafem_destroy": (None, [vp]),
         "rafem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -207,6 +221,7 @@ class Context:
         self.offsets = offs
         self.N = int(offs[-1])
         self.n_inst = int(n.value)
+        self.n_tets = int(sum(int(np.asarray(m.tets).shape[0]) for m in meshes))
         return self
 
     def batch_stats(self):
@@ -235,6 +250,7 @@ class Context:
                                ctypes.byref(self._ctx))
         _check(s, "rafem_create")
         self._keep = None
+        self.n_tets = int(t.shape[0])
         self.n_inst = 1
         self.offsets = np.array([0, self.N], np.int32)
 
@@ -347,6 +363,50 @@ class Context:
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+    # -- differentiation form -------------------------------------------------------------------------------
+    def reset(self):
+        _check(lib().rafem_reset(self._ctx), "rafem_reset")
+
+    def set_params(self, sigma0=None, k=None):
+        """Host arrays (numpy) or device tensors/pointers of E doubles, mesh element order."""
+        if sigma0 is None and k is None:
+            raise ValueError("nothing to set")
+        host = [isinstance(x, np.ndarray) for x in (sigma0, k) if x is not None]
+        if any(host) and not all(host):
+            raise ValueError("sigma0 and k must both be host arrays or both device buffers")
+        if host and host[0]:
+            s0 = None if sigma0 is None else np.ascontiguousarray(sigma0, dtype=np.float64)
+            kk = None if k is None else np.ascontiguousarray(k, dtype=np.float64)
+            _check(lib().rafem_set_params(self._ctx, None if s0 is None else s0.ctypes.data,
+                                          None if kk is None else kk.ctypes.data, 0), "rafem_set_params")
+        else:
+            _check(lib().rafem_set_params(self._ctx, _dev(sigma0), _dev(k), 1), "rafem_set_params")
+
+    def tape_begin(self, checkpoint_every: int):
+        _check(lib().rafem_tape_begin(self._ctx, int(checkpoint_every)), "rafem_tape_begin")
+
+    def adjoint_ptr(self, dL_dT, dL_dV=None, in_on_device=1, dsigma0=None, dk=None, dT0=None, out_on_device=1):
+        """rafem_adjoint with raw pointers (ints) or tensors; returns (status, stats dict)."""
+        st = rafem_adjoint_stats()
+        s = lib().rafem_adjoint(self._ctx, _dev(dL_dT), _dev(dL_dV), int(in_on_device), _dev(dsigma0), _dev(dk),
+                                _dev(dT0), int(out_on_device), ctypes.byref(st))
+        return _check(s, "rafem_adjoint"), st.as_dict()
+
+    def adjoint(self, dL_dT, dL_dV=None, n_tets: int | None = None):
+        """Host form: numpy dL/dT (and dL/dV) in, numpy (dL/dsigma0, dL/dk, dL/dT0, stats) out."""
+        if n_tets is None:
+            n_tets = self.n_tets
+        gT = np.ascontiguousarray(dL_dT, dtype=np.float64)
+        gV = None if dL_dV is None else np.ascontiguousarray(dL_dV, dtype=np.float64)
+        gs = np.empty(n_tets)
+        gk = np.empty(n_tets)
+        g0 = np.empty(self.N)
+        st = rafem_adjoint_stats()
+        s = lib().rafem_adjoint(self._ctx, gT.ctypes.data, None if gV is None else gV.ctypes.data, 0,
+                                gs.ctypes.data, gk.ctypes.data, g0.ctypes.data, 0, ctypes.byref(st))
+        _check(s, "rafem_adjoint")
+        return gs, gk, g0, st.as_dict()
 
 
 def pcg_csr_noalloc(n_rows, row_ptr, col, vals, b, x, tol=1e-10, max_iter=20000, stream=None):
