@@ -384,3 +384,91 @@ def gradient_fd(model: "Model", n_steps, target, which, elems, eps=1e-6, T0=None
             vals.append(loss_final_T(m, n_steps, target, T0))
         out[i] = (vals[0] - vals[1]) / (2.0 * h)
     return out
+
+
+# ----------------------------------------------------------------------------------------------------------
+# ILU(0) preconditioner (Sec. II-B: preconditioning accelerates the Krylov solvers). The factorisation is taken
+# on a symmetric permutation P A P^T of the system in which rows of one level never depend on each other:
+#   "multicolor": nodes sorted (stably) by a greedy colouring of the matrix graph (each node takes the smallest
+#                 colour not used by an already-coloured neighbour, nodes visited in index order); levels = colours;
+#   "natural":    nodes sorted (stably) by dependency level in the given numbering,
+#                 lev(i) = 1 + max{lev(j) : j < i, a_ij != 0} (0 if none); levels = these sets.
+# ----------------------------------------------------------------------------------------------------------
+
+def greedy_node_colors(A):
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    color = np.full(N, -1, dtype=np.int64)
+    for i in range(N):
+        used = {int(color[j]) for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and color[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        color[i] = c
+    return color
+
+
+def dependency_levels(A):
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    lev = np.zeros(N, dtype=np.int64)
+    for i in range(N):
+        lower = [j for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j < i]
+        lev[i] = 1 + max(lev[j] for j in lower) if lower else 0
+    return lev
+
+
+def ilu_permutation(A, order="multicolor"):
+    """(perm, level_of_new_row): perm[new] = old row; rows sorted stably by colour or dependency level."""
+    key = greedy_node_colors(A) if order == "multicolor" else dependency_levels(A)
+    perm = np.argsort(key, kind="stable")
+    return perm, key[perm]
+
+
+def permute_symmetric(A, perm):
+    """P A P^T with (P A P^T)[a, b] = A[perm[a], perm[b]], indices sorted."""
+    B = sp.csr_matrix(A)[perm][:, perm].tocsr()
+    B.sort_indices()
+    return B
+
+
+def ilu0(A):
+    """ILU(0) on the stored pattern of A (CSR, sorted indices, every diagonal stored), row by row (IKJ form):
+    for row i, for each stored k < i in increasing order: w_k <- w_k / u_kk, then w_j <- w_j - w_k u_kj for every
+    stored j > k of row k that is also stored in row i; no fill outside the pattern. Returns F on A's pattern with
+    the strictly lower part = L (unit diagonal implied) and the diagonal + upper part = U."""
+    A = sp.csr_matrix(A, dtype=np.float64, copy=True)
+    A.sort_indices()
+    ip, ix, F = A.indptr, A.indices, A.data
+    N = A.shape[0]
+    diag = np.empty(N, dtype=np.int64)
+    for i in range(N):
+        d = np.flatnonzero(ix[ip[i]:ip[i + 1]] == i)
+        if d.size != 1:
+            raise ValueError("every diagonal entry must be stored")
+        diag[i] = ip[i] + d[0]
+    for i in range(N):
+        pos = {int(ix[q]): q for q in range(ip[i], ip[i + 1])}
+        for q in range(ip[i], diag[i]):
+            k = int(ix[q])
+            F[q] = F[q] / F[diag[k]]
+            for t in range(diag[k] + 1, ip[k + 1]):
+                j = int(ix[t])
+                if j in pos:
+                    F[pos[j]] -= F[q] * F[t]
+    return sp.csr_matrix((F, ix.copy(), ip.copy()), shape=A.shape)
+
+
+def ilu0_split(F):
+    """(L, U) dense-free: L = I + strictly lower part of F, U = diagonal + upper part of F."""
+    F = sp.csr_matrix(F)
+    L = sp.tril(F, k=-1, format="csr") + sp.identity(F.shape[0], format="csr")
+    U = sp.triu(F, k=0, format="csr")
+    return L.tocsr(), U.tocsr()
+
+
+def ilu0_apply(F, r):
+    """z = U^{-1} L^{-1} r (forward then backward substitution)."""
+    L, U = ilu0_split(F)
+    y = spla.spsolve_triangular(L, np.asarray(r, dtype=np.float64), lower=True, unit_diagonal=True)
+    return spla.spsolve_triangular(U, y, lower=False)

@@ -7,6 +7,7 @@ import dataclasses
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from oracle import rafem_oracle as O
 from paper_2409_13036_b300 import meshgen as mg
@@ -256,3 +257,81 @@ def test_corrector_converges_to_fixed_point():
     lag = O.Model(m, dataclasses.replace(p, n_corrector=1))
     T1l, _, _ = lag.step(T0)
     assert np.abs(T1l - T1).max() > 1e-6
+
+
+# ---- ILU(0) ------------------------------------------------------------------------------------------------
+
+def _potential_system(n=5, seed=3):
+    m = mg.cube_mesh(n, jitter=0.1, seed=seed, sigma0="lognormal")
+    A, _ = O.Model(m).system_V(np.full(m.n_nodes, 45.0))
+    return A
+
+
+def test_ilu0_product_matches_matrix_on_pattern():
+    """Defining property of ILU(0): with L unit lower and U upper on the pattern of A, (L U)_ij = a_ij for every
+    stored (i, j); the product differs from A only outside the pattern (the dropped fill), and that fill is not
+    zero for a 3-D stencil (so the test would notice a factorisation that silently kept it)."""
+    A = _potential_system()
+    L, U = O.ilu0_split(O.ilu0(A))
+    P = (L @ U).toarray()
+    Ad = A.toarray()
+    patt = sp.csr_matrix((np.ones_like(A.data), A.indices, A.indptr), shape=A.shape).toarray() > 0
+    assert np.abs(P - Ad)[patt].max() <= 1e-14 * np.abs(Ad).max()
+    assert np.abs(P[~patt]).max() > 1e-6 * np.abs(Ad).max()
+
+
+def test_ilu0_is_exact_lu_without_fill():
+    """A tridiagonal matrix has no fill, so ILU(0) is its exact LU: L U = A everywhere, and L, U equal the
+    Doolittle factors of the dense matrix (no pivoting for a diagonally dominant matrix)."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(4)
+    n = 40
+    off = rng.uniform(-1.0, 1.0, n - 1)
+    A = sp.diags([off, 4.0 + rng.random(n), rng.uniform(-1.0, 1.0, n - 1)], [-1, 0, 1], format="csr")
+    L, U = O.ilu0_split(O.ilu0(A))
+    Pm, Ld, Ud = sla.lu(A.toarray())
+    assert np.array_equal(Pm, np.eye(n))
+    np.testing.assert_allclose(L.toarray(), Ld, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(U.toarray(), Ud, rtol=0, atol=1e-13)
+
+
+def test_ilu0_apply_inverts_the_factors():
+    """z = ilu0_apply(F, r) solves (L U) z = r."""
+    A = _potential_system(4, 8)
+    F = O.ilu0(A)
+    L, U = O.ilu0_split(F)
+    r = np.random.default_rng(5).normal(size=A.shape[0])
+    z = O.ilu0_apply(F, r)
+    np.testing.assert_allclose((L @ (U @ z)), r, rtol=0, atol=1e-12 * np.abs(r).max())
+
+
+def test_ilu_orderings_are_valid_level_orders():
+    """Greedy colours: no two neighbours share a colour (8 colours on the Kuhn lattice). Dependency levels: every
+    stored lower neighbour of a row lies on an earlier level (3 n + 1 levels on an (n+1)^3 lattice). After the
+    permutation the levels are contiguous and non-decreasing."""
+    n = 5
+    A = _potential_system(n)
+    col = O.greedy_node_colors(A)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    offd = rows != A.indices
+    assert np.all(col[rows[offd]] != col[A.indices[offd]])
+    assert col.max() + 1 == 8
+    lev = O.dependency_levels(A)
+    low = A.indices < rows
+    assert np.all(lev[A.indices[low]] < lev[rows[low]])
+    assert lev.max() + 1 == 3 * n + 1
+    for order in ("multicolor", "natural"):
+        perm, lv = O.ilu_permutation(A, order)
+        assert np.array_equal(np.sort(perm), np.arange(A.shape[0]))
+        assert np.all(np.diff(lv) >= 0)
+
+
+def test_ilu0_natural_level_sort_is_a_relabelling():
+    """Sorting rows by dependency level keeps the relative order of every pair of neighbours, so the ILU(0) of the
+    level-sorted matrix is the level-sorted ILU(0) of the original: P F(A) P^T = F(P A P^T) (to rounding)."""
+    A = _potential_system(4, 9)
+    perm, _ = O.ilu_permutation(A, "natural")
+    F1 = O.permute_symmetric(O.ilu0(A), perm)
+    F2 = O.ilu0(O.permute_symmetric(A, perm))
+    np.testing.assert_array_equal(F1.indices, F2.indices)
+    np.testing.assert_allclose(F1.data, F2.data, rtol=1e-13, atol=1e-14 * np.abs(F1.data).max())
