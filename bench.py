@@ -163,6 +163,16 @@ def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_byte
     return iters * inner + (refinements + 1) * outer
 
 
+def alg_bytes_ilu(Np: int, nnz_p: int, iters: float) -> float:
+    """Algorithmic HBM bytes of one ILU(0)-PCG solve launch (level-ordered SELL-32, 32-bit columns).
+    Per iteration: phase A streams A (12 B per stored entry) and reads z, p, q and writes p, q (40 Np); phase B
+    reads x, p, q, r and writes x, r (48 Np, plus z on level-0 rows); the forward and backward level sweeps stream
+    the factors once (12 B per stored entry) and read r twice, write z twice and read it once (40 Np). Start-up
+    (gather, residual, first preconditioning) and the final true residual add about two iterations' worth."""
+    per_iter = 24 * nnz_p + 136 * Np
+    return (iters + 2) * per_iter
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -184,12 +194,16 @@ def reference_arm(args):
     return 0
 
 
-def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks):
+def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, precond=0):
     """Warm up, time K steps with CUDA events on the context's stream, then a few traced steps."""
     stream = torch.cuda.Stream()
-    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision)
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision, precond=precond)
     N, nnz, n_colors = ctx.pattern_info()
     layout = ctx.layout_info()
+    if precond == rafem.RAFEM_PRECOND_ILU0:
+        info = ctx.precond_info()
+        layout["ilu"] = {"levels": info["n_levels"], "padded_rows": info["padded_rows"],
+                         "nnz_stored": info["nnz_stored"]}
     s, st = ctx.run(args.warmup)
     if s < 0:
         raise RuntimeError(f"warm-up failed: {rafem.status_string(s)}")
@@ -231,7 +245,11 @@ def roofline(res, mixed, peaks, peak_kind):
     iters = tr["iters_V"] / steps
     cb = res["layout"]["column_bytes"]
     code = res["layout"]["kernel_code"]
-    if mixed:
+    if "ilu" in res["layout"]:
+        ref = 0.0
+        alg = alg_bytes_ilu(res["layout"]["ilu"]["padded_rows"], res["layout"]["ilu"]["nnz_stored"], iters)
+        kern = "k_ilu_pcg"
+    elif mixed:
         ref = tr["refine_V"] / steps
         alg = alg_bytes_mixed(N, nnz, iters, ref, cb)
         kern = f"k_cg_mixed<{code}>"
@@ -305,6 +323,77 @@ def measure_batch(rafem, torch, mg, args):
     return out
 
 
+def measure_adjoint(rafem, torch, mg, args):
+    """Differentiation form on the 64^3-cell workload (274,625 nodes): loss = |T^N - T_target|^2 after N steps,
+    with T_target from the same forward model run with the hidden two-region sigma0 (tumour sphere, 0.5 S/m
+    inside 0.333 S/m liver). Parameters are FP32 tensors (uniform liver sigma0 and k); the gradient comes from
+    the torch.autograd bridge (rafem_tape_begin + rafem_adjoint, checkpoint every 10 steps). Central differences
+    (relative step 1e-6, FP64 parameters) on 32 seeded random elements check dL/dsigma0."""
+    import numpy as np
+    from paper_2409_13036_b300.adjoint import final_temperature
+    n_steps, every, n_fd = args.adjoint_steps, 10, args.fd_elements
+    mesh = mg.cube_mesh(64, jitter=0.10, seed=mg.SEED_BASE + 4)
+    dev = torch.device("cuda")
+    ctx = rafem.Context(mesh, tol=1e-12)
+    # target field: the same forward model with the hidden tumour conductivity
+    ctx.set_params(mg.tumour_sigma0(mesh), mesh.k)
+    ctx.reset()
+    ctx.run(n_steps)
+    target = torch.empty(mesh.n_nodes, dtype=torch.float64, device=dev)
+    ctx.get_field_device(rafem.RAFEM_SYS_T, target)
+    s0 = torch.tensor(mesh.sigma0, dtype=torch.float32, device=dev, requires_grad=True)
+    kk = torch.tensor(mesh.k, dtype=torch.float32, device=dev, requires_grad=True)
+    # warm-up: one full forward + backward (graph capture, checkpoint and adjoint workspace, lazy module loads)
+    ((final_temperature(ctx, s0, kk, n_steps, checkpoint_every=every) - target) ** 2).sum().backward()
+    s0.grad = None
+    kk.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T = final_temperature(ctx, s0, kk, n_steps, checkpoint_every=every)
+    loss = ((T - target) ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    adj = T.grad_fn.adjoint_stats if hasattr(T.grad_fn, "adjoint_stats") else {}
+    g = s0.grad.double().cpu().numpy()
+    # central differences on seeded random elements, FP64 parameters at the FP32-rounded values
+    base_s = s0.detach().double().cpu().numpy()
+    base_k = kk.detach().double().cpu().numpy()
+    tgt = target.cpu().numpy()
+    rng = np.random.default_rng(mg.SEED_BASE + 5)
+    elems = rng.choice(mesh.n_tets, size=n_fd, replace=False)
+
+    def fd_at(eps):
+        fd = np.empty(n_fd)
+        for i, e in enumerate(elems):
+            h = eps * base_s[e]
+            vals = []
+            for sgn in (1.0, -1.0):
+                q = base_s.copy()
+                q[e] += sgn * h
+                ctx.set_params(q, base_k)
+                ctx.reset()
+                ctx.run(n_steps)
+                vals.append(float(np.sum((ctx.get_field(rafem.RAFEM_SYS_T) - tgt) ** 2)))
+            fd[i] = (vals[0] - vals[1]) / (2 * h)
+        err = np.abs(g[elems] - fd)
+        return {"eps": eps, "max_abs_err_over_max_abs_grad": float(err.max() / np.abs(fd).max()),
+                "median_rel_err": float(np.median(err / np.maximum(np.abs(fd), 1e-300))),
+                "max_abs_grad": float(np.abs(fd).max())}
+
+    t3 = time.perf_counter()
+    checks = [fd_at(1e-6), fd_at(1e-3)]
+    t4 = time.perf_counter()
+    ctx.close()
+    return {"workload": "64^3 cells (274,625 nodes, 1,572,864 tets), jitter +-10%, tumour-sigma0 target",
+            "steps": n_steps, "checkpoint_every": every, "solver_tol": 1e-12, "params_dtype": "float32",
+            "loss": float(loss.item()), "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
+            "backward_over_forward": (t2 - t1) / (t1 - t0), "adjoint": adj,
+            "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +405,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="run one precision only")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=120, help="steps of the differentiation form (0 = skip)")
+    ap.add_argument("--ilu-steps", type=int, default=10, help="timed steps with the ILU(0) preconditioner (0 = skip)")
+    ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -360,6 +452,16 @@ def main():
         if name == "fp64" and args.only is None:
             r["ctx"].close()
             r["ctx"] = None
+    if args.ilu_steps > 0 and args.only is None:
+        ilu_args = argparse.Namespace(**vars(args))
+        ilu_args.steps = args.ilu_steps
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, ilu_args, local, dist, want_clocks=False,
+                    precond=rafem.RAFEM_PRECOND_ILU0)
+        r["roofline"] = roofline(r, False, peaks, peak_kind)
+        r["steps"] = args.ilu_steps
+        r["ctx"].close()
+        r["ctx"] = None
+        runs["fp64_ilu0"] = r
     head_name = "mixed" if "mixed" in runs else "fp64"
     head = runs[head_name]
     ctx = head["ctx"]
@@ -383,7 +485,8 @@ def main():
 
     def summary(r):
         tr = r["trace"]
-        return {"value": world * args.steps / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / args.steps,
+        k = r.get("steps", args.steps)
+        return {"value": world * k / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / k, "steps": k,
                 "status": r["status"], "last_step": r["last"],
                 "iters_V_per_step": tr["iters_V"] / tr["steps"], "iters_T_per_step": tr["iters_T"] / tr["steps"],
                 "refine_V_per_step": tr["refine_V"] / tr["steps"],
@@ -421,6 +524,9 @@ def main():
             "rel_err_V": float(np.linalg.norm(Vm - Vf) / np.linalg.norm(Vf)),
             "psnr_T_db": float("inf") if mse_T == 0 else float(20 * np.log10(Tf.max() / np.sqrt(mse_T))),
             "speedup": head_sum["value"] / line["fp64"]["value"]}
+    if "fp64_ilu0" in runs:
+        line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
+        line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if args.batch_steps > 0 and args.only is None and args.cells == 127:
@@ -428,6 +534,11 @@ def main():
             line["batch"] = measure_batch(rafem, torch, mg, args)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
+    if args.adjoint_steps > 0 and args.only is None and args.cells == 127:
+        try:
+            line["adjoint"] = measure_adjoint(rafem, torch, mg, args)
+        except Exception as exc:
+            line["adjoint"] = {"error": repr(exc)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

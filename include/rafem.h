@@ -52,7 +52,10 @@ extern "C" {
 #define RAFEM_SYS_T 2                /* the thermal system                                                     */
 
 #define RAFEM_PRECOND_JACOBI 0       /* diagonal preconditioner                                               */
-#define RAFEM_PRECOND_ILU0   1       /* incomplete LU(0) on the fixed pattern, multicolour level order         */
+#define RAFEM_PRECOND_ILU0   1       /* incomplete LU(0) on the fixed pattern (single instance, FP64 only)     */
+
+#define RAFEM_ILU_MULTICOLOR 0       /* ILU(0) ordering: greedy colours of the matrix graph, levels = colours  */
+#define RAFEM_ILU_NATURAL    1       /* ILU(0) ordering: the mesh numbering, levels = dependency levels        */
 
 #define RAFEM_PRECISION_FP64  0      /* every Krylov operation in FP64                                        */
 #define RAFEM_PRECISION_MIXED 1      /* FP32 inner Krylov (FP32 values, vectors, dots) + FP64 residual refinement */
@@ -100,6 +103,7 @@ typedef struct rafem_params {
     int32_t assembly;                /* RAFEM_ASSEMBLY_GATHER (default with SELL-32) or RAFEM_ASSEMBLY_COLOR      */
     int32_t predictor;               /* 1 = start each solve from the linear extrapolation 2 x^n - x^{n-1}
                                         (the predictor of the predictor-corrector loop), 0 = from x^n (1)    */
+    int32_t ilu_order;               /* RAFEM_PRECOND_ILU0 only: RAFEM_ILU_MULTICOLOR (0) or RAFEM_ILU_NATURAL  */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
@@ -252,6 +256,27 @@ int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
 int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* vals,
                           const double* b, double* x, double tol, int32_t max_iter, void* stream,
                           rafem_step_stats* stats);
+
+/* ---- preconditioner inspection ----------------------------------------------------------------------------
+ * ILU(0) (Sec. II-B preconditioning): the factors are those of P A P^T, where P sorts the rows by level (greedy
+ * colour or dependency level, stable within a level; rafem_params.ilu_order) so that rows of one level never
+ * depend on each other; levels are solved one after the other. The potential system is refactored after every
+ * assembly, the constant thermal system once (and again when k changes). */
+
+/* n_levels, padded_rows (rows of the level-ordered layout, each level padded to a multiple of 32), nnz_stored
+ * (entries of its SELL-32 storage, padding included) and order [N] (host): the original row of the k-th row in
+ * factor order. Any out pointer may be NULL. Returns BAD_INPUT unless the context uses RAFEM_PRECOND_ILU0. */
+int rafem_precond_info(rafem_ctx* ctx, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored,
+                       int32_t* order);
+
+/* ILU(0) factors of system `which` mapped back onto the original CSR pattern (host, [nnz]): the entry of (i, j)
+ * holds L_ij (below the diagonal of P A P^T, unit diagonal implied) or U_ij (diagonal and above), where "below"
+ * refers to the factor order. BAD_INPUT unless ILU(0) is in use. */
+int rafem_get_precond(rafem_ctx* ctx, int which, double* factors);
+
+/* z = M^-1 r with the context's preconditioner for system `which` (ILU(0): forward and backward level sweeps;
+ * Jacobi: r / diag(A)). r_dev, z_dev: device pointers to N doubles (distinct). */
+int rafem_precond_apply(rafem_ctx* ctx, int which, const double* r_dev, double* z_dev);
 
 /* ---- differentiation form ----------------------------------------------------------------------------------
  * Gradients of a loss on the final fields with respect to the per-element conductivities sigma0 and k (and the

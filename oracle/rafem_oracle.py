@@ -389,10 +389,12 @@ def gradient_fd(model: "Model", n_steps, target, which, elems, eps=1e-6, T0=None
 # ----------------------------------------------------------------------------------------------------------
 # ILU(0) preconditioner (Sec. II-B: preconditioning accelerates the Krylov solvers). The factorisation is taken
 # on a symmetric permutation P A P^T of the system in which rows of one level never depend on each other:
-#   "multicolor": nodes sorted (stably) by a greedy colouring of the matrix graph (each node takes the smallest
-#                 colour not used by an already-coloured neighbour, nodes visited in index order); levels = colours;
 #   "natural":    nodes sorted (stably) by dependency level in the given numbering,
-#                 lev(i) = 1 + max{lev(j) : j < i, a_ij != 0} (0 if none); levels = these sets.
+#                 lev(i) = 1 + max{lev(j) : j < i, a_ij != 0} (0 if none); levels = these sets;
+#   "multicolor": nodes sorted (stably) by a colour. With g the largest |lev(i) - lev(j)| over the edges, the
+#                 colouring lev mod (g + 1) is proper (neighbours are 1..g levels apart); it is used unless the
+#                 greedy colouring (each node takes the smallest colour not used by an already-coloured
+#                 neighbour, nodes visited in index order) needs fewer colours. Levels = colours.
 # ----------------------------------------------------------------------------------------------------------
 
 def greedy_node_colors(A):
@@ -418,9 +420,24 @@ def dependency_levels(A):
     return lev
 
 
+def level_modulo_colors(A):
+    """lev mod (g + 1), g = the largest dependency-level gap along an edge (capped at the number of levels)."""
+    A = sp.csr_matrix(A)
+    lev = dependency_levels(A)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    gap = int(np.abs(lev[rows] - lev[A.indices]).max()) if A.nnz else 0
+    m = min(gap + 1, int(lev.max()) + 1)
+    return lev % m
+
+
 def ilu_permutation(A, order="multicolor"):
     """(perm, level_of_new_row): perm[new] = old row; rows sorted stably by colour or dependency level."""
-    key = greedy_node_colors(A) if order == "multicolor" else dependency_levels(A)
+    if order == "multicolor":
+        mod = level_modulo_colors(A)
+        greedy = greedy_node_colors(A)
+        key = mod if mod.max() <= greedy.max() else greedy
+    else:
+        key = dependency_levels(A)
     perm = np.argsort(key, kind="stable")
     return perm, key[perm]
 

@@ -97,6 +97,16 @@ struct rafem_ctx {
     bool tracing = false;
     rafem_trace trace{};
     cudaEvent_t ev[6] = {};
+    // ILU(0) preconditioner (precond == RAFEM_PRECOND_ILU0)
+    bool ilu = false;
+    IluLayout il;
+    std::vector<int32_t> ilu_pmap_csr;   // [nnz_p] CSR position of each factor entry (host), < 0 none
+    std::vector<int32_t> ilu_perm;       // [Np] original row of each padded row (host), -1 dummy
+    double *ilu_AV = nullptr, *ilu_FV = nullptr, *ilu_AT = nullptr, *ilu_FT = nullptr;
+    double *ilu_DV = nullptr, *ilu_DT = nullptr;  // 1 / diag(U)
+    double *ilu_xv = nullptr, *ilu_bv = nullptr, *ilu_r = nullptr, *ilu_z = nullptr, *ilu_p = nullptr,
+           *ilu_q = nullptr, *ilu_partial = nullptr;
+    int ilu_grid = 0;
     // differentiation: element order map, tape of checkpoints, adjoint workspace
     int32_t* e_order = nullptr;      // [E] sorted element -> mesh element
     double* p_tmpE = nullptr;        // [E] staging of parameter uploads / gradient downloads
@@ -231,6 +241,12 @@ __global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ xp
 
 __global__ void k_reset_hist(StatsDev* s) { s->hist = 0; }
 
+__global__ void k_jacobi_apply(int N, const int32_t* __restrict__ diag, const double* __restrict__ A,
+                               const double* __restrict__ r, double* __restrict__ z) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) z[i] = r[i] / A[diag[i]];
+}
+
 __global__ void k_fold_worst(const StatsDev* s, int32_t* acc) {
     const int w = s->worst, a = *acc;
     *acc = (w < 0 || a < 0) ? min(w, a) : max(w, a);
@@ -276,7 +292,16 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     return a;
 }
 
+cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old);
+
+// Assembly of one system; with ILU(0) the potential matrix is refactored right after it is assembled.
 cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
+    cudaError_t e = enqueue_assemble_raw(c, which, T_sigma, T_old);
+    if (e != cudaSuccess || !c->ilu || which != RAFEM_SYS_V) return e;
+    return launch_ilu_refactor(c->il, c->valsV, c->ilu_AV, c->ilu_FV, c->ilu_DV, c->stream);
+}
+
+cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
     cudaError_t e;
     if (c->gather) {
         float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
@@ -308,6 +333,28 @@ cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, con
 }
 
 cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
+    if (c->ilu) {
+        IluSolveArgs s{};
+        s.L = &c->il;
+        s.A = which == RAFEM_SYS_V ? c->ilu_AV : c->ilu_AT;
+        s.F = which == RAFEM_SYS_V ? c->ilu_FV : c->ilu_FT;
+        s.dinv = which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT;
+        s.b = b;
+        s.x = x;
+        s.xv = c->ilu_xv;
+        s.bv = c->ilu_bv;
+        s.r = c->ilu_r;
+        s.z = c->ilu_z;
+        s.p = c->ilu_p;
+        s.q = c->ilu_q;
+        s.partial = c->ilu_partial;
+        s.bar = c->bar;
+        s.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
+        s.tol = c->prm.tol;
+        s.max_iter = c->prm.max_iter;
+        s.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        return launch_ilu_pcg(s, c->ilu_grid, c->stream);
+    }
     SolveArgs a = make_args(c, which, b, x);
     return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
 }
@@ -685,6 +732,17 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         dev_ci = col;
         c->nnz_store = c->nnz;
     }
+    IluHost ih;
+    if (prm->precond == RAFEM_PRECOND_ILU0) {
+        if (n_inst != 1) return RAFEM_ERR_BAD_INPUT;
+        if (build_ilu(N, rp, col, prm->ilu_order, ih) != 0) return RAFEM_ERR_BAD_INPUT;
+        c->ilu = true;
+        c->ilu_pmap_csr = ih.pmap;
+        c->ilu_perm = ih.perm;
+        if (c->sell)
+            for (auto& q : ih.pmap)
+                if (q >= 0) q = c->h_map[q];
+    }
     std::vector<int32_t> nodes_soa(4LL * E);
     std::vector<double> sig_s(E), k_s(E);
     for (int64_t ep = 0; ep < E; ++ep) {
@@ -822,6 +880,47 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         const int t = build_tiles(c, prm->rows_per_tile);
         if (t != RAFEM_OK) return t;
     }
+    if (c->ilu) {
+        const size_t nz = ih.sc.size(), Np = (size_t)ih.Np;
+        int32_t *lvl, *sp, *sc, *pm, *pr;
+        uint8_t *rl, *dk;
+        CK(dalloc(c, &lvl, ih.lvl.size()));
+        CK(dalloc(c, &sp, ih.sp.size()));
+        CK(dalloc(c, &sc, nz));
+        CK(dalloc(c, &pm, nz));
+        CK(dalloc(c, &pr, Np));
+        CK(dalloc(c, &rl, Np));
+        CK(dalloc(c, &dk, Np));
+        CK(cudaMemcpyAsync(lvl, ih.lvl.data(), ih.lvl.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(sp, ih.sp.data(), ih.sp.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(sc, ih.sc.data(), nz * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(pm, ih.pmap.data(), nz * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(pr, ih.perm.data(), Np * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(rl, ih.rlen.data(), Np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dk, ih.dk.data(), Np, cudaMemcpyHostToDevice, st));
+        c->il.Np = ih.Np;
+        c->il.n_levels = ih.n_levels;
+        c->il.nnz = (long long)nz;
+        c->il.lvl = lvl;
+        c->il.sp = sp;
+        c->il.sc = sc;
+        c->il.pmap = pm;
+        c->il.rlen = rl;
+        c->il.dk = dk;
+        c->il.perm = pr;
+        c->il.h_lvl = ih.lvl;
+        CK(dalloc(c, &c->ilu_AV, nz));
+        CK(dalloc(c, &c->ilu_FV, nz));
+        CK(dalloc(c, &c->ilu_AT, nz));
+        CK(dalloc(c, &c->ilu_FT, nz));
+        CK(dalloc(c, &c->ilu_DV, Np));
+        CK(dalloc(c, &c->ilu_DT, Np));
+        for (double** v : {&c->ilu_xv, &c->ilu_bv, &c->ilu_r, &c->ilu_z, &c->ilu_p, &c->ilu_q}) CK(dalloc(c, v, Np));
+        int bt = 0;
+        c->ilu_grid = ilu_max_blocks(&bt);
+        if (c->ilu_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &c->ilu_partial, (size_t)kIluPartialSlots * c->ilu_grid));
+    }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
     CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
     if (c->gather) {
@@ -835,6 +934,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     for (int q = 0; q < c->n_colors; ++q)
         CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                              prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, st));
+    if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     k_init_fields<<<(N + 255) / 256, 256, 0, st>>>(N, prm->T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
     CK(cudaGetLastError());
     k_set_step<<<1, 1, 0, st>>>(c->stats, 0);
@@ -857,7 +957,11 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         return RAFEM_ERR_BAD_INPUT;
     if (prm->precision != RAFEM_PRECISION_FP64 && prm->precision != RAFEM_PRECISION_MIXED) return RAFEM_ERR_BAD_INPUT;
     if (prm->precision == RAFEM_PRECISION_MIXED && !(prm->inner_tol > 0 && prm->inner_tol < 1)) return RAFEM_ERR_BAD_INPUT;
-    if (prm->precond != RAFEM_PRECOND_JACOBI) return RAFEM_ERR_BAD_INPUT;
+    if (prm->precond != RAFEM_PRECOND_JACOBI && prm->precond != RAFEM_PRECOND_ILU0) return RAFEM_ERR_BAD_INPUT;
+    if (prm->precond == RAFEM_PRECOND_ILU0 &&
+        (prm->precision != RAFEM_PRECISION_FP64 ||
+         (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL)))
+        return RAFEM_ERR_BAD_INPUT;
     if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
@@ -1169,8 +1273,47 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
         for (int q = 0; q < c->n_colors; ++q)
             CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                                  c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, st));
+        if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     }
     CK(cudaStreamSynchronize(st));
+    return RAFEM_OK;
+}
+
+int rafem_precond_info(rafem_ctx* c, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored, int32_t* order) {
+    if (!c || !c->ilu) return RAFEM_ERR_BAD_INPUT;
+    if (n_levels) *n_levels = c->il.n_levels;
+    if (padded_rows) *padded_rows = c->il.Np;
+    if (nnz_stored) *nnz_stored = c->il.nnz;
+    if (order) {
+        int k = 0;
+        for (int32_t o : c->ilu_perm)
+            if (o >= 0) order[k++] = o;
+    }
+    return RAFEM_OK;
+}
+
+int rafem_get_precond(rafem_ctx* c, int which, double* factors) {
+    if (!c || !c->ilu || !factors || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    std::vector<double> F(c->il.nnz);
+    CK(cudaMemcpyAsync(F.data(), which == RAFEM_SYS_V ? c->ilu_FV : c->ilu_FT, F.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t q = 0; q < F.size(); ++q)
+        if (c->ilu_pmap_csr[q] >= 0) factors[c->ilu_pmap_csr[q]] = F[q];
+    return RAFEM_OK;
+}
+
+int rafem_precond_apply(rafem_ctx* c, int which, const double* r, double* z) {
+    if (!c || !r || !z || r == z || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
+    if (c->ilu) {
+        CK(launch_ilu_apply(c->il, which == RAFEM_SYS_V ? c->ilu_FV : c->ilu_FT,
+                            which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT, r, z, c->ilu_r, c->ilu_z, c->stream));
+    } else {
+        k_jacobi_apply<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->diag,
+                                                                   which == RAFEM_SYS_V ? c->valsV : c->valsT, r, z);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(c->stream));
     return RAFEM_OK;
 }
 

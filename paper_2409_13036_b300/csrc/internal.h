@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/rafem.h"
 
@@ -164,5 +165,54 @@ cudaError_t launch_mask(int N, const uint8_t* bc, const double* in, double* out,
 cudaError_t launch_permute(int n, const int32_t* perm, const double* in, double* out, int scatter, cudaStream_t st);
 cudaError_t launch_adj_count(const InstState* inst, int n_inst, const GridBarrier* bar, int32_t* acc, int slot,
                              cudaStream_t st);
+
+}  // namespace rafem
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// ILU(0) preconditioner (ilu.cu): level-ordered permuted SELL-32 layout (setup.h IluHost) on the device.
+// ------------------------------------------------------------------------------------------------------------
+struct IluLayout {
+    int Np = 0, n_levels = 0;
+    long long nnz = 0;               // stored entries (with padding)
+    const int32_t* lvl = nullptr;    // [n_levels + 1] (device)
+    const int32_t* sp = nullptr;     // [Np/32 + 1]
+    const int32_t* sc = nullptr;     // [nnz]
+    const int32_t* pmap = nullptr;   // [nnz] source position in the system's value storage; -1 pad, -2 unit
+    const uint8_t* rlen = nullptr;   // [Np]
+    const uint8_t* dk = nullptr;     // [Np]
+    const int32_t* perm = nullptr;   // [Np] original row, -1 dummy
+    std::vector<int32_t> h_lvl;      // host copy of lvl
+};
+
+constexpr int kIluPartialSlots = 5;  // partial-sum slots of the ILU solver, each [grid]
+
+struct IluSolveArgs {
+    const IluLayout* L;              // host pointer (fields copied into the kernel arguments)
+    const double* A;                 // [nnz] permuted system values
+    const double* F;                 // [nnz] factors
+    const double* dinv;              // [Np] 1 / u_ii
+    const double* b;                 // [N] original ordering
+    double* x;                       // [N] original ordering: initial guess in, solution out
+    double *xv, *bv, *r, *z, *p, *q; // [Np] padded ordering
+    double* partial;                 // [kIluPartialSlots][grid]
+    GridBarrier* bar;
+    InstState* inst;                 // [1]
+    double tol;
+    int max_iter;
+    long long spin_limit_ns;
+};
+
+// Ap = permuted values of `vals` (the system in its primary storage), F = ILU(0) factors of Ap, level by level,
+// dinv = 1 / diag(U).
+cudaError_t launch_ilu_refactor(const IluLayout& L, const double* vals, double* Ap, double* F, double* dinv,
+                                cudaStream_t st);
+// Persistent ILU(0)-preconditioned CG (FP64), one cooperative launch per solve.
+int ilu_max_blocks(int* block_threads);
+cudaError_t launch_ilu_pcg(const IluSolveArgs& a, int grid, cudaStream_t st);
+// z = U^-1 L^-1 r (original ordering; rv, zv: [Np] scratch).
+cudaError_t launch_ilu_apply(const IluLayout& L, const double* F, const double* dinv, const double* r, double* z,
+                             double* rv, double* zv, cudaStream_t st);
 
 }  // namespace rafem

@@ -38,6 +38,7 @@
 
 #include <cmath>
 
+#include "grid_sync.cuh"
 #include "internal.h"
 
 namespace rafem {
@@ -63,16 +64,6 @@ enum { Q_GAMMA = 0, Q_RR = 1, Q_DELTA = 2, Q_BB = 3, Q_RR64 = 4, NQ_ALL = 5 };
 static_assert(NQ_ALL == kPartialQ, "partial-sum buffer size");
 enum { ST_OUTER = 1, ST_START = 2, ST_ITER = 3 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Loads of data written by other blocks during the kernel go through L2 (L1 is not coherent).
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -206,31 +197,10 @@ __device__ __forceinline__ void block_sum(T (&v)[NQ], T* sm /* [kSumMax * kBlock
     __syncthreads();
 }
 
-// Grid barrier on a counter that only grows during a launch: every block adds 1 and waits until the counter
-// reaches its own running target (gridDim.x per barrier). No block has a special role, so the release is one
-// atomic plus one poll latency. Returns true when the solve must stop because an error was recorded.
+// Grid barrier of the solver launch (bounded wait; see grid_sync.cuh). Returns true when the solve must stop
+// because an error was recorded.
 __device__ __forceinline__ bool grid_wait(const SolveArgs& a, unsigned& target) {
-    __shared__ int s_err;
-    __syncthreads();
-    target += gridDim.x;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&a.bar->count, 1u);
-        const unsigned long long t0 = globaltimer();
-        long long spins = 0;
-        while ((int)(ld_acquire_u32(&a.bar->count) - target) < 0) {
-            ++spins;
-            if ((spins & 255) == 0 &&
-                ((long long)(globaltimer() - t0) > a.spin_limit_ns || spins > (1LL << 40))) {
-                atomicExch(&a.bar->err, RAFEM_ERR_TIMEOUT);
-                break;
-            }
-        }
-        __threadfence();
-        s_err = *(volatile int*)&a.bar->err;
-    }
-    __syncthreads();
-    return s_err != 0;
+    return grid_barrier(a.bar, a.spin_limit_ns, target);
 }
 
 // ---- SpMV over the rows of one tile -------------------------------------------------------------------------

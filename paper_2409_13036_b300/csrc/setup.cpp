@@ -269,3 +269,120 @@ void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::v
 }
 
 }  // namespace rafem
+
+namespace rafem {
+
+int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int order, IluHost& out) {
+    // dependency levels in the given numbering: lev(i) = 1 + the largest level of an earlier neighbour
+    std::vector<int32_t> lev(N, 0);
+    int n_dep = 0, gap = 0;
+    for (int i = 0; i < N; ++i) {
+        int lv = 0;
+        for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+            if (col[q] < i) lv = std::max(lv, lev[col[q]] + 1);
+        lev[i] = lv;
+        n_dep = std::max(n_dep, lv + 1);
+        for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+            if (col[q] < i) gap = std::max(gap, lv - lev[col[q]]);
+    }
+    std::vector<int32_t> key;
+    int n_levels = 0;
+    if (order == 1) {
+        key = lev;
+        n_levels = n_dep;
+    } else {
+        // colours: neighbours are at most `gap` levels apart, so lev mod (gap + 1) is a proper colouring; the greedy
+        // colouring (smallest colour unused by an earlier neighbour, nodes in index order) is taken when it needs
+        // fewer colours
+        std::vector<int32_t> greedy(N, 0), mark;
+        int n_greedy = 0;
+        for (int i = 0; i < N; ++i) {
+            for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+                const int j = col[q];
+                if (j < i) {
+                    const int c = greedy[j];
+                    if ((int)mark.size() <= c) mark.resize(c + 1, -1);
+                    mark[c] = i;
+                }
+            }
+            int c = 0;
+            while (c < (int)mark.size() && mark[c] == i) ++c;
+            greedy[i] = c;
+            n_greedy = std::max(n_greedy, c + 1);
+        }
+        const int n_mod = std::min(gap + 1, n_dep);
+        if (n_mod <= n_greedy) {
+            key.resize(N);
+            for (int i = 0; i < N; ++i) key[i] = lev[i] % n_mod;
+            n_levels = n_mod;
+        } else {
+            key = std::move(greedy);
+            n_levels = n_greedy;
+        }
+    }
+    for (int i = 0; i < N; ++i)
+        if (rp[i + 1] - rp[i] > 255) return -1;
+    // padded level-contiguous numbering: level l occupies [lvl[l], lvl[l+1]), a multiple of 32 rows
+    std::vector<int64_t> cnt(n_levels, 0);
+    for (int i = 0; i < N; ++i) cnt[key[i]]++;
+    out.n_levels = n_levels;
+    out.lvl.assign(n_levels + 1, 0);
+    for (int l = 0; l < n_levels; ++l) {
+        const int64_t next = out.lvl[l] + (cnt[l] + SELL_C - 1) / SELL_C * SELL_C;
+        if (next > INT32_MAX / 2) return -1;
+        out.lvl[l + 1] = (int32_t)next;
+    }
+    const int Np = out.lvl[n_levels];
+    out.Np = Np;
+    out.perm.assign(Np, -1);
+    std::vector<int32_t> pos(N), fill(out.lvl.begin(), out.lvl.end() - 1);
+    for (int i = 0; i < N; ++i) {
+        const int r = fill[key[i]]++;
+        out.perm[r] = i;
+        pos[i] = r;
+    }
+    // rows of P A P^T with columns in the new numbering, sorted; SELL-32 over the padded rows
+    out.rlen.assign(Np, 1);
+    out.dk.assign(Np, 0);
+    const int S = Np / SELL_C;
+    out.sp.assign(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        int w = 1;
+        for (int r = s * SELL_C; r < (s + 1) * SELL_C; ++r)
+            if (out.perm[r] >= 0) w = std::max(w, rp[out.perm[r] + 1] - rp[out.perm[r]]);
+        out.sp[s + 1] = out.sp[s] + w * SELL_C;
+    }
+    out.sc.assign(out.sp[S], 0);
+    out.pmap.assign(out.sp[S], -1);
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < S; ++s) {
+        const int w = (out.sp[s + 1] - out.sp[s]) / SELL_C;
+        std::vector<std::pair<int32_t, int32_t>> row;
+        for (int l = 0; l < SELL_C; ++l) {
+            const int r = s * SELL_C + l;
+            const int old = out.perm[r];
+            row.clear();
+            if (old >= 0) {
+                for (int32_t q = rp[old]; q < rp[old + 1]; ++q) row.emplace_back(pos[col[q]], q);
+                std::sort(row.begin(), row.end());
+            } else {
+                row.emplace_back(r, -2);  // dummy row: unit diagonal
+            }
+            out.rlen[r] = (uint8_t)row.size();
+            for (int k = 0; k < w; ++k) {
+                const int64_t at = out.sp[s] + (int64_t)k * SELL_C + l;
+                if (k < (int)row.size()) {
+                    out.sc[at] = row[k].first;
+                    out.pmap[at] = row[k].second;
+                    if (row[k].first == r) out.dk[r] = (uint8_t)k;
+                } else {
+                    out.sc[at] = r;
+                    out.pmap[at] = -1;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+}  // namespace rafem

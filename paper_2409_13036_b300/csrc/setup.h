@@ -47,4 +47,24 @@ void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::
 void build_incidence(int N, int E, const std::vector<int32_t>& nodes_soa, std::vector<int32_t>& inc_off,
                      std::vector<int32_t>& inc_cnt, std::vector<int32_t>& inc_elem);
 
+// ILU(0) layout: a symmetric permutation P in which the rows of one level never depend on each other, levels
+// stored contiguously and each padded to a multiple of 32 rows (dummy rows carry a unit diagonal), and P A P^T in
+// SELL-32 with 32-bit columns (new numbering). With the dependency levels lev(i) = 1 + max lev(j) over earlier
+// neighbours j and g the largest level gap along an edge: order 1 uses the levels themselves; order 0 uses the
+// colouring lev mod (g + 1) (neighbours are 1..g levels apart, so it is proper; 4 colours on the Kuhn lattice),
+// or the greedy colouring (smallest colour unused by an earlier neighbour, nodes in index order) when that needs
+// fewer colours. Within a level rows keep their original order.
+struct IluHost {
+    int Np = 0, n_levels = 0;
+    std::vector<int32_t> lvl;    // [n_levels + 1] first padded row of each level
+    std::vector<int32_t> perm;   // [Np] original row of each padded row, -1 for a dummy row
+    std::vector<int32_t> sp;     // [Np/32 + 1] slice pointers
+    std::vector<int32_t> sc;     // columns (new numbering); padding entries point at their own row
+    std::vector<int32_t> pmap;   // source CSR position of each entry; -1 padding (0), -2 dummy diagonal (1)
+    std::vector<uint8_t> rlen;   // entries per row
+    std::vector<uint8_t> dk;     // index of the diagonal within the row
+};
+// Returns 0, or -1 when a row has more than 255 entries or the padded size overflows.
+int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int order, IluHost& out);
+
 }  // namespace rafem

@@ -36,6 +36,8 @@ RAFEM_PRECISION_FP64 = 0
 RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
+RAFEM_ILU_MULTICOLOR = 0
+RAFEM_ILU_NATURAL = 1
 RAFEM_ASSEMBLY_GATHER = 0
 RAFEM_ASSEMBLY_COLOR = 1
 
@@ -56,7 +58,7 @@ class rafem_params(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("n_corrector", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
-                ("predictor", ctypes.c_int32)]
+                ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):
@@ -127,6 +129,10 @@ def lib() -> ctypes.CDLL:
         "rafem_set_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
         "rafem_get_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]),
+        "rafem_precond_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int64), vp]),
+        "rafem_get_precond": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+        "rafem_precond_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_reset": (ctypes.c_int, [vp]),
         "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
@@ -363,6 +369,23 @@ class Context:
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+    # -- preconditioner ---------------------------------------------------------------------------------------
+    def precond_info(self) -> dict:
+        nl, npad, nz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        order = np.empty(self.N, np.int32)
+        _check(lib().rafem_precond_info(self._ctx, ctypes.byref(nl), ctypes.byref(npad), ctypes.byref(nz),
+                                        order.ctypes.data), "rafem_precond_info")
+        return {"n_levels": nl.value, "padded_rows": npad.value, "nnz_stored": nz.value, "order": order}
+
+    def get_precond(self, which: int) -> np.ndarray:
+        _, nnz, _ = self.pattern_info()
+        out = np.empty(nnz, np.float64)
+        _check(lib().rafem_get_precond(self._ctx, which, out.ctypes.data), "rafem_get_precond")
+        return out
+
+    def precond_apply(self, which: int, r_dev, z_dev):
+        _check(lib().rafem_precond_apply(self._ctx, which, _dev(r_dev), _dev(z_dev)), "rafem_precond_apply")
 
     # -- differentiation form -------------------------------------------------------------------------------
     def reset(self):

@@ -306,16 +306,20 @@ def test_ilu0_apply_inverts_the_factors():
 
 
 def test_ilu_orderings_are_valid_level_orders():
-    """Greedy colours: no two neighbours share a colour (8 colours on the Kuhn lattice). Dependency levels: every
-    stored lower neighbour of a row lies on an earlier level (3 n + 1 levels on an (n+1)^3 lattice). After the
-    permutation the levels are contiguous and non-decreasing."""
+    """Greedy colours and level-modulo colours are proper colourings (no two neighbours share one): 8 greedy
+    colours and 4 = 1 + the largest level gap (offsets of the Kuhn stencil sum to 1, 2 or 3) on the Kuhn
+    lattice, the fewest possible since every tetrahedron is a 4-clique. Dependency levels: every stored lower
+    neighbour of a row lies on an earlier level (3 n + 1 levels on an (n+1)^3 lattice). After the permutation
+    the levels are contiguous and non-decreasing."""
     n = 5
     A = _potential_system(n)
-    col = O.greedy_node_colors(A)
     rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
     offd = rows != A.indices
-    assert np.all(col[rows[offd]] != col[A.indices[offd]])
-    assert col.max() + 1 == 8
+    for col, count in ((O.greedy_node_colors(A), 8), (O.level_modulo_colors(A), 4)):
+        assert np.all(col[rows[offd]] != col[A.indices[offd]])
+        assert col.max() + 1 == count
+    _, lv = O.ilu_permutation(A, "multicolor")
+    assert lv.max() + 1 == 4
     lev = O.dependency_levels(A)
     low = A.indices < rows
     assert np.all(lev[A.indices[low]] < lev[rows[low]])
