@@ -42,6 +42,7 @@ class Params:
     T_a: float = 37.0            # degC
     dt: float = 1.0              # s
     n_corrector: int = 1         # fixed-point passes per step (1 = lagged coefficients)
+    lift: str = "symmetric"      # Dirichlet lift: "symmetric" (SPD systems) or "row" (nonsymmetric, same solution)
     corrector_tol: float = 1e-6  # degC, infinity norm of the temperature change between passes
 
 
@@ -136,6 +137,21 @@ def dirichlet_lift(A, b, bc, g):
     return A, b
 
 
+def dirichlet_lift_row(A, b, bc, g):
+    """Row-only Dirichlet lift: rows of D become identity rows with b_D = g_D; columns are kept, so the system is
+    nonsymmetric but has the same solution as the symmetric lift. The pattern of A is kept."""
+    bc = np.asarray(bc).astype(bool)
+    g = np.where(bc, np.asarray(g, dtype=np.float64), 0.0)
+    b = np.asarray(b, dtype=np.float64).copy()
+    A = A.tocsr(copy=True)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    kill = bc[rows]
+    A.data[kill] = 0.0
+    A.data[kill & (rows == A.indices)] = 1.0
+    b[bc] = g[bc]
+    return A, b
+
+
 def solve(A, b):
     """Direct solve: dense LU with partial pivoting for N <= 3000, SuperLU (symmetric ordering) otherwise."""
     N = A.shape[0]
@@ -173,7 +189,10 @@ class Model:
     def system_V(self, T):
         """Lifted (A_V, b_V) for sigma evaluated at temperature T."""
         K = assemble(element_stiffness(self.sigma(T), self.vol, self.grad), self.tets, self.N)
-        return dirichlet_lift(K, np.zeros(self.N), self.bc_V, self.g_V)
+        return self._lift(K, np.zeros(self.N), self.bc_V, self.g_V)
+
+    def _lift(self, A, b, bc, g):
+        return (dirichlet_lift_row if self.p.lift == "row" else dirichlet_lift)(A, b, bc, g)
 
     # -- the thermal system ---------------------------------------------------------------------------
     def rhs_T_unlifted(self, T_old, Q_e):
@@ -182,7 +201,7 @@ class Model:
                 + load_vector(Q_e, self.vol, self.tets, self.N))
 
     def system_T(self, T_old, Q_e):
-        return dirichlet_lift(self.A_T, self.rhs_T_unlifted(T_old, Q_e), self.bc_T, self.g_T)
+        return self._lift(self.A_T, self.rhs_T_unlifted(T_old, Q_e), self.bc_T, self.g_T)
 
     def solve_T(self, T_old, Q_e):
         """Solve the lifted thermal system; its matrix is constant, so its factorisation is kept."""

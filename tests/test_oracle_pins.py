@@ -339,3 +339,30 @@ def test_ilu0_natural_level_sort_is_a_relabelling():
     F2 = O.ilu0(O.permute_symmetric(A, perm))
     np.testing.assert_array_equal(F1.indices, F2.indices)
     np.testing.assert_allclose(F1.data, F2.data, rtol=1e-13, atol=1e-14 * np.abs(F1.data).max())
+
+
+def test_row_lift_same_solution_nonsymmetric_system():
+    """The row-only lift keeps the Dirichlet columns: the matrix is nonsymmetric (Dirichlet nodes have free
+    neighbours), its Dirichlet rows are identity rows, its free rows equal the unlifted rows, and its solution
+    equals the symmetric lift's (to 1e-12), for the potential and the thermal system."""
+    m = mg.cube_mesh(6, jitter=0.1, seed=12, sigma0="lognormal")
+    T = 37.0 + 10.0 * np.random.default_rng(2).random(m.n_nodes)
+    T = np.where(m.bc_T.astype(bool), m.g_T, T)
+    sym = O.Model(m)
+    row = O.Model(m, O.Params(lift="row"))
+    for which in ("V", "T"):
+        if which == "V":
+            (As, bs), (Ar, br) = sym.system_V(T), row.system_V(T)
+            bc = m.bc_V.astype(bool)
+            K = O.assemble(O.element_stiffness(sym.sigma(T), sym.vol, sym.grad), m.tets, m.n_nodes)
+        else:
+            Q = np.full(m.n_tets, 1e5)
+            (As, bs), (Ar, br) = sym.system_T(T, Q), row.system_T(T, Q)
+            bc = m.bc_T.astype(bool)
+            K = sym.A_T
+        assert abs(Ar - Ar.T).max() > 1e-6 * abs(Ar).max()
+        Ad = Ar.toarray()
+        np.testing.assert_array_equal(Ad[bc], np.eye(m.n_nodes)[bc])
+        np.testing.assert_allclose(Ad[~bc], K.toarray()[~bc], rtol=0, atol=1e-15 * abs(K).max())
+        xs, xr = O.solve(As, bs), O.solve(Ar, br)
+        np.testing.assert_allclose(xr, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
