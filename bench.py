@@ -173,6 +173,15 @@ def alg_bytes_ilu(Np: int, nnz_p: int, iters: float) -> float:
     return (iters + 2) * per_iter
 
 
+def alg_bytes_bicgstab(N: int, nnz: int, iters: float, col_bytes: int) -> float:
+    """Algorithmic HBM bytes of one Jacobi-BiCGSTAB solve launch (SELL-32 primary storage): two SpMVs per
+    iteration ((8 + col_bytes) B per stored entry each, plus the gathered vector read and the product written, 16N)
+    and the row-local phases (A: 5 reads + 2 writes, B: 1 read, C: 3 reads + 2 writes, D: 1 read, E: 7 reads +
+    2 writes of 8N = 168N). Start-up and the final true residual add about one iteration's worth."""
+    per_iter = 2 * ((8 + col_bytes) * nnz + 16 * N) + 168 * N
+    return (iters + 1) * per_iter
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -194,10 +203,10 @@ def reference_arm(args):
     return 0
 
 
-def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, precond=0):
+def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, precond=0, solver=0):
     """Warm up, time K steps with CUDA events on the context's stream, then a few traced steps."""
     stream = torch.cuda.Stream()
-    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision, precond=precond)
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision, precond=precond, solver=solver)
     N, nnz, n_colors = ctx.pattern_info()
     layout = ctx.layout_info()
     if precond == rafem.RAFEM_PRECOND_ILU0:
@@ -245,7 +254,11 @@ def roofline(res, mixed, peaks, peak_kind):
     iters = tr["iters_V"] / steps
     cb = res["layout"]["column_bytes"]
     code = res["layout"]["kernel_code"]
-    if "ilu" in res["layout"]:
+    if res.get("solver") == "bicgstab":
+        ref = 0.0
+        alg = alg_bytes_bicgstab(N, nnz, iters, cb)
+        kern = "k_bicgstab"
+    elif "ilu" in res["layout"]:
         ref = 0.0
         alg = alg_bytes_ilu(res["layout"]["ilu"]["padded_rows"], res["layout"]["ilu"]["nnz_stored"], iters)
         kern = "k_ilu_pcg"
@@ -407,6 +420,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=120, help="steps of the differentiation form (0 = skip)")
     ap.add_argument("--ilu-steps", type=int, default=10, help="timed steps with the ILU(0) preconditioner (0 = skip)")
+    ap.add_argument("--bicgstab-steps", type=int, default=5, help="timed steps with BiCGSTAB (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -462,6 +476,17 @@ def main():
         r["ctx"].close()
         r["ctx"] = None
         runs["fp64_ilu0"] = r
+    if args.bicgstab_steps > 0 and args.only is None:
+        b_args = argparse.Namespace(**vars(args))
+        b_args.steps = args.bicgstab_steps
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, b_args, local, dist, want_clocks=False,
+                    solver=rafem.RAFEM_SOLVER_BICGSTAB)
+        r["solver"] = "bicgstab"
+        r["roofline"] = roofline(r, False, peaks, peak_kind)
+        r["steps"] = args.bicgstab_steps
+        r["ctx"].close()
+        r["ctx"] = None
+        runs["fp64_bicgstab"] = r
     head_name = "mixed" if "mixed" in runs else "fp64"
     head = runs[head_name]
     ctx = head["ctx"]
@@ -524,6 +549,8 @@ def main():
             "rel_err_V": float(np.linalg.norm(Vm - Vf) / np.linalg.norm(Vf)),
             "psnr_T_db": float("inf") if mse_T == 0 else float(20 * np.log10(Tf.max() / np.sqrt(mse_T))),
             "speedup": head_sum["value"] / line["fp64"]["value"]}
+    if "fp64_bicgstab" in runs:
+        line["fp64_bicgstab"] = summary(runs["fp64_bicgstab"])
     if "fp64_ilu0" in runs:
         line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
         line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]

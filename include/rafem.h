@@ -61,7 +61,13 @@ extern "C" {
 #define RAFEM_PRECISION_MIXED 1      /* FP32 inner Krylov (FP32 values, vectors, dots) + FP64 residual refinement */
 
 #define RAFEM_SOLVER_PCG      0      /* conjugate gradients (SPD systems)                                      */
-#define RAFEM_SOLVER_BICGSTAB 1      /* BiCGSTAB (general nonsymmetric systems)                                */
+#define RAFEM_SOLVER_BICGSTAB 1      /* BiCGSTAB (general nonsymmetric systems): FP64, Jacobi, SELL-32 layout,
+                                        single instance                                                        */
+
+#define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known
+                                        values moved to the right-hand side: the systems stay SPD              */
+#define RAFEM_LIFT_ROW        1      /* Dirichlet rows replaced by identity rows, columns kept: the same solution
+                                        from a nonsymmetric system (needs RAFEM_SOLVER_BICGSTAB; no adjoint)   */
 
 #define RAFEM_ASSEMBLY_GATHER 0      /* row-owner assembly: one thread per matrix row sums the element
                                         contributions of its entries (SELL-32 layout only)                    */
@@ -104,6 +110,7 @@ typedef struct rafem_params {
     int32_t predictor;               /* 1 = start each solve from the linear extrapolation 2 x^n - x^{n-1}
                                         (the predictor of the predictor-corrector loop), 0 = from x^n (1)    */
     int32_t ilu_order;               /* RAFEM_PRECOND_ILU0 only: RAFEM_ILU_MULTICOLOR (0) or RAFEM_ILU_NATURAL  */
+    int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric; BiCGSTAB only)  */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */

@@ -107,6 +107,10 @@ struct rafem_ctx {
     double *ilu_xv = nullptr, *ilu_bv = nullptr, *ilu_r = nullptr, *ilu_z = nullptr, *ilu_p = nullptr,
            *ilu_q = nullptr, *ilu_partial = nullptr;
     int ilu_grid = 0;
+    // BiCGSTAB (solver == RAFEM_SOLVER_BICGSTAB)
+    double *bg_r = nullptr, *bg_rh = nullptr, *bg_p = nullptr, *bg_ph = nullptr, *bg_v = nullptr, *bg_s = nullptr,
+           *bg_sh = nullptr, *bg_t = nullptr, *bg_dinv = nullptr, *bg_partial = nullptr;
+    int bg_grid = 0;
     // differentiation: element order map, tape of checkpoints, adjoint workspace
     int32_t* e_order = nullptr;      // [E] sorted element -> mesh element
     double* p_tmpE = nullptr;        // [E] staging of parameter uploads / gradient downloads
@@ -307,7 +311,7 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
         float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
         if (which == RAFEM_SYS_V)
             return launch_assemble_V_gather(c->gd, c->N, c->rp, c->ci, c->diag, c->el, T_sigma, c->prm.alpha_sigma,
-                                            c->bcV, c->gV, c->valsV, v32, c->bV, c->stream);
+                                            c->bcV, c->gV, c->valsV, v32, c->bV, c->prm.lift, c->stream);
         return launch_rhs_T_gather(c->gd, c->N, c->el, T_sigma, T_old, c->V, c->bcT, c->gT, c->bTc,
                                    c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->bT, c->stream);
     }
@@ -317,7 +321,7 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
         float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
         for (int col = 0; col < c->n_colors; ++col) {
             e = launch_assemble_V(c->el, c->color_off[col], c->color_off[col + 1], T_sigma, c->bcV, c->gV,
-                                  c->prm.alpha_sigma, c->valsV, v32, c->bV, c->stream);
+                                  c->prm.alpha_sigma, c->valsV, v32, c->bV, c->prm.lift, c->stream);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -354,6 +358,33 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         s.max_iter = c->prm.max_iter;
         s.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
         return launch_ilu_pcg(s, c->ilu_grid, c->stream);
+    }
+    if (c->prm.solver == RAFEM_SOLVER_BICGSTAB) {
+        BicgArgs g{};
+        g.N = c->N;
+        g.sp = c->rp;
+        g.sc = c->ci;
+        g.sc16 = c->ci16;
+        g.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
+        g.diag = c->diag;
+        g.b = b;
+        g.x = x;
+        g.r = c->bg_r;
+        g.rh = c->bg_rh;
+        g.p = c->bg_p;
+        g.ph = c->bg_ph;
+        g.v = c->bg_v;
+        g.s = c->bg_s;
+        g.sh = c->bg_sh;
+        g.t = c->bg_t;
+        g.dinv = c->bg_dinv;
+        g.partial = c->bg_partial;
+        g.bar = c->bar;
+        g.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
+        g.tol = c->prm.tol;
+        g.max_iter = c->prm.max_iter;
+        g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        return launch_bicgstab(g, c->bg_grid, c->stream);
     }
     SolveArgs a = make_args(c, which, b, x);
     return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
@@ -880,6 +911,15 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         const int t = build_tiles(c, prm->rows_per_tile);
         if (t != RAFEM_OK) return t;
     }
+    if (prm->solver == RAFEM_SOLVER_BICGSTAB) {
+        if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
+        for (double** v : {&c->bg_r, &c->bg_rh, &c->bg_p, &c->bg_ph, &c->bg_v, &c->bg_s, &c->bg_sh, &c->bg_t,
+                           &c->bg_dinv})
+            CK(dalloc(c, v, (size_t)N + SELL_C));
+        c->bg_grid = bicgstab_max_blocks();
+        if (c->bg_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &c->bg_partial, (size_t)bicgstab_partial_slots() * c->bg_grid));
+    }
     if (c->ilu) {
         const size_t nz = ih.sc.size(), Np = (size_t)ih.Np;
         int32_t *lvl, *sp, *sc, *pm, *pr;
@@ -933,7 +973,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     const double c_matrix = prm->rho_c / prm->dt + prm->perf;
     for (int q = 0; q < c->n_colors; ++q)
         CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
-                             prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, st));
+                             prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, prm->lift, st));
     if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     k_init_fields<<<(N + 255) / 256, 256, 0, st>>>(N, prm->T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
     CK(cudaGetLastError());
@@ -962,7 +1002,13 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         (prm->precision != RAFEM_PRECISION_FP64 ||
          (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL)))
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->solver != RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
+    if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB) return RAFEM_ERR_BAD_INPUT;
+    if (prm->solver == RAFEM_SOLVER_BICGSTAB &&
+        (prm->precision != RAFEM_PRECISION_FP64 || prm->precond != RAFEM_PRECOND_JACOBI ||
+         (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
+    if (prm->lift == RAFEM_LIFT_ROW && prm->solver != RAFEM_SOLVER_BICGSTAB) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
 }
@@ -1272,7 +1318,7 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
         const double c_matrix = c->prm.rho_c / c->prm.dt + c->prm.perf;
         for (int q = 0; q < c->n_colors; ++q)
             CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
-                                 c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, st));
+                                 c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, st));
         if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -1318,7 +1364,8 @@ int rafem_precond_apply(rafem_ctx* c, int which, const double* r, double* z) {
 }
 
 int rafem_tape_begin(rafem_ctx* c, int32_t checkpoint_every) {
-    if (!c || checkpoint_every < 1 || c->prm.n_corrector != 1) return RAFEM_ERR_BAD_INPUT;
+    if (!c || checkpoint_every < 1 || c->prm.n_corrector != 1 || c->prm.lift != RAFEM_LIFT_SYMMETRIC)
+        return RAFEM_ERR_BAD_INPUT;
     c->tape_every = 0;
     c->n_ckpt = 0;
     const int s = tape_save(c, 0);

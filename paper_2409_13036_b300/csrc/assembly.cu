@@ -84,11 +84,14 @@ __global__ void k_set_identity(int N, const uint8_t* __restrict__ bc, const int3
 // MODE 1: thermal matrix    k_e * G_e + c_matrix * vol_e/20 * (1 + delta_ab), constant rhs perf*T_a*vol/4
 // Memory accesses are batched into three dependent rounds (element data; nodal gathers; previous values of the
 // slots to accumulate into) followed by the stores, instead of one read-modify-write chain per entry.
+// row_lift = 1 keeps the Dirichlet columns of free rows in the matrix (no right-hand-side lift): the system is
+// then nonsymmetric, with the same solution.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int e1, const double* __restrict__ T,
                                                        const uint8_t* __restrict__ bc, const double* __restrict__ g,
                                                        double coef_a, double coef_b, double* __restrict__ vals,
-                                                       float* __restrict__ vals32, double* __restrict__ rhs) {
+                                                       float* __restrict__ vals32, double* __restrict__ rhs,
+                                                       int row_lift) {
     const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= e1) return;
     const size_t E = (size_t)el.E;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int a = q >> 2, b = q & 3;
-        const bool acc = !d[a] && !d[b] && !(code[q] & SLOT_FIRST);
+        const bool acc = !d[a] && (row_lift || !d[b]) && !(code[q] & SLOT_FIRST);
         old[q] = acc ? vals[code[q] & SLOT_MASK] : 0.0;
     }
     double rold[4];
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
             const int q = a * 4 + b;
             double v = scale * Ge[gidx(a, b)];
             if (MODE == 1) v += (a == b) ? mdiag : moff;
-            if (d[b]) {
+            if (d[b] && !row_lift) {
                 lift += v * gn[b];
             } else {
                 const int32_t c = code[q];
@@ -232,7 +235,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble_V_gather(
     int N, const int32_t* __restrict__ sp, const int32_t* __restrict__ sc, const int32_t* __restrict__ diag,
     const int32_t* __restrict__ goff, const int32_t* __restrict__ gcnt, const double* __restrict__ cval,
     const int32_t* __restrict__ celem, const double* __restrict__ f, const uint8_t* __restrict__ bc,
-    const double* __restrict__ g, double* __restrict__ vals, float* __restrict__ vals32, double* __restrict__ b) {
+    const double* __restrict__ g, double* __restrict__ vals, float* __restrict__ vals32, double* __restrict__ b,
+    int row_lift) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= N) return;
     if (bc[row]) {
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble_V_gather(
         for (int m = 0; m < P; ++m) acc = fma(__ldg(cval + off + 32 * m), f[__ldg(celem + off + 32 * m)], acc);
         dsum += acc;
         const int j = __ldg(sc + pos);
-        if (j != row && bc[j]) {
+        if (j != row && bc[j] && !row_lift) {
             lift = fma(acc, g[j], lift);
         } else {
             vals[pos] = acc;
@@ -396,19 +400,20 @@ cudaError_t launch_set_dirichlet_identity(int N, const uint8_t* bc, const int32_
 }
 
 cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* T, const uint8_t* bc,
-                              const double* g, double alpha, double* vals, float* vals32, double* b,
+                              const double* g, double alpha, double* vals, float* vals32, double* b, int row_lift,
                               cudaStream_t st) {
     if (e1 <= e0) return cudaSuccess;
-    k_assemble<0><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, T, bc, g, alpha, 0.0, vals, vals32, b);
+    k_assemble<0><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, T, bc, g, alpha, 0.0, vals, vals32, b,
+                                                            row_lift);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
                               double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
-                              cudaStream_t st) {
+                              int row_lift, cudaStream_t st) {
     if (e1 <= e0) return cudaSuccess;
     k_assemble<1><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, nullptr, bc, g, c_matrix, perf_Ta, vals,
-                                                            vals32, bconst);
+                                                            vals32, bconst, row_lift);
     return cudaGetLastError();
 }
 
@@ -439,12 +444,12 @@ cudaError_t launch_fill_cval(long long nc, const int32_t* celem, const uint8_t* 
 cudaError_t launch_assemble_V_gather(const GatherData& gd, int N, const int32_t* sp, const int32_t* sc,
                                      const int32_t* diag, const ElemData& el, const double* T, double alpha,
                                      const uint8_t* bc, const double* g, double* vals, float* vals32, double* b,
-                                     cudaStream_t st) {
+                                     int row_lift, cudaStream_t st) {
     k_sigma_factor<<<blocks_for(el.E), kThreads, 0, st>>>(el.E, el.nodes, T, alpha, gd.ework);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_assemble_V_gather<<<blocks_for(N), kThreads, 0, st>>>(N, sp, sc, diag, gd.goff, gd.gcnt, gd.cval, gd.celem,
-                                                            gd.ework, bc, g, vals, vals32, b);
+                                                            gd.ework, bc, g, vals, vals32, b, row_lift);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ cudaError_t launch_fill_cval(long long nc, const int32_t* celem, const uint8_t* 
 cudaError_t launch_assemble_V_gather(const GatherData& gd, int N, const int32_t* sp, const int32_t* sc,
                                      const int32_t* diag, const ElemData& el, const double* T, double alpha,
                                      const uint8_t* bc, const double* g, double* vals, float* vals32, double* b,
-                                     cudaStream_t st);
+                                     int row_lift, cudaStream_t st);
 cudaError_t launch_rhs_T_gather(const GatherData& gd, int N, const ElemData& el, const double* T_sigma,
                                 const double* T_old, const double* V, const uint8_t* bc, const double* g,
                                 const double* bconst, double alpha, double c_mass, double* b, cudaStream_t st);
@@ -52,14 +52,15 @@ cudaError_t launch_init_rhs(int N, const uint8_t* bc, const double* g, const dou
                             cudaStream_t st);
 cudaError_t launch_set_dirichlet_identity(int N, const uint8_t* bc, const int32_t* diag, double* vals,
                                           float* vals32, cudaStream_t st);
-// A_V(sigma(T)) for elements [e0, e1) of one colour; lifted rhs contributions into b.
+// A_V(sigma(T)) for elements [e0, e1) of one colour; lifted rhs contributions into b (row_lift: Dirichlet columns
+// stay in the matrix, nothing moves to the rhs).
 cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* T, const uint8_t* bc,
-                              const double* g, double alpha, double* vals, float* vals32, double* b,
+                              const double* g, double alpha, double* vals, float* vals32, double* b, int row_lift,
                               cudaStream_t st);
 // Constant thermal matrix c_mass*M + K_k for one colour; constant rhs part (perfusion + lift) into bconst.
 cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
                               double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
-                              cudaStream_t st);
+                              int row_lift, cudaStream_t st);
 // Thermal right-hand side for one colour: Joule source + (rho_c/dt) M T_old, free rows only.
 cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sigma, const double* T_old,
                          const double* V, const uint8_t* bc, double alpha, double c_mass, double* b,
@@ -214,5 +215,33 @@ cudaError_t launch_ilu_pcg(const IluSolveArgs& a, int grid, cudaStream_t st);
 // z = U^-1 L^-1 r (original ordering; rv, zv: [Np] scratch).
 cudaError_t launch_ilu_apply(const IluLayout& L, const double* F, const double* dinv, const double* r, double* z,
                              double* rv, double* zv, cudaStream_t st);
+
+}  // namespace rafem
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// Persistent Jacobi-BiCGSTAB, FP64, single instance, SELL-32 primary storage (bicgstab.cu).
+// ------------------------------------------------------------------------------------------------------------
+struct BicgArgs {
+    int N;
+    const int32_t* sp;               // slice pointers
+    const int32_t* sc;               // 32-bit columns (used when sc16 is null)
+    const int16_t* sc16;             // 16-bit column deltas or null
+    const double* A;
+    const int32_t* diag;             // storage position of each row's diagonal
+    const double* b;
+    double* x;                       // initial guess in, solution out
+    double *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;  // [N] workspace
+    double* partial;                 // [bicgstab_partial_slots()][grid]
+    GridBarrier* bar;
+    InstState* inst;
+    double tol;
+    int max_iter;
+    long long spin_limit_ns;
+};
+int bicgstab_max_blocks();
+int bicgstab_partial_slots();
+cudaError_t launch_bicgstab(const BicgArgs& a, int grid, cudaStream_t st);
 
 }  // namespace rafem
