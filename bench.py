@@ -416,7 +416,8 @@ def main():
     ap.add_argument("--cells", type=int, default=127)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="run one precision only")
+    ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab"], default=None,
+                    help="run one solver configuration only")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=120, help="steps of the differentiation form (0 = skip)")
     ap.add_argument("--ilu-steps", type=int, default=10, help="timed steps with the ILU(0) preconditioner (0 = skip)")
@@ -466,17 +467,18 @@ def main():
         if name == "fp64" and args.only is None:
             r["ctx"].close()
             r["ctx"] = None
-    if args.ilu_steps > 0 and args.only is None:
+    if args.ilu_steps > 0 and args.only in (None, "ilu0"):
         ilu_args = argparse.Namespace(**vars(args))
         ilu_args.steps = args.ilu_steps
         r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, ilu_args, local, dist, want_clocks=False,
                     precond=rafem.RAFEM_PRECOND_ILU0)
         r["roofline"] = roofline(r, False, peaks, peak_kind)
         r["steps"] = args.ilu_steps
-        r["ctx"].close()
-        r["ctx"] = None
+        if args.only != "ilu0":
+            r["ctx"].close()
+            r["ctx"] = None
         runs["fp64_ilu0"] = r
-    if args.bicgstab_steps > 0 and args.only is None:
+    if args.bicgstab_steps > 0 and args.only in (None, "bicgstab"):
         b_args = argparse.Namespace(**vars(args))
         b_args.steps = args.bicgstab_steps
         r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, b_args, local, dist, want_clocks=False,
@@ -484,10 +486,11 @@ def main():
         r["solver"] = "bicgstab"
         r["roofline"] = roofline(r, False, peaks, peak_kind)
         r["steps"] = args.bicgstab_steps
-        r["ctx"].close()
-        r["ctx"] = None
+        if args.only != "bicgstab":
+            r["ctx"].close()
+            r["ctx"] = None
         runs["fp64_bicgstab"] = r
-    head_name = "mixed" if "mixed" in runs else "fp64"
+    head_name = next(n for n in ("mixed", "fp64", "fp64_ilu0", "fp64_bicgstab") if n in runs)
     head = runs[head_name]
     ctx = head["ctx"]
     N, nnz, n_colors = head["N"], head["nnz"], head["n_colors"]

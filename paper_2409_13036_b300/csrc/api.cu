@@ -112,7 +112,8 @@ struct rafem_ctx {
            *bg_sh = nullptr, *bg_t = nullptr, *bg_dinv = nullptr, *bg_partial = nullptr;
     int bg_grid = 0;
     // differentiation: element order map, tape of checkpoints, adjoint workspace
-    int32_t* e_order = nullptr;      // [E] sorted element -> mesh element
+    int32_t* e_order = nullptr;      // [E] stored element -> mesh element
+    int32_t* e_clist = nullptr;      // [E] stored elements in colour order (row-owner assembly), else null
     double* p_tmpE = nullptr;        // [E] staging of parameter uploads / gradient downloads
     int tape_every = 0;              // 0 = not recording
     int64_t tape_origin = 0;
@@ -724,6 +725,38 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     c->sell = c->lanes == 1;
     const bool want16 = prm->lanes_per_row == 0;
     c->gather = c->sell && prm->assembly == RAFEM_ASSEMBLY_GATHER;
+    // element storage order. The colour scatter needs the elements of a colour stored contiguously; the row-owner
+    // assembly does not, so there the elements are stored by their smallest node (a counting sort, stable in mesh
+    // order), which keeps the nodal gathers of the element passes local. The colour pass over the thermal matrix
+    // then walks a list of storage indices (clist) in colour order, and the slot codes keep the first/last-writer
+    // flags of that colour order.
+    std::vector<int32_t> clist;
+    if (c->gather) {
+        std::vector<int64_t> cnt(N + 1, 0), store(E);
+        std::vector<int32_t> key(E);
+        for (int64_t e = 0; e < E; ++e) {
+            const int32_t* t = m->tets + 4 * e;
+            key[e] = std::min(std::min(t[0], t[1]), std::min(t[2], t[3]));
+            cnt[key[e] + 1]++;
+        }
+        for (int i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+        std::vector<int32_t> pos_store(E);
+        for (int64_t e = 0; e < E; ++e) {
+            const int64_t q = cnt[key[e]]++;
+            store[q] = e;
+            pos_store[e] = (int32_t)q;
+        }
+        std::vector<int32_t> slots_store(slots.size());
+        clist.resize(E);
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < E; ++p) {
+            const int32_t q = pos_store[order[p]];
+            clist[p] = q;
+            for (int k = 0; k < 16; ++k) slots_store[(size_t)k * E + q] = slots[(size_t)k * E + p];
+        }
+        slots.swap(slots_store);
+        order.swap(store);
+    }
     std::vector<int32_t> dev_rp, dev_ci;
     std::vector<int16_t> d16;
     std::vector<int32_t> g_off, g_cnt, g_elem, i_off, i_cnt, i_elem;
@@ -842,6 +875,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->istats, n_inst));
     CK(dalloc(c, &c->bar, 1));
     CK(dalloc(c, &c->e_order, E));
+    if (!clist.empty()) {
+        CK(dalloc(c, &c->e_clist, E));
+        CK(cudaMemcpyAsync(c->e_clist, clist.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    }
     // ---- uploads
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->rp, dev_rp.data(), dev_rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -973,7 +1010,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     const double c_matrix = prm->rho_c / prm->dt + prm->perf;
     for (int q = 0; q < c->n_colors; ++q)
         CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
-                             prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, prm->lift, st));
+                             prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, prm->lift, c->e_clist, st));
     if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     k_init_fields<<<(N + 255) / 256, 256, 0, st>>>(N, prm->T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
     CK(cudaGetLastError());
@@ -1318,7 +1355,7 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
         const double c_matrix = c->prm.rho_c / c->prm.dt + c->prm.perf;
         for (int q = 0; q < c->n_colors; ++q)
             CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
-                                 c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, st));
+                                 c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
         if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     }
     CK(cudaStreamSynchronize(st));

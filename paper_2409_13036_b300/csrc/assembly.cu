@@ -91,9 +91,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
                                                        const uint8_t* __restrict__ bc, const double* __restrict__ g,
                                                        double coef_a, double coef_b, double* __restrict__ vals,
                                                        float* __restrict__ vals32, double* __restrict__ rhs,
-                                                       int row_lift) {
-    const int e = e0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= e1) return;
+                                                       int row_lift, const int32_t* __restrict__ list) {
+    const int ep = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (ep >= e1) return;
+    const int e = list ? __ldg(list + ep) : ep;  // storage index of the element
     const size_t E = (size_t)el.E;
     // round 1: element data
     int n[4];
@@ -404,16 +405,16 @@ cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* 
                               cudaStream_t st) {
     if (e1 <= e0) return cudaSuccess;
     k_assemble<0><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, T, bc, g, alpha, 0.0, vals, vals32, b,
-                                                            row_lift);
+                                                            row_lift, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
                               double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
-                              int row_lift, cudaStream_t st) {
+                              int row_lift, const int32_t* list, cudaStream_t st) {
     if (e1 <= e0) return cudaSuccess;
     k_assemble<1><<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, nullptr, bc, g, c_matrix, perf_Ta, vals,
-                                                            vals32, bconst, row_lift);
+                                                            vals32, bconst, row_lift, list);
     return cudaGetLastError();
 }
 

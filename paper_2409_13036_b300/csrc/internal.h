@@ -10,7 +10,8 @@
 namespace rafem {
 
 // ------------------------------------------------------------------------------------------------------------
-// Element data, SoA over the colour-sorted element order. G holds the 10 distinct entries of
+// Element data, SoA over the element storage order (colour-sorted for the colour scatter, by smallest node for
+// the row-owner assembly). G holds the 10 distinct entries of
 // vol_e * grad(phi_a) . grad(phi_b) in the order (00,11,22,33,01,02,03,12,13,23).
 // ------------------------------------------------------------------------------------------------------------
 struct ElemData {
@@ -57,10 +58,12 @@ cudaError_t launch_set_dirichlet_identity(int N, const uint8_t* bc, const int32_
 cudaError_t launch_assemble_V(const ElemData& el, int e0, int e1, const double* T, const uint8_t* bc,
                               const double* g, double alpha, double* vals, float* vals32, double* b, int row_lift,
                               cudaStream_t st);
-// Constant thermal matrix c_mass*M + K_k for one colour; constant rhs part (perfusion + lift) into bconst.
+// Constant thermal matrix c_mass*M + K_k for one colour; constant rhs part (perfusion + lift) into bconst. The
+// colour's elements are positions [e0, e1) of `list` (storage indices in colour order), or storage indices
+// [e0, e1) themselves when list is null.
 cudaError_t launch_assemble_T(const ElemData& el, int e0, int e1, const uint8_t* bc, const double* g,
                               double c_matrix, double perf_Ta, double* vals, float* vals32, double* bconst,
-                              int row_lift, cudaStream_t st);
+                              int row_lift, const int32_t* list, cudaStream_t st);
 // Thermal right-hand side for one colour: Joule source + (rho_c/dt) M T_old, free rows only.
 cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sigma, const double* T_old,
                          const double* V, const uint8_t* bc, double alpha, double c_mass, double* b,
