@@ -414,7 +414,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rafem", choices=["rafem", "reference"])
     ap.add_argument("--cells", type=int, default=127)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0 = the timed K steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab"], default=None,
                     help="run one solver configuration only")
@@ -495,16 +495,19 @@ def main():
     ctx = head["ctx"]
     N, nnz, n_colors = head["N"], head["nnz"], head["n_colors"]
 
-    # end to end through the C-ABI with host buffers: H2D of the state, one step, D2H of both fields
+    # end to end through the C-ABI with host buffers, over the same steps as the device-timed region: back to the
+    # initial state, the W warm-up steps, then per step H2D of the state, one step, D2H of both fields
     hT = torch.empty(N, dtype=torch.float64).pin_memory()
     hV = torch.empty(N, dtype=torch.float64).pin_memory()
+    ctx.reset()
+    ctx.run(args.warmup)
     ctx.get_field_ptr(rafem.RAFEM_SYS_T, hT.data_ptr(), 0)
     ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)
+    e2e_steps = args.steps if args.e2e_steps <= 0 else min(args.e2e_steps, args.steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    n_done = head["last"]["step"] + 3  # timed steps + the traced ones
-    for k in range(args.e2e_steps):
-        ctx.set_state_ptr(hT.data_ptr(), hV.data_ptr(), 0, n_done + k)
+    for k in range(e2e_steps):
+        ctx.set_state_ptr(hT.data_ptr(), hV.data_ptr(), 0, args.warmup + k)
         ctx.run(1)
         ctx.get_field_ptr(rafem.RAFEM_SYS_T, hT.data_ptr(), 0)
         ctx.get_field_ptr(rafem.RAFEM_SYS_V, hV.data_ptr(), 0)
@@ -537,8 +540,9 @@ def main():
             "refine_V_per_step": head_sum["refine_V_per_step"],
             "regions_ms_per_step": head_sum["regions_ms_per_step"],
             "roofline": head["roofline"],
-            "e2e": {"value": world * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
-                    "d2h_bytes_per_step": 16 * N},
+            "e2e": {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+                    "d2h_bytes_per_step": 16 * N, "steps": e2e_steps,
+                    "note": "same steps as the device-timed region, replayed from the initial state"},
             "gpu_launches": per_step_launches * args.steps,
             "clocks": head["clocks"]}
     if "fp64" in runs and head_name != "fp64":

@@ -107,8 +107,10 @@ typedef struct rafem_params {
                                         with that many lanes per row                                          */
     int32_t rows_per_tile;           /* rows per work tile of the persistent solver: 0 = automatic            */
     int32_t assembly;                /* RAFEM_ASSEMBLY_GATHER (default with SELL-32) or RAFEM_ASSEMBLY_COLOR      */
-    int32_t predictor;               /* 1 = start each solve from the linear extrapolation 2 x^n - x^{n-1}
-                                        (the predictor of the predictor-corrector loop), 0 = from x^n (1)    */
+    int32_t predictor;               /* initial guess of each solve (the predictor of the predictor-corrector
+                                        loop): polynomial extrapolation in time of order 0..3 (0 = x^n,
+                                        1 = 2 x^n - x^{n-1}, 2 = 3 x^n - 3 x^{n-1} + x^{n-2} (default),
+                                        3 = 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3})                          */
     int32_t ilu_order;               /* RAFEM_PRECOND_ILU0 only: RAFEM_ILU_MULTICOLOR (0) or RAFEM_ILU_NATURAL  */
     int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric; BiCGSTAB only)  */
 } rafem_params;
@@ -129,7 +131,7 @@ typedef struct rafem_step_stats {
 typedef struct rafem_ctx rafem_ctx;
 
 /* Liver defaults: alpha 0.015, rho_c 3.6e6, perf 2.4e4, T_a 37, dt 1, tol 1e-10, inner_tol 1e-4, FP64, Jacobi,
- * PCG, one corrector pass, automatic SpMV schedule. */
+ * PCG, one corrector pass, automatic SpMV schedule, quadratic predictor, symmetric lift. */
 void rafem_default_params(rafem_params* p);
 
 /* Build a context: validates the mesh (ids in range, non-degenerate tetrahedra), builds the fixed CSR pattern,
@@ -304,7 +306,7 @@ int rafem_set_params(rafem_ctx* ctx, const double* sigma0, const double* k, int 
 
 /* Start recording: the current state is the tape's origin (checkpoint 0); every later time step taken by
  * rafem_run or rafem_solve_step stores a checkpoint of the state (fields, predictor history, statistics) each time
- * (step - origin) is a multiple of checkpoint_every (>= 1). Checkpoint memory: 4 N doubles each, kept for reuse
+ * (step - origin) is a multiple of checkpoint_every (>= 1). Checkpoint memory: 8 N doubles each, kept for reuse
  * until rafem_destroy. Requires n_corrector = 1. rafem_set_state, rafem_reset, rafem_set_params and rafem_solve end
  * the tape. Errors: BAD_INPUT. */
 int rafem_tape_begin(rafem_ctx* ctx, int32_t checkpoint_every);

@@ -66,6 +66,8 @@ struct rafem_ctx {
     // fields
     double *V = nullptr, *T = nullptr, *T_old = nullptr, *T_prev = nullptr;
     double *V_hist = nullptr, *T_hist = nullptr;   // predictor history (x^{n-1})
+    double *V_hist2 = nullptr, *T_hist2 = nullptr; // predictor history (x^{n-2}), quadratic and cubic predictors
+    double *V_hist3 = nullptr, *T_hist3 = nullptr; // predictor history (x^{n-3}), cubic predictor
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -234,14 +236,30 @@ __global__ void k_set_step(StatsDev* s, long long step) {
     s->worst = 0;
 }
 
-// Predictor: x <- 2 x^n - x^{n-1} on free rows once a previous step exists; the history keeps x^n.
-__global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ xprev, const uint8_t* __restrict__ bc,
-                          const StatsDev* s) {
+// Predictor: polynomial extrapolation in time of the free rows' solution from the last q + 1 solutions, used as
+// the initial guess: linear 2 x^n - x^{n-1}, quadratic 3 x^n - 3 x^{n-1} + x^{n-2}, cubic
+// 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3}, with q = min(order, hist - lag): after hist steps the temperature has
+// hist + 1 states (T^0 included, lag 0) while the potential has been solved hist times (its initial field is not a
+// solution, lag 1). The history shifts to keep the last `order` values.
+__global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ h1, double* __restrict__ h2,
+                          double* __restrict__ h3, const uint8_t* __restrict__ bc, const StatsDev* s, int order,
+                          int lag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double t = x[i];
-    if (s->hist >= 1 && !bc[i]) x[i] = 2.0 * t - xprev[i];
-    xprev[i] = t;
+    const double t1 = order >= 1 ? h1[i] : 0.0, t2 = order >= 2 ? h2[i] : 0.0, t3 = order >= 3 ? h3[i] : 0.0;
+    const int q = min(order, s->hist - lag);
+    if (!bc[i]) {
+        if (q >= 3)
+            x[i] = 4.0 * (t + t2) - 6.0 * t1 - t3;
+        else if (q == 2)
+            x[i] = 3.0 * (t - t1) + t2;
+        else if (q == 1)
+            x[i] = 2.0 * t - t1;
+    }
+    if (order >= 3) h3[i] = t2;
+    if (order >= 2) h2[i] = t1;
+    if (order >= 1) h1[i] = t;
 }
 
 __global__ void k_reset_hist(StatsDev* s) { s->hist = 0; }
@@ -395,9 +413,11 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
 cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     if (!c->prm.predictor) return cudaSuccess;
     if (which == RAFEM_SYS_V)
-        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->V, c->V_hist, c->bcV, c->stats);
+        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->V, c->V_hist, c->V_hist2, c->V_hist3, c->bcV,
+                                                             c->stats, c->prm.predictor, 1);
     else
-        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->T, c->T_hist, c->bcT, c->stats);
+        k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->T, c->T_hist, c->T_hist2, c->T_hist3, c->bcT,
+                                                             c->stats, c->prm.predictor, 0);
     return cudaGetLastError();
 }
 
@@ -504,22 +524,23 @@ cudaError_t launch_step(rafem_ctx* c) {
     return enqueue_step(c);
 }
 
-// ---- checkpoints of the differentiation tape: [T | V | T_hist | V_hist] (N doubles each), StatsDev, istats
+// ---- checkpoints of the differentiation tape: T, V and their predictor histories (8 x N doubles), StatsDev,
+// istats
 size_t state_bytes(const rafem_ctx* c) {
-    return 4 * (size_t)c->N * sizeof(double) + sizeof(StatsDev) + (size_t)c->n_inst * sizeof(rafem_step_stats);
+    return 8 * (size_t)c->N * sizeof(double) + sizeof(StatsDev) + (size_t)c->n_inst * sizeof(rafem_step_stats);
 }
 
 cudaError_t state_copy(rafem_ctx* c, void* buf, bool save) {
     char* p = static_cast<char*>(buf);
     const size_t nb = (size_t)c->N * sizeof(double);
-    double* f[4] = {c->T, c->V, c->T_hist, c->V_hist};
+    double* f[8] = {c->T, c->V, c->T_hist, c->V_hist, c->T_hist2, c->V_hist2, c->T_hist3, c->V_hist3};
     cudaError_t e;
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
         e = save ? cudaMemcpyAsync(p + q * nb, f[q], nb, cudaMemcpyDeviceToDevice, c->stream)
                  : cudaMemcpyAsync(f[q], p + q * nb, nb, cudaMemcpyDeviceToDevice, c->stream);
         if (e != cudaSuccess) return e;
     }
-    p += 4 * nb;
+    p += 8 * nb;
     e = save ? cudaMemcpyAsync(p, c->stats, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream)
              : cudaMemcpyAsync(c->stats, p, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
@@ -582,7 +603,7 @@ void rafem_default_params(rafem_params* p) {
     p->lanes_per_row = 0;
     p->rows_per_tile = 0;
     p->assembly = RAFEM_ASSEMBLY_GATHER;
-    p->predictor = 1;
+    p->predictor = 2;
 }
 
 const char* rafem_status_string(int s) {
@@ -849,6 +870,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->T_prev, N));
     CK(dalloc(c, &c->V_hist, N));
     CK(dalloc(c, &c->T_hist, N));
+    CK(dalloc(c, &c->V_hist2, N));
+    CK(dalloc(c, &c->T_hist2, N));
+    CK(dalloc(c, &c->V_hist3, N));
+    CK(dalloc(c, &c->T_hist3, N));
     CK(dalloc(c, &c->wr, N));
     CK(dalloc(c, &c->wu, N));
     CK(dalloc(c, &c->ww, N));
@@ -1045,6 +1070,7 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
          (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
+    if (prm->predictor < 0 || prm->predictor > 3) return RAFEM_ERR_BAD_INPUT;
     if (prm->lift == RAFEM_LIFT_ROW && prm->solver != RAFEM_SOLVER_BICGSTAB) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
@@ -1317,8 +1343,8 @@ int rafem_reset(rafem_ctx* c) {
     const int N = c->N;
     k_init_fields<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->prm.T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(c->T_hist, 0, N * sizeof(double), c->stream));
-    CK(cudaMemsetAsync(c->V_hist, 0, N * sizeof(double), c->stream));
+    for (double* h : {c->T_hist, c->V_hist, c->T_hist2, c->V_hist2, c->T_hist3, c->V_hist3})
+        CK(cudaMemsetAsync(h, 0, N * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->istats, 0, c->n_inst * sizeof(rafem_step_stats), c->stream));
     CK(cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream));
     c->step = 0;

@@ -305,3 +305,18 @@ def test_full_size_sampled_rows(n):
         assert s == rafem.RAFEM_OK, st.as_dict()
         assert st.relres_V <= 1e-10 and st.relres_T <= 1e-10
         _sampled_check(m, ctx, rafem, T_before, rng)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_predictor_reproduces_steady_fields(order):
+    """With alpha_sigma = 0 the potential does not change from step to step, and every extrapolation order
+    reproduces a constant sequence exactly (its coefficients sum to one), so from the second step on the potential
+    solve starts at its converged solution and takes no iteration."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=61, sigma0="lognormal")
+    with rafem.Context(m, alpha_sigma=0.0, predictor=order) as ctx:
+        s, st = ctx.solve_step()
+        assert s == 0 and st.iters_V > 0
+        for _ in range(4):
+            s, st = ctx.solve_step()
+            assert s == 0 and st.iters_V == 0
