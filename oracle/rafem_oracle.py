@@ -214,9 +214,17 @@ class Model:
 
     # -- one backward-Euler step with optional fixed-point corrector -------------------------------------
     def step(self, T_old):
+        T, V, passes, _ = self.step_detail(T_old)
+        return T, V, passes
+
+    def step_detail(self, T_old):
+        """One step; returns (T, V, passes, converged). With n_corrector > 1 the corrector passes (sigma at the
+        newest temperature iterate, mass term at T^n) stop once max |T^{k+1} - T^k| < corrector_tol; converged
+        tells whether that happened within n_corrector passes (always True for the lagged single pass)."""
         p = self.p
         T_it = T_old
         passes = 0
+        converged = p.n_corrector <= 1
         for passes in range(1, max(1, p.n_corrector) + 1):
             sig = self.sigma(T_it)
             A_V, b_V = self.system_V(T_it)
@@ -226,8 +234,9 @@ class Model:
             change = float(np.max(np.abs(T_new - T_it)))
             T_it = T_new
             if p.n_corrector > 1 and change < p.corrector_tol:
+                converged = True
                 break
-        return T_it, V_new, passes
+        return T_it, V_new, passes, converged
 
     def run(self, n_steps, T0=None):
         """Returns arrays T [n_steps, N] and V [n_steps, N] after each step."""
@@ -238,6 +247,39 @@ class Model:
             Ts.append(T)
             Vs.append(V)
         return np.array(Ts), np.array(Vs)
+
+
+def model_with_dt(model: "Model", dt) -> "Model":
+    """A copy of `model` with time step dt (the thermal matrix depends on it)."""
+    m = Model.__new__(Model)
+    m.__dict__.update({key: val for key, val in model.__dict__.items() if key != "_lu_T"})
+    m.p = dataclasses.replace(model.p, dt=float(dt))
+    m.A_T = ((m.p.rho_c / m.p.dt + m.p.perf) * m.M + m.Kk).tocsr()
+    m.A_T.sort_indices()
+    return m
+
+
+def advance(model: "Model", duration, dt_min, T0=None):
+    """Dynamic time stepping of the main loop (Sec. II-A: dynamically sized steps; Sec. IV: a step whose corrector
+    does not converge within the maximum number of passes is not accepted and the step size is halved, so the
+    run still ends at the same final time). From T0 (default 37 everywhere), steps of the current size
+    dt = model.p.dt, the last one shortened to end exactly at `duration`; a step that does not converge is
+    rejected and retried from the same state with half the size, which is kept afterwards; when half the size would
+    fall below dt_min the step is accepted unconverged. Returns (T, V, log) with log = [(dt, passes, converged,
+    accepted), ...] for every attempted step."""
+    T = np.full(model.N, 37.0) if T0 is None else np.asarray(T0, dtype=np.float64).copy()
+    V = None
+    t, dt, log = 0.0, float(model.p.dt), []
+    while t < duration * (1.0 - 1e-12):
+        dt_step = min(dt, duration - t)
+        T_new, V_new, passes, ok = model_with_dt(model, dt_step).step_detail(T)
+        if ok or dt_step * 0.5 < dt_min:
+            T, V, t = T_new, V_new, t + dt_step
+            log.append((dt_step, passes, ok, True))
+        else:
+            dt = dt_step * 0.5
+            log.append((dt_step, passes, ok, False))
+    return T, V, log
 
 
 # ----------------------------------------------------------------------------------------------------------

@@ -366,3 +366,29 @@ def test_row_lift_same_solution_nonsymmetric_system():
         np.testing.assert_allclose(Ad[~bc], K.toarray()[~bc], rtol=0, atol=1e-15 * abs(K).max())
         xs, xr = O.solve(As, bs), O.solve(Ar, br)
         np.testing.assert_allclose(xr, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+
+
+def test_adaptive_time_stepping_rules():
+    """Dynamic step size (Sec. II-A, Sec. IV): with enough corrector passes and a duration that is a whole number
+    of steps, advance() equals the fixed-step loop exactly; with too few passes it rejects steps and halves the
+    size (every rejection halves, accepted sizes never grow, the last step is shortened), the accepted sizes add
+    up to the duration, and every accepted step converged."""
+    m = mg.cube_mesh(6, jitter=0.1, seed=71, sigma0="lognormal", V_electrode=40.0)
+    full = O.Model(m, O.Params(dt=30.0, n_corrector=50, corrector_tol=1e-6))
+    T, _, log = O.advance(full, 90.0, dt_min=1.0)
+    Tf = np.full(m.n_nodes, 37.0)
+    for _ in range(3):
+        Tf, _, _ = full.step(Tf)
+    np.testing.assert_array_equal(T, Tf)
+    assert [e[3] for e in log] == [True] * 3
+    few = O.Model(m, O.Params(dt=60.0, n_corrector=8, corrector_tol=1e-6))
+    T, _, log = O.advance(few, 100.0, dt_min=1.0)
+    acc = [e for e in log if e[3]]
+    rej = [e for e in log if not e[3]]
+    assert rej and all(not e[2] for e in rej) and all(e[2] for e in acc)
+    assert abs(sum(e[0] for e in acc) - 100.0) <= 1e-9
+    for a, b in zip(log, log[1:]):
+        if not a[3]:
+            assert b[0] == min(a[0] * 0.5, b[0]) or b[0] == a[0] * 0.5
+    sizes = [e[0] for e in acc]
+    assert all(x >= y for x, y in zip(sizes[:-2], sizes[1:-1]))
