@@ -151,8 +151,10 @@ int rafem_assemble(rafem_ctx* ctx, int which);
  * solver settings; fills *stats (nullable) for that system. Returns OK, NOT_CONVERGED or an error. */
 int rafem_solve(rafem_ctx* ctx, int which, rafem_step_stats* stats);
 
-/* One backward-Euler time step (the corrector pass of Sec. II-A): assemble V, solve V, assemble T, solve T,
- * repeated n_corrector times when fixed-point passes are on. stats: nullable. */
+/* One backward-Euler time step (the corrector pass of Sec. II-A): assemble V, solve V, assemble T, solve T.
+ * With n_corrector > 1 the pass repeats on the device (sigma at the newest temperature iterate, mass term at T^n)
+ * until max |T^{k+1} - T^k| < corrector_tol (status NOT_CONVERGED when n_corrector passes did not get there);
+ * stats->correctors holds the passes taken. stats: nullable. */
 int rafem_solve_step(rafem_ctx* ctx, rafem_step_stats* stats);
 
 /* n_steps time steps, each launched as one captured CUDA graph, with no host<->device traffic between steps
@@ -265,6 +267,36 @@ int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
 int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* vals,
                           const double* b, double* x, double tol, int32_t max_iter, void* stream,
                           rafem_step_stats* stats);
+
+/* ---- dynamic step size ---------------------------------------------------------------------------------------
+ * The main loop advances in dynamically sized steps (Sec. II-A); a step whose corrector passes do not converge
+ * within the maximum number of passes is not accepted and the step size is halved, so the simulation still ends
+ * at the requested time (Sec. IV). */
+
+/* Which step graphs are in use: 1 = captured and instantiated, 0 = capture failed (direct launches / host loop),
+ * -1 = not built yet (built at the first step). corrector_graph is the conditional-loop graph of n_corrector > 1. */
+int rafem_graph_info(rafem_ctx* ctx, int32_t* step_graph, int32_t* corrector_graph);
+
+/* Change the step size: reassembles the thermal matrix (and its ILU(0) factors) for the new dt. Ends any tape. */
+int rafem_set_dt(rafem_ctx* ctx, double dt);
+
+typedef struct rafem_advance_stats {
+    int32_t status;                  /* worst status of the accepted steps                                     */
+    int32_t accepted;                /* steps accepted                                                        */
+    int32_t rejected;                /* steps rejected (corrector not converged) and retried with dt / 2      */
+    int32_t passes;                  /* corrector passes over the accepted steps (0 for lagged steps)         */
+    double  dt;                      /* step size at the end (halvings persist; the last step may be shorter) */
+    double  time;                    /* simulated time advanced (= duration)                                  */
+} rafem_advance_stats;
+
+/* Advance the state by `duration` seconds in steps of the current dt, the last one shortened to end exactly at
+ * `duration`. With n_corrector > 1 each step runs its corrector passes on the device (one CUDA graph whose
+ * conditional loop repeats the pass until max |T^{k+1} - T^k| < corrector_tol or n_corrector passes are done); a
+ * step that did not converge is discarded (fields and statistics restored) and retried with half the step size,
+ * kept for later steps. When half the size would fall below dt_min the step is accepted unconverged (status
+ * NOT_CONVERGED). One small read-back per attempted step decides acceptance. Lagged steps (n_corrector = 1) are
+ * always accepted. Ends any tape. stats: nullable. */
+int rafem_advance(rafem_ctx* ctx, double duration, double dt_min, rafem_advance_stats* stats);
 
 /* ---- preconditioner inspection ----------------------------------------------------------------------------
  * ILU(0) (Sec. II-B preconditioning): the factors are those of P A P^T, where P sorts the rows by level (greedy

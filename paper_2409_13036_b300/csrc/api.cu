@@ -30,6 +30,12 @@ struct StatsDev {
     int32_t hist;           // steps completed since the last state reset (predictor history)
 };
 
+struct CorrDev {
+    int32_t pass;           // corrector passes done in the current step
+    int32_t converged;      // 1 once max |T^{k+1} - T^k| < corrector_tol
+    double change;          // max |T^{k+1} - T^k| of the last pass
+};
+
 }  // namespace
 
 struct rafem_ctx {
@@ -95,6 +101,14 @@ struct rafem_ctx {
     // graph
     cudaGraphExec_t graph = nullptr;
     bool graph_failed = false;
+    // corrector passes (n_corrector > 1): one graph per step whose conditional WHILE node repeats the pass on the
+    // device until the temperature change falls below corrector_tol or n_corrector passes are done
+    cudaGraphExec_t corr_graph = nullptr;
+    bool corr_graph_failed = false;
+    CorrDev* corr = nullptr;
+    double* V_old = nullptr;          // potential at the start of the step (restored when a step is rejected)
+    StatsDev* stats_save = nullptr;   // statistics at the start of the step (idem)
+    rafem_step_stats* istats_save = nullptr;
     // tracing
     bool tracing = false;
     rafem_trace trace{};
@@ -263,6 +277,46 @@ __global__ void k_predict(int N, double* __restrict__ x, double* __restrict__ h1
 }
 
 __global__ void k_reset_hist(StatsDev* s) { s->hist = 0; }
+
+__global__ void k_corr_init(CorrDev* c) {
+    c->pass = 0;
+    c->converged = 0;
+    c->change = 0.0;
+}
+
+// After a corrector pass: count it, read max |T^{k+1} - T^k| (non-negative double stored as its bit pattern) and
+// decide whether another pass follows; with a graph the decision drives the conditional WHILE node.
+__global__ void k_corr_check(CorrDev* c, const double* scratch, double tol, int max_pass,
+                             cudaGraphConditionalHandle h, int use_handle) {
+    const double change = *scratch;
+    c->pass += 1;
+    c->change = change;
+    c->converged = change < tol;
+    const int more = !(change < tol) && c->pass < max_pass && change == change;
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// End of a corrector step: pass count into the statistics, step counters advanced; a step whose passes did not
+// converge reports RAFEM_NOT_CONVERGED unless a worse status was recorded.
+__global__ void k_corr_finish(StatsDev* s, rafem_step_stats* istats, int n_inst, const CorrDev* c) {
+    const int st_add = c->converged ? RAFEM_OK : RAFEM_NOT_CONVERGED;
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        rafem_step_stats& q = istats[i];
+        q.correctors = c->pass;
+        q.step += 1;
+        if (q.status >= 0 && st_add > q.status) q.status = st_add;
+    }
+    if (threadIdx.x != 0) return;
+    rafem_step_stats& cur = s->cur;
+    cur.correctors = c->pass;
+    if (cur.status >= 0 && st_add > cur.status) cur.status = st_add;
+    cur.step += 1;
+    s->hist += 1;
+    if (cur.status < 0 || s->worst < 0)
+        s->worst = cur.status < s->worst ? cur.status : s->worst;
+    else
+        s->worst = cur.status > s->worst ? cur.status : s->worst;
+}
 
 __global__ void k_jacobi_apply(int N, const int32_t* __restrict__ diag, const double* __restrict__ A,
                                const double* __restrict__ r, double* __restrict__ z) {
@@ -497,6 +551,118 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     return cudaSuccess;
 }
 
+// ---- corrector passes on the device --------------------------------------------------------------------------
+// Prologue: T_old = T (the mass term keeps T^n), statistics and pass counter cleared.
+cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
+    k_corr_init<<<1, 1, 0, c->stream>>>(c->corr);
+    return cudaGetLastError();
+}
+
+// One corrector pass (sigma at the newest temperature iterate T, mass term at T_old), then the convergence test.
+cudaError_t enqueue_corrector_pass(rafem_ctx* c, cudaGraphConditionalHandle h, int use_handle) {
+    cudaError_t e = cudaMemcpyAsync(c->T_prev, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T_old)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
+    k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
+    if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T_old)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
+    k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 0);
+    if ((e = launch_max_abs_diff(c->N, c->T, c->T_prev, c->scratch, c->stream)) != cudaSuccess) return e;
+    k_corr_check<<<1, 1, 0, c->stream>>>(c->corr, c->scratch, c->prm.corrector_tol, c->prm.n_corrector, h,
+                                        use_handle);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_corr_epilogue(rafem_ctx* c) {
+    k_corr_finish<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst, c->corr);
+    return cudaGetLastError();
+}
+
+// The corrector step as one graph: prologue -> WHILE(more passes) { pass } -> epilogue. The body's last kernel
+// sets the loop condition, so a step needs no host round trip. If the graph cannot be built, steps fall back to
+// a host loop over the same launches (one small read-back per pass).
+void ensure_corr_graph(rafem_ctx* c) {
+    if (c->corr_graph || c->corr_graph_failed) return;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    cudaGraph_t g = nullptr;
+    bool ok = false;
+    do {
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+        cudaGraph_t out = nullptr;
+        if (cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, mode) != cudaSuccess) break;
+        cudaError_t e1 = enqueue_corr_prologue(c);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) break;
+        size_t n = 0;
+        if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) break;
+        std::vector<cudaGraphNode_t> nodes(n), sinks;
+        if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) break;
+        for (cudaGraphNode_t nd : nodes) {
+            size_t k = 0;
+            if (cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &k) == cudaSuccess && k == 0) sinks.push_back(nd);
+        }
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        if (cudaGraphAddNode(&loop, g, sinks.data(), nullptr, sinks.size(), &cp) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, mode) != cudaSuccess) break;
+        e1 = enqueue_corrector_pass(c, h, 1);
+        e2 = cudaStreamEndCapture(c->stream, &out);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) break;
+        if (cudaStreamBeginCaptureToGraph(c->stream, g, &loop, nullptr, 1, mode) != cudaSuccess) break;
+        e1 = enqueue_corr_epilogue(c);
+        e2 = cudaStreamEndCapture(c->stream, &out);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) break;
+        if (cudaGraphInstantiate(&c->corr_graph, g, 0) != cudaSuccess) {
+            c->corr_graph = nullptr;
+            break;
+        }
+        ok = true;
+    } while (false);
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        c->corr_graph_failed = true;
+        cudaGetLastError();
+    }
+}
+
+// One corrector step: the conditional graph, or the host loop when the graph is not available.
+cudaError_t launch_corrector_step(rafem_ctx* c) {
+    if (!c->tracing) {
+        ensure_corr_graph(c);
+        if (c->corr_graph) return cudaGraphLaunch(c->corr_graph, c->stream);
+    }
+    cudaError_t e = enqueue_corr_prologue(c);
+    if (e != cudaSuccess) return e;
+    for (int pass = 0; pass < c->prm.n_corrector; ++pass) {
+        if ((e = enqueue_corrector_pass(c, 0, 0)) != cudaSuccess) return e;
+        CorrDev h;
+        if ((e = cudaMemcpyAsync(&h, c->corr, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+        if (h.converged || !(h.change == h.change)) break;
+    }
+    return enqueue_corr_epilogue(c);
+}
+
+void drop_graphs(rafem_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->corr_graph) cudaGraphExecDestroy(c->corr_graph);
+    c->graph = nullptr;
+    c->corr_graph = nullptr;
+    c->graph_failed = false;
+    c->corr_graph_failed = false;
+}
+
 // The step graph (captured once; direct launches if capture is not possible).
 void ensure_graph(rafem_ctx* c) {
     if (c->graph || c->graph_failed) return;
@@ -626,6 +792,7 @@ void rafem_destroy(rafem_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->corr_graph) cudaGraphExecDestroy(c->corr_graph);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     for (void* p : c->tile_allocs) cudaFree(p);
@@ -900,6 +1067,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->istats, n_inst));
     CK(dalloc(c, &c->bar, 1));
     CK(dalloc(c, &c->e_order, E));
+    CK(dalloc(c, &c->corr, 1));
+    CK(dalloc(c, &c->V_old, N));
+    CK(dalloc(c, &c->stats_save, 1));
+    CK(dalloc(c, &c->istats_save, n_inst));
     if (!clist.empty()) {
         CK(dalloc(c, &c->e_clist, E));
         CK(cudaMemcpyAsync(c->e_clist, clist.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
@@ -1135,37 +1306,9 @@ int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
         const int t = tape_record(c, c->step);
         return t != RAFEM_OK ? t : s;
     }
-    // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n
-    CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
-    CK(cudaGetLastError());
-    int passes = 0;
-    for (passes = 1; passes <= c->prm.n_corrector; ++passes) {
-        CK(cudaMemcpyAsync(c->T_prev, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        CK(enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T_old));
-        CK(enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V));
-        k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
-        CK(enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T_old));
-        CK(enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T));
-        k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 0);
-        CK(launch_max_abs_diff(c->N, c->T, c->T_prev, c->scratch, c->stream));
-        double change = 0;
-        CK(cudaMemcpyAsync(&change, c->scratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        if (!(change >= c->prm.corrector_tol)) break;  // converged (or NaN: reported via status below)
-    }
-    passes = std::min(passes, c->prm.n_corrector);
-    rafem_step_stats h;
-    int s = finish(c, &h, false);
-    h.correctors = passes;
-    h.step = ++c->step;
-    k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)c->step);
-    CK(cudaStreamSynchronize(c->stream));
-    if (s == RAFEM_OK && passes == c->prm.n_corrector) {
-        // the last pass did not meet the corrector tolerance
-    }
-    if (stats) *stats = h;
-    return s;
+    // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n (device-side loop)
+    CK(launch_corrector_step(c));
+    return finish(c, stats, false);
 }
 
 int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
@@ -1174,19 +1317,8 @@ int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
     k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)c->step);
     CK(cudaGetLastError());
     if (c->prm.n_corrector > 1) {
-        int worst = 0;
-        rafem_step_stats h{};
-        for (int i = 0; i < n_steps; ++i) {
-            int s = rafem_solve_step(c, &h);
-            if (s < 0) {
-                if (last) *last = h;
-                return s;
-            }
-            worst = std::max(worst, s);
-        }
-        h.status = worst;
-        if (last) *last = h;
-        return worst;
+        for (int i = 0; i < n_steps; ++i) CK(launch_corrector_step(c));
+        return finish(c, last, true);
     }
     const int64_t s0 = c->step;
     for (int i = 0; i < n_steps; ++i) {
@@ -1424,6 +1556,103 @@ int rafem_precond_apply(rafem_ctx* c, int which, const double* r, double* z) {
     }
     CK(cudaStreamSynchronize(c->stream));
     return RAFEM_OK;
+}
+
+namespace {
+
+// Everything that depends on the step size: the thermal matrix and its constant right-hand side, the node masses
+// of the thermal right-hand side and the thermal ILU factors. The captured graphs are dropped because their
+// kernels take rho_c/dt as an argument.
+int apply_dt(rafem_ctx* c, double dt) {
+    c->prm.dt = dt;
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->bTc, 0, c->N * sizeof(double), st));
+    const double c_matrix = c->prm.rho_c / dt + c->prm.perf;
+    for (int q = 0; q < c->n_colors; ++q)
+        CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
+                             c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
+    if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
+    if (c->gd.mT) CK(launch_node_mass(c->gd, c->N, c->e_vol, c->prm.rho_c / dt, st));
+    drop_graphs(c);
+    return RAFEM_OK;
+}
+
+}  // namespace
+
+int rafem_graph_info(rafem_ctx* c, int32_t* step_graph, int32_t* corrector_graph) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (step_graph) *step_graph = c->graph ? 1 : (c->graph_failed ? 0 : -1);
+    if (corrector_graph) *corrector_graph = c->corr_graph ? 1 : (c->corr_graph_failed ? 0 : -1);
+    return RAFEM_OK;
+}
+
+int rafem_set_dt(rafem_ctx* c, double dt) {
+    if (!c || !(dt > 0) || !std::isfinite(dt)) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
+    const int s = apply_dt(c, dt);
+    if (s != RAFEM_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_advance(rafem_ctx* c, double duration, double dt_min, rafem_advance_stats* out) {
+    if (!c || !(duration > 0) || !std::isfinite(duration) || !(dt_min > 0)) return RAFEM_ERR_BAD_INPUT;
+    c->tape_every = 0;
+    cudaStream_t st = c->stream;
+    const size_t nb = (size_t)c->N * sizeof(double);
+    const bool corrector = c->prm.n_corrector > 1;
+    double t = 0.0, dt = c->prm.dt;
+    int32_t accepted = 0, rejected = 0, passes = 0;
+    k_set_step<<<1, 1, 0, st>>>(c->stats, (long long)c->step);
+    CK(cudaGetLastError());
+    while (t < duration * (1.0 - 1e-12)) {
+        const double dt_step = std::min(dt, duration - t);
+        if (dt_step != c->prm.dt) {
+            const int s = apply_dt(c, dt_step);
+            if (s != RAFEM_OK) return s;
+        }
+        CorrDev h{0, 1, 0.0};
+        if (corrector) {
+            CK(cudaMemcpyAsync(c->V_old, c->V, nb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c->stats_save, c->stats, sizeof(StatsDev), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c->istats_save, c->istats, c->n_inst * sizeof(rafem_step_stats),
+                               cudaMemcpyDeviceToDevice, st));
+            CK(launch_corrector_step(c));
+            CK(cudaMemcpyAsync(&h, c->corr, sizeof(h), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        } else {
+            CK(launch_step(c));
+        }
+        if (h.converged || dt_step * 0.5 < dt_min) {
+            t += dt_step;
+            ++accepted;
+            passes += h.pass;
+        } else {
+            // not accepted: back to the state at the start of the step, retried with half the step size
+            CK(cudaMemcpyAsync(c->T, c->T_old, nb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c->V, c->V_old, nb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c->stats, c->stats_save, sizeof(StatsDev), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c->istats, c->istats_save, c->n_inst * sizeof(rafem_step_stats),
+                               cudaMemcpyDeviceToDevice, st));
+            dt = dt_step * 0.5;
+            ++rejected;
+        }
+    }
+    if (c->prm.dt != dt) {  // keep the (possibly halved) step size, not the shortened last step
+        const int s = apply_dt(c, dt);
+        if (s != RAFEM_OK) return s;
+    }
+    rafem_step_stats last;
+    const int s = finish(c, &last, true);
+    if (out) {
+        out->status = s;
+        out->accepted = accepted;
+        out->rejected = rejected;
+        out->passes = passes;
+        out->dt = dt;
+        out->time = t;
+    }
+    return s;
 }
 
 int rafem_tape_begin(rafem_ctx* c, int32_t checkpoint_every) {

@@ -91,6 +91,14 @@ class rafem_adjoint_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rafem_advance_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("dt", ctypes.c_double), ("time", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -135,6 +143,9 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(ctypes.c_int64), vp]),
         "rafem_get_precond": (ctypes.c_int, [vp, ctypes.c_int, vp]),
         "rafem_precond_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "rafem_set_dt": (ctypes.c_int, [vp, ctypes.c_double]),
+        "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "rafem_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(rafem_advance_stats)]),
         "rafem_reset": (ctypes.c_int, [vp]),
         "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
@@ -371,6 +382,20 @@ class Context:
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+    # -- dynamic step size ------------------------------------------------------------------------------------
+    def graph_info(self) -> dict:
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rafem_graph_info(self._ctx, ctypes.byref(a), ctypes.byref(b)), "rafem_graph_info")
+        return {"step_graph": a.value, "corrector_graph": b.value}
+
+    def set_dt(self, dt: float):
+        _check(lib().rafem_set_dt(self._ctx, float(dt)), "rafem_set_dt")
+
+    def advance(self, duration: float, dt_min: float):
+        st = rafem_advance_stats()
+        s = lib().rafem_advance(self._ctx, float(duration), float(dt_min), ctypes.byref(st))
+        return _check(s, "rafem_advance"), st.as_dict()
 
     # -- preconditioner ---------------------------------------------------------------------------------------
     def precond_info(self) -> dict:
