@@ -182,6 +182,19 @@ def alg_bytes_bicgstab(N: int, nnz: int, iters: float, col_bytes: int) -> float:
     return (iters + 1) * per_iter
 
 
+def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: int, m: int = 30) -> float:
+    """Algorithmic HBM bytes of one GMRES(m) solve launch: per Arnoldi step j an SpMV ((8 + col_bytes) B per stored
+    entry, plus u and dinv gathered and v_j, w written: 32N) and three passes over the basis (j + 1 vectors read
+    by the dots, by the first and by the second orthogonalisation, with w read and written: 3 (j + 1) 8N + 32N);
+    per cycle the residual SpMV ((8 + col_bytes) nnz + 24N) and the update (k + 2 vectors). j averages about half
+    the steps per cycle."""
+    steps_per_cycle = steps / max(cycles, 1.0)
+    j_avg = (steps_per_cycle - 1) / 2.0
+    per_step = (8 + col_bytes) * nnz + 32 * N + 3 * (j_avg + 1) * 8 * N + 32 * N
+    per_cycle = (8 + col_bytes) * nnz + 24 * N + (steps_per_cycle + 2) * 8 * N
+    return steps * per_step + max(cycles, 1.0) * per_cycle
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -237,8 +250,12 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, preco
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     fields = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
+    # region split and iteration counts of the same K steps: replayed from the initial state with tracing on (the
+    # traced launches are identical; tracing only adds an event and a synchronisation between regions)
+    ctx.reset()
+    ctx.run(args.warmup)
     ctx.set_tracing(True)
-    ctx.run(3)
+    ctx.run(args.steps)
     tr = ctx.get_trace()
     ctx.set_tracing(False)
     return {"ctx": ctx, "ms": ms, "status": rafem.status_string(s), "last": st.as_dict(), "trace": tr,
@@ -254,7 +271,11 @@ def roofline(res, mixed, peaks, peak_kind):
     iters = tr["iters_V"] / steps
     cb = res["layout"]["column_bytes"]
     code = res["layout"]["kernel_code"]
-    if res.get("solver") == "bicgstab":
+    if res.get("solver") == "gmres":
+        ref = tr["refine_V"] / steps
+        alg = alg_bytes_gmres(N, nnz, iters, ref, cb)
+        kern = "k_gmres"
+    elif res.get("solver") == "bicgstab":
         ref = 0.0
         alg = alg_bytes_bicgstab(N, nnz, iters, cb)
         kern = "k_bicgstab"
@@ -347,7 +368,7 @@ def measure_adjoint(rafem, torch, mg, args):
     n_steps, every, n_fd = args.adjoint_steps, 10, args.fd_elements
     mesh = mg.cube_mesh(64, jitter=0.10, seed=mg.SEED_BASE + 4)
     dev = torch.device("cuda")
-    ctx = rafem.Context(mesh, tol=1e-12)
+    ctx = rafem.Context(mesh, tol=1e-13)
     # target field: the same forward model with the hidden tumour conductivity
     ctx.set_params(mg.tumour_sigma0(mesh), mesh.k)
     ctx.reset()
@@ -378,6 +399,12 @@ def measure_adjoint(rafem, torch, mg, args):
     rng = np.random.default_rng(mg.SEED_BASE + 5)
     elems = rng.choice(mesh.n_tets, size=n_fd, replace=False)
 
+    # central differences of the forward model solved as smoothly as possible in the parameters: tolerance 1e-13
+    # and each solve started from the previous step's solution (no extrapolation), so that both perturbed runs
+    # follow the same iteration paths
+    ctx.close()
+    ctx = rafem.Context(mesh, tol=1e-13, predictor=0)
+
     def fd_at(eps):
         fd = np.empty(n_fd)
         for i, e in enumerate(elems):
@@ -401,7 +428,8 @@ def measure_adjoint(rafem, torch, mg, args):
     t4 = time.perf_counter()
     ctx.close()
     return {"workload": "64^3 cells (274,625 nodes, 1,572,864 tets), jitter +-10%, tumour-sigma0 target",
-            "steps": n_steps, "checkpoint_every": every, "solver_tol": 1e-12, "params_dtype": "float32",
+            "steps": n_steps, "checkpoint_every": every, "solver_tol": 1e-13, "params_dtype": "float32",
+            "fd_forward": "tol 1e-13, predictor order 0",
             "loss": float(loss.item()), "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
             "backward_over_forward": (t2 - t1) / (t1 - t0), "adjoint": adj,
             "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
@@ -416,12 +444,13 @@ def main():
     ap.add_argument("--cells", type=int, default=127)
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0 = the timed K steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab"], default=None,
+    ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab", "gmres"], default=None,
                     help="run one solver configuration only")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=120, help="steps of the differentiation form (0 = skip)")
     ap.add_argument("--ilu-steps", type=int, default=10, help="timed steps with the ILU(0) preconditioner (0 = skip)")
     ap.add_argument("--bicgstab-steps", type=int, default=5, help="timed steps with BiCGSTAB (0 = skip)")
+    ap.add_argument("--gmres-steps", type=int, default=5, help="timed steps with GMRES(30) (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -490,7 +519,19 @@ def main():
             r["ctx"].close()
             r["ctx"] = None
         runs["fp64_bicgstab"] = r
-    head_name = next(n for n in ("mixed", "fp64", "fp64_ilu0", "fp64_bicgstab") if n in runs)
+    if args.gmres_steps > 0 and args.only in (None, "gmres"):
+        g_args = argparse.Namespace(**vars(args))
+        g_args.steps = args.gmres_steps
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, g_args, local, dist, want_clocks=False,
+                    solver=rafem.RAFEM_SOLVER_GMRES)
+        r["solver"] = "gmres"
+        r["roofline"] = roofline(r, False, peaks, peak_kind)
+        r["steps"] = args.gmres_steps
+        if args.only != "gmres":
+            r["ctx"].close()
+            r["ctx"] = None
+        runs["fp64_gmres30"] = r
+    head_name = next(n for n in ("mixed", "fp64", "fp64_ilu0", "fp64_bicgstab", "fp64_gmres30") if n in runs)
     head = runs[head_name]
     ctx = head["ctx"]
     N, nnz, n_colors = head["N"], head["nnz"], head["n_colors"]
@@ -558,6 +599,8 @@ def main():
             "speedup": head_sum["value"] / line["fp64"]["value"]}
     if "fp64_bicgstab" in runs:
         line["fp64_bicgstab"] = summary(runs["fp64_bicgstab"])
+    if "fp64_gmres30" in runs:
+        line["fp64_gmres30"] = summary(runs["fp64_gmres30"])
     if "fp64_ilu0" in runs:
         line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
         line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]

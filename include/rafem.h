@@ -64,10 +64,14 @@ extern "C" {
 #define RAFEM_SOLVER_BICGSTAB 1      /* BiCGSTAB (general nonsymmetric systems): FP64, Jacobi, SELL-32 layout,
                                         single instance                                                        */
 
+#define RAFEM_SOLVER_GMRES    2      /* restarted GMRES(m), the paper's iterative method (Sec. III-B): FP64, right
+                                        Jacobi, classical Gram-Schmidt with reorthogonalisation, SELL-32 layout,
+                                        single instance; m = gmres_restart                                      */
+
 #define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known
                                         values moved to the right-hand side: the systems stay SPD              */
 #define RAFEM_LIFT_ROW        1      /* Dirichlet rows replaced by identity rows, columns kept: the same solution
-                                        from a nonsymmetric system (needs RAFEM_SOLVER_BICGSTAB; no adjoint)   */
+                                        from a nonsymmetric system (BiCGSTAB or GMRES; no adjoint)              */
 
 #define RAFEM_ASSEMBLY_GATHER 0      /* row-owner assembly: one thread per matrix row sums the element
                                         contributions of its entries (SELL-32 layout only)                    */
@@ -112,7 +116,9 @@ typedef struct rafem_params {
                                         1 = 2 x^n - x^{n-1}, 2 = 3 x^n - 3 x^{n-1} + x^{n-2} (default),
                                         3 = 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3})                          */
     int32_t ilu_order;               /* RAFEM_PRECOND_ILU0 only: RAFEM_ILU_MULTICOLOR (0) or RAFEM_ILU_NATURAL  */
-    int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric; BiCGSTAB only)  */
+    int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric: BiCGSTAB or
+                                        GMRES)                                                                 */
+    int32_t gmres_restart;           /* GMRES restart length m, 1..64 (0 = 30)                                  */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
@@ -120,7 +126,8 @@ typedef struct rafem_step_stats {
     int32_t status;                  /* RAFEM_OK, RAFEM_NOT_CONVERGED or a negative error                     */
     int32_t iters_V;                 /* Krylov iterations of the potential solve (all refinements)             */
     int32_t iters_T;                 /* Krylov iterations of the thermal solve                                  */
-    int32_t refine_V;                /* FP64 refinements of the potential solve (mixed precision, else 0)     */
+    int32_t refine_V;                /* FP64 refinements of the potential solve (mixed precision), restart
+                                        cycles (GMRES), else 0                                                 */
     int32_t refine_T;                /* FP64 refinements of the thermal solve                                  */
     int32_t correctors;              /* corrector passes taken in this step                                    */
     double  relres_V;                /* final relative residual of the potential solve (FP64)                 */

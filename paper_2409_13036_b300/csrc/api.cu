@@ -127,6 +127,9 @@ struct rafem_ctx {
     double *bg_r = nullptr, *bg_rh = nullptr, *bg_p = nullptr, *bg_ph = nullptr, *bg_v = nullptr, *bg_s = nullptr,
            *bg_sh = nullptr, *bg_t = nullptr, *bg_dinv = nullptr, *bg_partial = nullptr;
     int bg_grid = 0;
+    // GMRES(m) (solver == RAFEM_SOLVER_GMRES)
+    int gm_m = 0, gm_grid = 0;
+    double *gm_V = nullptr, *gm_w0 = nullptr, *gm_w1 = nullptr, *gm_dinv = nullptr, *gm_partial = nullptr;
     // differentiation: element order map, tape of checkpoints, adjoint workspace
     int32_t* e_order = nullptr;      // [E] stored element -> mesh element
     int32_t* e_clist = nullptr;      // [E] stored elements in colour order (row-owner assembly), else null
@@ -431,6 +434,29 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         s.max_iter = c->prm.max_iter;
         s.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
         return launch_ilu_pcg(s, c->ilu_grid, c->stream);
+    }
+    if (c->prm.solver == RAFEM_SOLVER_GMRES) {
+        GmresArgs g{};
+        g.N = c->N;
+        g.m = c->gm_m;
+        g.sp = c->rp;
+        g.sc = c->ci;
+        g.sc16 = c->ci16;
+        g.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
+        g.diag = c->diag;
+        g.b = b;
+        g.x = x;
+        g.V = c->gm_V;
+        g.w0 = c->gm_w0;
+        g.w1 = c->gm_w1;
+        g.dinv = c->gm_dinv;
+        g.partial = c->gm_partial;
+        g.bar = c->bar;
+        g.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
+        g.tol = c->prm.tol;
+        g.max_iter = c->prm.max_iter;
+        g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        return launch_gmres(g, c->gm_grid, c->stream);
     }
     if (c->prm.solver == RAFEM_SOLVER_BICGSTAB) {
         BicgArgs g{};
@@ -1144,6 +1170,15 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         const int t = build_tiles(c, prm->rows_per_tile);
         if (t != RAFEM_OK) return t;
     }
+    if (prm->solver == RAFEM_SOLVER_GMRES) {
+        if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
+        c->gm_m = prm->gmres_restart > 0 ? prm->gmres_restart : 30;
+        CK(dalloc(c, &c->gm_V, (size_t)c->gm_m * N + SELL_C));
+        for (double** v : {&c->gm_w0, &c->gm_w1, &c->gm_dinv}) CK(dalloc(c, v, (size_t)N + SELL_C));
+        c->gm_grid = gmres_max_blocks(c->gm_m);
+        if (c->gm_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &c->gm_partial, (size_t)(2 * (c->gm_m + 1) + 2) * c->gm_grid));
+    }
     if (prm->solver == RAFEM_SOLVER_BICGSTAB) {
         if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
         for (double** v : {&c->bg_r, &c->bg_rh, &c->bg_p, &c->bg_ph, &c->bg_v, &c->bg_s, &c->bg_sh, &c->bg_t,
@@ -1235,14 +1270,16 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         (prm->precision != RAFEM_PRECISION_FP64 ||
          (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL)))
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB) return RAFEM_ERR_BAD_INPUT;
-    if (prm->solver == RAFEM_SOLVER_BICGSTAB &&
+    if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB && prm->solver != RAFEM_SOLVER_GMRES)
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->gmres_restart < 0 || prm->gmres_restart > 64) return RAFEM_ERR_BAD_INPUT;
+    if ((prm->solver == RAFEM_SOLVER_BICGSTAB || prm->solver == RAFEM_SOLVER_GMRES) &&
         (prm->precision != RAFEM_PRECISION_FP64 || prm->precond != RAFEM_PRECOND_JACOBI ||
          (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
     if (prm->predictor < 0 || prm->predictor > 3) return RAFEM_ERR_BAD_INPUT;
-    if (prm->lift == RAFEM_LIFT_ROW && prm->solver != RAFEM_SOLVER_BICGSTAB) return RAFEM_ERR_BAD_INPUT;
+    if (prm->lift == RAFEM_LIFT_ROW && prm->solver == RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
 }

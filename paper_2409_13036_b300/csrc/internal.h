@@ -248,3 +248,31 @@ int bicgstab_partial_slots();
 cudaError_t launch_bicgstab(const BicgArgs& a, int grid, cudaStream_t st);
 
 }  // namespace rafem
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// Persistent restarted GMRES(m), FP64, right Jacobi preconditioning, SELL-32 primary storage (gmres.cu).
+// ------------------------------------------------------------------------------------------------------------
+struct GmresArgs {
+    int N, m;                        // rows, restart length (1..64)
+    const int32_t* sp;
+    const int32_t* sc;
+    const int16_t* sc16;
+    const double* A;
+    const int32_t* diag;
+    const double* b;
+    double* x;
+    double* V;                       // [m][N] basis
+    double *w0, *w1, *dinv;          // [N]
+    double* partial;                 // [2 (m + 1) + 2][grid]
+    GridBarrier* bar;
+    InstState* inst;                 // iters = Arnoldi steps, refine = restart cycles
+    double tol;
+    int max_iter;
+    long long spin_limit_ns;
+};
+int gmres_max_blocks(int m);
+cudaError_t launch_gmres(const GmresArgs& a, int grid, cudaStream_t st);
+
+}  // namespace rafem

@@ -36,6 +36,7 @@ RAFEM_PRECISION_FP64 = 0
 RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
+RAFEM_SOLVER_GMRES = 2
 RAFEM_LIFT_SYMMETRIC = 0
 RAFEM_LIFT_ROW = 1
 RAFEM_ILU_MULTICOLOR = 0
@@ -60,7 +61,8 @@ class rafem_params(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("n_corrector", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
-                ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32)]
+                ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):
