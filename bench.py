@@ -435,6 +435,33 @@ def measure_adjoint(rafem, torch, mg, args):
             "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
 
 
+def measure_numbering(rafem, torch, mg, mesh, args):
+    """Sensitivity to the node numbering (mixed precision, 127^3): the lattice numbering, a seeded random
+    renumbering (no locality: 32-bit columns, scattered gathers) and that random mesh renumbered by the library's
+    reverse Cuthill-McKee order (rafem_reorder_rcm). Same K-step timing as the headline, fresh context each."""
+    out = {"steps": args.numbering_steps}
+    shuffled, _ = mg.shuffled_nodes(mesh, mg.SEED_BASE + 6)
+    t0 = time.perf_counter()
+    perm = rafem.reorder_rcm(shuffled)
+    out["rcm_host_s"] = time.perf_counter() - t0
+    for name, m in (("lattice", mesh), ("random", shuffled), ("rcm_of_random", mg.permute_nodes(shuffled, perm))):
+        stream = torch.cuda.Stream()
+        ctx = rafem.Context(m, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_MIXED)
+        lay = ctx.layout_info()
+        ctx.run(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s, st = ctx.run(args.numbering_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"steps_per_s": args.numbering_steps / (ms * 1e-3), "kernel_code": lay["kernel_code"],
+                     "column_bytes": lay["column_bytes"], "status": rafem.status_string(s)}
+        ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +478,7 @@ def main():
     ap.add_argument("--ilu-steps", type=int, default=10, help="timed steps with the ILU(0) preconditioner (0 = skip)")
     ap.add_argument("--bicgstab-steps", type=int, default=5, help="timed steps with BiCGSTAB (0 = skip)")
     ap.add_argument("--gmres-steps", type=int, default=5, help="timed steps with GMRES(30) (0 = skip)")
+    ap.add_argument("--numbering-steps", type=int, default=10, help="timed steps per node numbering (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -611,6 +639,11 @@ def main():
             line["batch"] = measure_batch(rafem, torch, mg, args)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
+    if args.numbering_steps > 0 and args.only is None and args.cells == 127:
+        try:
+            line["numbering"] = measure_numbering(rafem, torch, mg, mesh, args)
+        except Exception as exc:
+            line["numbering"] = {"error": repr(exc)[:300]}
     if args.adjoint_steps > 0 and args.only is None and args.cells == 127:
         try:
             line["adjoint"] = measure_adjoint(rafem, torch, mg, args)

@@ -179,6 +179,15 @@ int rafem_get_field(rafem_ctx* ctx, int which, double* dst, int dst_on_device);
  * its solves from the given fields); when it is equal the run continues and the history is kept. */
 int rafem_set_state(rafem_ctx* ctx, const double* T, const double* V, int on_device, int64_t step);
 
+/* Reverse Cuthill-McKee node order of a mesh (host only, no device work): perm [n_nodes] receives perm[new] = old.
+ * Meshes whose node numbering has no locality (exported from unstructured generators, shuffled) lose the
+ * coalescing of the solver's gathers and the 16-bit column deltas; renumbering them by this order before
+ * rafem_create restores both. Per connected component (in order of its lowest node): start at its smallest-degree
+ * node (lowest index on ties), move to the smallest-degree node of the last breadth-first level while that
+ * increases the eccentricity, number breadth first with unvisited neighbours in increasing (degree, index), and
+ * reverse the whole order. tets: [n_tets*4] host. Errors: BAD_INPUT (index out of range), OOM. */
+int rafem_reorder_rcm(int32_t n_nodes, int32_t n_tets, const int32_t* tets, int32_t* perm);
+
 /* Sizes of the fixed CSR pattern: n_rows (= N), nnz, number of element colours. Any out pointer may be NULL. */
 int rafem_pattern_info(rafem_ctx* ctx, int32_t* n_rows, int64_t* nnz, int32_t* n_colors);
 

@@ -550,3 +550,73 @@ def ilu0_apply(F, r):
     L, U = ilu0_split(F)
     y = spla.spsolve_triangular(L, np.asarray(r, dtype=np.float64), lower=True, unit_diagonal=True)
     return spla.spsolve_triangular(U, y, lower=False)
+
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Node renumbering (locality of unstructured-like numberings): reverse Cuthill-McKee
+# ----------------------------------------------------------------------------------------------------------
+
+def rcm_order(A):
+    """Reverse Cuthill-McKee order of the graph of A (perm[new] = old). For each connected component, taken in
+    order of its lowest node: start at the smallest-degree node (lowest index on ties); while the smallest-degree
+    node of the last breadth-first level (lowest index on ties) has a larger eccentricity, move there; then number
+    breadth first, appending each node's unnumbered neighbours in increasing (degree, index). Reverse at the end."""
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    nbrs = [[int(j) for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i] for i in range(N)]
+    deg = [len(x) for x in nbrs]
+    done = [False] * N
+    order = []
+
+    def levels(s):
+        depth = {s: 0}
+        frontier = [s]
+        while True:
+            nxt = []
+            for u in frontier:
+                for v in nbrs[u]:
+                    if not done[v] and v not in depth:
+                        depth[v] = depth[u] + 1
+                        nxt.append(v)
+            if not nxt:
+                return depth[frontier[0]], frontier
+            frontier = nxt
+
+    def smallest(nodes):
+        return min(nodes, key=lambda v: (deg[v], v))
+
+    for first in range(N):
+        if done[first]:
+            continue
+        comp, seen = [first], {first}
+        for u in comp:
+            for v in nbrs[u]:
+                if not done[v] and v not in seen:
+                    seen.add(v)
+                    comp.append(v)
+        s = smallest(comp)
+        ecc, last = levels(s)
+        while True:
+            c = smallest(last)
+            e2, last2 = levels(c)
+            if e2 <= ecc:
+                break
+            s, ecc, last = c, e2, last2
+        start = len(order)
+        order.append(s)
+        done[s] = True
+        h = start
+        while h < len(order):
+            u = order[h]
+            for v in sorted((v for v in nbrs[u] if not done[v]), key=lambda v: (deg[v], v)):
+                done[v] = True
+                order.append(v)
+            h += 1
+    return np.array(order[::-1], dtype=np.int64)
+
+
+def bandwidth(A):
+    """max |i - j| over the stored entries."""
+    A = sp.coo_matrix(A)
+    return int(np.abs(A.row - A.col).max()) if A.nnz else 0

@@ -174,6 +174,21 @@ __global__ void k_permute(int n, const int32_t* __restrict__ perm, const double*
         out[i] = in[perm[i]];
 }
 
+// Initial guess of an adjoint solve: polynomial extrapolation (order q, see the forward predictor) of the last
+// solutions of the backward sweep; x holds the newest and is overwritten, the history shifts.
+__global__ void k_adj_extrapolate(int N, double* __restrict__ x, double* __restrict__ h1, double* __restrict__ h2,
+                                  int q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double t = x[i], t1 = h1[i], t2 = h2[i];
+    if (q >= 2)
+        x[i] = 3.0 * (t - t1) + t2;
+    else if (q == 1)
+        x[i] = 2.0 * t - t1;
+    h2[i] = t1;
+    h1[i] = t;
+}
+
 // Sum of the Krylov iterations of one adjoint solve (maximum over instances) and the worst status.
 __global__ void k_adj_count(const InstState* __restrict__ inst, int n_inst, const GridBarrier* __restrict__ bar,
                             int32_t* __restrict__ acc /* [iters_V, iters_T, status] */, int slot) {
@@ -227,6 +242,11 @@ cudaError_t launch_mask(int N, const uint8_t* bc, const double* in, double* out,
 cudaError_t launch_permute(int n, const int32_t* perm, const double* in, double* out, int scatter, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     k_permute<<<blocks_for(n), kThreads, 0, st>>>(n, perm, in, out, scatter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_extrapolate(int N, double* x, double* h1, double* h2, int q, cudaStream_t st) {
+    k_adj_extrapolate<<<blocks_for(N), kThreads, 0, st>>>(N, x, h1, h2, q);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,7 @@ struct rafem_ctx {
     double *a_segT = nullptr, *a_segV = nullptr;   // [seg_cap + 1][N], [seg_cap][N]
     double *a_lam = nullptr, *a_mu = nullptr, *a_nu = nullptr, *a_h = nullptr, *a_dv = nullptr;
     double *a_ew4 = nullptr, *a_w = nullptr, *a_gs = nullptr, *a_gk = nullptr;
+    double *a_mu1 = nullptr, *a_mu2 = nullptr, *a_nu1 = nullptr, *a_nu2 = nullptr;  // backward-sweep histories
     int32_t* a_count = nullptr;      // [iters_V, iters_T, adjoint status, recomputation status]
 };
 
@@ -1420,6 +1421,20 @@ int rafem_set_state(rafem_ctx* c, const double* T, const double* V, int on_devic
     return RAFEM_OK;
 }
 
+int rafem_reorder_rcm(int32_t n_nodes, int32_t n_tets, const int32_t* tets, int32_t* perm) {
+    if (!tets || !perm || n_nodes < 1 || n_tets < 1) return RAFEM_ERR_BAD_INPUT;
+    for (int64_t q = 0; q < 4LL * n_tets; ++q)
+        if (tets[q] < 0 || tets[q] >= n_nodes) return RAFEM_ERR_BAD_INPUT;
+    try {
+        std::vector<int32_t> p;
+        reorder_rcm(n_nodes, n_tets, tets, p);
+        std::copy(p.begin(), p.end(), perm);
+    } catch (const std::bad_alloc&) {
+        return RAFEM_ERR_OOM;
+    }
+    return RAFEM_OK;
+}
+
 int rafem_pattern_info(rafem_ctx* c, int32_t* n_rows, int64_t* nnz, int32_t* n_colors) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     if (n_rows) *n_rows = c->N;
@@ -1743,6 +1758,7 @@ int ensure_adjoint(rafem_ctx* c) {
         CK(dalloc(c, &c->a_gs, E));
         CK(dalloc(c, &c->a_gk, E));
         CK(dalloc(c, &c->a_count, 4));
+        for (double** v : {&c->a_mu1, &c->a_mu2, &c->a_nu1, &c->a_nu2}) CK(dalloc(c, v, N));
         char* live = nullptr;
         CK(dalloc(c, &live, state_bytes(c)));
         c->ckpt_live = live;
@@ -1798,6 +1814,7 @@ int rafem_adjoint(rafem_ctx* c, const double* dL_dT, const double* dL_dV, int in
         CK(launch_mask(N, c->bcT, c->a_h, c->a_lam, st));
         CK(state_copy(c, c->ckpt_live, true));
         const int64_t live_step = c->step;
+        int64_t done = 0;  // backward steps taken (history available to the extrapolation)
         const int saved_every = c->tape_every;
         c->tape_every = 0;  // the recomputation must not write checkpoints
         for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
@@ -1817,15 +1834,20 @@ int rafem_adjoint(rafem_ctx* c, const double* dL_dT, const double* dL_dV, int in
                 const double* Tn = c->a_segT + (size_t)j * N;
                 const double* T1 = c->a_segT + (size_t)(j + 1) * N;
                 const double* V1 = c->a_segV + (size_t)j * N;
+                // initial guesses extrapolated along the backward sweep (the forward predictor's order, at most 2)
+                const int q = (int)std::min<int64_t>(std::min(c->prm.predictor, 2), done);
+                CK(launch_adj_extrapolate(N, c->a_mu, c->a_mu1, c->a_mu2, q, st));
                 CK(enqueue_solve(c, RAFEM_SYS_T, c->a_lam, c->a_mu));
                 CK(launch_adj_count(c->instT, c->n_inst, c->bar, c->a_count, 1, st));
                 CK(enqueue_assemble(c, RAFEM_SYS_V, Tn, Tn));
                 CK(launch_adj_h(c->el, c->gd, N, Tn, V1, c->a_mu, alpha, c->bcV,
                                 (dL_dV && n == nsteps - 1) ? c->a_dv : nullptr, c->a_ew4, c->a_h, st));
+                CK(launch_adj_extrapolate(N, c->a_nu, c->a_nu1, c->a_nu2, q, st));
                 CK(enqueue_solve(c, RAFEM_SYS_V, c->a_h, c->a_nu));
                 CK(launch_adj_count(c->instV, c->n_inst, c->bar, c->a_count, 0, st));
                 CK(launch_adj_g(c->el, c->gd, N, Tn, V1, T1, c->a_mu, c->a_nu, alpha, c_mass, c->bcT, n != 0,
                                 c->a_gs, c->a_gk, c->a_w, c->a_lam, st));
+                ++done;
             }
         }
         CK(state_copy(c, c->ckpt_live, false));

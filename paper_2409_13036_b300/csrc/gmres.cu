@@ -114,6 +114,28 @@ __device__ __forceinline__ void totals(const double* part, int n, double* tot) {
     __syncthreads();
 }
 
+// acc[warp][i] += (w, v_i) over this warp's rows for i < n. Each lane keeps kDot running sums in registers over
+// all its rows and the warp reduces them once per group of kDot basis vectors (a warp reduction per row and
+// vector would serialise the warp on shuffle latency). w holds values this thread wrote itself.
+constexpr int kDot = 8;
+__device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, int S) {
+    for (int i0 = 0; i0 < n; i0 += kDot) {
+        double sum[kDot];
+#pragma unroll
+        for (int t = 0; t < kDot; ++t) sum[t] = 0.0;
+        for_slices(S, [&](int, int row) {
+            if (row >= a.N) return;
+            const double wi = w[row];
+#pragma unroll
+            for (int t = 0; t < kDot; ++t)
+                if (i0 + t < n) sum[t] = fma(wi, ldcg(a.Vb + (size_t)(i0 + t) * a.N + row), sum[t]);
+        });
+#pragma unroll
+        for (int t = 0; t < kDot; ++t)
+            if (i0 + t < n) warp_add(acc, i0 + t, sum[t]);
+    }
+}
+
 __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     extern __shared__ double smem[];
     // layout: acc [kWarps][72] | H [(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | tot[72] | y[m]
@@ -186,36 +208,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
             double* wn = a.w[cur ^ 1];
             double* vj = a.Vb + (size_t)j * N;
             const double inv = 1.0 / scale;
-            // S: v_j = u / s, w = A M^-1 u / s, h_ij = (w, v_i) for i <= j
+            // S: v_j = u / s, w = A M^-1 u / s, then h_ij = (w, v_i) for i <= j
             for_slices(S, [&](int s, int row) {
-                const bool ok = row < N;
-                double wi = 0.0, vji = 0.0;
-                if (ok) {
-                    wi = spmv_row(a, u, a.dinv, s, row) * inv;
-                    vji = ldcg(u + row) * inv;
-                    vj[row] = vji;
-                    wn[row] = wi;
-                }
-                for (int i = 0; i < j; ++i) warp_add(acc, i, ok ? wi * ldcg(a.Vb + (size_t)i * N + row) : 0.0);
-                warp_add(acc, j, wi * vji);
+                if (row >= N) return;
+                wn[row] = spmv_row(a, u, a.dinv, s, row) * inv;
+                vj[row] = ldcg(u + row) * inv;
             });
+            dots(a, acc, wn, j + 1, S);
             publish(acc, j + 1, PA);
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
             totals(PA, j + 1, tot);
             for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(size_t)j * (m + 1) + i] = tot[i];
             __syncthreads();
-            // O1: w -= sum_i h_ij v_i, c_ij = (w, v_i)
+            // O1: w -= sum_i h_ij v_i, then c_ij = (w, v_i)
             for_slices(S, [&](int, int row) {
-                const bool ok = row < N;
-                double wi = 0.0;
-                if (ok) {
-                    wi = wn[row];
-                    for (int i = 0; i <= j; ++i)
-                        wi = fma(-H[(size_t)j * (m + 1) + i], ldcg(a.Vb + (size_t)i * N + row), wi);
-                    wn[row] = wi;
-                }
-                for (int i = 0; i <= j; ++i) warp_add(acc, i, ok ? wi * ldcg(a.Vb + (size_t)i * N + row) : 0.0);
+                if (row >= N) return;
+                double wi = wn[row];
+                for (int i = 0; i <= j; ++i)
+                    wi = fma(-H[(size_t)j * (m + 1) + i], ldcg(a.Vb + (size_t)i * N + row), wi);
+                wn[row] = wi;
             });
+            dots(a, acc, wn, j + 1, S);
             publish(acc, j + 1, PB);
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
             totals(PB, j + 1, tot);

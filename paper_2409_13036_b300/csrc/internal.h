@@ -169,6 +169,8 @@ cudaError_t launch_mask(int N, const uint8_t* bc, const double* in, double* out,
 cudaError_t launch_permute(int n, const int32_t* perm, const double* in, double* out, int scatter, cudaStream_t st);
 cudaError_t launch_adj_count(const InstState* inst, int n_inst, const GridBarrier* bar, int32_t* acc, int slot,
                              cudaStream_t st);
+// x <- extrapolation of order q (0..2) from x (newest), h1, h2; history shifted (h2 <- h1 <- x).
+cudaError_t launch_adj_extrapolate(int N, double* x, double* h1, double* h2, int q, cudaStream_t st);
 
 }  // namespace rafem
 

@@ -386,3 +386,98 @@ int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>&
 }
 
 }  // namespace rafem
+
+namespace rafem {
+
+int reorder_rcm(int N, int E, const int32_t* tets, std::vector<int32_t>& perm) {
+    std::vector<int32_t> rp, col;
+    build_pattern(N, E, tets, rp, col);
+    std::vector<int32_t> deg(N);
+    for (int i = 0; i < N; ++i) deg[i] = rp[i + 1] - rp[i] - 1;  // the pattern stores the diagonal
+    std::vector<char> seen(N, 0);
+    std::vector<int32_t> order;
+    order.reserve(N);
+    std::vector<int32_t> level(N, -1), nb;
+    // breadth-first level structure from s over the unvisited component; returns (eccentricity, last level)
+    auto bfs_levels = [&](int s, std::vector<int32_t>& last) {
+        std::vector<int32_t> cur{s}, next, touched{s};
+        level[s] = 0;
+        int ecc = 0;
+        while (true) {
+            next.clear();
+            for (int u : cur)
+                for (int32_t q = rp[u]; q < rp[u + 1]; ++q) {
+                    const int v = col[q];
+                    if (v == u || seen[v] || level[v] >= 0) continue;
+                    level[v] = ecc + 1;
+                    next.push_back(v);
+                    touched.push_back(v);
+                }
+            if (next.empty()) break;
+            ++ecc;
+            cur.swap(next);
+        }
+        last = cur;
+        for (int v : touched) level[v] = -1;
+        return ecc;
+    };
+    for (int first = 0; first < N; ++first) {
+        if (seen[first]) continue;
+        // start: the smallest-degree unvisited node of this component (lowest index on ties) ...
+        int s = first;
+        {
+            // collect the component by a plain traversal (level[] marks members, cleared afterwards)
+            std::vector<int32_t> comp{first};
+            level[first] = 0;
+            for (size_t h = 0; h < comp.size(); ++h) {
+                const int u = comp[h];
+                for (int32_t q = rp[u]; q < rp[u + 1]; ++q) {
+                    const int v = col[q];
+                    if (v == u || seen[v] || level[v] >= 0) continue;
+                    level[v] = 0;
+                    comp.push_back(v);
+                }
+            }
+            for (int v : comp) {
+                level[v] = -1;
+                if (deg[v] < deg[s] || (deg[v] == deg[s] && v < s)) s = v;
+            }
+        }
+        // ... moved to a pseudo-peripheral node: the smallest-degree node of the last level while that increases
+        // the eccentricity
+        std::vector<int32_t> last;
+        int ecc = bfs_levels(s, last);
+        while (true) {
+            int c = last[0];
+            for (int v : last)
+                if (deg[v] < deg[c] || (deg[v] == deg[c] && v < c)) c = v;
+            std::vector<int32_t> last2;
+            const int e2 = bfs_levels(c, last2);
+            if (e2 <= ecc) break;
+            s = c;
+            ecc = e2;
+            last.swap(last2);
+        }
+        // Cuthill-McKee: breadth first from s, unvisited neighbours in increasing (degree, index)
+        const size_t h0 = order.size();
+        order.push_back(s);
+        seen[s] = 1;
+        for (size_t h = h0; h < order.size(); ++h) {
+            const int u = order[h];
+            nb.clear();
+            for (int32_t q = rp[u]; q < rp[u + 1]; ++q) {
+                const int v = col[q];
+                if (!seen[v]) nb.push_back(v);
+            }
+            std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+            for (int v : nb) {
+                seen[v] = 1;
+                order.push_back(v);
+            }
+        }
+    }
+    perm.assign(order.rbegin(), order.rend());
+    return 0;
+}
+
+}  // namespace rafem

@@ -67,4 +67,10 @@ struct IluHost {
 // Returns 0, or -1 when a row has more than 255 entries or the padded size overflows.
 int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int order, IluHost& out);
 
+// Reverse Cuthill-McKee order of the node graph: perm[new] = old. Per connected component (taken in order of its
+// lowest node): start at the component's smallest-degree node (lowest index on ties), move to the smallest-degree
+// node of the last breadth-first level while that increases the eccentricity, then number breadth first with the
+// unvisited neighbours of each node in increasing (degree, index); the whole order is reversed at the end.
+int reorder_rcm(int N, int E, const int32_t* tets, std::vector<int32_t>& perm);
+
 }  // namespace rafem

@@ -152,6 +152,25 @@ def cube_mesh(n: int, *, jitter: float = 0.0, seed: int | None = None, side_mm: 
                 electrode=electrode.astype(np.uint8), V_electrode=float(V_electrode))
 
 
+def permute_nodes(mesh: Mesh, perm) -> Mesh:
+    """The same mesh with its nodes renumbered: new node k is old node perm[k] (element order unchanged)."""
+    perm = np.asarray(perm, dtype=np.int64)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.shape[0])
+    return dataclasses.replace(
+        mesh, coords=np.ascontiguousarray(mesh.coords[perm]), tets=np.ascontiguousarray(inv[mesh.tets], dtype=np.int32),
+        lattice=np.ascontiguousarray(mesh.lattice[perm]), bc_V=np.ascontiguousarray(mesh.bc_V[perm]),
+        g_V=np.ascontiguousarray(mesh.g_V[perm]), bc_T=np.ascontiguousarray(mesh.bc_T[perm]),
+        g_T=np.ascontiguousarray(mesh.g_T[perm]), electrode=np.ascontiguousarray(mesh.electrode[perm]))
+
+
+def shuffled_nodes(mesh: Mesh, seed: int) -> tuple[Mesh, np.ndarray]:
+    """A seeded random renumbering of the nodes (an unstructured-like numbering without locality); returns the
+    renumbered mesh and perm (new node k = old node perm[k])."""
+    perm = np.random.default_rng(seed).permutation(mesh.n_nodes)
+    return permute_nodes(mesh, perm), perm
+
+
 # ---------------------------------------------------------------------------------------------------------
 # Named workloads (sizes and draws of the liver-cube workloads)
 # ---------------------------------------------------------------------------------------------------------

@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
         "rafem_set_dt": (ctypes.c_int, [vp, ctypes.c_double]),
         "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "rafem_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(rafem_advance_stats)]),
+        "rafem_reorder_rcm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, vp]),
         "rafem_reset": (ctypes.c_int, [vp]),
         "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
@@ -468,6 +469,15 @@ def pcg_csr_noalloc(n_rows, row_ptr, col, vals, b, x, tol=1e-10, max_iter=20000,
     s = lib().rafem_pcg_csr_noalloc(int(n_rows), _dev(row_ptr), _dev(col), _dev(vals), _dev(b), _dev(x), float(tol),
                                     int(max_iter), ctypes.c_void_p(stream or 0), ctypes.byref(st))
     return s, st
+
+
+def reorder_rcm(mesh) -> np.ndarray:
+    """rafem_reorder_rcm: reverse Cuthill-McKee node order of a mesh (perm[new] = old)."""
+    tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+    perm = np.empty(int(np.asarray(mesh.coords).shape[0]), np.int32)
+    _check(lib().rafem_reorder_rcm(perm.shape[0], tets.shape[0], tets.ctypes.data, perm.ctypes.data),
+           "rafem_reorder_rcm")
+    return perm
 
 
 # C names, for callers that prefer the flat API

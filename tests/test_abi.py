@@ -62,3 +62,23 @@ def test_mesh_generator_counts():
         assert (m.n_nodes, m.n_tets, int(m.electrode.sum())) == (N, E, el)
     m = mg.cube_mesh(127, jitter=0.0)
     assert int(m.electrode.sum()) == 16 * 32
+
+
+def test_reorder_rcm_matches_oracle():
+    """rafem_reorder_rcm (host-only entry point) returns the oracle's reverse Cuthill-McKee order bit for bit, on
+    a shuffled jittered cube and on a mesh of two disconnected cubes."""
+    import dataclasses
+    import numpy as np
+    from oracle import rafem_oracle as O
+    from paper_2409_13036_b300 import meshgen as mg, rafem
+    a, _ = mg.shuffled_nodes(mg.cube_mesh(6, jitter=0.1, seed=3), 9)
+    b, _ = mg.shuffled_nodes(mg.cube_mesh(4, jitter=0.1, seed=4), 10)
+    two = dataclasses.replace(
+        a, coords=np.vstack([a.coords, b.coords + 1.0]), tets=np.vstack([a.tets, b.tets + a.n_nodes]).astype(np.int32),
+        lattice=np.vstack([a.lattice, b.lattice]), bc_V=np.concatenate([a.bc_V, b.bc_V]),
+        g_V=np.concatenate([a.g_V, b.g_V]), bc_T=np.concatenate([a.bc_T, b.bc_T]), g_T=np.concatenate([a.g_T, b.g_T]),
+        sigma0=np.concatenate([a.sigma0, b.sigma0]), k=np.concatenate([a.k, b.k]),
+        electrode=np.concatenate([a.electrode, b.electrode]))
+    for m in (a, two):
+        A = O.Model(m).system_V(np.full(m.n_nodes, 37.0))[0]
+        np.testing.assert_array_equal(rafem.reorder_rcm(m), O.rcm_order(A))
