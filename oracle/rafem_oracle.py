@@ -620,3 +620,90 @@ def bandwidth(A):
     """max |i - j| over the stored entries."""
     A = sp.coo_matrix(A)
     return int(np.abs(A.row - A.col).max()) if A.nnz else 0
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Monolithic coupled step (the paper's 2N x 2N system shape, Table II): V and T of a step solved together by
+# Newton's method on
+#   R_V = K(sigma(T)) V                                            (free potential rows)
+#   R_T = A_T T - (rho_c/dt) M T^n - perf T_a M 1 - F(V, sigma(T))  (free thermal rows)
+# with sigma at the element mean of the new T (no lagging). Its solution is the fixed point the corrector passes
+# converge to. Unknowns are interleaved per node: x[2i] = V_i, x[2i+1] = T_i.
+# ----------------------------------------------------------------------------------------------------------
+
+def coupled_residual(model: "Model", V, T, T_old):
+    """R (length 2N, interleaved) of the coupled step at (V, T); Dirichlet rows hold x - g."""
+    p = model.p
+    tets = model.tets
+    sig = model.sigma(T)
+    K = assemble(element_stiffness(sig, model.vol, model.grad), tets, model.N)
+    RV = K @ V
+    Q = joule(sig, V, tets, model.grad)
+    RT = model.A_T @ T - model.rhs_T_unlifted(T_old, Q)
+    RV = np.where(model.bc_V, V - model.g_V, RV)
+    RT = np.where(model.bc_T, T - model.g_T, RT)
+    R = np.empty(2 * model.N)
+    R[0::2] = RV
+    R[1::2] = RT
+    return R
+
+
+def coupled_jacobian(model: "Model", V, T):
+    """dR/dx of coupled_residual (2N x 2N CSR, interleaved), from the element derivatives:
+      d(K V)_i/dT_a   = sum_e (sigma0_e alpha / 4) (G_e V_e)_i
+      dF_i/dV_j       = sum_e (sigma_e / 4) 2 (G_e V_e)_j
+      dF_i/dT_a       = sum_e (sigma0_e alpha / 4) (V_e^T G_e V_e) / 4
+    (sums over the elements containing both nodes), G_e = vol_e grad(phi) grad(phi)^T; Dirichlet rows are
+    identity rows of their own unknown."""
+    p = model.p
+    tets = model.tets
+    N, E = model.N, len(tets)
+    sig = model.sigma(T)
+    G = element_stiffness(np.ones(E), model.vol, model.grad)          # [E, 4, 4]
+    Ve = np.asarray(V)[tets]
+    GV = np.einsum("eab,eb->ea", G, Ve)                                  # [E, 4]
+    quad = np.einsum("ea,ea->e", Ve, GV)
+    ds = model.sigma0 * p.alpha_sigma / 4.0                              # d sigma_e / d T_a, a in e
+    KVV = sig[:, None, None] * G                                         # d R_V / d V
+    KVT = ds[:, None, None] * np.repeat(GV[:, :, None], 4, axis=2)      # [e, i, a] = ds_e (G V)_i
+    KTV = -(sig / 4.0)[:, None, None] * 2.0 * np.repeat(GV[:, None, :], 4, axis=1)   # [e, i, j] = -(s/4) 2 (G V)_j
+    KTT = -(ds * quad / 4.0)[:, None, None] * np.ones((1, 4, 4))        # - dF_i / dT_a
+    rows = np.repeat(tets, 4, axis=1).ravel()
+    cols = np.tile(tets, (1, 4)).ravel()
+    blocks = []
+    for (bi, bj, Ke) in ((0, 0, KVV), (0, 1, KVT), (1, 0, KTV), (1, 1, KTT)):
+        blocks.append((2 * rows + bi, 2 * cols + bj, Ke.ravel()))
+    AT = sp.coo_matrix(model.A_T)
+    blocks.append((2 * AT.row + 1, 2 * AT.col + 1, AT.data))
+    r = np.concatenate([b[0] for b in blocks])
+    c = np.concatenate([b[1] for b in blocks])
+    v = np.concatenate([b[2] for b in blocks])
+    J = sp.coo_matrix((v, (r, c)), shape=(2 * N, 2 * N)).tocsr()
+    J.sum_duplicates()
+    dir_rows = np.concatenate([2 * np.flatnonzero(model.bc_V), 2 * np.flatnonzero(model.bc_T) + 1])
+    J = J.tolil()
+    for rr in dir_rows:
+        J.rows[rr] = [int(rr)]
+        J.data[rr] = [1.0]
+    J = J.tocsr()
+    J.sort_indices()
+    return J
+
+
+def step_newton(model: "Model", T_old, V0=None, tol=1e-10, max_iter=50):
+    """One coupled step by Newton's method from (V0, T_old) (Dirichlet values imposed first); stops when
+    max |dT| < tol. Returns (T, V, iterations, [max |dT| per iteration])."""
+    N = model.N
+    V = np.where(model.bc_V, model.g_V, np.zeros(N) if V0 is None else np.asarray(V0, dtype=np.float64))
+    T = np.where(model.bc_T, model.g_T, np.asarray(T_old, dtype=np.float64))
+    hist = []
+    for it in range(1, max_iter + 1):
+        R = coupled_residual(model, V, T, T_old)
+        J = coupled_jacobian(model, V, T)
+        d = spla.spsolve(J.tocsc(), -R)
+        V = V + d[0::2]
+        T = T + d[1::2]
+        hist.append(float(np.max(np.abs(d[1::2]))))
+        if hist[-1] < tol:
+            break
+    return T, V, it, hist
