@@ -435,6 +435,31 @@ def measure_adjoint(rafem, torch, mg, args):
             "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
 
 
+def measure_monolithic(rafem, torch, mesh, args):
+    """The paper's 2N x 2N system shape: V and T of each step solved together by Newton's method (corrector_tol
+    1e-6 degC on max |dT|, at most 20 iterations), block-Jacobi BiCGSTAB to 1e-10 per linear solve, on the 127^3
+    workload; K steps after W warm-up, CUDA events on the context's stream. Reported beside the staggered
+    (lagged) step; the two compute different time discretisations (implicit vs lagged coupling)."""
+    stream = torch.cuda.Stream()
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, coupling=rafem.RAFEM_COUPLING_MONOLITHIC, n_corrector=20,
+                        corrector_tol=1e-6)
+    ctx.run(args.warmup)
+    ctx.set_tracing(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s, st = ctx.run(args.monolithic_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"steps": args.monolithic_steps, "steps_per_s": args.monolithic_steps / (ms * 1e-3),
+           "ms_per_step": ms / args.monolithic_steps, "newton_iterations_last_step": st.correctors,
+           "bicgstab_iterations_last_step": st.iters_V, "status": rafem.status_string(s),
+           "unknowns": 2 * ctx.N, "graph": ctx.graph_info()["corrector_graph"]}
+    ctx.close()
+    return out
+
+
 def measure_numbering(rafem, torch, mg, mesh, args):
     """Sensitivity to the node numbering (mixed precision, 127^3): the lattice numbering, a seeded random
     renumbering (no locality: 32-bit columns, scattered gathers) and that random mesh renumbered by the library's
@@ -479,6 +504,7 @@ def main():
     ap.add_argument("--bicgstab-steps", type=int, default=5, help="timed steps with BiCGSTAB (0 = skip)")
     ap.add_argument("--gmres-steps", type=int, default=5, help="timed steps with GMRES(30) (0 = skip)")
     ap.add_argument("--numbering-steps", type=int, default=10, help="timed steps per node numbering (0 = skip)")
+    ap.add_argument("--monolithic-steps", type=int, default=3, help="timed monolithic Newton steps (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -639,6 +665,11 @@ def main():
             line["batch"] = measure_batch(rafem, torch, mg, args)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
+    if args.monolithic_steps > 0 and args.only is None:
+        try:
+            line["monolithic"] = measure_monolithic(rafem, torch, mesh, args)
+        except Exception as exc:
+            line["monolithic"] = {"error": repr(exc)[:300]}
     if args.numbering_steps > 0 and args.only is None and args.cells == 127:
         try:
             line["numbering"] = measure_numbering(rafem, torch, mg, mesh, args)

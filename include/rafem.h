@@ -68,6 +68,14 @@ extern "C" {
                                         Jacobi, classical Gram-Schmidt with reorthogonalisation, SELL-32 layout,
                                         single instance; m = gmres_restart                                      */
 
+#define RAFEM_COUPLING_STAGGERED   0 /* V then T per pass (lagged sigma; corrector passes when n_corrector > 1) */
+#define RAFEM_COUPLING_MONOLITHIC  1 /* the paper's 2N x 2N system: V and T of a step solved together by Newton's
+                                        method (Jacobian with the sigma(T) and Joule couplings, unknowns
+                                        interleaved per node, 2 x 2 blocks on the node pattern, block-Jacobi
+                                        BiCGSTAB, row-only Dirichlet rows) until max |dT| < corrector_tol or
+                                        n_corrector iterations; FP64, SELL-32 layout, single instance; the
+                                        iterations run on the device like corrector passes                    */
+
 #define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known
                                         values moved to the right-hand side: the systems stay SPD              */
 #define RAFEM_LIFT_ROW        1      /* Dirichlet rows replaced by identity rows, columns kept: the same solution
@@ -119,6 +127,7 @@ typedef struct rafem_params {
     int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric: BiCGSTAB or
                                         GMRES)                                                                 */
     int32_t gmres_restart;           /* GMRES restart length m, 1..64 (0 = 30)                                  */
+    int32_t coupling;                /* RAFEM_COUPLING_STAGGERED (0) or RAFEM_COUPLING_MONOLITHIC               */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
@@ -231,6 +240,11 @@ int rafem_get_system(rafem_ctx* ctx, int which, int32_t* row_ptr, int32_t* col, 
  * solver settings, without touching the fields: b and x are device pointers to N doubles, x holds the
  * initial guess on entry. */
 int rafem_solve_rhs(rafem_ctx* ctx, int which, const double* b_dev, double* x_dev, rafem_step_stats* stats);
+
+/* Monolithic contexts only: assemble the coupled Newton system at the current state (T_old = T) and copy it out
+ * (host): blocks [4 nnz] = the 2 x 2 block of each entry of the CSR node pattern, row-major (dR_V/dV, dR_V/dT,
+ * dR_T/dV, dR_T/dT); residual [2N] interleaved (R_V, R_T per node). Either may be NULL. BAD_INPUT otherwise. */
+int rafem_get_coupled_system(rafem_ctx* ctx, double* blocks, double* residual);
 
 /* y = A x with the current lifted system `which` (FP64). x, y: device pointers to N doubles. */
 int rafem_spmv(rafem_ctx* ctx, int which, const double* x_dev, double* y_dev);

@@ -129,6 +129,13 @@ struct rafem_ctx {
     int bg_grid = 0;
     // GMRES(m) (solver == RAFEM_SOLVER_GMRES)
     int gm_m = 0, gm_grid = 0;
+    // monolithic coupled step (coupling == RAFEM_COUPLING_MONOLITHIC): 2 x 2 block Jacobian on the node pattern,
+    // interleaved residual and Newton correction, block-BiCGSTAB workspace (2N vectors)
+    bool mono = false;
+    double *m_vals4 = nullptr, *m_R = nullptr, *m_D = nullptr;
+    double *mb_r = nullptr, *mb_rh = nullptr, *mb_p = nullptr, *mb_ph = nullptr, *mb_v = nullptr, *mb_s = nullptr,
+           *mb_sh = nullptr, *mb_t = nullptr, *mb_dinv = nullptr, *mb_partial = nullptr;
+    int mb_grid = 0;
     double *gm_V = nullptr, *gm_w0 = nullptr, *gm_w1 = nullptr, *gm_dinv = nullptr, *gm_partial = nullptr;
     // differentiation: element order map, tape of checkpoints, adjoint workspace
     int32_t* e_order = nullptr;      // [E] stored element -> mesh element
@@ -588,10 +595,66 @@ cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
     return cudaGetLastError();
 }
 
-// One corrector pass (sigma at the newest temperature iterate T, mass term at T_old), then the convergence test.
+// One Newton iteration of the monolithic coupled step: assemble the 2N x 2N Jacobian and residual at the current
+// (V, T), solve J delta = R with block-Jacobi BiCGSTAB, (V, T) -= delta.
+cudaError_t enqueue_newton(rafem_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int N = c->N;
+    cudaError_t e = cudaMemsetAsync(c->m_R, 0, 2 * (size_t)N * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    for (int q = 0; q < c->n_colors; ++q) {
+        e = launch_coupled(c->el, c->color_off[q], c->color_off[q + 1], c->e_clist, c->V, c->T, c->T_old,
+                           c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->prm.perf, c->prm.T_a, c->m_vals4, c->m_R,
+                           st);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_coupled_dirichlet(N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
+                                 c->m_vals4, c->m_R, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->m_D, 0, 2 * (size_t)N * sizeof(double), st)) != cudaSuccess) return e;
+    BicgArgs g{};
+    g.block = 2;
+    g.N = N;
+    g.sp = c->rp;
+    g.sc = c->ci;
+    g.sc16 = c->ci16;
+    g.A = c->m_vals4;
+    g.diag = c->diag;
+    g.b = c->m_R;
+    g.x = c->m_D;
+    g.r = c->mb_r;
+    g.rh = c->mb_rh;
+    g.p = c->mb_p;
+    g.ph = c->mb_ph;
+    g.v = c->mb_v;
+    g.s = c->mb_s;
+    g.sh = c->mb_sh;
+    g.t = c->mb_t;
+    g.dinv = c->mb_dinv;
+    g.partial = c->mb_partial;
+    g.bar = c->bar;
+    g.inst = c->instV;
+    g.tol = c->prm.tol;
+    g.max_iter = c->prm.max_iter;
+    g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+    if ((e = launch_bicgstab(g, c->mb_grid, st)) != cudaSuccess) return e;
+    k_record<<<1, 128, 0, st>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_newton_update(N, c->m_D, c->V, c->T, st);
+}
+
+// One corrector pass (sigma at the newest temperature iterate T, mass term at T_old), or one Newton iteration of
+// the monolithic step, then the convergence test on max |T^{k+1} - T^k|.
 cudaError_t enqueue_corrector_pass(rafem_ctx* c, cudaGraphConditionalHandle h, int use_handle) {
     cudaError_t e = cudaMemcpyAsync(c->T_prev, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
+    if (c->mono) {
+        if ((e = enqueue_newton(c)) != cudaSuccess) return e;
+        if ((e = launch_max_abs_diff(c->N, c->T, c->T_prev, c->scratch, c->stream)) != cudaSuccess) return e;
+        k_corr_check<<<1, 1, 0, c->stream>>>(c->corr, c->scratch, c->prm.corrector_tol, c->prm.n_corrector, h,
+                                            use_handle);
+        return cudaGetLastError();
+    }
     if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T_old)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
@@ -1180,12 +1243,25 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         if (c->gm_grid <= 0) return RAFEM_ERR_CUDA;
         CK(dalloc(c, &c->gm_partial, (size_t)(2 * (c->gm_m + 1) + 2) * c->gm_grid));
     }
+    if (prm->coupling == RAFEM_COUPLING_MONOLITHIC) {
+        if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
+        c->mono = true;
+        const size_t n2 = 2 * (size_t)N + 2 * SELL_C;
+        CK(dalloc(c, &c->m_vals4, 4 * (size_t)c->nnz_store));
+        for (double** v : {&c->m_R, &c->m_D, &c->mb_r, &c->mb_rh, &c->mb_p, &c->mb_ph, &c->mb_v, &c->mb_s, &c->mb_sh,
+                           &c->mb_t})
+            CK(dalloc(c, v, n2));
+        CK(dalloc(c, &c->mb_dinv, 2 * n2));
+        c->mb_grid = bicgstab_max_blocks(2);
+        if (c->mb_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &c->mb_partial, (size_t)bicgstab_partial_slots() * c->mb_grid));
+    }
     if (prm->solver == RAFEM_SOLVER_BICGSTAB) {
         if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
         for (double** v : {&c->bg_r, &c->bg_rh, &c->bg_p, &c->bg_ph, &c->bg_v, &c->bg_s, &c->bg_sh, &c->bg_t,
                            &c->bg_dinv})
             CK(dalloc(c, v, (size_t)N + SELL_C));
-        c->bg_grid = bicgstab_max_blocks();
+        c->bg_grid = bicgstab_max_blocks(1);
         if (c->bg_grid <= 0) return RAFEM_ERR_CUDA;
         CK(dalloc(c, &c->bg_partial, (size_t)bicgstab_partial_slots() * c->bg_grid));
     }
@@ -1280,6 +1356,11 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
     if (prm->predictor < 0 || prm->predictor > 3) return RAFEM_ERR_BAD_INPUT;
+    if (prm->coupling != RAFEM_COUPLING_STAGGERED && prm->coupling != RAFEM_COUPLING_MONOLITHIC)
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->coupling == RAFEM_COUPLING_MONOLITHIC &&
+        (prm->precision != RAFEM_PRECISION_FP64 || (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
+        return RAFEM_ERR_BAD_INPUT;
     if (prm->lift == RAFEM_LIFT_ROW && prm->solver == RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
@@ -1338,7 +1419,7 @@ int rafem_solve_rhs(rafem_ctx* c, int which, const double* b, double* x, rafem_s
 
 int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
-    if (c->prm.n_corrector <= 1) {
+    if (c->prm.n_corrector <= 1 && !c->mono) {
         CK(c->tracing ? enqueue_step_traced(c) : enqueue_step(c));
         const int s = finish(c, stats, false);
         const int t = tape_record(c, c->step);
@@ -1354,7 +1435,7 @@ int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {
     if (n_steps == 0) return finish(c, last, true);
     k_set_step<<<1, 1, 0, c->stream>>>(c->stats, (long long)c->step);
     CK(cudaGetLastError());
-    if (c->prm.n_corrector > 1) {
+    if (c->prm.n_corrector > 1 || c->mono) {
         for (int i = 0; i < n_steps; ++i) CK(launch_corrector_step(c));
         return finish(c, last, true);
     }
@@ -1652,7 +1733,7 @@ int rafem_advance(rafem_ctx* c, double duration, double dt_min, rafem_advance_st
     c->tape_every = 0;
     cudaStream_t st = c->stream;
     const size_t nb = (size_t)c->N * sizeof(double);
-    const bool corrector = c->prm.n_corrector > 1;
+    const bool corrector = c->prm.n_corrector > 1 || c->mono;
     double t = 0.0, dt = c->prm.dt;
     int32_t accepted = 0, rejected = 0, passes = 0;
     k_set_step<<<1, 1, 0, st>>>(c->stats, (long long)c->step);
@@ -1708,7 +1789,7 @@ int rafem_advance(rafem_ctx* c, double duration, double dt_min, rafem_advance_st
 }
 
 int rafem_tape_begin(rafem_ctx* c, int32_t checkpoint_every) {
-    if (!c || checkpoint_every < 1 || c->prm.n_corrector != 1 || c->prm.lift != RAFEM_LIFT_SYMMETRIC)
+    if (!c || checkpoint_every < 1 || c->prm.n_corrector != 1 || c->prm.lift != RAFEM_LIFT_SYMMETRIC || c->mono)
         return RAFEM_ERR_BAD_INPUT;
     c->tape_every = 0;
     c->n_ckpt = 0;
@@ -1929,6 +2010,29 @@ int rafem_get_system(rafem_ctx* c, int which, int32_t* row_ptr, int32_t* col, do
         else
             std::copy(store.begin(), store.end(), vals);
     }
+    return RAFEM_OK;
+}
+
+int rafem_get_coupled_system(rafem_ctx* c, double* blocks, double* residual) {
+    if (!c || !c->mono) return RAFEM_ERR_BAD_INPUT;
+    CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->m_R, 0, 2 * (size_t)c->N * sizeof(double), st));
+    for (int q = 0; q < c->n_colors; ++q)
+        CK(launch_coupled(c->el, c->color_off[q], c->color_off[q + 1], c->e_clist, c->V, c->T, c->T_old,
+                          c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->prm.perf, c->prm.T_a, c->m_vals4, c->m_R,
+                          st));
+    CK(launch_coupled_dirichlet(c->N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
+                                c->m_vals4, c->m_R, st));
+    std::vector<double> v4(4 * (size_t)c->nnz_store);
+    CK(cudaMemcpyAsync(v4.data(), c->m_vals4, v4.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (residual) CK(cudaMemcpyAsync(residual, c->m_R, 2 * (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (blocks)
+        for (int64_t q = 0; q < c->nnz; ++q) {
+            const size_t pos = 4 * (size_t)(c->sell ? c->h_map[q] : q);
+            for (int k = 0; k < 4; ++k) blocks[4 * q + k] = v4[pos + k];
+        }
     return RAFEM_OK;
 }
 

@@ -161,6 +161,134 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
     }
 }
 
+// Monolithic Newton system of one colour (the 2N x 2N coupled step, unknowns (V_i, T_i) per node): residual
+//   R_V = K(sigma(T)) V,   R_T = A_T T - (rho_c/dt) M T_old - perf T_a M 1 - F(V, sigma(T)),
+// F_a = sum_e sigma_e V_e^T G_e V_e / 4, sigma_e = sigma0_e (1 + alpha (Tbar_e - 37)), and its Jacobian, one 2 x 2
+// block (row-major: V row, T row) per stored entry of the node pattern:
+//   dR_V/dV = sigma G,  dR_V/dT_b = ds (G V)_a,  dR_T/dV_b = -sigma (G V)_b / 2,
+//   dR_T/dT = k G + (rho_c/dt + perf) M - ds (V^T G V) / 4,   ds = sigma0 alpha / 4.
+// Blocks are stored by the slot's first writer and accumulated by the others (colour order); R accumulates
+// (zeroed before the first colour). Dirichlet rows are replaced afterwards (k_coupled_dirichlet).
+__global__ void __launch_bounds__(kThreads) k_coupled(ElemData el, int e0, int e1, const int32_t* __restrict__ list,
+                                                      const double* __restrict__ V, const double* __restrict__ T,
+                                                      const double* __restrict__ To, double alpha, double c_dt,
+                                                      double perf, double T_a, double* __restrict__ vals4,
+                                                      double* __restrict__ R) {
+    const int ep = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (ep >= e1) return;
+    const int e = list ? __ldg(list + ep) : ep;
+    const size_t E = (size_t)el.E;
+    int n[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) n[a] = __ldg(el.nodes + a * E + e);
+    double Ge[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) Ge[q] = __ldg(el.G + q * E + e);
+    const double sig0 = __ldg(el.sigma0 + e), kk = __ldg(el.k + e), vol = __ldg(el.vol + e);
+    double v[4], t[4], to[4], tsum = 0.0, tosum = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        v[a] = V[n[a]];
+        t[a] = T[n[a]];
+        to[a] = To[n[a]];
+        tsum += t[a];
+        tosum += to[a];
+    }
+    const double sig = sig0 * (1.0 + alpha * (0.25 * tsum - 37.0)), ds = 0.25 * sig0 * alpha;
+    double gv[4], gt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        gv[a] = 0.0;
+        gt[a] = 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            gv[a] = fma(Ge[gidx(a, b)], v[b], gv[a]);
+            gt[a] = fma(Ge[gidx(a, b)], t[b], gt[a]);
+        }
+    }
+    const double quad = v[0] * gv[0] + v[1] * gv[1] + v[2] * gv[2] + v[3] * gv[3];
+    const double mv = vol * (1.0 / 20.0), cm = c_dt + perf;
+    double old[16][4];
+    int32_t code[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        code[q] = __ldg(el.slots + q * E + e);
+        const bool acc = !(code[q] & SLOT_FIRST);
+        const size_t pos = 4 * (size_t)(code[q] & SLOT_MASK);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) old[q][c] = acc ? vals4[pos + c] : 0.0;
+    }
+    double rv[4], rt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        rv[a] = R[2 * (size_t)n[a]];
+        rt[a] = R[2 * (size_t)n[a] + 1];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int q = a * 4 + b;
+            const double g = Ge[gidx(a, b)];
+            const size_t pos = 4 * (size_t)(code[q] & SLOT_MASK);
+            vals4[pos + 0] = fma(sig, g, old[q][0]);
+            vals4[pos + 1] = fma(ds, gv[a], old[q][1]);
+            vals4[pos + 2] = fma(-0.5 * sig, gv[b], old[q][2]);
+            vals4[pos + 3] = old[q][3] + (fma(kk, g, cm * mv * (a == b ? 2.0 : 1.0)) - 0.25 * ds * quad);
+        }
+        R[2 * (size_t)n[a]] = fma(sig, gv[a], rv[a]);
+        R[2 * (size_t)n[a] + 1] =
+            rt[a] + (fma(kk, gt[a], cm * mv * (tsum + t[a])) - c_dt * mv * (tosum + to[a]) - perf * T_a * 0.25 * vol -
+                     0.25 * sig * quad);
+    }
+}
+
+// Dirichlet rows of the monolithic system: the V (T) row of a node with a prescribed potential (temperature)
+// becomes the identity row of its own unknown with residual x_i - g_i; columns are kept (row-only lift).
+__global__ void k_coupled_dirichlet(int N, int sell, const int32_t* __restrict__ rp, const int32_t* __restrict__ diag,
+                                    const uint8_t* __restrict__ bcV, const uint8_t* __restrict__ bcT,
+                                    const double* __restrict__ gV, const double* __restrict__ gT,
+                                    const double* __restrict__ V, const double* __restrict__ T,
+                                    double* __restrict__ vals4, double* __restrict__ R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const bool dv = bcV[i] != 0, dt = bcT[i] != 0;
+    if (!dv && !dt) return;
+    int q0, q1, stride;
+    if (sell) {
+        const int s = i >> 5, base = rp[s];
+        q0 = base + (i & 31);
+        q1 = base + (rp[s + 1] - base) + (i & 31);
+        stride = 32;
+    } else {
+        q0 = rp[i];
+        q1 = rp[i + 1];
+        stride = 1;
+    }
+    for (int q = q0; q < q1; q += stride) {
+        if (dv) vals4[4 * (size_t)q + 0] = vals4[4 * (size_t)q + 1] = 0.0;
+        if (dt) vals4[4 * (size_t)q + 2] = vals4[4 * (size_t)q + 3] = 0.0;
+    }
+    const size_t d = 4 * (size_t)diag[i];
+    if (dv) {
+        vals4[d + 0] = 1.0;
+        R[2 * (size_t)i] = V[i] - gV[i];
+    }
+    if (dt) {
+        vals4[d + 3] = 1.0;
+        R[2 * (size_t)i + 1] = T[i] - gT[i];
+    }
+}
+
+// Newton update x <- x - delta (interleaved delta) of the potential and the temperature.
+__global__ void k_newton_update(int N, const double* __restrict__ delta, double* __restrict__ V,
+                                double* __restrict__ T) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    V[i] -= delta[2 * (size_t)i];
+    T[i] -= delta[2 * (size_t)i + 1];
+}
+
 // Thermal right-hand side contributions of one element (free rows only):
 //   Joule:  Q_e vol_e / 4 with Q_e vol_e = sigma_e * V_e^T G_e V_e   (= sigma_e vol_e |grad V|^2)
 //   mass:   (rho_c/dt) (M_e T_old)_a = (rho_c/dt) vol_e/20 (sum_b T_b + T_a)
@@ -479,6 +607,27 @@ cudaError_t launch_rhs_T_gather(const GatherData& gd, int N, const ElemData& el,
 
 cudaError_t launch_node_mass(const GatherData& gd, int N, const double* vol, double c_mass, cudaStream_t st) {
     k_node_mass<<<blocks_for(N), kThreads, 0, st>>>(N, gd.ioff, gd.icnt, gd.ielem, vol, c_mass, gd.mT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coupled(const ElemData& el, int e0, int e1, const int32_t* list, const double* V, const double* T,
+                           const double* T_old, double alpha, double c_dt, double perf, double T_a, double* vals4,
+                           double* R, cudaStream_t st) {
+    if (e1 <= e0) return cudaSuccess;
+    k_coupled<<<blocks_for(e1 - e0), kThreads, 0, st>>>(el, e0, e1, list, V, T, T_old, alpha, c_dt, perf, T_a, vals4,
+                                                         R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coupled_dirichlet(int N, int sell, const int32_t* rp, const int32_t* diag, const uint8_t* bcV,
+                                     const uint8_t* bcT, const double* gV, const double* gT, const double* V,
+                                     const double* T, double* vals4, double* R, cudaStream_t st) {
+    k_coupled_dirichlet<<<blocks_for(N), kThreads, 0, st>>>(N, sell, rp, diag, bcV, bcT, gV, gT, V, T, vals4, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_newton_update(int N, const double* delta, double* V, double* T, cudaStream_t st) {
+    k_newton_update<<<blocks_for(N), kThreads, 0, st>>>(N, delta, V, T);
     return cudaGetLastError();
 }
 

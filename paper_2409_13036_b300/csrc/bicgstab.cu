@@ -1,4 +1,5 @@
-// Persistent Jacobi-preconditioned BiCGSTAB (FP64) for general (nonsymmetric) systems on the SELL-32 layout.
+// Persistent Jacobi-preconditioned BiCGSTAB (FP64) for general (nonsymmetric) systems on the SELL-32 layout, for
+// scalar rows (B = 1) or 2 x 2 block rows (B = 2: the monolithic potential/temperature system, block Jacobi).
 //
 // Sec. II-B: CG suits symmetric positive-definite systems; for nonsymmetric ones a method that does not need
 // symmetry is used (the paper's own choice there is GMRES). BiCGSTAB (van der Vorst) with right
@@ -28,15 +29,15 @@ constexpr int kBatch = 8;
 constexpr int kSlots = 6;
 
 struct Args {
-    int N;
+    int N;                // block rows
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
-    const double* A;
+    const double* A;      // B x B block per stored entry (row-major within the block)
     const int32_t* diag;
     const double* b;
     double* x;
-    double *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;
+    double *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;  // B values per row (dinv: B x B)
     double* partial;
     GridBarrier* bar;
     InstState* inst;
@@ -85,30 +86,51 @@ __device__ __forceinline__ void totals(const double* part, double* s_tot) {
     __syncthreads();
 }
 
-// (A y)_row over the SELL-32 slice s (column indices 32-bit, or 16-bit deltas when sc16 is set); entries are
-// loaded in batches before the gathers that depend on them
-__device__ __forceinline__ double spmv_row(const Args& a, const double* y, int s, int row) {
+// (A y)_row (B values) over the SELL-32 slice s; entries are loaded in batches before the gathers that depend on
+// them
+template <int B>
+__device__ __forceinline__ void spmv_row(const Args& a, const double* y, int s, int row, double (&out)[B]) {
     const int lane = row & 31;
     const int base = __ldg(a.sp + s), w = (__ldg(a.sp + s + 1) - base) >> 5;
-    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < B; ++q) out[q] = 0.0;
     for (int k = 0; k < w; k += kBatch) {
-        double m[kBatch], yv[kBatch];
         int c[kBatch];
+        double m[kBatch][B * B], yv[kBatch][B];
 #pragma unroll
         for (int t = 0; t < kBatch; ++t) {
             const int pos = base + 32 * (k + t) + lane;
             const bool ok = k + t < w;
-            m[t] = ok ? __ldg(a.A + pos) : 0.0;
             c[t] = ok ? (a.sc16 ? row + (int)__ldg(a.sc16 + pos) : __ldg(a.sc + pos)) : -1;
+#pragma unroll
+            for (int q = 0; q < B * B; ++q) m[t][q] = ok ? __ldg(a.A + (size_t)B * B * pos + q) : 0.0;
         }
 #pragma unroll
-        for (int t = 0; t < kBatch; ++t) yv[t] = c[t] >= 0 ? ldcg(y + c[t]) : 0.0;
+        for (int t = 0; t < kBatch; ++t)
 #pragma unroll
-        for (int t = 0; t < kBatch; ++t) acc = fma(m[t], yv[t], acc);
+            for (int q = 0; q < B; ++q) yv[t][q] = c[t] >= 0 ? ldcg(y + (size_t)B * c[t] + q) : 0.0;
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t)
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int q = 0; q < B; ++q) out[i] = fma(m[t][B * i + q], yv[t][q], out[i]);
     }
-    return acc;
 }
 
+// z = D^-1 u with the inverse diagonal block of the row
+template <int B>
+__device__ __forceinline__ void apply_dinv(const double* dinv, int row, const double (&u)[B], double (&z)[B]) {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < B; ++q) acc = fma(dinv[(size_t)B * B * row + B * i + q], u[q], acc);
+        z[i] = acc;
+    }
+}
+
+template <int B>
 __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
     __shared__ double sm[2 * kBlock];
     __shared__ double s_tot[2];
@@ -117,19 +139,36 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
     bool err = false;
     int iters = 0, status = RAFEM_NOT_CONVERGED;
     double bb, rr, rho, alpha = 1.0, omega = 1.0, beta = 0.0;
-    // r = b - A x, rh = r, p = v = 0, dinv; (b, b), (r, r)
+    // r = b - A x, rh = r, p = v = 0, inverse diagonal blocks; (b, b), (r, r)
     {
         double q[2] = {0.0, 0.0};
         for_slices(S, [&](int s, int row) {
             if (row >= N) return;
-            const double ri = a.b[row] - spmv_row(a, a.x, s, row);
-            a.r[row] = ri;
-            a.rh[row] = ri;
-            a.p[row] = 0.0;
-            a.v[row] = 0.0;
-            a.dinv[row] = 1.0 / __ldg(a.A + __ldg(a.diag + row));
-            q[0] = fma(a.b[row], a.b[row], q[0]);
-            q[1] = fma(ri, ri, q[1]);
+            double ax[B];
+            spmv_row<B>(a, a.x, s, row, ax);
+            const double* d = a.A + (size_t)B * B * __ldg(a.diag + row);
+            if constexpr (B == 1) {
+                a.dinv[row] = 1.0 / __ldg(d);
+            } else {
+                const double d00 = __ldg(d), d01 = __ldg(d + 1), d10 = __ldg(d + 2), d11 = __ldg(d + 3);
+                const double inv = 1.0 / (d00 * d11 - d01 * d10);
+                double* o = a.dinv + 4 * (size_t)row;
+                o[0] = d11 * inv;
+                o[1] = -d01 * inv;
+                o[2] = -d10 * inv;
+                o[3] = d00 * inv;
+            }
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const size_t i = (size_t)B * row + k;
+                const double bi = a.b[i], ri = bi - ax[k];
+                a.r[i] = ri;
+                a.rh[i] = ri;
+                a.p[i] = 0.0;
+                a.v[i] = 0.0;
+                q[0] = fma(bi, bi, q[0]);
+                q[1] = fma(ri, ri, q[1]);
+            }
         });
         publish<2>(q, sm, slot(a, 4));
         err = grid_barrier(a.bar, a.spin_limit_ns, target);
@@ -152,9 +191,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
         // A: p = r + beta (p - omega v), ph = M^-1 p
         for_slices(S, [&](int, int row) {
             if (row >= N) return;
-            const double pi = fma(beta, fma(-omega, a.v[row], a.p[row]), a.r[row]);
-            a.p[row] = pi;
-            a.ph[row] = pi * a.dinv[row];
+            double pv[B], z[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const size_t i = (size_t)B * row + k;
+                pv[k] = fma(beta, fma(-omega, a.v[i], a.p[i]), a.r[i]);
+                a.p[i] = pv[k];
+            }
+            apply_dinv<B>(a.dinv, row, pv, z);
+#pragma unroll
+            for (int k = 0; k < B; ++k) a.ph[(size_t)B * row + k] = z[k];
         });
         if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
         // B: v = A ph, (rh, v)
@@ -162,9 +208,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
             double q[1] = {0.0};
             for_slices(S, [&](int s, int row) {
                 if (row >= N) return;
-                const double vi = spmv_row(a, a.ph, s, row);
-                a.v[row] = vi;
-                q[0] = fma(a.rh[row], vi, q[0]);
+                double vv[B];
+                spmv_row<B>(a, a.ph, s, row, vv);
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const size_t i = (size_t)B * row + k;
+                    a.v[i] = vv[k];
+                    q[0] = fma(a.rh[i], vv[k], q[0]);
+                }
             });
             publish<1>(q, sm, slot(a, 0));
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
@@ -181,17 +232,29 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
             double q[1] = {0.0};
             for_slices(S, [&](int, int row) {
                 if (row >= N) return;
-                const double si = fma(-alpha, a.v[row], a.r[row]);
-                a.s[row] = si;
-                a.sh[row] = si * a.dinv[row];
-                q[0] = fma(si, si, q[0]);
+                double sv[B], z[B];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const size_t i = (size_t)B * row + k;
+                    sv[k] = fma(-alpha, a.v[i], a.r[i]);
+                    a.s[i] = sv[k];
+                    q[0] = fma(sv[k], sv[k], q[0]);
+                }
+                apply_dinv<B>(a.dinv, row, sv, z);
+#pragma unroll
+                for (int k = 0; k < B; ++k) a.sh[(size_t)B * row + k] = z[k];
             });
             publish<1>(q, sm, slot(a, 1));
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
             totals<1>(slot(a, 1), s_tot);
             if (s_tot[0] <= thr) {  // converged on the half step: x += alpha ph
                 for_slices(S, [&](int, int row) {
-                    if (row < N) a.x[row] = fma(alpha, a.ph[row], a.x[row]);
+                    if (row >= N) return;
+#pragma unroll
+                    for (int k = 0; k < B; ++k) {
+                        const size_t i = (size_t)B * row + k;
+                        a.x[i] = fma(alpha, a.ph[i], a.x[i]);
+                    }
                 });
                 ++iters;
                 status = RAFEM_OK;
@@ -203,10 +266,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
             double q[2] = {0.0, 0.0};
             for_slices(S, [&](int s, int row) {
                 if (row >= N) return;
-                const double ti = spmv_row(a, a.sh, s, row);
-                a.t[row] = ti;
-                q[0] = fma(ti, a.s[row], q[0]);
-                q[1] = fma(ti, ti, q[1]);
+                double tv[B];
+                spmv_row<B>(a, a.sh, s, row, tv);
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const size_t i = (size_t)B * row + k;
+                    a.t[i] = tv[k];
+                    q[0] = fma(tv[k], a.s[i], q[0]);
+                    q[1] = fma(tv[k], tv[k], q[1]);
+                }
             });
             publish<2>(q, sm, slot(a, 2));
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
@@ -222,11 +290,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
             double q[2] = {0.0, 0.0};
             for_slices(S, [&](int, int row) {
                 if (row >= N) return;
-                a.x[row] = fma(omega, a.sh[row], fma(alpha, a.ph[row], a.x[row]));
-                const double ri = fma(-omega, a.t[row], a.s[row]);
-                a.r[row] = ri;
-                q[0] = fma(ri, ri, q[0]);
-                q[1] = fma(a.rh[row], ri, q[1]);
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const size_t i = (size_t)B * row + k;
+                    a.x[i] = fma(omega, a.sh[i], fma(alpha, a.ph[i], a.x[i]));
+                    const double ri = fma(-omega, a.t[i], a.s[i]);
+                    a.r[i] = ri;
+                    q[0] = fma(ri, ri, q[0]);
+                    q[1] = fma(a.rh[i], ri, q[1]);
+                }
             });
             publish<2>(q, sm, slot(a, 4));
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
@@ -252,8 +324,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
         double q[1] = {0.0};
         for_slices(S, [&](int s, int row) {
             if (row >= N) return;
-            const double ri = a.b[row] - spmv_row(a, a.x, s, row);
-            q[0] = fma(ri, ri, q[0]);
+            double ax[B];
+            spmv_row<B>(a, a.x, s, row, ax);
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const double ri = a.b[(size_t)B * row + k] - ax[k];
+                q[0] = fma(ri, ri, q[0]);
+            }
         });
         publish<1>(q, sm, slot(a, 3));
         err = grid_barrier(a.bar, a.spin_limit_ns, target);
@@ -275,11 +352,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
 
 }  // namespace
 
-int bicgstab_max_blocks() {
+int bicgstab_max_blocks(int block) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab, kBlock, 0) != cudaSuccess) return 0;
+    const void* f = block == 2 ? (const void*)k_bicgstab<2> : (const void*)k_bicgstab<1>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, kBlock, 0) != cudaSuccess) return 0;
     return sms * (per < 1 ? per : 1);
 }
 
@@ -291,7 +369,8 @@ cudaError_t launch_bicgstab(const BicgArgs& s, int grid, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
-    return cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(grid), dim3(kBlock), params, 0, st);
+    const void* f = s.block == 2 ? (const void*)k_bicgstab<2> : (const void*)k_bicgstab<1>;
+    return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(kBlock), params, 0, st);
 }
 
 }  // namespace rafem

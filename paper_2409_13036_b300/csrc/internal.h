@@ -72,6 +72,15 @@ cudaError_t launch_rhs_T(const ElemData& el, int e0, int e1, const double* T_sig
 cudaError_t launch_spmv64(int N, int sell, const int32_t* rp_or_sp, const int32_t* ci_or_sc, const double* A,
                           const double* x, double* y, cudaStream_t st);
 cudaError_t launch_max_abs_diff(int N, const double* a, const double* b, double* out, cudaStream_t st);
+// Monolithic coupled step: Jacobian blocks (4 per stored entry) and interleaved residual of the colour [e0, e1)
+// (positions of `list`, or storage indices when null); Dirichlet rows; Newton update.
+cudaError_t launch_coupled(const ElemData& el, int e0, int e1, const int32_t* list, const double* V, const double* T,
+                           const double* T_old, double alpha, double c_dt, double perf, double T_a, double* vals4,
+                           double* R, cudaStream_t st);
+cudaError_t launch_coupled_dirichlet(int N, int sell, const int32_t* rp, const int32_t* diag, const uint8_t* bcV,
+                                     const uint8_t* bcT, const double* gV, const double* gT, const double* V,
+                                     const double* T, double* vals4, double* R, cudaStream_t st);
+cudaError_t launch_newton_update(int N, const double* delta, double* V, double* T, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------------------------
 // Persistent Krylov solver (krylov.cu)
@@ -229,6 +238,8 @@ namespace rafem {
 // Persistent Jacobi-BiCGSTAB, FP64, single instance, SELL-32 primary storage (bicgstab.cu).
 // ------------------------------------------------------------------------------------------------------------
 struct BicgArgs {
+    int block = 1;                   // 1: scalar rows; 2: 2 x 2 block rows (A holds 4 values per stored entry,
+                                     // vectors 2 values per row, block-Jacobi preconditioner)
     int N;
     const int32_t* sp;               // slice pointers
     const int32_t* sc;               // 32-bit columns (used when sc16 is null)
@@ -245,7 +256,7 @@ struct BicgArgs {
     int max_iter;
     long long spin_limit_ns;
 };
-int bicgstab_max_blocks();
+int bicgstab_max_blocks(int block);
 int bicgstab_partial_slots();
 cudaError_t launch_bicgstab(const BicgArgs& a, int grid, cudaStream_t st);
 

@@ -37,6 +37,8 @@ RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
 RAFEM_SOLVER_GMRES = 2
+RAFEM_COUPLING_STAGGERED = 0
+RAFEM_COUPLING_MONOLITHIC = 1
 RAFEM_LIFT_SYMMETRIC = 0
 RAFEM_LIFT_ROW = 1
 RAFEM_ILU_MULTICOLOR = 0
@@ -62,7 +64,7 @@ class rafem_params(ctypes.Structure):
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
                 ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32),
-                ("gmres_restart", ctypes.c_int32)]
+                ("gmres_restart", ctypes.c_int32), ("coupling", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):
@@ -149,6 +151,7 @@ def lib() -> ctypes.CDLL:
         "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "rafem_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(rafem_advance_stats)]),
         "rafem_reorder_rcm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, vp]),
+        "rafem_get_coupled_system": (ctypes.c_int, [vp, vp, vp]),
         "rafem_reset": (ctypes.c_int, [vp]),
         "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
@@ -385,6 +388,14 @@ class Context:
 
     def spmv(self, which: int, x_dev, y_dev):
         _check(lib().rafem_spmv(self._ctx, which, _dev(x_dev), _dev(y_dev)), "rafem_spmv")
+
+    def get_coupled_system(self):
+        """(blocks [nnz, 2, 2], residual [N, 2]) of the monolithic Newton system at the current state."""
+        _, nnz, _ = self.pattern_info()
+        blocks = np.empty((nnz, 2, 2), np.float64)
+        res = np.empty((self.N, 2), np.float64)
+        _check(lib().rafem_get_coupled_system(self._ctx, blocks.ctypes.data, res.ctypes.data), "rafem_get_coupled_system")
+        return blocks, res
 
     # -- dynamic step size ------------------------------------------------------------------------------------
     def graph_info(self) -> dict:

@@ -1,0 +1,84 @@
+"""Monolithic coupled step (the paper's 2N x 2N system, Newton's method) on the GPU vs the oracle (needs a B300)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import rafem_oracle as O
+from paper_2409_13036_b300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2409_13036_b300 import build
+    build.build()
+    torch.cuda.init()
+    yield
+
+
+def R():
+    from paper_2409_13036_b300 import rafem
+    return rafem
+
+
+@pytest.mark.parametrize("assembly", [0, 1], ids=["gather", "colour"])
+def test_coupled_jacobian_and_residual_match_oracle(assembly):
+    """The 2 x 2 Jacobian blocks on the node pattern and the interleaved residual of the monolithic step at a
+    non-trivial (V, T), entry by entry against the oracle's coupled_jacobian / coupled_residual (T_old = T)."""
+    rafem = R()
+    m = mg.cube_mesh(8, jitter=0.1, seed=81, sigma0="lognormal", V_electrode=40.0)
+    rng = np.random.default_rng(1)
+    V = np.where(m.bc_V.astype(bool), m.g_V, 20.0 * rng.random(m.n_nodes))
+    T = np.where(m.bc_T.astype(bool), m.g_T, 37.0 + 20.0 * rng.random(m.n_nodes))
+    model = O.Model(m, O.Params(dt=30.0))
+    with rafem.Context(m, dt=30.0, coupling=1, assembly=assembly) as ctx:
+        ctx.set_state(T=T, V=V)
+        blocks, res = ctx.get_coupled_system()
+        rp, col, _, _ = ctx.get_system(rafem.RAFEM_SYS_V)
+    J = O.coupled_jacobian(model, V, T).tocsr()
+    Rref = O.coupled_residual(model, V, T, T)
+    rows = np.repeat(np.arange(m.n_nodes), np.diff(rp))
+    for a in range(2):
+        for b in range(2):
+            ref = np.asarray(J[2 * rows + a, 2 * col + b]).ravel()
+            np.testing.assert_allclose(blocks[:, a, b], ref, rtol=1e-12, atol=1e-13 * np.abs(J.data).max())
+    np.testing.assert_allclose(res.ravel(), Rref, rtol=1e-11, atol=1e-12 * np.abs(Rref).max())
+
+
+def test_monolithic_steps_match_oracle_fixed_point():
+    """Two monolithic steps (dt = 30 s, 40 V, Newton to max |dT| < 1e-9) agree with the oracle's Newton step and
+    with the corrector's fixed point (1e-9), in a few Newton iterations, through the device-side loop."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=82, sigma0="lognormal", V_electrode=40.0)
+    model = O.Model(m, O.Params(dt=30.0, n_corrector=50, corrector_tol=1e-11))
+    T = np.full(m.n_nodes, 37.0)
+    with rafem.Context(m, dt=30.0, coupling=1, n_corrector=20, corrector_tol=1e-9, tol=1e-13) as ctx:
+        for k in range(2):
+            Tn, Vn, it, _ = O.step_newton(model, T, tol=1e-11)
+            Tp, Vp, _ = model.step(T)
+            s, st = ctx.solve_step()
+            assert s == 0 and 2 <= st.correctors <= 8
+            Tg, Vg = ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V)
+            for ref_T, ref_V in ((Tn, Vn), (Tp, Vp)):
+                assert O.rel_err(Tg, ref_T) <= 1e-9
+                assert O.rel_err(Vg, ref_V) <= 1e-9
+            T = Tn
+        assert ctx.graph_info()["corrector_graph"] == 1
+
+
+def test_monolithic_rejections():
+    """Monolithic coupling needs FP64, the SELL-32 layout and a single instance; it has no adjoint."""
+    rafem = R()
+    m = mg.cube_mesh(6, jitter=0.1, seed=83)
+    for kw in (dict(coupling=1, precision=1), dict(coupling=1, lanes_per_row=8), dict(coupling=2)):
+        with pytest.raises(rafem.RafemError):
+            rafem.Context(m, **kw)
+    with pytest.raises(rafem.RafemError):
+        rafem.Context.batch([m, m], coupling=1)
+    with rafem.Context(m, coupling=1) as ctx:
+        with pytest.raises(rafem.RafemError):
+            ctx.tape_begin(2)
