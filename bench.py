@@ -292,6 +292,15 @@ def roofline(res, mixed, peaks, peak_kind):
         alg = alg_bytes_cg64(N, nnz, iters, cb)
         kern = f"k_cg64<{code}>"
     achieved = alg / (solve_ms * 1e-3) / 1e9
+    fp64_pipe = None
+    if kern.startswith("k_cg64"):
+        # the FP64 solver is co-limited by the FP64 pipe: B300 retires 2 FP64 FMAs per clock per SM (148 SMs at
+        # 2.032 GHz: 0.60 TFMA/s); per iteration one FMA per stored entry (SpMV) and ~10 per row (vector phase)
+        fma = (iters + 2) * (res["layout"]["nnz_stored"] + 10 * N)
+        peak_fma = 148 * 2 * 2.032e9
+        fp64_pipe = {"bound": "alu", "achieved": fma / (solve_ms * 1e-3) / 1e12, "peak": peak_fma / 1e12,
+                     "unit": "TFMA/s (FP64)", "frac": fma / (solve_ms * 1e-3) / peak_fma,
+                     "peak_kind": "2 FP64 FMA/clk/SM x 148 SMs x 2.032 GHz (unit count and clock)"}
     nc = _ncu_traffic(kern)
     traffic = None
     if nc:
@@ -305,7 +314,7 @@ def roofline(res, mixed, peaks, peak_kind):
             "traffic_note": ("ncu DRAM read+write of the 112^3 capture scaled by algorithmic bytes" if traffic else
                              "no ncu capture for the current source"),
             "launch_ms": solve_ms, "iters_per_launch": iters, "refinements_per_launch": ref,
-            "alg_bytes_per_launch": alg}
+            "alg_bytes_per_launch": alg, **({"fp64_pipe": fp64_pipe} if fp64_pipe else {})}
 
 
 def measure_batch(rafem, torch, mg, args):
@@ -616,8 +625,9 @@ def main():
                 "status": r["status"], "last_step": r["last"],
                 "iters_V_per_step": tr["iters_V"] / tr["steps"], "iters_T_per_step": tr["iters_T"] / tr["steps"],
                 "refine_V_per_step": tr["refine_V"] / tr["steps"],
-                "regions_ms_per_step": {k: tr[k] / tr["steps"] for k in ("ms_assemble_V", "ms_solve_V",
-                                                                          "ms_assemble_T", "ms_solve_T")},
+                "regions_ms_per_step": {k: tr[k] / tr["steps"] for k in ("ms_assemble_V", "ms_predict_V",
+                                                                          "ms_solve_V", "ms_assemble_T",
+                                                                          "ms_predict_T", "ms_solve_T")},
                 "roofline": r["roofline"]}
 
     per_step_launches = 1 + (1 + n_colors + 2 + 1) + (1 + n_colors + 2 + 1)

@@ -68,6 +68,11 @@ extern "C" {
                                         Jacobi, classical Gram-Schmidt with reorthogonalisation, SELL-32 layout,
                                         single instance; m = gmres_restart                                      */
 
+#define RAFEM_PREDICT_PROJECT 4      /* predictor: for the potential, A-orthogonal projection of the new
+                                        solution onto the span of its last four solutions (difference basis,
+                                        free rows; one extra pass over the matrix per solve; PCG with the
+                                        symmetric lift); quadratic extrapolation otherwise and for T          */
+
 #define RAFEM_COUPLING_STAGGERED   0 /* V then T per pass (lagged sigma; corrector passes when n_corrector > 1) */
 #define RAFEM_COUPLING_MONOLITHIC  1 /* the paper's 2N x 2N system: V and T of a step solved together by Newton's
                                         method (Jacobian with the sigma(T) and Joule couplings, unknowns
@@ -121,8 +126,9 @@ typedef struct rafem_params {
     int32_t assembly;                /* RAFEM_ASSEMBLY_GATHER (default with SELL-32) or RAFEM_ASSEMBLY_COLOR      */
     int32_t predictor;               /* initial guess of each solve (the predictor of the predictor-corrector
                                         loop): polynomial extrapolation in time of order 0..3 (0 = x^n,
-                                        1 = 2 x^n - x^{n-1}, 2 = 3 x^n - 3 x^{n-1} + x^{n-2} (default),
-                                        3 = 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3})                          */
+                                        1 = 2 x^n - x^{n-1}, 2 = 3 x^n - 3 x^{n-1} + x^{n-2},
+                                        3 = 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3}), or
+                                        RAFEM_PREDICT_PROJECT (default)                                       */
     int32_t ilu_order;               /* RAFEM_PRECOND_ILU0 only: RAFEM_ILU_MULTICOLOR (0) or RAFEM_ILU_NATURAL  */
     int32_t lift;                    /* RAFEM_LIFT_SYMMETRIC (0) or RAFEM_LIFT_ROW (nonsymmetric: BiCGSTAB or
                                         GMRES)                                                                 */
@@ -147,7 +153,7 @@ typedef struct rafem_step_stats {
 typedef struct rafem_ctx rafem_ctx;
 
 /* Liver defaults: alpha 0.015, rho_c 3.6e6, perf 2.4e4, T_a 37, dt 1, tol 1e-10, inner_tol 1e-4, FP64, Jacobi,
- * PCG, one corrector pass, automatic SpMV schedule, quadratic predictor, symmetric lift. */
+ * PCG, one corrector pass, automatic SpMV schedule, projection predictor, symmetric lift. */
 void rafem_default_params(rafem_params* p);
 
 /* Build a context: validates the mesh (ids in range, non-degenerate tetrahedra), builds the fixed CSR pattern,
@@ -249,7 +255,8 @@ int rafem_get_coupled_system(rafem_ctx* ctx, double* blocks, double* residual);
 /* y = A x with the current lifted system `which` (FP64). x, y: device pointers to N doubles. */
 int rafem_spmv(rafem_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
-/* Region timing (the paper's trace regions of Sec. III-C: Assembly, Solve, memcpyH2D, memcpyD2H), measured
+/* Region timing (the paper's trace regions of Sec. III-C: Assembly, Solve, memcpyH2D, memcpyD2H, plus Predict),
+ * measured
  * with CUDA events on the context's stream. While tracing is on, rafem_solve_step and rafem_run launch each
  * region directly (no graph) with an event on each side and NVTX ranges of the same names. */
 typedef struct rafem_trace {
@@ -263,6 +270,9 @@ typedef struct rafem_trace {
     double  ms_solve_T;              /* "Solve" of the thermal system                                         */
     double  ms_memcpy_h2d;           /* rafem_set_state copies                                                */
     double  ms_memcpy_d2h;           /* rafem_get_field copies                                                */
+    double  ms_predict_V;            /* "Predict": initial guess of the potential solve (extrapolation or
+                                        projection)                                                            */
+    double  ms_predict_T;            /* "Predict" of the thermal solve                                        */
 } rafem_trace;
 
 /* enable: 1 = on (accumulators cleared), 0 = off. */

@@ -73,7 +73,12 @@ struct rafem_ctx {
     double *V = nullptr, *T = nullptr, *T_old = nullptr, *T_prev = nullptr;
     double *V_hist = nullptr, *T_hist = nullptr;   // predictor history (x^{n-1})
     double *V_hist2 = nullptr, *T_hist2 = nullptr; // predictor history (x^{n-2}), quadratic and cubic predictors
-    double *V_hist3 = nullptr, *T_hist3 = nullptr; // predictor history (x^{n-3}), cubic predictor
+    double *V_hist3 = nullptr, *T_hist3 = nullptr; // predictor history (x^{n-3}), cubic predictor and projection
+    double* proj_partial = nullptr;                // [14][n_tiles * proj_sub] projection sums
+    int proj_sub = 1;
+    double* proj_coef = nullptr;                   // [4 n_inst]
+    int32_t *proj_kin = nullptr, *proj_kout = nullptr;
+    double* proj_D = nullptr;                      // [N][4] projection basis
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -112,7 +117,7 @@ struct rafem_ctx {
     // tracing
     bool tracing = false;
     rafem_trace trace{};
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};
     // ILU(0) preconditioner (precond == RAFEM_PRECOND_ILU0)
     bool ilu = false;
     IluLayout il;
@@ -497,15 +502,49 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
     return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
 }
 
-// Initial guess of a step's solve (the predictor of Sec. II-A's predictor-corrector loop).
+// Initial guess of a step's solve (the predictor of Sec. II-A's predictor-corrector loop): polynomial
+// extrapolation of order 1..3, or (predictor 4) for the potential the A-orthogonal projection onto its last four
+// solutions, which needs an SPD system (PCG, symmetric lift; order 2 otherwise, and for the thermal system, whose
+// few iterations would not repay the extra pass).
 cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     if (!c->prm.predictor) return cudaSuccess;
-    if (which == RAFEM_SYS_V)
+    const bool V = which == RAFEM_SYS_V;
+    const bool spd = c->prm.solver == RAFEM_SOLVER_PCG && c->prm.lift == RAFEM_LIFT_SYMMETRIC;
+    if (c->prm.predictor == RAFEM_PREDICT_PROJECT && spd && V) {
+        ProjArgs a{};
+        a.n_tiles = c->n_tiles;
+        a.n_sub = c->proj_sub;
+        a.tile_r0 = c->tile_r0;
+        a.tile_r1 = c->tile_r1;
+        a.tile_inst = c->tile_inst;
+        a.n_inst = c->n_inst;
+        a.inst_t0 = c->inst_t0;
+        a.inst_t1 = c->inst_t1;
+        a.sell = c->sell ? 1 : 0;
+        a.rp = c->rp;
+        a.ci = c->ci;
+        a.ci16 = c->ci16;
+        a.A = V ? c->valsV : c->valsT;
+        a.bc = V ? c->bcV : c->bcT;
+        a.b = V ? c->bV : c->bT;
+        a.x = V ? c->V : c->T;
+        a.h1 = V ? c->V_hist : c->T_hist;
+        a.h2 = V ? c->V_hist2 : c->T_hist2;
+        a.h3 = V ? c->V_hist3 : c->T_hist3;
+        a.partial = c->proj_partial;
+        a.coef = c->proj_coef;
+        a.kin = c->proj_kin;
+        a.kout = c->proj_kout;
+        a.D = c->proj_D;
+        return launch_projection(a, &c->stats->hist, 1, c->stream);
+    }
+    const int order = c->prm.predictor == RAFEM_PREDICT_PROJECT ? 2 : c->prm.predictor;
+    if (V)
         k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->V, c->V_hist, c->V_hist2, c->V_hist3, c->bcV,
-                                                             c->stats, c->prm.predictor, 1);
+                                                             c->stats, order, 1);
     else
         k_predict<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->T, c->T_hist, c->T_hist2, c->T_hist3, c->bcT,
-                                                             c->stats, c->prm.predictor, 0);
+                                                             c->stats, order, 0);
     return cudaGetLastError();
 }
 
@@ -526,10 +565,10 @@ cudaError_t enqueue_step(rafem_ctx* c) {
     return cudaGetLastError();
 }
 
-// Traced step: the same launches as enqueue_step with an event between regions.
+// Traced step: the same launches as enqueue_step with an event between regions (Assembly, Predict, Solve).
 cudaError_t enqueue_step_traced(rafem_ctx* c) {
     cudaError_t e;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 8; ++i)
         if (!c->ev[i] && (e = cudaEventCreate(&c->ev[i])) != cudaSuccess) return e;
     k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -538,8 +577,11 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[1], c->stream);
     nvtxRangePop();
-    nvtxRangePushA("Solve");
+    nvtxRangePushA("Predict");
     if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[6], c->stream);
+    nvtxRangePop();
+    nvtxRangePushA("Solve");
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[2], c->stream);
     nvtxRangePop();
@@ -549,23 +591,30 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[4], c->stream);
     nvtxRangePop();
-    nvtxRangePushA("Solve");
+    nvtxRangePushA("Predict");
     if ((e = enqueue_predict(c, RAFEM_SYS_T)) != cudaSuccess) return e;
+    cudaEventRecord(c->ev[7], c->stream);
+    nvtxRangePop();
+    nvtxRangePushA("Solve");
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
     cudaEventRecord(c->ev[5], c->stream);
     nvtxRangePop();
     k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
-    float ms[4];
+    float ms[6];
     cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]);
-    cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&ms[1], c->ev[6], c->ev[2]);
     cudaEventElapsedTime(&ms[2], c->ev[3], c->ev[4]);
-    cudaEventElapsedTime(&ms[3], c->ev[4], c->ev[5]);
+    cudaEventElapsedTime(&ms[3], c->ev[7], c->ev[5]);
+    cudaEventElapsedTime(&ms[4], c->ev[1], c->ev[6]);
+    cudaEventElapsedTime(&ms[5], c->ev[4], c->ev[7]);
     c->trace.ms_assemble_V += ms[0];
     c->trace.ms_solve_V += ms[1];
     c->trace.ms_assemble_T += ms[2];
     c->trace.ms_solve_T += ms[3];
+    c->trace.ms_predict_V += ms[4];
+    c->trace.ms_predict_T += ms[5];
     c->trace.steps += 1;
     c->trace.solves += 1;
     std::vector<InstState> iv(c->n_inst), it(c->n_inst);
@@ -859,7 +908,7 @@ void rafem_default_params(rafem_params* p) {
     p->lanes_per_row = 0;
     p->rows_per_tile = 0;
     p->assembly = RAFEM_ASSEMBLY_GATHER;
-    p->predictor = 2;
+    p->predictor = RAFEM_PREDICT_PROJECT;
 }
 
 const char* rafem_status_string(int s) {
@@ -913,10 +962,7 @@ static int build_tiles(rafem_ctx* c, int rows_per_tile) {
     }
     cudaStream_t st = c->stream;
     CK(cudaStreamSynchronize(st));
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);  // the captured graphs hold the tile arrays freed below
     for (void* p : c->tile_allocs) cudaFree(p);
     c->tile_allocs.clear();
     const int nt = (int)t0.size();
@@ -935,6 +981,10 @@ static int build_tiles(rafem_ctx* c, int rows_per_tile) {
     CK(talloc(&c->inst_t0, n_inst));
     CK(talloc(&c->inst_t1, n_inst));
     CK(talloc(&c->partial, (size_t)kPartialQ * nt));
+    int max_rows = 1;
+    for (int t = 0; t < nt; ++t) max_rows = std::max(max_rows, t1[t] - t0[t]);
+    c->proj_sub = (max_rows + kProjChunk - 1) / kProjChunk;
+    CK(talloc(&c->proj_partial, (size_t)14 * nt * c->proj_sub));
     CK(cudaMemcpyAsync(c->tile_r0, t0.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->tile_r1, t1.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->tile_inst, ti.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -1158,6 +1208,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->bar, 1));
     CK(dalloc(c, &c->e_order, E));
     CK(dalloc(c, &c->corr, 1));
+    CK(dalloc(c, &c->proj_coef, 4 * (size_t)n_inst));
+    CK(dalloc(c, &c->proj_kin, n_inst));
+    CK(dalloc(c, &c->proj_kout, n_inst));
+    if (prm->predictor == RAFEM_PREDICT_PROJECT) CK(dalloc(c, &c->proj_D, 4 * (size_t)N + 4));
     CK(dalloc(c, &c->V_old, N));
     CK(dalloc(c, &c->stats_save, 1));
     CK(dalloc(c, &c->istats_save, n_inst));
@@ -1355,7 +1409,7 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
          (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
-    if (prm->predictor < 0 || prm->predictor > 3) return RAFEM_ERR_BAD_INPUT;
+    if (prm->predictor < 0 || prm->predictor > RAFEM_PREDICT_PROJECT) return RAFEM_ERR_BAD_INPUT;
     if (prm->coupling != RAFEM_COUPLING_STAGGERED && prm->coupling != RAFEM_COUPLING_MONOLITHIC)
         return RAFEM_ERR_BAD_INPUT;
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC &&

@@ -289,3 +289,38 @@ int gmres_max_blocks(int m);
 cudaError_t launch_gmres(const GmresArgs& a, int grid, cudaStream_t st);
 
 }  // namespace rafem
+
+namespace rafem {
+
+// ------------------------------------------------------------------------------------------------------------
+// Initial guess by A-orthogonal projection onto the last solutions (project.cu).
+// ------------------------------------------------------------------------------------------------------------
+constexpr int kProjChunk = 512;   // rows per block of the projection passes
+
+struct ProjArgs {
+    int n_tiles;
+    int n_sub;                       // chunks of kProjChunk rows per tile (the largest tile's count)
+    const int32_t* tile_r0;
+    const int32_t* tile_r1;
+    const int32_t* tile_inst;
+    int n_inst;
+    const int32_t* inst_t0;
+    const int32_t* inst_t1;
+    int sell;                        // 1: SELL-32 slice pointers in rp; 0: CSR row pointers
+    const int32_t* rp;
+    const int32_t* ci;
+    const int16_t* ci16;             // 16-bit column deltas or null
+    const double* A;                 // lifted SPD system (storage layout)
+    const uint8_t* bc;               // Dirichlet rows
+    const double* b;
+    double* x;                       // x_n in, initial guess out
+    double *h1, *h2, *h3;            // x_{n-1}, x_{n-2}, x_{n-3} (shifted)
+    double* D;                       // [N][4] basis (32-byte aligned)
+    double* partial;                 // [14][n_tiles * n_sub]
+    double* coef;                    // [4 n_inst]
+    int32_t *kin, *kout;             // [n_inst] solutions available / basis size used
+};
+// hist: steps completed (device); lag: 1 when the initial field is not a solution (potential), 0 otherwise.
+cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);
+
+}  // namespace rafem

@@ -37,6 +37,7 @@ RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
 RAFEM_SOLVER_GMRES = 2
+RAFEM_PREDICT_PROJECT = 4
 RAFEM_COUPLING_STAGGERED = 0
 RAFEM_COUPLING_MONOLITHIC = 1
 RAFEM_LIFT_SYMMETRIC = 0
@@ -80,7 +81,8 @@ class rafem_trace(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("iters_V", ctypes.c_int64), ("iters_T", ctypes.c_int64),
                 ("solves", ctypes.c_int64), ("refine_V", ctypes.c_int64), ("ms_assemble_V", ctypes.c_double),
                 ("ms_solve_V", ctypes.c_double), ("ms_assemble_T", ctypes.c_double), ("ms_solve_T", ctypes.c_double),
-                ("ms_memcpy_h2d", ctypes.c_double), ("ms_memcpy_d2h", ctypes.c_double)]
+                ("ms_memcpy_h2d", ctypes.c_double), ("ms_memcpy_d2h", ctypes.c_double),
+                ("ms_predict_V", ctypes.c_double), ("ms_predict_T", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

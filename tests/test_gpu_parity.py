@@ -307,7 +307,7 @@ def test_full_size_sampled_rows(n):
         _sampled_check(m, ctx, rafem, T_before, rng)
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 def test_predictor_reproduces_steady_fields(order):
     """With alpha_sigma = 0 the potential does not change from step to step, and every extrapolation order
     reproduces a constant sequence exactly (its coefficients sum to one), so from the second step on the potential
