@@ -295,7 +295,7 @@ namespace rafem {
 // ------------------------------------------------------------------------------------------------------------
 // Initial guess by A-orthogonal projection onto the last solutions (project.cu).
 // ------------------------------------------------------------------------------------------------------------
-constexpr int kProjChunk = 512;   // rows per block of the projection passes
+constexpr int kProjChunk = 1024;  // rows per block of the projection passes
 
 struct ProjArgs {
     int n_tiles;

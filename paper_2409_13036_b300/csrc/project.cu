@@ -30,8 +30,28 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kQ = 14;  // 10 entries of the symmetric 4 x 4 Gram matrix + 4 right-hand sides
 constexpr int kChunk = kProjChunk;  // rows per block: tiles are split so that the pass has enough parallelism
+constexpr int kBatch = 5;  // interior rows of the Kuhn lattice have 15 entries
+constexpr int kSolveThreads = 256;
 
 __device__ __forceinline__ int tri(int i, int l) { return i <= l ? l * (l + 1) / 2 + i : i * (i + 1) / 2 + l; }
+
+// Sums 16 values over the warp by recursive halving: at each of the offsets 16, 8, 4, 2 a lane keeps one half of
+// its values and adds the partner's copy of that half, so 16 shuffles replace the 80 of one butterfly per value.
+// On return lane l holds the warp total of value l >> 1 (fixed order, deterministic).
+__device__ __forceinline__ double warp_sum16(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = lane & (2 * h);
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? v[i] : v[i + h];
+            const double keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 // difference basis at node j from x_n and the history (components i >= k are zero)
 __device__ __forceinline__ void basis(const double* x, const double* h1, const double* h2, const double* h3, int k,
@@ -70,16 +90,16 @@ __global__ void __launch_bounds__(kThreads) k_proj_basis(ProjArgs a) {
 }
 
 // One block per chunk of a tile: A d_i for the chunk's rows, then its partial sums of G and D^T b over free rows.
-__global__ void __launch_bounds__(kThreads) k_proj_gram(ProjArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_proj_gram(ProjArgs a) {
     __shared__ double red[kQ][kThreads / 32];
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
         const int inst = a.tile_inst[t];
         const int k = a.kin[inst];
-        double acc[kQ];
+        double acc[16];
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
+        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
         if (k > 0) {
             for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
                 if (a.bc[row]) continue;
@@ -96,14 +116,31 @@ __global__ void __launch_bounds__(kThreads) k_proj_gram(ProjArgs a) {
                     stride = 1;
                 }
                 const double2* D = reinterpret_cast<const double2*>(a.D);  // written by the previous launch
-                for (int q = q0; q < q1; q += stride) {
-                    const double v = __ldg(a.A + q);
-                    const int j = a.ci16 ? row + (int)__ldg(a.ci16 + q) : __ldg(a.ci + q);
-                    const double2 lo = __ldg(D + 2 * j), hi = __ldg(D + 2 * j + 1);
-                    y[0] = fma(v, lo.x, y[0]);
-                    y[1] = fma(v, lo.y, y[1]);
-                    y[2] = fma(v, hi.x, y[2]);
-                    y[3] = fma(v, hi.y, y[3]);
+                // entries in batches: values and columns first, then the gathers, then the FMAs, so that a row
+                // waits for two memory round trips per batch rather than two per entry
+                for (int q = q0; q < q1; q += kBatch * stride) {
+                    double v[kBatch];
+                    int j[kBatch];
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int qq = q + u * stride;
+                        const bool ok = qq < q1;
+                        v[u] = ok ? __ldg(a.A + qq) : 0.0;
+                        j[u] = ok ? (a.ci16 ? row + (int)__ldg(a.ci16 + qq) : __ldg(a.ci + qq)) : row;
+                    }
+                    double2 lo[kBatch], hi[kBatch];
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        lo[u] = __ldg(D + 2 * j[u]);
+                        hi[u] = __ldg(D + 2 * j[u] + 1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        y[0] = fma(v[u], lo[u].x, y[0]);
+                        y[1] = fma(v[u], lo[u].y, y[1]);
+                        y[2] = fma(v[u], hi[u].x, y[2]);
+                        y[3] = fma(v[u], hi[u].y, y[3]);
+                    }
                 }
                 const double2 lo = __ldg(D + 2 * row), hi = __ldg(D + 2 * row + 1);
                 const double d[4] = {lo.x, lo.y, hi.x, hi.y};
@@ -118,13 +155,8 @@ __global__ void __launch_bounds__(kThreads) k_proj_gram(ProjArgs a) {
         }
         // block reduction (fixed order)
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            double v = acc[q];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[q][warp] = v;
-        }
+        const double v = warp_sum16(acc);
+        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
         __syncthreads();
         if (threadIdx.x < kQ) {
             double v = 0.0;
@@ -135,25 +167,37 @@ __global__ void __launch_bounds__(kThreads) k_proj_gram(ProjArgs a) {
     }
 }
 
-// One warp per instance: G and D^T b summed from the chunks' partials (lanes stride over the chunks), then lane 0
-// solves: G scaled to unit diagonal, Cholesky, c (0 when there is no history).
-__global__ void k_proj_solve(ProjArgs a) {
+// One block per instance: G and D^T b summed from the chunks' partials (threads stride over the chunks, fixed-order
+// reduction), then thread 0 solves: G scaled to unit diagonal, Cholesky, c (0 when there is no history).
+__global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
+    __shared__ double red[kQ][kSolveThreads / 32];
     const int inst = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (inst >= a.n_inst) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k0 = a.kin[inst];
     double G[10], r[4], c[4] = {0.0, 0.0, 0.0, 0.0};
     const int c0 = a.inst_t0[inst] * a.n_sub, c1 = a.inst_t1[inst] * a.n_sub;
+    {
+        // the 14 quantities of a chunk are loaded together, so their latencies overlap
+        double acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+        const size_t nq = (size_t)a.n_tiles * a.n_sub;
+        for (int ch = c0 + threadIdx.x; ch < c1; ch += kSolveThreads) {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) acc[q] += a.partial[q * nq + ch];
+        }
+        const double v = warp_sum16(acc);
+        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         double v = 0.0;
-        for (int ch = c0 + lane; ch < c1; ch += 32) v += a.partial[(size_t)q * a.n_tiles * a.n_sub + ch];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int w = 0; w < kSolveThreads / 32; ++w) v += red[q][w];
         if (q < 10) G[q] = v;
         else r[q - 10] = v;
     }
-    if (lane != 0) return;
     int k = k0;
     while (k > 0) {
         // scale to unit diagonal, factorise L L^T
@@ -238,7 +282,7 @@ cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, c
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_proj_gram<<<grid, kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_solve<<<a.n_inst, 32, 0, st>>>(a);
+    k_proj_solve<<<a.n_inst, kSolveThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_proj_combine<<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();
