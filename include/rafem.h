@@ -90,6 +90,16 @@ extern "C" {
                                         contributions of its entries (SELL-32 layout only)                    */
 #define RAFEM_ASSEMBLY_COLOR  1      /* element-owner scatter, one launch per element colour, no atomics     */
 
+#define RAFEM_ARITH_AUTO      0      /* element and node passes of the gather assembly in double-word arithmetic
+                                        when the mesh's scales allow it (element volumes in [2^-90, 2^60] m^3,
+                                        coefficients and boundary values below 2^60 in magnitude), FP64
+                                        otherwise                                                              */
+#define RAFEM_ARITH_FP64      1      /* FP64 element and node passes                                           */
+#define RAFEM_ARITH_DW        2      /* double-word element and node passes (pairs of floats, 48 significant
+                                        bits, on the FP32 pipes; FP64 only to write FP64 results): B300 issues
+                                        FP64 at 1/64 of its FP32 rate, which bounds the FP64 passes. Gather
+                                        assembly only; BAD_INPUT at create when the scales are out of range    */
+
 /* Mesh and boundary data of one instance. All pointers are host pointers, read only during rafem_create. */
 typedef struct rafem_mesh {
     int32_t n_nodes;                 /* N >= 4                                                                 */
@@ -134,6 +144,7 @@ typedef struct rafem_params {
                                         GMRES)                                                                 */
     int32_t gmres_restart;           /* GMRES restart length m, 1..64 (0 = 30)                                  */
     int32_t coupling;                /* RAFEM_COUPLING_STAGGERED (0) or RAFEM_COUPLING_MONOLITHIC               */
+    int32_t arith;                   /* RAFEM_ARITH_AUTO (0), RAFEM_ARITH_FP64 or RAFEM_ARITH_DW                 */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
@@ -234,9 +245,10 @@ int rafem_get_schedule(rafem_ctx* ctx, int32_t* rows_per_tile, int32_t* n_tiles,
 
 /* Storage actually used by the solver: kernel_code 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit
  * column deltas, 4/8/16/32 = CSR with that many lanes per row; nnz_stored includes slice padding; column_bytes is
- * 2 or 4; assembly is the RAFEM_ASSEMBLY_* in use. Any out pointer may be NULL. */
+ * 2 or 4; assembly is the RAFEM_ASSEMBLY_* in use; arith is RAFEM_ARITH_FP64 or RAFEM_ARITH_DW (what
+ * RAFEM_ARITH_AUTO resolved to). Any out pointer may be NULL. */
 int rafem_layout_info(rafem_ctx* ctx, int32_t* kernel_code, int64_t* nnz_stored, int32_t* column_bytes,
-                      int32_t* assembly);
+                      int32_t* assembly, int32_t* arith);
 
 /* Copy the current lifted system `which` to host buffers: row_ptr [N+1], col [nnz], vals [nnz], rhs [N].
  * Any pointer may be NULL to skip it. For inspection and tests. */

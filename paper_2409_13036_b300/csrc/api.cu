@@ -79,6 +79,7 @@ struct rafem_ctx {
     double* proj_coef = nullptr;                   // [4 n_inst]
     int32_t *proj_kin = nullptr, *proj_kout = nullptr;
     double* proj_D = nullptr;                      // [N][4] projection basis
+    double* proj_Y = nullptr;                      // [N][4] A times the basis (double-word passes)
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -101,6 +102,8 @@ struct rafem_ctx {
     // row-owner assembly
     bool gather = false;
     GatherData gd;
+    bool dw = false;  // double-word element and node passes (RAFEM_ARITH_DW resolved at create)
+    GatherDw gdw;
     uint8_t* gather_cg = nullptr;
     long long gather_nc = 0;
     // graph
@@ -396,6 +399,15 @@ cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, con
 
 cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
     cudaError_t e;
+    if (c->dw) {
+        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        if (which == RAFEM_SYS_V)
+            return launch_assemble_V_gather_dw(c->gd, c->gdw, c->N, c->rp, c->ci, c->diag, c->el, T_sigma,
+                                               c->prm.alpha_sigma, c->bcV, c->gV, c->valsV, v32, c->bV, c->prm.lift,
+                                               c->stream);
+        return launch_rhs_T_gather_dw(c->gd, c->gdw, c->N, c->el, T_sigma, T_old, c->V, c->bcT, c->gT, c->bTc,
+                                      c->prm.alpha_sigma, c->bT, c->stream);
+    }
     if (c->gather) {
         float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
         if (which == RAFEM_SYS_V)
@@ -514,6 +526,7 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
         ProjArgs a{};
         a.n_tiles = c->n_tiles;
         a.n_sub = c->proj_sub;
+        a.dw = c->dw ? 1 : 0;
         a.tile_r0 = c->tile_r0;
         a.tile_r1 = c->tile_r1;
         a.tile_inst = c->tile_inst;
@@ -536,6 +549,7 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
         a.kin = c->proj_kin;
         a.kout = c->proj_kout;
         a.D = c->proj_D;
+        a.Y = c->proj_Y;
         return launch_projection(a, &c->stats->hist, 1, c->stream);
     }
     const int order = c->prm.predictor == RAFEM_PREDICT_PROJECT ? 2 : c->prm.predictor;
@@ -1015,7 +1029,8 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     }
     // ---- host setup
     std::vector<int8_t> orient;
-    int v = validate_mesh(N, E, m->tets, m->coords, orient);
+    double vol_min = 0.0, vol_max = 0.0;
+    int v = validate_mesh(N, E, m->tets, m->coords, orient, &vol_min, &vol_max);
     if (v == -1) return RAFEM_ERR_BAD_INPUT;
     if (v == -2) return RAFEM_ERR_BAD_MESH;
     for (int64_t i = 0; i < 3LL * N; ++i)
@@ -1053,6 +1068,18 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     c->sell = c->lanes == 1;
     const bool want16 = prm->lanes_per_row == 0;
     c->gather = c->sell && prm->assembly == RAFEM_ASSEMBLY_GATHER;
+    {
+        // double-word passes: the element constants and fields must sit well inside the float exponent range so
+        // that the low words keep their 24 bits (volumes, and through them the G entries, drive the smallest ones)
+        const double big = std::ldexp(1.0, 60);
+        double amax = std::max({std::fabs(prm->alpha_sigma), std::fabs(prm->T_a), prm->perf, prm->rho_c / prm->dt});
+        for (int64_t e = 0; e < E; ++e) amax = std::max(amax, std::fabs(m->sigma0[e]));
+        for (int64_t i = 0; i < N; ++i) amax = std::max({amax, std::fabs(m->g_V[i]), std::fabs(m->g_T[i])});
+        const bool scales_ok = vol_min >= std::ldexp(1.0, -90) && vol_max <= big && amax <= big &&
+                               prm->rho_c / prm->dt >= std::ldexp(1.0, -30);
+        if (prm->arith == RAFEM_ARITH_DW && (!c->gather || !scales_ok)) return RAFEM_ERR_BAD_INPUT;
+        c->dw = c->gather && scales_ok && prm->arith != RAFEM_ARITH_FP64;
+    }
     // element storage order. The colour scatter needs the elements of a colour stored contiguously; the row-owner
     // assembly does not, so there the elements are stored by their smallest node (a counting sort, stable in mesh
     // order), which keeps the nodal gathers of the element passes local. The colour pass over the thermal matrix
@@ -1211,7 +1238,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->proj_coef, 4 * (size_t)n_inst));
     CK(dalloc(c, &c->proj_kin, n_inst));
     CK(dalloc(c, &c->proj_kout, n_inst));
-    if (prm->predictor == RAFEM_PREDICT_PROJECT) CK(dalloc(c, &c->proj_D, 4 * (size_t)N + 4));
+    if (prm->predictor == RAFEM_PREDICT_PROJECT) {
+        CK(dalloc(c, &c->proj_D, 4 * (size_t)N + 4));
+        if (c->dw) CK(dalloc(c, &c->proj_Y, 4 * (size_t)N + 4));
+    }
     CK(dalloc(c, &c->V_old, N));
     CK(dalloc(c, &c->stats_save, 1));
     CK(dalloc(c, &c->istats_save, n_inst));
@@ -1246,7 +1276,16 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         CK(dalloc(c, &gcnt, g_cnt.size()));
         CK(dalloc(c, &celem, g_elem.size()));
         CK(dalloc(c, &cg, g_idx.size()));
-        CK(dalloc(c, &cval, g_elem.size()));
+        if (c->dw) {
+            cval = nullptr;
+            CK(dalloc(c, &c->gdw.cval, g_elem.size()));
+            CK(dalloc(c, &c->gdw.tq, 7 * (size_t)E));
+            CK(dalloc(c, &c->gdw.Ts, N));
+            CK(dalloc(c, &c->gdw.To, N));
+            CK(dalloc(c, &c->gdw.V, N));
+        } else {
+            CK(dalloc(c, &cval, g_elem.size()));
+        }
         CK(dalloc(c, &ioff, i_off.size()));
         CK(dalloc(c, &icnt, i_cnt.size()));
         CK(dalloc(c, &ielem, i_elem.size()));
@@ -1362,7 +1401,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
     CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
-    if (c->gather) {
+    if (c->dw) {
+        CK(launch_fill_dw(c->gdw, c->gather_nc, c->gd.celem, c->gather_cg, c->el, prm->rho_c / prm->dt, st));
+        CK(launch_node_mass(c->gd, N, c->e_vol, prm->rho_c / prm->dt, st));
+    } else if (c->gather) {
         CK(launch_fill_cval(c->gather_nc, c->gd.celem, c->gather_cg, c->e_sig0, c->e_G, E, const_cast<double*>(c->gd.cval),
                             st));
         CK(launch_node_mass(c->gd, N, c->e_vol, prm->rho_c / prm->dt, st));
@@ -1417,6 +1459,8 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift == RAFEM_LIFT_ROW && prm->solver == RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
+    if (prm->arith != RAFEM_ARITH_AUTO && prm->arith != RAFEM_ARITH_FP64 && prm->arith != RAFEM_ARITH_DW)
+        return RAFEM_ERR_BAD_INPUT;
     return RAFEM_OK;
 }
 
@@ -1687,7 +1731,9 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
     if (sigma0) {
         CK(cudaMemcpyAsync(c->p_tmpE, sigma0, E * sizeof(double), kind, st));
         CK(launch_permute(E, c->e_order, c->p_tmpE, c->e_sig0, 0, st));
-        if (c->gather)
+        if (c->dw)
+            CK(launch_fill_dw(c->gdw, c->gather_nc, c->gd.celem, c->gather_cg, c->el, c->prm.rho_c / c->prm.dt, st));
+        else if (c->gather)
             CK(launch_fill_cval(c->gather_nc, c->gd.celem, c->gather_cg, c->e_sig0, c->e_G, E,
                                 const_cast<double*>(c->gd.cval), st));
     }
@@ -1760,6 +1806,7 @@ int apply_dt(rafem_ctx* c, double dt) {
                              c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
     if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
     if (c->gd.mT) CK(launch_node_mass(c->gd, c->N, c->e_vol, c->prm.rho_c / dt, st));
+    if (c->dw) CK(launch_fill_dw(c->gdw, 0, nullptr, nullptr, c->el, c->prm.rho_c / dt, st));
     drop_graphs(c);
     return RAFEM_OK;
 }
@@ -2034,12 +2081,13 @@ int rafem_get_schedule(rafem_ctx* c, int32_t* rows_per_tile, int32_t* n_tiles, i
 }
 
 int rafem_layout_info(rafem_ctx* c, int32_t* kernel_code, int64_t* nnz_stored, int32_t* column_bytes,
-                      int32_t* assembly) {
+                      int32_t* assembly, int32_t* arith) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     if (kernel_code) *kernel_code = c->lanes;
     if (nnz_stored) *nnz_stored = c->nnz_store;
     if (column_bytes) *column_bytes = c->ci16 ? 2 : 4;
     if (assembly) *assembly = c->gather ? RAFEM_ASSEMBLY_GATHER : RAFEM_ASSEMBLY_COLOR;
+    if (arith) *arith = c->dw ? RAFEM_ARITH_DW : RAFEM_ARITH_FP64;
     return RAFEM_OK;
 }
 

@@ -37,6 +37,25 @@ struct GatherData {
     double* mT = nullptr;            // [N] (rho_c/dt) sum vol/20
 };
 
+// Double-word (float pair) data of the gather assembly (assembly_dw.cu): the element constants, split once per
+// context, and per-pass node copies of the fields.
+struct GatherDw {
+    float2* cval = nullptr;  // sigma0_e G_e[a][b] per contribution, as GatherData::cval
+    float2* tq = nullptr;    // [7][E]: -sigma0_e G_e[ab] / 4 for the six edges, then (rho_c/dt) vol_e / 20
+    float2* Ts = nullptr;    // [N] temperature of sigma(T)
+    float2* To = nullptr;    // [N] temperature of the mass term (T^n)
+    float2* V = nullptr;     // [N] potential
+};
+cudaError_t launch_fill_dw(const GatherDw& d, long long nc, const int32_t* celem, const uint8_t* cg,
+                           const ElemData& el, double c_mass, cudaStream_t st);
+cudaError_t launch_assemble_V_gather_dw(const GatherData& gd, const GatherDw& d, int N, const int32_t* sp,
+                                        const int32_t* sc, const int32_t* diag, const ElemData& el, const double* T,
+                                        double alpha, const uint8_t* bc, const double* g, double* vals, float* vals32,
+                                        double* b, int row_lift, cudaStream_t st);
+cudaError_t launch_rhs_T_gather_dw(const GatherData& gd, const GatherDw& d, int N, const ElemData& el,
+                                   const double* T_sigma, const double* T_old, const double* V, const uint8_t* bc,
+                                   const double* g, const double* bconst, double alpha, double* b, cudaStream_t st);
+
 // Launchers (assembly.cu). Every launcher only enqueues work on `st`.
 cudaError_t launch_fill_cval(long long nc, const int32_t* celem, const uint8_t* cg, const double* sigma0,
                              const double* G, int E, double* cval, cudaStream_t st);
@@ -316,9 +335,11 @@ struct ProjArgs {
     double* x;                       // x_n in, initial guess out
     double *h1, *h2, *h3;            // x_{n-1}, x_{n-2}, x_{n-3} (shifted)
     double* D;                       // [N][4] basis (32-byte aligned)
+    double* Y;                       // [N][4] A D (double-word passes only)
     double* partial;                 // [14][n_tiles * n_sub]
     double* coef;                    // [4 n_inst]
     int32_t *kin, *kout;             // [n_inst] solutions available / basis size used
+    int dw;                          // 1: double-word passes (D and partial hold float pairs)
 };
 // hist: steps completed (device); lag: 1 when the initial field is not a solution (potential), 0 otherwise.
 cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);

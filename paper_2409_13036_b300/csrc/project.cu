@@ -21,6 +21,7 @@
 
 #include <cmath>
 
+#include "dw.cuh"
 #include "internal.h"
 
 namespace rafem {
@@ -32,25 +33,52 @@ constexpr int kQ = 14;  // 10 entries of the symmetric 4 x 4 Gram matrix + 4 rig
 constexpr int kChunk = kProjChunk;  // rows per block: tiles are split so that the pass has enough parallelism
 constexpr int kBatch = 5;  // interior rows of the Kuhn lattice have 15 entries
 constexpr int kSolveThreads = 256;
+constexpr int kBatchApply = 3;  // double-word apply: fewer live registers, four blocks per SM
 
 __device__ __forceinline__ int tri(int i, int l) { return i <= l ? l * (l + 1) / 2 + i : i * (i + 1) / 2 + l; }
+
+// Arithmetic of the sums: FP64, or double-word (dw.cuh: float pairs on the FP32 pipes, stored as float2).
+struct ArithF64 {
+    using T = double;
+    using S = double;  // storage
+    __device__ static T zero() { return 0.0; }
+    __device__ static T add(T x, T y) { return x + y; }
+    __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+    __device__ static T load(const S* p) { return *p; }
+    __device__ static void store(S* p, T v) { *p = v; }
+    __device__ static double value(T v) { return v; }
+};
+struct ArithDW {
+    using T = dw::df;
+    using S = float2;
+    __device__ static T zero() { return dw::make(0.0f); }
+    __device__ static T add(T x, T y) { return dw::add(x, y); }
+    __device__ static T shfl(T v, int o) {
+        return {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    }
+    __device__ static T load(const S* p) { return dw::load(p); }
+    __device__ static void store(S* p, T v) { dw::store(p, v); }
+    __device__ static double value(T v) { return dw::to_double(v); }
+};
 
 // Sums 16 values over the warp by recursive halving: at each of the offsets 16, 8, 4, 2 a lane keeps one half of
 // its values and adds the partner's copy of that half, so 16 shuffles replace the 80 of one butterfly per value.
 // On return lane l holds the warp total of value l >> 1 (fixed order, deterministic).
-__device__ __forceinline__ double warp_sum16(double (&v)[16]) {
+template <class Ar>
+__device__ __forceinline__ typename Ar::T warp_sum16(typename Ar::T (&v)[16]) {
+    using T = typename Ar::T;
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int h = 8; h >= 1; h >>= 1) {
         const bool up = lane & (2 * h);
 #pragma unroll
         for (int i = 0; i < h; ++i) {
-            const double send = up ? v[i] : v[i + h];
-            const double keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = Ar::add(keep, Ar::shfl(send, 2 * h));
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return Ar::add(v[0], Ar::shfl(v[0], 1));
 }
 
 // difference basis at node j from x_n and the history (components i >= k are zero)
@@ -155,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_proj_gram(ProjArgs a) {
         }
         // block reduction (fixed order)
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const double v = warp_sum16(acc);
+        const double v = warp_sum16<ArithF64>(acc);
         if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
         __syncthreads();
         if (threadIdx.x < kQ) {
@@ -169,8 +197,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_proj_gram(ProjArgs a) {
 
 // One block per instance: G and D^T b summed from the chunks' partials (threads stride over the chunks, fixed-order
 // reduction), then thread 0 solves: G scaled to unit diagonal, Cholesky, c (0 when there is no history).
+template <class Ar>
 __global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
-    __shared__ double red[kQ][kSolveThreads / 32];
+    using T = typename Ar::T;
+    __shared__ T red[kQ][kSolveThreads / 32];
     const int inst = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k0 = a.kin[inst];
@@ -178,25 +208,26 @@ __global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
     const int c0 = a.inst_t0[inst] * a.n_sub, c1 = a.inst_t1[inst] * a.n_sub;
     {
         // the 14 quantities of a chunk are loaded together, so their latencies overlap
-        double acc[16];
+        T acc[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+        for (int q = 0; q < 16; ++q) acc[q] = Ar::zero();
         const size_t nq = (size_t)a.n_tiles * a.n_sub;
+        const typename Ar::S* partial = reinterpret_cast<const typename Ar::S*>(a.partial);
         for (int ch = c0 + threadIdx.x; ch < c1; ch += kSolveThreads) {
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) acc[q] += a.partial[q * nq + ch];
+            for (int q = 0; q < kQ; ++q) acc[q] = Ar::add(acc[q], Ar::load(partial + q * nq + ch));
         }
-        const double v = warp_sum16(acc);
+        const T v = warp_sum16<Ar>(acc);
         if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-        double v = 0.0;
-        for (int w = 0; w < kSolveThreads / 32; ++w) v += red[q][w];
-        if (q < 10) G[q] = v;
-        else r[q - 10] = v;
+        T v = Ar::zero();
+        for (int w = 0; w < kSolveThreads / 32; ++w) v = Ar::add(v, red[q][w]);
+        if (q < 10) G[q] = Ar::value(v);
+        else r[q - 10] = Ar::value(v);
     }
     int k = k0;
     while (k > 0) {
@@ -262,6 +293,158 @@ __global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
     }
 }
 
+// ---- double-word variants of the three passes over the nodes and the matrix (dw.cuh). D holds four float pairs
+// per node (32 bytes, as in FP64), the partial sums float pairs; the FP64 matrix values and vectors are split by
+// integer operations as they are read, and x = D c is written with one FP64 addition per node.
+
+__device__ __forceinline__ dw::df pair(float a, float b) { return dw::make(a, b); }
+
+// d_0 = x, d_1 = x - h1, d_2 = d_1 - (h1 - h2), d_3 = d_2 - ((h1 - h2) - (h2 - h3)) from the split values
+__global__ void __launch_bounds__(kThreads) k_proj_basis_dw(ProjArgs a) {
+    float4* D = reinterpret_cast<float4*>(a.D);
+    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
+        int t, r0, r1;
+        chunk_rows(a, ch, t, r0, r1);
+        const int k = a.kin[a.tile_inst[t]];
+        for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+            const dw::df x = dw::split(a.x[row]);
+            const dw::df h1 = k > 1 ? dw::split(a.h1[row]) : dw::make(0.0f);
+            const dw::df h2 = k > 2 ? dw::split(a.h2[row]) : dw::make(0.0f);
+            const dw::df h3 = k > 3 ? dw::split(a.h3[row]) : dw::make(0.0f);
+            const dw::df e1 = dw::sub(x, h1), e2 = dw::sub(h1, h2), e3 = dw::sub(h2, h3);
+            const dw::df d1 = k > 1 ? e1 : dw::make(0.0f);
+            const dw::df d2 = k > 2 ? dw::sub(e1, e2) : dw::make(0.0f);
+            const dw::df d3 = k > 3 ? dw::sub(d2, dw::sub(e2, e3)) : dw::make(0.0f);
+            D[2 * row] = make_float4(x.h, x.l, d1.h, d1.l);
+            D[2 * row + 1] = make_float4(d2.h, d2.l, d3.h, d3.l);
+        }
+    }
+}
+
+// Y = A D on the free rows of instances with history (four float pairs per node, the layout of D). Kept apart
+// from the sums below so that few registers stay live and enough warps hide the gathers' latency.
+__global__ void __launch_bounds__(kThreads, 4) k_proj_apply_dw(ProjArgs a) {
+    const float4* D = reinterpret_cast<const float4*>(a.D);  // written by the previous launch
+    float4* Y = reinterpret_cast<float4*>(a.Y);
+    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
+        int t, r0, r1;
+        chunk_rows(a, ch, t, r0, r1);
+        if (a.kin[a.tile_inst[t]] == 0) continue;
+        for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+            if (a.bc[row]) continue;
+            dw::df y[4] = {dw::make(0.0f), dw::make(0.0f), dw::make(0.0f), dw::make(0.0f)};
+            int q0, q1, stride;
+            if (a.sell) {
+                const int s = row >> 5, base = __ldg(a.rp + s);
+                q0 = base + (row & 31);
+                q1 = __ldg(a.rp + s + 1) + (row & 31);
+                stride = 32;
+            } else {
+                q0 = __ldg(a.rp + row);
+                q1 = __ldg(a.rp + row + 1);
+                stride = 1;
+            }
+            for (int q = q0; q < q1; q += kBatchApply * stride) {
+                double v[kBatchApply];
+                int j[kBatchApply];
+#pragma unroll
+                for (int u = 0; u < kBatchApply; ++u) {
+                    const int qq = q + u * stride;
+                    const bool ok = qq < q1;
+                    v[u] = ok ? __ldg(a.A + qq) : 0.0;
+                    j[u] = ok ? (a.ci16 ? row + (int)__ldg(a.ci16 + qq) : __ldg(a.ci + qq)) : row;
+                }
+                float4 lo[kBatchApply], hi[kBatchApply];
+#pragma unroll
+                for (int u = 0; u < kBatchApply; ++u) {
+                    lo[u] = __ldg(D + 2 * j[u]);
+                    hi[u] = __ldg(D + 2 * j[u] + 1);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatchApply; ++u) {
+                    const dw::df av = dw::split(v[u]);
+                    dw::dot_acc(y[0], av, pair(lo[u].x, lo[u].y));
+                    dw::dot_acc(y[1], av, pair(lo[u].z, lo[u].w));
+                    dw::dot_acc(y[2], av, pair(hi[u].x, hi[u].y));
+                    dw::dot_acc(y[3], av, pair(hi[u].z, hi[u].w));
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) y[l] = dw::finish(y[l]);
+            Y[2 * row] = make_float4(y[0].h, y[0].l, y[1].h, y[1].l);
+            Y[2 * row + 1] = make_float4(y[2].h, y[2].l, y[3].h, y[3].l);
+        }
+    }
+}
+
+// Per chunk: the partial sums of G = D^T Y and D^T b over its free rows.
+__global__ void __launch_bounds__(kThreads) k_proj_gram_dw(ProjArgs a) {
+    __shared__ float2 red[kQ][kThreads / 32];
+    const float4* D = reinterpret_cast<const float4*>(a.D);
+    const float4* Y = reinterpret_cast<const float4*>(a.Y);
+    float2* partial = reinterpret_cast<float2*>(a.partial);
+    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
+        int t, r0, r1;
+        chunk_rows(a, ch, t, r0, r1);
+        const int k = a.kin[a.tile_inst[t]];
+        dw::df acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = dw::make(0.0f);
+        if (k > 0) {
+            for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+                if (a.bc[row]) continue;
+                const float4 dlo = __ldg(D + 2 * row), dhi = __ldg(D + 2 * row + 1);
+                const float4 ylo = __ldg(Y + 2 * row), yhi = __ldg(Y + 2 * row + 1);
+                const dw::df d[4] = {pair(dlo.x, dlo.y), pair(dlo.z, dlo.w), pair(dhi.x, dhi.y), pair(dhi.z, dhi.w)};
+                const dw::df y[4] = {pair(ylo.x, ylo.y), pair(ylo.z, ylo.w), pair(yhi.x, yhi.y), pair(yhi.z, yhi.w)};
+                const dw::df bi = dw::split(a.b[row]);
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+#pragma unroll
+                    for (int i = 0; i <= l; ++i) dw::dot_acc(acc[l * (l + 1) / 2 + i], d[i], y[l]);
+                    dw::dot_acc(acc[10 + l], d[l], bi);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) acc[q] = dw::finish(acc[q]);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const dw::df v = warp_sum16<ArithDW>(acc);
+        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = make_float2(v.h, v.l);
+        __syncthreads();
+        if (threadIdx.x < kQ) {
+            dw::df s = dw::make(0.0f);
+            for (int w = 0; w < kThreads / 32; ++w) s = dw::add(s, dw::load(&red[threadIdx.x][w]));
+            dw::store(partial + (size_t)threadIdx.x * a.n_tiles * a.n_sub + ch, s);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_proj_combine_dw(ProjArgs a) {
+    const float4* D = reinterpret_cast<const float4*>(a.D);
+    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
+        int t, r0, r1;
+        chunk_rows(a, ch, t, r0, r1);
+        const int inst = a.tile_inst[t];
+        const int k = a.kout[inst];
+        const dw::df c0 = dw::split(a.coef[4 * inst]), c1 = dw::split(a.coef[4 * inst + 1]),
+                     c2 = dw::split(a.coef[4 * inst + 2]), c3 = dw::split(a.coef[4 * inst + 3]);
+        for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+            const double xn = a.x[row], x1 = a.h1[row], x2 = a.h2[row];
+            if (k > 0 && !a.bc[row]) {
+                const float4 lo = D[2 * row], hi = D[2 * row + 1];
+                const dw::df s01 = dw::add(dw::mul(c0, pair(lo.x, lo.y)), dw::mul(c1, pair(lo.z, lo.w)));
+                const dw::df s23 = dw::add(dw::mul(c2, pair(hi.x, hi.y)), dw::mul(c3, pair(hi.z, hi.w)));
+                a.x[row] = dw::to_double(dw::add(s01, s23));
+            }
+            a.h3[row] = x2;
+            a.h2[row] = x1;
+            a.h1[row] = xn;
+        }
+    }
+}
+
 // Solutions available to each instance: min(4, hist - lag) (hist from the step statistics).
 __global__ void k_proj_count(ProjArgs a, const int32_t* hist, int lag) {
     const int inst = blockIdx.x * blockDim.x + threadIdx.x;
@@ -278,11 +461,23 @@ cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, c
     if (e != cudaSuccess) return e;
     const long long nch = (long long)a.n_tiles * a.n_sub;
     const int grid = (int)(nch < 148 * 32 ? nch : 148 * 32);
+    if (a.dw) {
+        k_proj_basis_dw<<<grid, kThreads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_proj_apply_dw<<<grid, kThreads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_proj_gram_dw<<<grid, kThreads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_proj_solve<ArithDW><<<a.n_inst, kSolveThreads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_proj_combine_dw<<<grid, kThreads, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     k_proj_basis<<<grid, kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_proj_gram<<<grid, kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_solve<<<a.n_inst, kSolveThreads, 0, st>>>(a);
+    k_proj_solve<ArithF64><<<a.n_inst, kSolveThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_proj_combine<<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();

@@ -19,11 +19,13 @@
 
 namespace rafem {
 
-int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient) {
+int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient,
+                  double* vol_min, double* vol_max) {
     if (N < 4 || E < 1) return -1;
     int bad_index = 0, bad_vol = 0;
+    double vmin = INFINITY, vmax = 0.0;
     orient.assign(E, 1);
-#pragma omp parallel for reduction(+ : bad_index, bad_vol) schedule(static)
+#pragma omp parallel for reduction(+ : bad_index, bad_vol) reduction(min : vmin) reduction(max : vmax) schedule(static)
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* t = tets + 4 * e;
         bool ok = true;
@@ -45,7 +47,11 @@ int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vec
         for (int c = 0; c < 3; ++c) scale = std::max({scale, std::fabs(e1[c]), std::fabs(e2[c]), std::fabs(e3[c])});
         if (!(std::fabs(det) > 1e-14 * scale * scale * scale) || !std::isfinite(det)) bad_vol++;
         orient[e] = det > 0 ? 1 : -1;
+        vmin = std::min(vmin, std::fabs(det) / 6.0);
+        vmax = std::max(vmax, std::fabs(det) / 6.0);
     }
+    if (vol_min) *vol_min = vmin;
+    if (vol_max) *vol_max = vmax;
     if (bad_index) return -1;
     if (bad_vol) return -2;
     return 0;

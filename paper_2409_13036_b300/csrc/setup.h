@@ -11,7 +11,8 @@ constexpr int32_t SLOT_LAST = 1 << 29;    // this element is the last writer of 
 constexpr int32_t SLOT_MASK = (1 << 29) - 1;
 
 // 0 ok, -1 bad index / repeated node, -2 degenerate element. orient[e] = sign of the element's volume.
-int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient);
+int validate_mesh(int N, int E, const int32_t* tets, const double* xyz, std::vector<int8_t>& orient,
+                  double* vol_min = nullptr, double* vol_max = nullptr);
 
 // CSR pattern of the node graph: row i lists every node sharing an element with i (itself included), sorted.
 void build_pattern(int N, int E, const int32_t* tets, std::vector<int32_t>& row_ptr, std::vector<int32_t>& col);

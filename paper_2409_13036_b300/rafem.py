@@ -46,6 +46,9 @@ RAFEM_ILU_MULTICOLOR = 0
 RAFEM_ILU_NATURAL = 1
 RAFEM_ASSEMBLY_GATHER = 0
 RAFEM_ASSEMBLY_COLOR = 1
+RAFEM_ARITH_AUTO = 0
+RAFEM_ARITH_FP64 = 1
+RAFEM_ARITH_DW = 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -65,7 +68,7 @@ class rafem_params(ctypes.Structure):
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
                 ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32),
-                ("gmres_restart", ctypes.c_int32), ("coupling", ctypes.c_int32)]
+                ("gmres_restart", ctypes.c_int32), ("coupling", ctypes.c_int32), ("arith", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):
@@ -131,7 +134,8 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(ctypes.c_int32)]),
         "rafem_get_system": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
         "rafem_layout_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
-                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]),
         "rafem_solve_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rafem_step_stats)]),
         "rafem_spmv": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_tracing": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -353,10 +357,11 @@ class Context:
         return {"rows_per_tile": r.value, "n_tiles": n.value, "grid": g.value}
 
     def layout_info(self) -> dict:
-        code, nst, cb, asm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        code, nst, cb, asm, ar = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib().rafem_layout_info(self._ctx, ctypes.byref(code), ctypes.byref(nst), ctypes.byref(cb),
-                                       ctypes.byref(asm)), "rafem_layout_info")
-        return {"kernel_code": code.value, "nnz_stored": nst.value, "column_bytes": cb.value, "assembly": asm.value}
+                                       ctypes.byref(asm), ctypes.byref(ar)), "rafem_layout_info")
+        return {"kernel_code": code.value, "nnz_stored": nst.value, "column_bytes": cb.value, "assembly": asm.value,
+                "arith": ar.value}
 
     def get_system(self, which: int):
         """(row_ptr, col, vals, rhs) of the current lifted system, as host arrays."""
