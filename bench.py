@@ -408,11 +408,12 @@ def measure_adjoint(rafem, torch, mg, args):
     rng = np.random.default_rng(mg.SEED_BASE + 5)
     elems = rng.choice(mesh.n_tets, size=n_fd, replace=False)
 
-    # central differences of the forward model solved as smoothly as possible in the parameters: tolerance 1e-13
-    # and each solve started from the previous step's solution (no extrapolation), so that both perturbed runs
-    # follow the same iteration paths
+    # central differences of the forward model solved as smoothly as possible in the parameters: tolerance 1e-13,
+    # each solve started from the previous step's solution (no extrapolation) so that both perturbed runs follow
+    # the same iteration paths, and FP64 element passes (the double-word passes round at 2^-48, which the
+    # difference quotient divides by eps)
     ctx.close()
-    ctx = rafem.Context(mesh, tol=1e-13, predictor=0)
+    ctx = rafem.Context(mesh, tol=1e-13, predictor=0, arith=rafem.RAFEM_ARITH_FP64)
 
     def fd_at(eps):
         fd = np.empty(n_fd)
@@ -438,7 +439,7 @@ def measure_adjoint(rafem, torch, mg, args):
     ctx.close()
     return {"workload": "64^3 cells (274,625 nodes, 1,572,864 tets), jitter +-10%, tumour-sigma0 target",
             "steps": n_steps, "checkpoint_every": every, "solver_tol": 1e-13, "params_dtype": "float32",
-            "fd_forward": "tol 1e-13, predictor order 0",
+            "fd_forward": "tol 1e-13, predictor order 0, FP64 element passes",
             "loss": float(loss.item()), "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
             "backward_over_forward": (t2 - t1) / (t1 - t0), "adjoint": adj,
             "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
