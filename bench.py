@@ -250,6 +250,7 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, preco
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     fields = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
+    graph = ctx.graph_info()
     # region split and iteration counts of the same K steps: replayed from the initial state with tracing on (the
     # traced launches are identical; tracing only adds an event and a synchronisation between regions)
     ctx.reset()
@@ -259,7 +260,7 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, preco
     tr = ctx.get_trace()
     ctx.set_tracing(False)
     return {"ctx": ctx, "ms": ms, "status": rafem.status_string(s), "last": st.as_dict(), "trace": tr,
-            "fields": fields, "N": N, "nnz": nnz, "n_colors": n_colors, "layout": layout,
+            "fields": fields, "N": N, "nnz": nnz, "n_colors": n_colors, "layout": layout, "graph": graph,
             "clocks": clk.summary() if clk else None}
 
 
@@ -445,6 +446,51 @@ def measure_adjoint(rafem, torch, mg, args):
             "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
 
 
+def measure_accuracy(rafem, torch, mesh, args):
+    """Tolerance sweep and long-run parity on the headline workload: the mixed path at relative residuals 1e-6,
+    1e-8, 1e-10 and 1e-12 against the FP64 path at 1e-12 over the first `accuracy_steps` steps of the run
+    (default 900, the paper's 15 simulated minutes), with the relative L2 differences of T and V and the PSNR of T
+    (Eq. 1-2: the peak over the whole run) every 100 steps."""
+    import numpy as np
+    n = args.accuracy_steps
+    marks = list(range(100, n, 100)) + [n]
+    stream = torch.cuda.Stream()
+
+    def trajectory(ctx):
+        Ts, Vs, done, t_run, iters = [], [], 0, 0.0, 0
+        ctx.reset()
+        for m in marks:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s, st = ctx.run(m - done)
+            torch.cuda.synchronize()
+            t_run += time.perf_counter() - t0
+            if s < 0:
+                raise RuntimeError(rafem.status_string(s))
+            done = m
+            Ts.append(ctx.get_field(rafem.RAFEM_SYS_T))
+            Vs.append(ctx.get_field(rafem.RAFEM_SYS_V))
+        return Ts, Vs, n / t_run
+
+    ref = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_FP64, tol=1e-12)
+    Tr, Vr, ref_rate = trajectory(ref)
+    ref.close()
+    peak = max(float(T.max()) for T in Tr)
+    out = {"steps": n, "reference": {"precision": "fp64", "tol": 1e-12, "steps_per_s": ref_rate},
+           "marks": marks, "mixed": []}
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_MIXED)
+    for tol in (1e-6, 1e-8, 1e-10, 1e-12):
+        ctx.set_tol(tol)
+        Tm, Vm, rate = trajectory(ctx)
+        eT = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Tm, Tr)]
+        eV = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Vm, Vr)]
+        psnr = [float(20 * np.log10(peak / np.sqrt(max(float(np.mean((a - b) ** 2)), 1e-300)))) for a, b in zip(Tm, Tr)]
+        out["mixed"].append({"tol": tol, "steps_per_s": rate, "rel_err_T_max": max(eT), "rel_err_V_max": max(eV),
+                             "psnr_T_db_min": min(psnr), "rel_err_T": eT, "rel_err_V": eV})
+    ctx.close()
+    return out
+
+
 def measure_monolithic(rafem, torch, mesh, args):
     """The paper's 2N x 2N system shape: V and T of each step solved together by Newton's method (corrector_tol
     1e-6 degC on max |dT|, at most 20 iterations), block-Jacobi BiCGSTAB to 1e-10 per linear solve, on the 127^3
@@ -516,6 +562,8 @@ def main():
     ap.add_argument("--numbering-steps", type=int, default=10, help="timed steps per node numbering (0 = skip)")
     ap.add_argument("--monolithic-steps", type=int, default=3, help="timed monolithic Newton steps (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
+    ap.add_argument("--accuracy-steps", type=int, default=900,
+                    help="steps of the tolerance sweep / long-run parity against FP64 (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -631,7 +679,9 @@ def main():
                                                                           "ms_predict_T", "ms_solve_T")},
                 "roofline": r["roofline"]}
 
-    per_step_launches = 1 + (1 + n_colors + 2 + 1) + (1 + n_colors + 2 + 1)
+    # kernels of the timed region: the kernel nodes of the captured step graph per step, plus the step-counter
+    # kernel rafem_run launches once
+    per_step_launches = head["graph"]["step_kernels"]
     head_sum = summary(head)
     line = {"metric": METRIC, "value": head_sum["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head_sum["ms_per_step"], "higher_is_better": True,
@@ -639,6 +689,7 @@ def main():
             "dtype": "f32+f64" if head_name == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": N, "nnz_per_system": nnz, "colours": n_colors,
                        "precision": head_name, "layout": "SELL-32",
+                       "element_arith": "double-word" if head["layout"]["arith"] == rafem.RAFEM_ARITH_DW else "fp64",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (two 373 MB FP64 matrices + element data per step)"},
             "status": head_sum["status"], "last_step": head_sum["last_step"],
@@ -649,7 +700,7 @@ def main():
             "e2e": {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 16 * N, "steps": e2e_steps,
                     "note": "same steps as the device-timed region, replayed from the initial state"},
-            "gpu_launches": per_step_launches * args.steps,
+            "gpu_launches": per_step_launches * args.steps + 1,
             "clocks": head["clocks"]}
     if "fp64" in runs and head_name != "fp64":
         line["fp64"] = summary(runs["fp64"])
@@ -676,6 +727,11 @@ def main():
             line["batch"] = measure_batch(rafem, torch, mg, args)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
+    if args.accuracy_steps > 0 and args.only is None:
+        try:
+            line["accuracy"] = measure_accuracy(rafem, torch, mesh, args)
+        except Exception as exc:
+            line["accuracy"] = {"error": repr(exc)[:300]}
     if args.monolithic_steps > 0 and args.only is None:
         try:
             line["monolithic"] = measure_monolithic(rafem, torch, mesh, args)

@@ -326,11 +326,18 @@ int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t*
  * at the requested time (Sec. IV). */
 
 /* Which step graphs are in use: 1 = captured and instantiated, 0 = capture failed (direct launches / host loop),
- * -1 = not built yet (built at the first step). corrector_graph is the conditional-loop graph of n_corrector > 1. */
-int rafem_graph_info(rafem_ctx* ctx, int32_t* step_graph, int32_t* corrector_graph);
+ * -1 = not built yet (built at the first step). corrector_graph is the conditional-loop graph of n_corrector > 1.
+ * step_kernels: kernel launches per step of the captured step graph (0 when there is none). Any out pointer may
+ * be NULL. */
+int rafem_graph_info(rafem_ctx* ctx, int32_t* step_graph, int32_t* corrector_graph, int32_t* step_kernels);
 
 /* Change the step size: reassembles the thermal matrix (and its ILU(0) factors) for the new dt. Ends any tape. */
 int rafem_set_dt(rafem_ctx* ctx, double dt);
+
+/* Change the solver tolerances of a live context (the state and the predictor history are kept): tol, the
+ * relative residual to reach (> 0), and, when inner_tol > 0, the mixed solver's inner reduction (< 1); inner_tol
+ * <= 0 keeps the current one. The captured step graphs are rebuilt at the next step. Errors: BAD_INPUT. */
+int rafem_set_tol(rafem_ctx* ctx, double tol, double inner_tol);
 
 typedef struct rafem_advance_stats {
     int32_t status;                  /* worst status of the accepted steps                                     */

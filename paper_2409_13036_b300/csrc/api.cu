@@ -108,6 +108,7 @@ struct rafem_ctx {
     long long gather_nc = 0;
     // graph
     cudaGraphExec_t graph = nullptr;
+    int32_t graph_kernels = 0;  // kernel nodes of the captured step graph
     bool graph_failed = false;
     // corrector passes (n_corrector > 1): one graph per step whose conditional WHILE node repeats the pass on the
     // device until the temperature change falls below corrector_tol or n_corrector passes are done
@@ -826,6 +827,17 @@ void ensure_graph(rafem_ctx* c) {
         cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
         if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
             if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) c->graph = nullptr;
+            size_t n = 0;
+            c->graph_kernels = 0;
+            if (c->graph && cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess && n > 0) {
+                std::vector<cudaGraphNode_t> nodes(n);
+                if (cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess)
+                    for (size_t q = 0; q < n; ++q) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            c->graph_kernels += 1;
+                    }
+            }
         }
         if (g) cudaGraphDestroy(g);
     }
@@ -1813,8 +1825,9 @@ int apply_dt(rafem_ctx* c, double dt) {
 
 }  // namespace
 
-int rafem_graph_info(rafem_ctx* c, int32_t* step_graph, int32_t* corrector_graph) {
+int rafem_graph_info(rafem_ctx* c, int32_t* step_graph, int32_t* corrector_graph, int32_t* step_kernels) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
+    if (step_kernels) *step_kernels = c->graph ? c->graph_kernels : 0;
     if (step_graph) *step_graph = c->graph ? 1 : (c->graph_failed ? 0 : -1);
     if (corrector_graph) *corrector_graph = c->corr_graph ? 1 : (c->corr_graph_failed ? 0 : -1);
     return RAFEM_OK;
@@ -1826,6 +1839,14 @@ int rafem_set_dt(rafem_ctx* c, double dt) {
     const int s = apply_dt(c, dt);
     if (s != RAFEM_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_tol(rafem_ctx* c, double tol, double inner_tol) {
+    if (!c || !(tol > 0) || !std::isfinite(tol) || !(inner_tol < 1) || std::isnan(inner_tol)) return RAFEM_ERR_BAD_INPUT;
+    c->prm.tol = tol;
+    if (inner_tol > 0) c->prm.inner_tol = inner_tol;
+    drop_graphs(c);  // the solver launches carry the tolerances as arguments
     return RAFEM_OK;
 }
 

@@ -154,7 +154,9 @@ def lib() -> ctypes.CDLL:
         "rafem_get_precond": (ctypes.c_int, [vp, ctypes.c_int, vp]),
         "rafem_precond_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_dt": (ctypes.c_int, [vp, ctypes.c_double]),
-        "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "rafem_set_tol": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
+        "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
         "rafem_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(rafem_advance_stats)]),
         "rafem_reorder_rcm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, vp]),
         "rafem_get_coupled_system": (ctypes.c_int, [vp, vp, vp]),
@@ -406,12 +408,16 @@ class Context:
 
     # -- dynamic step size ------------------------------------------------------------------------------------
     def graph_info(self) -> dict:
-        a, b = ctypes.c_int32(), ctypes.c_int32()
-        _check(lib().rafem_graph_info(self._ctx, ctypes.byref(a), ctypes.byref(b)), "rafem_graph_info")
-        return {"step_graph": a.value, "corrector_graph": b.value}
+        a, b, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rafem_graph_info(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)),
+               "rafem_graph_info")
+        return {"step_graph": a.value, "corrector_graph": b.value, "step_kernels": k.value}
 
     def set_dt(self, dt: float):
         _check(lib().rafem_set_dt(self._ctx, float(dt)), "rafem_set_dt")
+
+    def set_tol(self, tol: float, inner_tol: float = 0.0):
+        _check(lib().rafem_set_tol(self._ctx, float(tol), float(inner_tol)), "rafem_set_tol")
 
     def advance(self, duration: float, dt_min: float):
         st = rafem_advance_stats()

@@ -344,3 +344,22 @@ def test_renumbered_meshes_give_the_same_fields():
     for name in ("random", "rcm"):
         assert O.rel_err(out[name][0], out["lattice"][0]) <= 1e-9
         assert O.rel_err(out[name][1], out["lattice"][1]) <= 1e-9
+
+
+def test_set_tol_and_graph_kernels():
+    """rafem_set_tol changes the residual target of a live context (graphs rebuilt, state kept); the step graph
+    reports its kernel count."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=12, sigma0="lognormal")
+    with rafem.Context(m, precision=rafem.RAFEM_PRECISION_MIXED, tol=1e-6) as ctx:
+        s, st = ctx.run(3)
+        assert s == 0 and st.relres_V <= 1e-6 and st.relres_T <= 1e-6
+        g = ctx.graph_info()
+        assert g["step_graph"] == 1 and g["step_kernels"] >= 8
+        ctx.set_tol(1e-12, 1e-5)
+        s, st = ctx.run(1)
+        assert s == 0 and st.relres_V <= 1e-12 and st.relres_T <= 1e-12 and st.step == 4
+        with pytest.raises(rafem.RafemError):
+            ctx.set_tol(0.0)
+        with pytest.raises(rafem.RafemError):
+            ctx.set_tol(1e-8, 1.5)
