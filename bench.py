@@ -152,6 +152,15 @@ def alg_bytes_cg64(N: int, nnz: int, iters: float, col_bytes: int) -> float:
     return (iters + 2) * per_iter
 
 
+def alg_bytes_pipecg(N: int, nnz: int, iters: float, col_bytes: int) -> float:
+    """Algorithmic HBM bytes of one FP64 pipelined Jacobi-PCG solve launch (stored format).
+    Per iteration: SpMV n = A m streams (8 + col_bytes) B per nonzero and gathers m once (8N); the fused row
+    epilogue reads m, w, u, z, q, s, p, x, r, dinv and writes z, q, s, p, x, r, u, w and the next m (152N).
+    Start-up (r = b - Ax and u; w = Au and m) and the final true-residual SpMV add three iterations' worth."""
+    per_iter = (8 + col_bytes) * nnz + 160 * N
+    return (iters + 3) * per_iter
+
+
 def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_bytes: int) -> float:
     """Algorithmic HBM bytes of one mixed-precision solve launch (stored format).
     Inner FP32 iteration: SpMV (4 + col_bytes) B per nonzero + 8N (u read, w written); vector phase 12 x 4N.
@@ -276,6 +285,10 @@ def roofline(res, mixed, peaks, peak_kind):
         ref = tr["refine_V"] / steps
         alg = alg_bytes_gmres(N, nnz, iters, ref, cb)
         kern = "k_gmres"
+    elif res.get("solver") == "pipecg":
+        ref = 0.0
+        alg = alg_bytes_pipecg(N, nnz, iters, cb)
+        kern = f"k_pcg64<{code}>"
     elif res.get("solver") == "bicgstab":
         ref = 0.0
         alg = alg_bytes_bicgstab(N, nnz, iters, cb)
@@ -491,6 +504,37 @@ def measure_accuracy(rafem, torch, mesh, args):
     return out
 
 
+def measure_small(rafem, torch, mg, args):
+    """The 48^3-cell workload (117,649 nodes, jitter 10%): its matrices and vectors fit in L2, so a solver
+    iteration is bounded by its grid barriers and latency rather than HBM (no roofline fraction is claimed).
+    FP64 CG, FP64 pipelined CG (one barrier per iteration instead of two) and the mixed path over the same
+    W + K steps."""
+    mesh = mg.workload_48()
+    stream = torch.cuda.Stream()
+    out = {"workload": "48^3 cells, 117,649 nodes, jitter 10%, dt = 1 s, tol 1e-10", "steps": args.small_steps}
+    for name, kw in (("fp64_cg", {}), ("fp64_pipecg", {"solver": rafem.RAFEM_SOLVER_PIPECG}),
+                     ("mixed", {"precision": rafem.RAFEM_PRECISION_MIXED})):
+        ctx = rafem.Context(mesh, stream=stream.cuda_stream, **kw)
+        ctx.run(args.warmup)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s, st = ctx.run(args.small_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        ctx.reset()
+        ctx.run(args.warmup)
+        ctx.set_tracing(True)
+        ctx.run(args.small_steps)
+        tr = ctx.get_trace()
+        ctx.close()
+        out[name] = {"steps_per_s": args.small_steps / (ms * 1e-3), "status": rafem.status_string(s),
+                     "iters_V_per_step": tr["iters_V"] / tr["steps"], "iters_T_per_step": tr["iters_T"] / tr["steps"],
+                     "solve_V_us_per_iter": 1e3 * tr["ms_solve_V"] / max(tr["iters_V"], 1)}
+    return out
+
+
 def measure_monolithic(rafem, torch, mesh, args):
     """The paper's 2N x 2N system shape: V and T of each step solved together by Newton's method (corrector_tol
     1e-6 degC on max |dT|, at most 20 iterations), block-Jacobi BiCGSTAB to 1e-10 per linear solve, on the 127^3
@@ -552,7 +596,7 @@ def main():
     ap.add_argument("--cells", type=int, default=127)
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0 = the timed K steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab", "gmres"], default=None,
+    ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab", "gmres", "pipecg"], default=None,
                     help="run one solver configuration only")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=120, help="steps of the differentiation form (0 = skip)")
@@ -562,6 +606,8 @@ def main():
     ap.add_argument("--numbering-steps", type=int, default=10, help="timed steps per node numbering (0 = skip)")
     ap.add_argument("--monolithic-steps", type=int, default=3, help="timed monolithic Newton steps (0 = skip)")
     ap.add_argument("--fd-elements", type=int, default=32, help="finite-difference checks of the gradient")
+    ap.add_argument("--pipecg-steps", type=int, default=10, help="timed steps with pipelined CG (0 = skip)")
+    ap.add_argument("--small-steps", type=int, default=60, help="timed steps of the 48^3 workload (0 = skip)")
     ap.add_argument("--accuracy-steps", type=int, default=900,
                     help="steps of the tolerance sweep / long-run parity against FP64 (0 = skip)")
     args = ap.parse_args()
@@ -643,7 +689,20 @@ def main():
             r["ctx"].close()
             r["ctx"] = None
         runs["fp64_gmres30"] = r
-    head_name = next(n for n in ("mixed", "fp64", "fp64_ilu0", "fp64_bicgstab", "fp64_gmres30") if n in runs)
+    if args.pipecg_steps > 0 and args.only in (None, "pipecg"):
+        p_args = argparse.Namespace(**vars(args))
+        p_args.steps = args.pipecg_steps
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, p_args, local, dist, want_clocks=False,
+                    solver=rafem.RAFEM_SOLVER_PIPECG)
+        r["solver"] = "pipecg"
+        r["roofline"] = roofline(r, False, peaks, peak_kind)
+        r["steps"] = args.pipecg_steps
+        if args.only != "pipecg":
+            r["ctx"].close()
+            r["ctx"] = None
+        runs["fp64_pipecg"] = r
+    head_name = next(n for n in ("mixed", "fp64", "fp64_ilu0", "fp64_bicgstab", "fp64_gmres30", "fp64_pipecg")
+                     if n in runs)
     head = runs[head_name]
     ctx = head["ctx"]
     N, nnz, n_colors = head["N"], head["nnz"], head["n_colors"]
@@ -717,6 +776,8 @@ def main():
         line["fp64_bicgstab"] = summary(runs["fp64_bicgstab"])
     if "fp64_gmres30" in runs:
         line["fp64_gmres30"] = summary(runs["fp64_gmres30"])
+    if "fp64_pipecg" in runs and head_name != "fp64_pipecg":
+        line["fp64_pipecg"] = summary(runs["fp64_pipecg"])
     if "fp64_ilu0" in runs:
         line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
         line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]
@@ -727,6 +788,11 @@ def main():
             line["batch"] = measure_batch(rafem, torch, mg, args)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
+    if args.small_steps > 0 and args.only in (None, "pipecg"):
+        try:
+            line["small_48"] = measure_small(rafem, torch, mg, args)
+        except Exception as exc:
+            line["small_48"] = {"error": repr(exc)[:300]}
     if args.accuracy_steps > 0 and args.only is None:
         try:
             line["accuracy"] = measure_accuracy(rafem, torch, mesh, args)

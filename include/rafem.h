@@ -67,11 +67,17 @@ extern "C" {
 #define RAFEM_SOLVER_GMRES    2      /* restarted GMRES(m), the paper's iterative method (Sec. III-B): FP64, right
                                         Jacobi, classical Gram-Schmidt with reorthogonalisation, SELL-32 layout,
                                         single instance; m = gmres_restart                                      */
+#define RAFEM_SOLVER_PIPECG   3      /* pipelined Jacobi-PCG (Ghysels-Vanroose): CG's iterates with one grid
+                                        barrier per iteration instead of two, at the cost of 20 vector touches
+                                        instead of 14; for small systems and batches of small instances. FP64,
+                                        Jacobi, symmetric lift; the solve ends with the true residual and
+                                        restarts from x (at most 3 times) while the recurrences have drifted   */
 
 #define RAFEM_PREDICT_PROJECT 4      /* predictor: for the potential, A-orthogonal projection of the new
                                         solution onto the span of its last four solutions (difference basis,
-                                        free rows; one extra pass over the matrix per solve; PCG with the
-                                        symmetric lift); quadratic extrapolation otherwise and for T          */
+                                        free rows; one extra pass over the matrix per solve; needs the
+                                        symmetric lift, any solver); quadratic extrapolation otherwise and for
+                                        T                                                                      */
 
 #define RAFEM_COUPLING_STAGGERED   0 /* V then T per pass (lagged sigma; corrector passes when n_corrector > 1) */
 #define RAFEM_COUPLING_MONOLITHIC  1 /* the paper's 2N x 2N system: V and T of a step solved together by Newton's

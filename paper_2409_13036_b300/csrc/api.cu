@@ -83,7 +83,7 @@ struct rafem_ctx {
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
-    float *fz = nullptr, *fq = nullptr, *fm0 = nullptr, *fm1 = nullptr;
+    double *pz = nullptr, *pq = nullptr, *pm0 = nullptr, *pm1 = nullptr;  // pipelined CG workspace
     int32_t *tile_r0 = nullptr, *tile_r1 = nullptr, *tile_inst = nullptr, *inst_t0 = nullptr, *inst_t1 = nullptr;
     int n_tiles = 0, grid = 0, block = 0, lanes = 8;
     InstState* instV = nullptr;        // [n_inst]
@@ -370,7 +370,7 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.x = x;
     a.r = c->wr; a.u = c->wu; a.w = c->ww; a.p = c->wp; a.s = c->ws; a.dinv = c->wdinv;
     a.r32 = c->fr; a.u32 = c->fu; a.w32 = c->fw; a.p32 = c->fp; a.s32 = c->fs; a.d32 = c->fd; a.dinv32 = c->fdinv;
-    a.z32 = c->fz; a.q32 = c->fq; a.m32a = c->fm0; a.m32b = c->fm1;
+    a.z = c->pz; a.q = c->pq; a.ma = c->pm0; a.mb = c->pm1;
     a.n_tiles = c->n_tiles;
     a.tile_r0 = c->tile_r0;
     a.tile_r1 = c->tile_r1;
@@ -512,7 +512,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         return launch_bicgstab(g, c->bg_grid, c->stream);
     }
     SolveArgs a = make_args(c, which, b, x);
-    return launch_krylov(a, c->lanes, c->prm.precision, c->grid, c->block, c->stream);
+    return launch_krylov(a, c->lanes, c->prm.precision, c->prm.solver == RAFEM_SOLVER_PIPECG, c->grid, c->block,
+                         c->stream);
 }
 
 // Initial guess of a step's solve (the predictor of Sec. II-A's predictor-corrector loop): polynomial
@@ -522,7 +523,7 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
 cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     if (!c->prm.predictor) return cudaSuccess;
     const bool V = which == RAFEM_SYS_V;
-    const bool spd = c->prm.solver == RAFEM_SOLVER_PCG && c->prm.lift == RAFEM_LIFT_SYMMETRIC;
+    const bool spd = c->prm.lift == RAFEM_LIFT_SYMMETRIC;  // the projection needs A SPD, whatever the solver
     if (c->prm.predictor == RAFEM_PREDICT_PROJECT && spd && V) {
         ProjArgs a{};
         a.n_tiles = c->n_tiles;
@@ -1234,11 +1235,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         CK(dalloc(c, &c->fs, N));
         CK(dalloc(c, &c->fd, N));
         CK(dalloc(c, &c->fdinv, N));
-        CK(dalloc(c, &c->fz, N));
-        CK(dalloc(c, &c->fq, N));
-        CK(dalloc(c, &c->fm0, N));
-        CK(dalloc(c, &c->fm1, N));
     }
+    if (prm->solver == RAFEM_SOLVER_PIPECG)
+        for (double** v : {&c->pz, &c->pq, &c->pm0, &c->pm1}) CK(dalloc(c, v, N));
     CK(dalloc(c, &c->stats, 1));
     CK(dalloc(c, &c->scratch, 8));
     CK(dalloc(c, &c->instV, n_inst));
@@ -1331,7 +1330,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     c->el.k = c->e_k;
     // ---- solver schedule: one tile per co-resident block (SELL tiles start on a slice boundary)
     int block = 0;
-    int maxb = krylov_max_blocks(c->lanes, prm->precision, &block);
+    int maxb = krylov_max_blocks(c->lanes, prm->precision, prm->solver == RAFEM_SOLVER_PIPECG, &block);
     if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
     c->block = block;
     c->maxb = maxb;
@@ -1455,7 +1454,12 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         (prm->precision != RAFEM_PRECISION_FP64 ||
          (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL)))
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB && prm->solver != RAFEM_SOLVER_GMRES)
+    if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB && prm->solver != RAFEM_SOLVER_GMRES &&
+        prm->solver != RAFEM_SOLVER_PIPECG)
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->solver == RAFEM_SOLVER_PIPECG &&
+        (prm->precision != RAFEM_PRECISION_FP64 || prm->precond != RAFEM_PRECOND_JACOBI ||
+         prm->coupling != RAFEM_COUPLING_STAGGERED))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->gmres_restart < 0 || prm->gmres_restart > 64) return RAFEM_ERR_BAD_INPUT;
     if ((prm->solver == RAFEM_SOLVER_BICGSTAB || prm->solver == RAFEM_SOLVER_GMRES) &&
@@ -1469,7 +1473,8 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC &&
         (prm->precision != RAFEM_PRECISION_FP64 || (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
         return RAFEM_ERR_BAD_INPUT;
-    if (prm->lift == RAFEM_LIFT_ROW && prm->solver == RAFEM_SOLVER_PCG) return RAFEM_ERR_BAD_INPUT;
+    if (prm->lift == RAFEM_LIFT_ROW && (prm->solver == RAFEM_SOLVER_PCG || prm->solver == RAFEM_SOLVER_PIPECG))
+        return RAFEM_ERR_BAD_INPUT;
     if (prm->assembly != RAFEM_ASSEMBLY_GATHER && prm->assembly != RAFEM_ASSEMBLY_COLOR) return RAFEM_ERR_BAD_INPUT;
     if (prm->arith != RAFEM_ARITH_AUTO && prm->arith != RAFEM_ARITH_FP64 && prm->arith != RAFEM_ARITH_DW)
         return RAFEM_ERR_BAD_INPUT;

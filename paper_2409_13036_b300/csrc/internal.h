@@ -153,7 +153,7 @@ struct SolveArgs {
     double *r, *u, *w, *p, *s, *dinv;
     // FP32 workspace (mixed precision)
     float *r32, *u32, *w32, *p32, *s32, *d32, *dinv32;
-    float *z32, *q32, *m32a, *m32b;  // pipelined inner CG: z = A q, q = M^-1 s, m = M^-1 w (double-buffered)
+    double *z, *q, *ma, *mb;  // pipelined CG: z = A q, q = M^-1 s, m = M^-1 w (double-buffered ma / mb)
     // work tiles: contiguous row ranges, each belonging to one instance
     int n_tiles;
     const int32_t* tile_r0;
@@ -173,8 +173,9 @@ struct SolveArgs {
 
 // Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 4/8/16/32 = CSR with that
 // many lanes per row.
-int krylov_max_blocks(int lanes, int precision, int* block_threads);
-cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st);
+int krylov_max_blocks(int lanes, int precision, bool pipelined, int* block_threads);
+cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, bool pipelined, int grid, int block,
+                          cudaStream_t st);
 
 }  // namespace rafem
 

@@ -812,6 +812,201 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
     }
 }
 
+// ---- FP64 pipelined Jacobi-PCG ---------------------------------------------------------------------------------
+// Ghysels and Vanroose, "Hiding global synchronization latency in the preconditioned Conjugate Gradient
+// algorithm", Parallel Computing 40(7), 2014: the same iterates as CG in exact arithmetic, with the dot products
+// of an iteration computed from vectors that already exist when its SpMV starts. In this persistent kernel that
+// leaves ONE grid barrier per iteration: after it every block reduces (gamma_i, delta_i, rr_i), forms alpha_i and
+// beta_i, and runs n_i = A m_i with every vector update fused into the rows' epilogue:
+//   z = n + beta z,  q = m + beta q,  s = w + beta s,  p = u + beta p,
+//   x += alpha p,  r -= alpha s,  u -= alpha q,  w -= alpha z,  m' = M^-1 w,
+//   partial sums gamma' = (r, u), delta' = (w, u), rr' = (r, r)
+// (n is never stored). m is double-buffered: the SpMV of iteration i gathers m_i from other tiles while rows
+// write m_{i+1}. The recurrences drift further from the true residual than CG's, so a solve ends with the true
+// residual and restarts from the current x (residual replacement) while it misses the target, at most
+// kPipeRestarts times; the recurrence is run to half the target so that a restart, which loses the Krylov
+// space, is rarely needed. It trades one barrier per iteration for 20 vector touches instead of 14: a gain where
+// barriers dominate (small systems, batches of small instances), a loss where the vector streams do.
+constexpr int kPipeRestarts = 3;
+
+// w = A u at start-up; m = M^-1 w, partials gamma = (r, u), delta = (w, u), rr = (r, r)
+struct EmPipeInit {
+    const SolveArgs& a;
+    double* m;
+    double* v;
+    __device__ __forceinline__ double pre(int row) const { return ldcg(a.u + row); }
+    __device__ __forceinline__ void fin(int row, double wi, double ui) const {
+        const double ri = ldcg(a.r + row);
+        a.w[row] = wi;
+        m[row] = ldcg(a.dinv + row) * wi;
+        v[0] = fma(ri, ui, v[0]);
+        v[1] = fma(wi, ui, v[1]);
+        v[2] = fma(ri, ri, v[2]);
+    }
+};
+
+// one pipelined iteration's row epilogue (see above); n = (A m_in)_row
+struct EmPipe {
+    const SolveArgs& a;
+    const double* m_in;
+    double* m_out;
+    double alpha, beta;
+    bool first;
+    double* v;
+    __device__ __forceinline__ double pre(int row) const { return ldcg(m_in + row); }
+    __device__ __forceinline__ void fin(int row, double n, double mi) const {
+        const double wi = ldcg(a.w + row), ui = ldcg(a.u + row);
+        double zi, qi, si, pi;
+        if (first) {
+            zi = n;
+            qi = mi;
+            si = wi;
+            pi = ui;
+        } else {
+            zi = fma(beta, ldcg(a.z + row), n);
+            qi = fma(beta, ldcg(a.q + row), mi);
+            si = fma(beta, ldcg(a.s + row), wi);
+            pi = fma(beta, ldcg(a.p + row), ui);
+        }
+        const double xi = fma(alpha, pi, ldcg(a.x + row));
+        const double ri = fma(-alpha, si, ldcg(a.r + row));
+        const double un = fma(-alpha, qi, ui);
+        const double wn = fma(-alpha, zi, wi);
+        a.z[row] = zi;
+        a.q[row] = qi;
+        a.s[row] = si;
+        a.p[row] = pi;
+        a.x[row] = xi;
+        a.r[row] = ri;
+        a.u[row] = un;
+        a.w[row] = wn;
+        m_out[row] = ldcg(a.dinv + row) * wn;
+        v[0] = fma(ri, un, v[0]);
+        v[1] = fma(wn, un, v[1]);
+        v[2] = fma(ri, ri, v[2]);
+    }
+};
+
+template <int L>
+__global__ void __launch_bounds__(kBlock, 1) k_pcg64(SolveArgs a) {
+    RAFEM_RING_SETUP(L)
+    __shared__ double sm[kSumMax * kBlock];
+    __shared__ InstState sst[kMaxInst];
+    init_shared_state(a, sst);
+    const int nt = a.n_tiles;
+    const double tol2 = a.tol * a.tol;
+    const double rec2 = 0.25 * tol2;  // recurrence target: half the tolerance
+    unsigned target = 0;
+    bool ok = true;
+    int n_active = a.n_inst;
+    for (int restart = 0; n_active > 0; ++restart) {
+        // init 1: r = b - A x, dinv, bb; u = dinv r (row-local, same block)
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            if (!sst[a.tile_inst[t]].active) continue;
+            const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
+            double v[1] = {0.0};
+            ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmInitResidual{a, v}) && ok;
+            block_sum<1>(v, sm);
+            if (threadIdx.x == 0) a.partial[(size_t)Q_BB * nt + t] = v[0];
+            for (int i = r0 + threadIdx.x; i < r1; i += kBlock) a.u[i] = ldcg(a.dinv + i) * ldcg(a.r + i);
+        }
+        if (grid_wait(a, target) || !ok) return;
+        // init 2: w = A u, m_0, gamma, delta, rr
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            if (!sst[a.tile_inst[t]].active) continue;
+            const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
+            double v[3] = {0.0, 0.0, 0.0};
+            ok = spmv_tile<L, double, double>(a, ring, a.A, a.u, r0, r1, EmPipeInit{a, a.ma, v}) && ok;
+            double v2[2] = {v[0], v[1]}, v1[1] = {v[2]};
+            block_sum<2>(v2, sm);
+            block_sum<1>(v1, sm);
+            if (threadIdx.x == 0) {
+                a.partial[(size_t)Q_GAMMA * nt + t] = v2[0];
+                a.partial[(size_t)Q_DELTA * nt + t] = v2[1];
+                a.partial[(size_t)Q_RR * nt + t] = v1[0];
+            }
+        }
+        if (grid_wait(a, target) || !ok) return;
+        n_active = reduce_shared<4>(a, sst, [&](int, const double* s, InstState& st) {
+            st.bb = s[Q_BB];
+            st.first = 1;
+            cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], rec2, a.max_iter, false);
+        });
+        int parity = 0;
+        while (n_active > 0) {
+            const double* m_in = parity ? a.mb : a.ma;
+            double* m_out = parity ? a.ma : a.mb;
+            for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+                const InstState& st = sst[a.tile_inst[t]];
+                if (!st.active) continue;
+                const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
+                double v[3] = {0.0, 0.0, 0.0};
+                ok = spmv_tile<L, double, double>(
+                         a, ring, a.A, m_in, r0, r1,
+                         EmPipe{a, m_in, m_out, st.alpha, st.beta, st.first != 0, v}) &&
+                     ok;
+                double v2[2] = {v[0], v[1]}, v1[1] = {v[2]};
+                block_sum<2>(v2, sm);
+                block_sum<1>(v1, sm);
+                if (threadIdx.x == 0) {
+                    a.partial[(size_t)Q_GAMMA * nt + t] = v2[0];
+                    a.partial[(size_t)Q_DELTA * nt + t] = v2[1];
+                    a.partial[(size_t)Q_RR * nt + t] = v1[0];
+                }
+            }
+            parity ^= 1;
+            if (grid_wait(a, target) || !ok) return;
+            n_active = reduce_shared<3>(a, sst, [&](int, const double* s, InstState& st) {
+                st.first = 0;
+                cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], rec2, a.max_iter, true);
+            });
+        }
+        // true residual ||b - A x|| of every instance; those that converged by their recurrence but miss the
+        // target start again from x (residual replacement)
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
+            double v[1] = {0.0};
+            ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmTrueResidual{a.b, v}) && ok;
+            block_sum<1>(v, sm);
+            if (threadIdx.x == 0) a.partial[(size_t)Q_RR64 * nt + t] = v[0];
+        }
+        if (grid_wait(a, target) || !ok) return;
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            __shared__ int s_restart;
+            if (threadIdx.x == 0) s_restart = 0;
+            __syncthreads();
+            for (int i = warp; i < a.n_inst; i += kWarps) {
+                double v = 0.0;
+                for (int t = a.inst_t0[i] + lane; t < a.inst_t1[i]; t += 32)
+                    v += ldcg(a.partial + (size_t)Q_RR64 * nt + t);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    InstState& st = sst[i];
+                    const double bb = st.bb > 0.0 ? st.bb : 1.0;
+                    st.relres = sqrt(v / bb);
+                    if (!isfinite(v)) {
+                        if (st.status >= 0) st.status = RAFEM_ERR_NONFINITE;
+                    } else if (st.status == RAFEM_OK && v > tol2 * bb) {
+                        if (restart < kPipeRestarts && st.iters < a.max_iter) {
+                            st.active = 1;
+                            st.status = 0;
+                            atomicAdd(&s_restart, 1);
+                        } else {
+                            st.status = RAFEM_NOT_CONVERGED;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            n_active = s_restart;
+            __syncthreads();
+        }
+    }
+    publish_state(a, sst);
+}
+
 // ---- mixed precision: FP32 Chronopoulos-Gear inner iterations, FP64 residual refinement ---------------------
 // Each instance runs a state machine over rounds of [phase A, barrier, phase B, barrier + reduce]:
 //   OUTER: A: x64 += d32 (after an inner solve)   B: r64 = b - A64 x64 (FP64 SpMV), r32 = (float) r64, d32 = 0,
@@ -1016,18 +1211,19 @@ __global__ void k_reset(InstState* inst, int n_inst, GridBarrier* bar) {
 }
 
 template <int L>
-void* kernel_ptr(int precision) {
+void* kernel_ptr(int precision, bool pipelined) {
+    if (pipelined) return precision == RAFEM_PRECISION_FP64 ? (void*)k_pcg64<L> : nullptr;
     return precision == RAFEM_PRECISION_MIXED ? (void*)k_cg_mixed<L> : (void*)k_cg64<L>;
 }
 
-void* select_kernel(int lanes, int precision) {
+void* select_kernel(int lanes, int precision, bool pipelined) {
     switch (lanes) {
-        case 1: return kernel_ptr<1>(precision);
-        case 2: return kernel_ptr<2>(precision);
-        case 4: return kernel_ptr<4>(precision);
-        case 8: return kernel_ptr<8>(precision);
-        case 16: return kernel_ptr<16>(precision);
-        case 32: return kernel_ptr<32>(precision);
+        case 1: return kernel_ptr<1>(precision, pipelined);
+        case 2: return kernel_ptr<2>(precision, pipelined);
+        case 4: return kernel_ptr<4>(precision, pipelined);
+        case 8: return kernel_ptr<8>(precision, pipelined);
+        case 16: return kernel_ptr<16>(precision, pipelined);
+        case 32: return kernel_ptr<32>(precision, pipelined);
         default: return nullptr;
     }
 }
@@ -1037,8 +1233,8 @@ void* select_kernel(int lanes, int precision) {
 // Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32, none for CSR.
 static int dyn_smem(int lanes) { return lanes <= 2 ? kRingBytes : 0; }
 
-int krylov_max_blocks(int lanes, int precision, int* block_threads) {
-    void* k = select_kernel(lanes, precision);
+int krylov_max_blocks(int lanes, int precision, bool pipelined, int* block_threads) {
+    void* k = select_kernel(lanes, precision, pipelined);
     if (!k) return 0;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -1050,8 +1246,9 @@ int krylov_max_blocks(int lanes, int precision, int* block_threads) {
     return per_sm * sms;
 }
 
-cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, int grid, int block, cudaStream_t st) {
-    void* k = select_kernel(lanes, precision);
+cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, bool pipelined, int grid, int block,
+                          cudaStream_t st) {
+    void* k = select_kernel(lanes, precision, pipelined);
     if (!k) return cudaErrorInvalidValue;
     k_reset<<<(a.n_inst + 255) / 256, 256, 0, st>>>(a.inst, a.n_inst, a.bar);
     cudaError_t e = cudaGetLastError();

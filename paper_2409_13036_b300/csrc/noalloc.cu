@@ -145,7 +145,7 @@ extern "C" int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, con
     Carve c = carve(base);
 
     int block = 0;
-    const int maxb = krylov_max_blocks(kLanes, RAFEM_PRECISION_FP64, &block);
+    const int maxb = krylov_max_blocks(kLanes, RAFEM_PRECISION_FP64, false, &block);
     if (maxb <= 0) return RAFEM_ERR_CUDA;
     const int rows_per_tile = (n_rows + maxb - 1) / maxb;
     const int n_tiles = (n_rows + rows_per_tile - 1) / rows_per_tile;
@@ -190,7 +190,7 @@ extern "C" int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, con
     a.tol = tol;
     a.max_iter = max_iter;
     a.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
-    if ((e = launch_krylov(a, kLanes, RAFEM_PRECISION_FP64, std::min(n_tiles, maxb), block, st)) != cudaSuccess)
+    if ((e = launch_krylov(a, kLanes, RAFEM_PRECISION_FP64, false, std::min(n_tiles, maxb), block, st)) != cudaSuccess)
         return to_status(e);
     InstState s;
     GridBarrier g;

@@ -37,6 +37,7 @@ RAFEM_PRECISION_MIXED = 1
 RAFEM_SOLVER_PCG = 0
 RAFEM_SOLVER_BICGSTAB = 1
 RAFEM_SOLVER_GMRES = 2
+RAFEM_SOLVER_PIPECG = 3
 RAFEM_PREDICT_PROJECT = 4
 RAFEM_COUPLING_STAGGERED = 0
 RAFEM_COUPLING_MONOLITHIC = 1
