@@ -1077,9 +1077,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
     unsigned target = 0;
     bool ok = true;
 
-    // init: dinv32 from the FP32 diagonal (row-local; read again only by the same block after a barrier)
-    for (int t = blockIdx.x; t < nt; t += gridDim.x)
-        for (int i = a.tile_r0[t] + threadIdx.x; i < a.tile_r1[t]; i += kBlock) a.dinv32[i] = 1.0f / a.A32[a.diag[i]];
+    // init: dinv32 from the FP32 diagonal (row-local; read again only by the same block after a barrier). The
+    // rows of a thread are taken eight at a time so that their slot and diagonal loads overlap.
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int r1 = a.tile_r1[t];
+        for (int i0 = a.tile_r0[t] + threadIdx.x; i0 < r1; i0 += 8 * kBlock) {
+            int slot[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) slot[k] = i0 + k * kBlock < r1 ? __ldg(a.diag + i0 + k * kBlock) : -1;
+            float dv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dv[k] = slot[k] >= 0 ? __ldcg(a.A32 + slot[k]) : 1.0f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (slot[k] >= 0) a.dinv32[i0 + k * kBlock] = 1.0f / dv[k];
+        }
+    }
     __syncthreads();
     bool first_round = true;
     int n_active = a.n_inst;
