@@ -824,8 +824,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
 // (n is never stored). m is double-buffered: the SpMV of iteration i gathers m_i from other tiles while rows
 // write m_{i+1}. The recurrences drift further from the true residual than CG's, so a solve ends with the true
 // residual and restarts from the current x (residual replacement) while it misses the target, at most
-// kPipeRestarts times; the recurrence is run to half the target so that a restart, which loses the Krylov
-// space, is rarely needed. It trades one barrier per iteration for 20 vector touches instead of 14: a gain where
+// kPipeRestarts times. It trades one barrier per iteration for 20 vector touches instead of 14: a gain where
 // barriers dominate (small systems, batches of small instances), a loss where the vector streams do.
 constexpr int kPipeRestarts = 3;
 
@@ -895,7 +894,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg64(SolveArgs a) {
     init_shared_state(a, sst);
     const int nt = a.n_tiles;
     const double tol2 = a.tol * a.tol;
-    const double rec2 = 0.25 * tol2;  // recurrence target: half the tolerance
     unsigned target = 0;
     bool ok = true;
     int n_active = a.n_inst;
@@ -930,7 +928,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg64(SolveArgs a) {
         n_active = reduce_shared<4>(a, sst, [&](int, const double* s, InstState& st) {
             st.bb = s[Q_BB];
             st.first = 1;
-            cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], rec2, a.max_iter, false);
+            cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, false);
         });
         int parity = 0;
         while (n_active > 0) {
@@ -958,7 +956,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg64(SolveArgs a) {
             if (grid_wait(a, target) || !ok) return;
             n_active = reduce_shared<3>(a, sst, [&](int, const double* s, InstState& st) {
                 st.first = 0;
-                cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], rec2, a.max_iter, true);
+                cg_update(st, s[Q_GAMMA], s[Q_RR], s[Q_DELTA], tol2, a.max_iter, true);
             });
         }
         // true residual ||b - A x|| of every instance; those that converged by their recurrence but miss the
