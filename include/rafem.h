@@ -74,10 +74,10 @@ extern "C" {
                                         restarts from x (at most 3 times) while the recurrences have drifted   */
 
 #define RAFEM_PREDICT_PROJECT 4      /* predictor: for the potential, A-orthogonal projection of the new
-                                        solution onto the span of its last four solutions (difference basis,
-                                        free rows; one extra pass over the matrix per solve; needs the
-                                        symmetric lift, any solver); quadratic extrapolation otherwise and for
-                                        T                                                                      */
+                                        solution onto the span of its last proj_basis (default 4) solutions
+                                        (difference basis, free rows; one extra pass over the matrix per
+                                        solve; needs the symmetric lift, any solver); quadratic extrapolation
+                                        otherwise and for T                                                    */
 
 #define RAFEM_COUPLING_STAGGERED   0 /* V then T per pass (lagged sigma; corrector passes when n_corrector > 1) */
 #define RAFEM_COUPLING_MONOLITHIC  1 /* the paper's 2N x 2N system: V and T of a step solved together by Newton's
@@ -151,6 +151,7 @@ typedef struct rafem_params {
     int32_t gmres_restart;           /* GMRES restart length m, 1..64 (0 = 30)                                  */
     int32_t coupling;                /* RAFEM_COUPLING_STAGGERED (0) or RAFEM_COUPLING_MONOLITHIC               */
     int32_t arith;                   /* RAFEM_ARITH_AUTO (0), RAFEM_ARITH_FP64 or RAFEM_ARITH_DW                 */
+    int32_t proj_basis;              /* RAFEM_PREDICT_PROJECT: solutions in the basis, 1..8 (0 = 4)             */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */

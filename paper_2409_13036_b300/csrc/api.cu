@@ -74,12 +74,13 @@ struct rafem_ctx {
     double *V_hist = nullptr, *T_hist = nullptr;   // predictor history (x^{n-1})
     double *V_hist2 = nullptr, *T_hist2 = nullptr; // predictor history (x^{n-2}), quadratic and cubic predictors
     double *V_hist3 = nullptr, *T_hist3 = nullptr; // predictor history (x^{n-3}), cubic predictor and projection
-    double* proj_partial = nullptr;                // [14][n_tiles * proj_sub] projection sums
+    double* proj_partial = nullptr;                // [kProjQ][n_tiles * proj_sub] projection sums
     int proj_sub = 1;
-    double* proj_coef = nullptr;                   // [4 n_inst]
+    double* proj_coef = nullptr;                   // [kProjMax n_inst]
+    int proj_k = kProjDefault;                     // basis size limit
     int32_t *proj_kin = nullptr, *proj_kout = nullptr;
-    double* proj_D = nullptr;                      // [N][4] projection basis
-    double* proj_Y = nullptr;                      // [N][4] A times the basis (double-word passes)
+    double* proj_D = nullptr;                      // [N][proj_stride(proj_k)] projection basis (its history)
+    double* proj_Y = nullptr;                      // [N][proj_stride(proj_k)] A times the basis
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -543,9 +544,7 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
         a.bc = V ? c->bcV : c->bcT;
         a.b = V ? c->bV : c->bT;
         a.x = V ? c->V : c->T;
-        a.h1 = V ? c->V_hist : c->T_hist;
-        a.h2 = V ? c->V_hist2 : c->T_hist2;
-        a.h3 = V ? c->V_hist3 : c->T_hist3;
+        a.kmax = c->proj_k;
         a.partial = c->proj_partial;
         a.coef = c->proj_coef;
         a.kin = c->proj_kin;
@@ -859,7 +858,8 @@ cudaError_t launch_step(rafem_ctx* c) {
 // ---- checkpoints of the differentiation tape: T, V and their predictor histories (8 x N doubles), StatsDev,
 // istats
 size_t state_bytes(const rafem_ctx* c) {
-    return 8 * (size_t)c->N * sizeof(double) + sizeof(StatsDev) + (size_t)c->n_inst * sizeof(rafem_step_stats);
+    const size_t fields = 8 + (c->proj_D ? proj_stride(c->proj_k) : 0);
+    return fields * (size_t)c->N * sizeof(double) + sizeof(StatsDev) + (size_t)c->n_inst * sizeof(rafem_step_stats);
 }
 
 cudaError_t state_copy(rafem_ctx* c, void* buf, bool save) {
@@ -873,6 +873,13 @@ cudaError_t state_copy(rafem_ctx* c, void* buf, bool save) {
         if (e != cudaSuccess) return e;
     }
     p += 8 * nb;
+    if (c->proj_D) {  // the projection predictor's history: the previous call's basis
+        const size_t rb = (size_t)proj_stride(c->proj_k) * nb;
+        e = save ? cudaMemcpyAsync(p, c->proj_D, rb, cudaMemcpyDeviceToDevice, c->stream)
+                 : cudaMemcpyAsync(c->proj_D, p, rb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+        p += rb;
+    }
     e = save ? cudaMemcpyAsync(p, c->stats, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream)
              : cudaMemcpyAsync(c->stats, p, sizeof(StatsDev), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
@@ -1011,7 +1018,7 @@ static int build_tiles(rafem_ctx* c, int rows_per_tile) {
     int max_rows = 1;
     for (int t = 0; t < nt; ++t) max_rows = std::max(max_rows, t1[t] - t0[t]);
     c->proj_sub = (max_rows + kProjChunk - 1) / kProjChunk;
-    CK(talloc(&c->proj_partial, (size_t)14 * nt * c->proj_sub));
+    CK(talloc(&c->proj_partial, (size_t)kProjQ * nt * c->proj_sub));
     CK(cudaMemcpyAsync(c->tile_r0, t0.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->tile_r1, t1.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->tile_inst, ti.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -1246,12 +1253,15 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     CK(dalloc(c, &c->bar, 1));
     CK(dalloc(c, &c->e_order, E));
     CK(dalloc(c, &c->corr, 1));
-    CK(dalloc(c, &c->proj_coef, 4 * (size_t)n_inst));
+    CK(dalloc(c, &c->proj_coef, (size_t)kProjMax * n_inst));
     CK(dalloc(c, &c->proj_kin, n_inst));
     CK(dalloc(c, &c->proj_kout, n_inst));
     if (prm->predictor == RAFEM_PREDICT_PROJECT) {
-        CK(dalloc(c, &c->proj_D, 4 * (size_t)N + 4));
-        if (c->dw) CK(dalloc(c, &c->proj_Y, 4 * (size_t)N + 4));
+        c->proj_k = prm->proj_basis > 0 ? prm->proj_basis : kProjDefault;
+        const size_t nd = (size_t)proj_stride(c->proj_k) * N;
+        CK(dalloc(c, &c->proj_D, nd + 8));
+        CK(dalloc(c, &c->proj_Y, nd + 8));
+        CK(cudaMemsetAsync(c->proj_D, 0, nd * sizeof(double), c->stream));
     }
     CK(dalloc(c, &c->V_old, N));
     CK(dalloc(c, &c->stats_save, 1));
@@ -1468,6 +1478,7 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift != RAFEM_LIFT_SYMMETRIC && prm->lift != RAFEM_LIFT_ROW) return RAFEM_ERR_BAD_INPUT;
     if (prm->predictor < 0 || prm->predictor > RAFEM_PREDICT_PROJECT) return RAFEM_ERR_BAD_INPUT;
+    if (prm->proj_basis < 0 || prm->proj_basis > kProjMax) return RAFEM_ERR_BAD_INPUT;
     if (prm->coupling != RAFEM_COUPLING_STAGGERED && prm->coupling != RAFEM_COUPLING_MONOLITHIC)
         return RAFEM_ERR_BAD_INPUT;
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC &&
@@ -1725,6 +1736,7 @@ int rafem_reset(rafem_ctx* c) {
     CK(cudaGetLastError());
     for (double* h : {c->T_hist, c->V_hist, c->T_hist2, c->V_hist2, c->T_hist3, c->V_hist3})
         CK(cudaMemsetAsync(h, 0, N * sizeof(double), c->stream));
+    if (c->proj_D) CK(cudaMemsetAsync(c->proj_D, 0, (size_t)proj_stride(c->proj_k) * N * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->istats, 0, c->n_inst * sizeof(rafem_step_stats), c->stream));
     CK(cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream));
     c->step = 0;

@@ -316,6 +316,12 @@ namespace rafem {
 // Initial guess by A-orthogonal projection onto the last solutions (project.cu).
 // ------------------------------------------------------------------------------------------------------------
 constexpr int kProjChunk = 1024;  // rows per block of the projection passes
+constexpr int kProjMax = 8;                                       // solutions in the basis, at most
+constexpr int kProjDefault = 4;  // default: the best time to solution over a whole run (larger bases cost more
+                                 // per step than they save once the solves take a few iterations)
+constexpr int kProjQ = kProjMax * (kProjMax + 1) / 2 + kProjMax;  // Gram entries + right-hand sides, at most
+// Entries per node of the basis arrays for a limit of k solutions (even, so that pairs load as 16 bytes).
+inline int proj_stride(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : (k <= 6 ? 6 : 8)); }
 
 struct ProjArgs {
     int n_tiles;
@@ -334,13 +340,14 @@ struct ProjArgs {
     const uint8_t* bc;               // Dirichlet rows
     const double* b;
     double* x;                       // x_n in, initial guess out
-    double *h1, *h2, *h3;            // x_{n-1}, x_{n-2}, x_{n-3} (shifted)
-    double* D;                       // [N][4] basis (32-byte aligned)
-    double* Y;                       // [N][4] A D (double-word passes only)
-    double* partial;                 // [14][n_tiles * n_sub]
-    double* coef;                    // [4 n_inst]
+    int kmax;                        // basis size limit (1..kProjMax)
+    double* D;                       // [N][proj_stride(kmax)] basis, 8-byte entries (FP64 or float pairs); the
+                                     // previous call's basis on entry (the predictor's history)
+    double* Y;                       // [N][proj_stride(kmax)] A D
+    double* partial;                 // [kProjQ][n_tiles * n_sub]
+    double* coef;                    // [kProjMax n_inst]
     int32_t *kin, *kout;             // [n_inst] solutions available / basis size used
-    int dw;                          // 1: double-word passes (D and partial hold float pairs)
+    int dw;                          // 1: double-word passes (D, Y and partial hold float pairs)
 };
 // hist: steps completed (device); lag: 1 when the initial field is not a solution (potential), 0 otherwise.
 cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);

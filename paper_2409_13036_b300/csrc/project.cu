@@ -1,22 +1,30 @@
 // Initial guess by projection onto the recent solutions (an extension of the predictor step of the main loop,
 // Sec. II-A: the solution is extrapolated in time before the corrector solves).
 //
-// With x_n, x_{n-1}, ... the last k solutions (k <= 4) of an SPD system A x = b whose matrix changed since, the
-// guess is the A-orthogonal projection of the new solution onto their span:
+// With x_n, x_{n-1}, ... the last k solutions (k <= kProjMax) of an SPD system A x = b whose matrix changed since,
+// the guess is the A-orthogonal projection of the new solution onto their span:
 //     x_0 = D c,   (D^T A D) c = D^T b,
-// with D the difference basis d_0 = x_n, d_1 = x_n - x_{n-1}, d_2 = x_n - 2 x_{n-1} + x_{n-2}, d_3 = third
-// difference (the same span, much better conditioned than the raw solutions). This minimises the A-norm error
-// over the span, which contains every polynomial extrapolation of the same solutions, so the Krylov solve starts
-// closer than with the polynomial predictor. Sums run over free rows only (the symmetric lift makes A block
-// diagonal with identity Dirichlet rows), and Dirichlet entries are set to their prescribed values.
+// with D the difference basis d_0 = x_n, d_1 = x_n - x_{n-1}, d_j = the j-th backward difference (the same span,
+// much better conditioned than the raw solutions). This minimises the A-norm error over the span, which contains
+// every polynomial extrapolation of the same solutions, so the Krylov solve starts closer than with the
+// polynomial predictor. Sums run over free rows only (the symmetric lift makes A block diagonal with identity
+// Dirichlet rows), and Dirichlet entries are set to their prescribed values.
 //
-// Four launches per solve, per problem instance of a batch (the solver's work tiles never straddle instances):
-//   k_proj_basis:   the basis D at every node, interleaved (one 32-byte sector per node);
-//   k_proj_gram:    one pass over A (SELL-32 or CSR) computing A d_i (four FMAs per stored entry: on B300 this
-//                   pass is bound by the FP64 pipe), and per chunk the partial sums of G = D^T A D and D^T b;
+// No past solution is stored: the backward differences obey d_j(n) = d_{j-1}(n) - d_{j-1}(n-1), so each call
+// builds its basis from the current solution and the previous call's basis, which stays in memory (and in the
+// differentiation form's checkpoints) as the predictor's history: K - 1 subtractions per node.
+//
+// Launches per solve, per problem instance of a batch (the solver's work tiles never straddle instances), all
+// compiled for the context's basis limit K (2, 4, 6 or 8):
+//   k_proj_count:   one thread: the basis size of every instance;
+//   k_proj_basis:   the basis D at every node from the solution and the previous basis (K 8-byte entries each);
+//   k_proj_apply:   Y = A D, one pass over A (SELL-32 or CSR), entries in batches;
+//   k_proj_gram:    per chunk of rows the partial sums of G = D^T Y and D^T b; with many quantities (K = 6, 8)
+//                   two or four warps share a row set, each accumulating a share of them;
 //   k_proj_solve:   per instance, G scaled to unit diagonal and factorised by Cholesky (the basis shrinks while a
 //                   pivot is not positive), c solved;
-//   k_proj_combine: x = D c on free rows, history shifted (x_{n-3} <- x_{n-2} <- x_{n-1} <- x_n).
+//   k_proj_combine: x = D c on free rows.
+// Every pass runs in FP64 or in double-word arithmetic (dw.cuh), as the assembly does; the Cholesky is FP64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,37 +37,89 @@ namespace rafem {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kQ = 14;  // 10 entries of the symmetric 4 x 4 Gram matrix + 4 right-hand sides
-constexpr int kChunk = kProjChunk;  // rows per block: tiles are split so that the pass has enough parallelism
-constexpr int kBatch = 5;  // interior rows of the Kuhn lattice have 15 entries
+constexpr int kChunk = kProjChunk;  // rows per block: tiles are split so that the passes have enough parallelism
 constexpr int kSolveThreads = 256;
-constexpr int kBatchApply = 3;  // double-word apply: fewer live registers, four blocks per SM
 
-__device__ __forceinline__ int tri(int i, int l) { return i <= l ? l * (l + 1) / 2 + i : i * (i + 1) / 2 + l; }
+// Quantities of a basis of K: the Gram entries G[i][l] (i <= l) at l (l + 1) / 2 + i, then (D^T b)[l].
+template <int K>
+struct Basis {
+    static constexpr int kGram = K * (K + 1) / 2;
+    static constexpr int kQ = kGram + K;
+    static constexpr int kGroups = kQ <= 16 ? 1 : (kQ <= 32 ? 2 : 4);  // warps sharing a row set in the Gram pass
+    static constexpr int kPerGroup = (kQ + kGroups - 1) / kGroups;
+    static_assert(kPerGroup <= 16, "warp_sum16 reduces at most 16 quantities per thread");
+    static_assert(K % 2 == 0 && K <= kProjMax, "even basis sizes up to kProjMax");
+};
 
-// Arithmetic of the sums: FP64, or double-word (dw.cuh: float pairs on the FP32 pipes, stored as float2).
+// Arithmetic of the passes: FP64, or double-word (float pairs on the FP32 pipes, stored as float2).
 struct ArithF64 {
     using T = double;
-    using S = double;  // storage
+    using S = double;  // 8-byte storage
     __device__ static T zero() { return 0.0; }
+    __device__ static T from(double x) { return x; }
+    __device__ static double value(T v) { return v; }
     __device__ static T add(T x, T y) { return x + y; }
+    __device__ static T sub(T x, T y) { return x - y; }
+    __device__ static void dot(T& acc, T x, T y) { acc = fma(x, y, acc); }
+    __device__ static T finish(T v) { return v; }
     __device__ static T shfl(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     __device__ static T load(const S* p) { return *p; }
     __device__ static void store(S* p, T v) { *p = v; }
-    __device__ static double value(T v) { return v; }
+    // two consecutive entries as one 16-byte access
+    __device__ static void ldg2(const S* p, T& a, T& b) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void ld2(const S* p, T& a, T& b) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void st2(S* p, T a, T b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
 };
 struct ArithDW {
     using T = dw::df;
     using S = float2;
     __device__ static T zero() { return dw::make(0.0f); }
+    __device__ static T from(double x) { return dw::split(x); }
+    __device__ static double value(T v) { return dw::to_double(v); }
     __device__ static T add(T x, T y) { return dw::add(x, y); }
+    __device__ static T sub(T x, T y) { return dw::sub(x, y); }
+    __device__ static void dot(T& acc, T x, T y) { dw::dot_acc(acc, x, y); }
+    __device__ static T finish(T v) { return dw::finish(v); }
     __device__ static T shfl(T v, int o) {
         return {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
     }
     __device__ static T load(const S* p) { return dw::load(p); }
     __device__ static void store(S* p, T v) { dw::store(p, v); }
-    __device__ static double value(T v) { return dw::to_double(v); }
+    __device__ static void ldg2(const S* p, T& a, T& b) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        a = dw::make(v.x, v.y);
+        b = dw::make(v.z, v.w);
+    }
+    __device__ static void ld2(const S* p, T& a, T& b) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = dw::make(v.x, v.y);
+        b = dw::make(v.z, v.w);
+    }
+    __device__ static void st2(S* p, T a, T b) { *reinterpret_cast<float4*>(p) = make_float4(a.h, a.l, b.h, b.l); }
 };
+
+// Quantity q of a basis of K: (i, l) of G[i][l], or i = -1 and l for (D^T b)[l].
+template <int K>
+__host__ __device__ constexpr int q_col(int q) {
+    if (q >= Basis<K>::kGram) return q - Basis<K>::kGram;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= q) ++l;
+    return l;
+}
+template <int K>
+__host__ __device__ constexpr int q_row(int q) {
+    return q >= Basis<K>::kGram ? -1 : q - q_col<K>(q) * (q_col<K>(q) + 1) / 2;
+}
+
+__device__ __forceinline__ int tri(int i, int l) { return i <= l ? l * (l + 1) / 2 + i : i * (i + 1) / 2 + l; }
 
 // Sums 16 values over the warp by recursive halving: at each of the offsets 16, 8, 4, 2 a lane keeps one half of
 // its values and adds the partner's copy of that half, so 16 shuffles replace the 80 of one butterfly per value.
@@ -81,19 +141,6 @@ __device__ __forceinline__ typename Ar::T warp_sum16(typename Ar::T (&v)[16]) {
     return Ar::add(v[0], Ar::shfl(v[0], 1));
 }
 
-// difference basis at node j from x_n and the history (components i >= k are zero)
-__device__ __forceinline__ void basis(const double* x, const double* h1, const double* h2, const double* h3, int k,
-                                      int j, double (&d)[4]) {
-    const double a = x[j];
-    const double b = k > 1 ? h1[j] : 0.0;
-    const double c = k > 2 ? h2[j] : 0.0;
-    const double e = k > 3 ? h3[j] : 0.0;
-    d[0] = a;
-    d[1] = k > 1 ? a - b : 0.0;
-    d[2] = k > 2 ? a - 2.0 * b + c : 0.0;
-    d[3] = k > 3 ? a - 3.0 * b + 3.0 * c - e : 0.0;
-}
-
 // Rows of chunk c: chunk c = (tile c / n_sub, part c % n_sub), kChunk rows each (fewer at the tile's end).
 __device__ __forceinline__ void chunk_rows(const ProjArgs& a, int c, int& t, int& r0, int& r1) {
     t = c / a.n_sub;
@@ -102,237 +149,62 @@ __device__ __forceinline__ void chunk_rows(const ProjArgs& a, int c, int& t, int
     r1 = min(r0 + kChunk, a.tile_r1[t]);
 }
 
-// One block per chunk: the basis D at the chunk's nodes, interleaved [node][4] (32 bytes, one sector per node), so
-// the gathers of the next pass need no arithmetic.
+// One thread: the basis size of every instance, min(kmax, hist - lag) with hist the steps completed since the last
+// state reset.
+__global__ void k_proj_count(ProjArgs a, const int32_t* hist, int lag) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int s = *hist - lag;
+    const int k = s < 0 ? 0 : (s > a.kmax ? a.kmax : s);
+    for (int i = 0; i < a.n_inst; ++i) a.kin[i] = k;
+}
+
+// D at the chunk's nodes from the solution and the previous call's basis: d_0 = x, d_j = d_{j-1} - d_{j-1}(old)
+// (entries j >= k are 0). In place: every old entry of the row is read before any is written.
+template <class Ar, int K>
 __global__ void __launch_bounds__(kThreads) k_proj_basis(ProjArgs a) {
-    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
-        int t, r0, r1;
-        chunk_rows(a, ch, t, r0, r1);
-        const int k = a.kin[a.tile_inst[t]];
-        for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-            double d[4];
-            basis(a.x, a.h1, a.h2, a.h3, k, row, d);
-            reinterpret_cast<double4*>(a.D)[row] = make_double4(d[0], d[1], d[2], d[3]);
-        }
-    }
-}
-
-// One block per chunk of a tile: A d_i for the chunk's rows, then its partial sums of G and D^T b over free rows.
-__global__ void __launch_bounds__(kThreads, 3) k_proj_gram(ProjArgs a) {
-    __shared__ double red[kQ][kThreads / 32];
-    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
-        int t, r0, r1;
-        chunk_rows(a, ch, t, r0, r1);
-        const int inst = a.tile_inst[t];
-        const int k = a.kin[inst];
-        double acc[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-        if (k > 0) {
-            for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-                if (a.bc[row]) continue;
-                double y[4] = {0.0, 0.0, 0.0, 0.0};
-                int q0, q1, stride;
-                if (a.sell) {
-                    const int s = row >> 5, base = __ldg(a.rp + s);
-                    q0 = base + (row & 31);
-                    q1 = __ldg(a.rp + s + 1) + (row & 31);
-                    stride = 32;
-                } else {
-                    q0 = __ldg(a.rp + row);
-                    q1 = __ldg(a.rp + row + 1);
-                    stride = 1;
-                }
-                const double2* D = reinterpret_cast<const double2*>(a.D);  // written by the previous launch
-                // entries in batches: values and columns first, then the gathers, then the FMAs, so that a row
-                // waits for two memory round trips per batch rather than two per entry
-                for (int q = q0; q < q1; q += kBatch * stride) {
-                    double v[kBatch];
-                    int j[kBatch];
-#pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        const int qq = q + u * stride;
-                        const bool ok = qq < q1;
-                        v[u] = ok ? __ldg(a.A + qq) : 0.0;
-                        j[u] = ok ? (a.ci16 ? row + (int)__ldg(a.ci16 + qq) : __ldg(a.ci + qq)) : row;
-                    }
-                    double2 lo[kBatch], hi[kBatch];
-#pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        lo[u] = __ldg(D + 2 * j[u]);
-                        hi[u] = __ldg(D + 2 * j[u] + 1);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        y[0] = fma(v[u], lo[u].x, y[0]);
-                        y[1] = fma(v[u], lo[u].y, y[1]);
-                        y[2] = fma(v[u], hi[u].x, y[2]);
-                        y[3] = fma(v[u], hi[u].y, y[3]);
-                    }
-                }
-                const double2 lo = __ldg(D + 2 * row), hi = __ldg(D + 2 * row + 1);
-                const double d[4] = {lo.x, lo.y, hi.x, hi.y};
-                const double bi = a.b[row];
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-#pragma unroll
-                    for (int i = 0; i <= l; ++i) acc[l * (l + 1) / 2 + i] = fma(d[i], y[l], acc[l * (l + 1) / 2 + i]);
-                    acc[10 + l] = fma(d[l], bi, acc[10 + l]);
-                }
-            }
-        }
-        // block reduction (fixed order)
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const double v = warp_sum16<ArithF64>(acc);
-        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
-        __syncthreads();
-        if (threadIdx.x < kQ) {
-            double v = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) v += red[threadIdx.x][w];
-            a.partial[(size_t)threadIdx.x * a.n_tiles * a.n_sub + ch] = v;
-        }
-        __syncthreads();
-    }
-}
-
-// One block per instance: G and D^T b summed from the chunks' partials (threads stride over the chunks, fixed-order
-// reduction), then thread 0 solves: G scaled to unit diagonal, Cholesky, c (0 when there is no history).
-template <class Ar>
-__global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
     using T = typename Ar::T;
-    __shared__ T red[kQ][kSolveThreads / 32];
-    const int inst = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k0 = a.kin[inst];
-    double G[10], r[4], c[4] = {0.0, 0.0, 0.0, 0.0};
-    const int c0 = a.inst_t0[inst] * a.n_sub, c1 = a.inst_t1[inst] * a.n_sub;
-    {
-        // the 14 quantities of a chunk are loaded together, so their latencies overlap
-        T acc[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = Ar::zero();
-        const size_t nq = (size_t)a.n_tiles * a.n_sub;
-        const typename Ar::S* partial = reinterpret_cast<const typename Ar::S*>(a.partial);
-        for (int ch = c0 + threadIdx.x; ch < c1; ch += kSolveThreads) {
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) acc[q] = Ar::add(acc[q], Ar::load(partial + q * nq + ch));
-        }
-        const T v = warp_sum16<Ar>(acc);
-        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-#pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-        T v = Ar::zero();
-        for (int w = 0; w < kSolveThreads / 32; ++w) v = Ar::add(v, red[q][w]);
-        if (q < 10) G[q] = Ar::value(v);
-        else r[q - 10] = Ar::value(v);
-    }
-    int k = k0;
-    while (k > 0) {
-        // scale to unit diagonal, factorise L L^T
-        double s[4], L[10];
-        bool ok = true;
-        for (int i = 0; i < k && ok; ++i) {
-            ok = G[tri(i, i)] > 0.0;
-            s[i] = ok ? rsqrt(G[tri(i, i)]) : 0.0;
-        }
-        for (int l = 0; l < k && ok; ++l) {
-            for (int i = 0; i <= l && ok; ++i) {
-                double v = G[tri(i, l)] * s[i] * s[l];
-                for (int m = 0; m < i; ++m) v -= L[tri(m, i)] * L[tri(m, l)];
-                if (i == l) {
-                    ok = v > 1e-14;
-                    L[tri(l, l)] = ok ? sqrt(v) : 0.0;
-                } else {
-                    L[tri(i, l)] = v / L[tri(i, i)];
-                }
-            }
-        }
-        if (ok) {
-            double y[4];
-            for (int i = 0; i < k; ++i) {
-                double v = r[i] * s[i];
-                for (int m = 0; m < i; ++m) v -= L[tri(m, i)] * y[m];
-                y[i] = v / L[tri(i, i)];
-            }
-            for (int i = k - 1; i >= 0; --i) {
-                double v = y[i];
-                for (int m = i + 1; m < k; ++m) v -= L[tri(i, m)] * c[m];
-                c[i] = v / L[tri(i, i)];
-            }
-            for (int i = 0; i < k; ++i) c[i] *= s[i];
-            break;
-        }
-        --k;  // drop the highest difference and try again
-    }
-    for (int i = 0; i < 4; ++i) a.coef[4 * inst + i] = c[i];
-    a.kout[inst] = k;
-}
-
-// One block per chunk: x = D c on free rows (when the instance has history); history shifted.
-__global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
-    for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
-        int t, r0, r1;
-        chunk_rows(a, ch, t, r0, r1);
-        const int inst = a.tile_inst[t];
-        const int k = a.kout[inst];
-        const double c0 = a.coef[4 * inst], c1 = a.coef[4 * inst + 1], c2 = a.coef[4 * inst + 2],
-                     c3 = a.coef[4 * inst + 3];
-        for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-            const double xn = a.x[row], x1 = a.h1[row], x2 = a.h2[row];
-            if (k > 0 && !a.bc[row]) {
-                const double4 d = reinterpret_cast<const double4*>(a.D)[row];
-                a.x[row] = c0 * d.x + c1 * d.y + c2 * d.z + c3 * d.w;
-            }
-            a.h3[row] = x2;
-            a.h2[row] = x1;
-            a.h1[row] = xn;
-        }
-    }
-}
-
-// ---- double-word variants of the three passes over the nodes and the matrix (dw.cuh). D holds four float pairs
-// per node (32 bytes, as in FP64), the partial sums float pairs; the FP64 matrix values and vectors are split by
-// integer operations as they are read, and x = D c is written with one FP64 addition per node.
-
-__device__ __forceinline__ dw::df pair(float a, float b) { return dw::make(a, b); }
-
-// d_0 = x, d_1 = x - h1, d_2 = d_1 - (h1 - h2), d_3 = d_2 - ((h1 - h2) - (h2 - h3)) from the split values
-__global__ void __launch_bounds__(kThreads) k_proj_basis_dw(ProjArgs a) {
-    float4* D = reinterpret_cast<float4*>(a.D);
+    typename Ar::S* D = reinterpret_cast<typename Ar::S*>(a.D);
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
         const int k = a.kin[a.tile_inst[t]];
+        if (k == 0) continue;
         for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-            const dw::df x = dw::split(a.x[row]);
-            const dw::df h1 = k > 1 ? dw::split(a.h1[row]) : dw::make(0.0f);
-            const dw::df h2 = k > 2 ? dw::split(a.h2[row]) : dw::make(0.0f);
-            const dw::df h3 = k > 3 ? dw::split(a.h3[row]) : dw::make(0.0f);
-            const dw::df e1 = dw::sub(x, h1), e2 = dw::sub(h1, h2), e3 = dw::sub(h2, h3);
-            const dw::df d1 = k > 1 ? e1 : dw::make(0.0f);
-            const dw::df d2 = k > 2 ? dw::sub(e1, e2) : dw::make(0.0f);
-            const dw::df d3 = k > 3 ? dw::sub(d2, dw::sub(e2, e3)) : dw::make(0.0f);
-            D[2 * row] = make_float4(x.h, x.l, d1.h, d1.l);
-            D[2 * row + 1] = make_float4(d2.h, d2.l, d3.h, d3.l);
+            typename Ar::S* d = D + (size_t)row * K;
+            T old[K];
+#pragma unroll
+            for (int j = 0; j < K; j += 2) Ar::ld2(d + j, old[j], old[j + 1]);
+            T cur = Ar::from(a.x[row]);
+            T nw[K];
+            nw[0] = cur;
+#pragma unroll
+            for (int j = 1; j < K; ++j) {
+                if (j < k) cur = Ar::sub(cur, old[j - 1]);
+                nw[j] = j < k ? cur : Ar::zero();
+            }
+#pragma unroll
+            for (int j = 0; j < K; j += 2) Ar::st2(d + j, nw[j], nw[j + 1]);
         }
     }
 }
 
-// Y = A D on the free rows of instances with history (four float pairs per node, the layout of D). Kept apart
-// from the sums below so that few registers stay live and enough warps hide the gathers' latency.
-__global__ void __launch_bounds__(kThreads, 4) k_proj_apply_dw(ProjArgs a) {
-    const float4* D = reinterpret_cast<const float4*>(a.D);  // written by the previous launch
-    float4* Y = reinterpret_cast<float4*>(a.Y);
+// Y = A D on the free rows of instances with history, entries in batches of KB (columns and values, then the
+// basis gathers, then the arithmetic).
+template <class Ar, int K, int KB>
+__global__ void __launch_bounds__(kThreads, 3) k_proj_apply(ProjArgs a) {
+    using T = typename Ar::T;
+    const typename Ar::S* D = reinterpret_cast<const typename Ar::S*>(a.D);  // written by the previous launch
+    typename Ar::S* Y = reinterpret_cast<typename Ar::S*>(a.Y);
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
-        if (a.kin[a.tile_inst[t]] == 0) continue;
+        const int k = a.kin[a.tile_inst[t]];
+        if (k == 0) continue;
         for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
             if (a.bc[row]) continue;
-            dw::df y[4] = {dw::make(0.0f), dw::make(0.0f), dw::make(0.0f), dw::make(0.0f)};
+            T y[K];
+#pragma unroll
+            for (int d = 0; d < K; ++d) y[d] = Ar::zero();
             int q0, q1, stride;
             if (a.sell) {
                 const int s = row >> 5, base = __ldg(a.rp + s);
@@ -344,143 +216,246 @@ __global__ void __launch_bounds__(kThreads, 4) k_proj_apply_dw(ProjArgs a) {
                 q1 = __ldg(a.rp + row + 1);
                 stride = 1;
             }
-            for (int q = q0; q < q1; q += kBatchApply * stride) {
-                double v[kBatchApply];
-                int j[kBatchApply];
+            for (int q = q0; q < q1; q += KB * stride) {
+                double v[KB];
+                int j[KB];
 #pragma unroll
-                for (int u = 0; u < kBatchApply; ++u) {
+                for (int u = 0; u < KB; ++u) {
                     const int qq = q + u * stride;
                     const bool ok = qq < q1;
                     v[u] = ok ? __ldg(a.A + qq) : 0.0;
                     j[u] = ok ? (a.ci16 ? row + (int)__ldg(a.ci16 + qq) : __ldg(a.ci + qq)) : row;
                 }
-                float4 lo[kBatchApply], hi[kBatchApply];
+                T dj[KB][K];
 #pragma unroll
-                for (int u = 0; u < kBatchApply; ++u) {
-                    lo[u] = __ldg(D + 2 * j[u]);
-                    hi[u] = __ldg(D + 2 * j[u] + 1);
-                }
+                for (int u = 0; u < KB; ++u)
 #pragma unroll
-                for (int u = 0; u < kBatchApply; ++u) {
-                    const dw::df av = dw::split(v[u]);
-                    dw::dot_acc(y[0], av, pair(lo[u].x, lo[u].y));
-                    dw::dot_acc(y[1], av, pair(lo[u].z, lo[u].w));
-                    dw::dot_acc(y[2], av, pair(hi[u].x, hi[u].y));
-                    dw::dot_acc(y[3], av, pair(hi[u].z, hi[u].w));
+                    for (int d = 0; d < K; d += 2) Ar::ldg2(D + (size_t)j[u] * K + d, dj[u][d], dj[u][d + 1]);
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const T av = Ar::from(v[u]);
+#pragma unroll
+                    for (int d = 0; d < K; ++d)
+                        if (d < k) Ar::dot(y[d], av, dj[u][d]);
                 }
             }
+            typename Ar::S* yr = Y + (size_t)row * K;
 #pragma unroll
-            for (int l = 0; l < 4; ++l) y[l] = dw::finish(y[l]);
-            Y[2 * row] = make_float4(y[0].h, y[0].l, y[1].h, y[1].l);
-            Y[2 * row + 1] = make_float4(y[2].h, y[2].l, y[3].h, y[3].l);
+            for (int d = 0; d < K; ++d) Ar::store(yr + d, Ar::finish(y[d]));
         }
     }
 }
 
-// Per chunk: the partial sums of G = D^T Y and D^T b over its free rows.
-__global__ void __launch_bounds__(kThreads) k_proj_gram_dw(ProjArgs a) {
-    __shared__ float2 red[kQ][kThreads / 32];
-    const float4* D = reinterpret_cast<const float4*>(a.D);
-    const float4* Y = reinterpret_cast<const float4*>(a.Y);
-    float2* partial = reinterpret_cast<float2*>(a.partial);
+// Quantities G kPerGroup .. G kPerGroup + kPerGroup - 1 of one row into the group's accumulators.
+template <class Ar, int K, int G>
+__device__ __forceinline__ void gram_row(typename Ar::T (&acc)[16], const typename Ar::T (&d)[K],
+                                         const typename Ar::T (&y)[K], typename Ar::T bi) {
+    using B = Basis<K>;
+#pragma unroll
+    for (int j = 0; j < B::kPerGroup; ++j) {
+        const int q = G * B::kPerGroup + j;
+        if (q < B::kQ) {
+            if (q_row<K>(q) >= 0)
+                Ar::dot(acc[j], d[q_row<K>(q)], y[q_col<K>(q)]);
+            else
+                Ar::dot(acc[j], d[q_col<K>(q)], bi);
+        }
+    }
+}
+
+// Per chunk: partial sums of the basis's quantities over its free rows. Warp w of the block takes quantity group
+// w % groups for the rows of row set w / groups (32 rows at a time), so a row's D and Y are read by every group
+// (the repeats from L1) and every thread holds at most 16 accumulators.
+template <class Ar, int K>
+__global__ void __launch_bounds__(kThreads) k_proj_gram(ProjArgs a) {
+    using T = typename Ar::T;
+    using B = Basis<K>;
+    constexpr int kSets = kThreads / 32 / B::kGroups;  // row sets per block
+    __shared__ typename Ar::S red[B::kQ][kSets];
+    const typename Ar::S* D = reinterpret_cast<const typename Ar::S*>(a.D);
+    const typename Ar::S* Y = reinterpret_cast<const typename Ar::S*>(a.Y);
+    typename Ar::S* partial = reinterpret_cast<typename Ar::S*>(a.partial);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp % B::kGroups, set = warp / B::kGroups;
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
         const int k = a.kin[a.tile_inst[t]];
-        dw::df acc[16];
+        T acc[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = dw::make(0.0f);
+        for (int q = 0; q < 16; ++q) acc[q] = Ar::zero();
         if (k > 0) {
-            for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+            for (int row = r0 + set * 32 + lane; row < r1; row += kSets * 32) {
                 if (a.bc[row]) continue;
-                const float4 dlo = __ldg(D + 2 * row), dhi = __ldg(D + 2 * row + 1);
-                const float4 ylo = __ldg(Y + 2 * row), yhi = __ldg(Y + 2 * row + 1);
-                const dw::df d[4] = {pair(dlo.x, dlo.y), pair(dlo.z, dlo.w), pair(dhi.x, dhi.y), pair(dhi.z, dhi.w)};
-                const dw::df y[4] = {pair(ylo.x, ylo.y), pair(ylo.z, ylo.w), pair(yhi.x, yhi.y), pair(yhi.z, yhi.w)};
-                const dw::df bi = dw::split(a.b[row]);
+                T d[K], y[K];
 #pragma unroll
-                for (int l = 0; l < 4; ++l) {
-#pragma unroll
-                    for (int i = 0; i <= l; ++i) dw::dot_acc(acc[l * (l + 1) / 2 + i], d[i], y[l]);
-                    dw::dot_acc(acc[10 + l], d[l], bi);
+                for (int e = 0; e < K; e += 2) {
+                    Ar::ldg2(D + (size_t)row * K + e, d[e], d[e + 1]);
+                    Ar::ldg2(Y + (size_t)row * K + e, y[e], y[e + 1]);
+                }
+                const T bi = Ar::from(a.b[row]);
+                if constexpr (B::kGroups == 1) {
+                    gram_row<Ar, K, 0>(acc, d, y, bi);
+                } else if constexpr (B::kGroups == 2) {
+                    if (g == 0) gram_row<Ar, K, 0>(acc, d, y, bi);
+                    else gram_row<Ar, K, 1>(acc, d, y, bi);
+                } else {
+                    switch (g) {  // warp-uniform
+                        case 0: gram_row<Ar, K, 0>(acc, d, y, bi); break;
+                        case 1: gram_row<Ar, K, 1>(acc, d, y, bi); break;
+                        case 2: gram_row<Ar, K, 2>(acc, d, y, bi); break;
+                        default: gram_row<Ar, K, 3>(acc, d, y, bi); break;
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) acc[q] = dw::finish(acc[q]);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const dw::df v = warp_sum16<ArithDW>(acc);
-        if (!(lane & 1) && (lane >> 1) < kQ) red[lane >> 1][warp] = make_float2(v.h, v.l);
+        for (int q = 0; q < B::kPerGroup; ++q) acc[q] = Ar::finish(acc[q]);
+        const T v = warp_sum16<Ar>(acc);
+        const int q = g * B::kPerGroup + (lane >> 1);
+        if (!(lane & 1) && (lane >> 1) < B::kPerGroup && q < B::kQ) Ar::store(&red[q][set], v);
         __syncthreads();
-        if (threadIdx.x < kQ) {
-            dw::df s = dw::make(0.0f);
-            for (int w = 0; w < kThreads / 32; ++w) s = dw::add(s, dw::load(&red[threadIdx.x][w]));
-            dw::store(partial + (size_t)threadIdx.x * a.n_tiles * a.n_sub + ch, s);
+        for (int qq = threadIdx.x; qq < B::kQ; qq += blockDim.x) {
+            T s = Ar::zero();
+            for (int w = 0; w < kSets; ++w) s = Ar::add(s, Ar::load(&red[qq][w]));
+            Ar::store(partial + (size_t)qq * a.n_tiles * a.n_sub + ch, s);
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_proj_combine_dw(ProjArgs a) {
-    const float4* D = reinterpret_cast<const float4*>(a.D);
+// One block per instance: every warp sums a share of the quantities over the instance's chunks (lanes stride over
+// the chunks, fixed-order reduction), then thread 0 solves: G scaled to unit diagonal, Cholesky, c (0 when there
+// is no history).
+template <class Ar, int K>
+__global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
+    using T = typename Ar::T;
+    using B = Basis<K>;
+    __shared__ double tot[B::kQ];
+    const int inst = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k0 = a.kin[inst];
+    const int c0 = a.inst_t0[inst] * a.n_sub, c1 = a.inst_t1[inst] * a.n_sub;
+    const size_t nq = (size_t)a.n_tiles * a.n_sub;
+    const typename Ar::S* partial = reinterpret_cast<const typename Ar::S*>(a.partial);
+    for (int q = warp; q < B::kQ; q += kSolveThreads / 32) {
+        T v = Ar::zero();
+        if (k0 > 0)
+            for (int ch = c0 + lane; ch < c1; ch += 32) v = Ar::add(v, Ar::load(partial + q * nq + ch));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v = Ar::add(v, Ar::shfl(v, o));
+        if (lane == 0) tot[q] = Ar::value(v);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double c[K];
+    for (int i = 0; i < K; ++i) c[i] = 0.0;
+    int k = k0;
+    while (k > 0) {
+        // scale to unit diagonal, factorise L L^T
+        double s[K], L[B::kGram];
+        bool ok = true;
+        for (int i = 0; i < k && ok; ++i) {
+            ok = tot[tri(i, i)] > 0.0;
+            s[i] = ok ? rsqrt(tot[tri(i, i)]) : 0.0;
+        }
+        for (int l = 0; l < k && ok; ++l) {
+            for (int i = 0; i <= l && ok; ++i) {
+                double v = tot[tri(i, l)] * s[i] * s[l];
+                for (int m = 0; m < i; ++m) v -= L[tri(m, i)] * L[tri(m, l)];
+                if (i == l) {
+                    ok = v > 1e-14;
+                    L[tri(l, l)] = ok ? sqrt(v) : 0.0;
+                } else {
+                    L[tri(i, l)] = v / L[tri(i, i)];
+                }
+            }
+        }
+        if (ok) {
+            double y[K];
+            for (int i = 0; i < k; ++i) {
+                double v = tot[B::kGram + i] * s[i];
+                for (int m = 0; m < i; ++m) v -= L[tri(m, i)] * y[m];
+                y[i] = v / L[tri(i, i)];
+            }
+            for (int i = k - 1; i >= 0; --i) {
+                double v = y[i];
+                for (int m = i + 1; m < k; ++m) v -= L[tri(i, m)] * c[m];
+                c[i] = v / L[tri(i, i)];
+            }
+            for (int i = 0; i < k; ++i) c[i] *= s[i];
+            break;
+        }
+        for (int i = 0; i < K; ++i) c[i] = 0.0;
+        --k;  // drop the highest difference and try again
+    }
+    for (int i = 0; i < K; ++i) a.coef[kProjMax * inst + i] = c[i];
+    a.kout[inst] = k;
+}
+
+// One block per chunk: x = D c on free rows (when the instance has history).
+template <class Ar, int K>
+__global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
+    using T = typename Ar::T;
+    const typename Ar::S* D = reinterpret_cast<const typename Ar::S*>(a.D);
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
         const int inst = a.tile_inst[t];
         const int k = a.kout[inst];
-        const dw::df c0 = dw::split(a.coef[4 * inst]), c1 = dw::split(a.coef[4 * inst + 1]),
-                     c2 = dw::split(a.coef[4 * inst + 2]), c3 = dw::split(a.coef[4 * inst + 3]);
+        T c[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) c[i] = Ar::from(a.coef[kProjMax * inst + i]);
         for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-            const double xn = a.x[row], x1 = a.h1[row], x2 = a.h2[row];
             if (k > 0 && !a.bc[row]) {
-                const float4 lo = D[2 * row], hi = D[2 * row + 1];
-                const dw::df s01 = dw::add(dw::mul(c0, pair(lo.x, lo.y)), dw::mul(c1, pair(lo.z, lo.w)));
-                const dw::df s23 = dw::add(dw::mul(c2, pair(hi.x, hi.y)), dw::mul(c3, pair(hi.z, hi.w)));
-                a.x[row] = dw::to_double(dw::add(s01, s23));
+                T s = Ar::zero();
+#pragma unroll
+                for (int d = 0; d < K; d += 2) {
+                    T d0, d1;
+                    Ar::ldg2(D + (size_t)row * K + d, d0, d1);
+                    if (d < k) Ar::dot(s, c[d], d0);
+                    if (d + 1 < k) Ar::dot(s, c[d + 1], d1);
+                }
+                a.x[row] = Ar::value(Ar::finish(s));
             }
-            a.h3[row] = x2;
-            a.h2[row] = x1;
-            a.h1[row] = xn;
         }
     }
 }
 
-// Solutions available to each instance: min(4, hist - lag) (hist from the step statistics).
-__global__ void k_proj_count(ProjArgs a, const int32_t* hist, int lag) {
-    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
-    if (inst >= a.n_inst) return;
-    const int h = *hist - lag;
-    a.kin[inst] = h < 0 ? 0 : (h > 4 ? 4 : h);
+template <class Ar, int K>
+cudaError_t launch_passes(const ProjArgs& a, int grid, cudaStream_t st) {
+    cudaError_t e;
+    k_proj_basis<Ar, K><<<grid, kThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_proj_apply<Ar, K, K <= 4 ? 3 : 2><<<grid, kThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_proj_gram<Ar, K><<<grid, kThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_proj_solve<Ar, K><<<a.n_inst, kSolveThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_proj_combine<Ar, K><<<grid, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class Ar>
+cudaError_t launch_sized(const ProjArgs& a, int grid, cudaStream_t st) {
+    switch (proj_stride(a.kmax)) {
+        case 2: return launch_passes<Ar, 2>(a, grid, st);
+        case 4: return launch_passes<Ar, 4>(a, grid, st);
+        case 6: return launch_passes<Ar, 6>(a, grid, st);
+        default: return launch_passes<Ar, 8>(a, grid, st);
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st) {
-    k_proj_count<<<(a.n_inst + 127) / 128, 128, 0, st>>>(a, hist, lag);
+    k_proj_count<<<1, 32, 0, st>>>(a, hist, lag);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long nch = (long long)a.n_tiles * a.n_sub;
     const int grid = (int)(nch < 148 * 32 ? nch : 148 * 32);
-    if (a.dw) {
-        k_proj_basis_dw<<<grid, kThreads, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_proj_apply_dw<<<grid, kThreads, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_proj_gram_dw<<<grid, kThreads, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_proj_solve<ArithDW><<<a.n_inst, kSolveThreads, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_proj_combine_dw<<<grid, kThreads, 0, st>>>(a);
-        return cudaGetLastError();
-    }
-    k_proj_basis<<<grid, kThreads, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_gram<<<grid, kThreads, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_solve<ArithF64><<<a.n_inst, kSolveThreads, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_combine<<<grid, kThreads, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.dw ? launch_sized<ArithDW>(a, grid, st) : launch_sized<ArithF64>(a, grid, st);
 }
 
 }  // namespace rafem
