@@ -518,9 +518,9 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
 }
 
 // Initial guess of a step's solve (the predictor of Sec. II-A's predictor-corrector loop): polynomial
-// extrapolation of order 1..3, or (predictor 4) for the potential the A-orthogonal projection onto its last four
-// solutions, which needs an SPD system (PCG, symmetric lift; order 2 otherwise, and for the thermal system, whose
-// few iterations would not repay the extra pass).
+// extrapolation of order 1..3, or (predictor 4) for the potential the A-orthogonal projection onto its last
+// proj_basis solutions, which needs an SPD system (the symmetric lift, any solver; order 2 otherwise, and for the
+// thermal system, whose few iterations would not repay the extra pass).
 cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     if (!c->prm.predictor) return cudaSuccess;
     const bool V = which == RAFEM_SYS_V;
