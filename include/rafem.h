@@ -202,6 +202,16 @@ int rafem_solve_step(rafem_ctx* ctx, rafem_step_stats* stats);
  * last step and, in status, the worst status met over all steps. */
 int rafem_run(rafem_ctx* ctx, int32_t n_steps, rafem_step_stats* last);
 
+/* One time step with its state in host memory (as rafem_set_state at the current step, rafem_solve_step and
+ * rafem_get_field in one call): T_in and V_in (N doubles each, nullable) replace the state before the step, T_out
+ * and V_out (nullable, may be the same buffers as the inputs) receive the fields after it; the predictor history
+ * is kept. The copies overlap the step where the data allows: V goes in while the potential is assembled and
+ * comes out while the thermal system is assembled and solved, on a second stream; T goes in first and out last.
+ * Pinned host buffers let the whole step (copies included) run as one captured graph, rebuilt when the buffers
+ * change; pageable buffers work with direct launches. Returns like rafem_solve_step. */
+int rafem_step_host(rafem_ctx* ctx, const double* T_in, const double* V_in, double* T_out, double* V_out,
+                    rafem_step_stats* stats);
+
 /* Copy a field (RAFEM_SYS_V = potential, RAFEM_SYS_T = temperature) of N doubles to dst.
  * dst_on_device: 0 = host pointer, 1 = device pointer. */
 int rafem_get_field(rafem_ctx* ctx, int which, double* dst, int dst_on_device);

@@ -114,6 +114,13 @@ struct rafem_ctx {
     // corrector passes (n_corrector > 1): one graph per step whose conditional WHILE node repeats the pass on the
     // device until the temperature change falls below corrector_tol or n_corrector passes are done
     cudaGraphExec_t corr_graph = nullptr;
+    // host-state step (rafem_step_host): copies on a second stream, overlapped with the step, captured as a graph
+    // for one set of host buffers
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t io_graph = nullptr;
+    bool io_graph_failed = false;
+    const void* io_key[4] = {nullptr, nullptr, nullptr, nullptr};
     bool corr_graph_failed = false;
     CorrDev* corr = nullptr;
     double* V_old = nullptr;          // potential at the start of the step (restored when a step is rejected)
@@ -563,22 +570,57 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     return cudaGetLastError();
 }
 
-// One lagged pass: sigma and the mass term both use the current T.
-cudaError_t enqueue_step(rafem_ctx* c) {
+// Host buffers of a host-state step (any may be null): state in before the step, fields out after it.
+struct StepIO {
+    const double *T_in, *V_in;
+    double *T_out, *V_out;
+};
+
+// One lagged pass: sigma and the mass term both use the current T. With io, the step also moves its state to
+// and from host memory: T in first on the step's stream (the potential assembly reads it), V in on the second
+// stream while the potential is assembled (only its predictor reads V), V out on the second stream as soon as
+// the potential is solved (during the thermal half of the step), T out at the end; the second stream joins
+// before the step ends.
+cudaError_t enqueue_step_io(rafem_ctx* c, const StepIO* io) {
     cudaError_t e;
-    k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
+    cudaStream_t S = c->stream, I = c->io_stream;
+    const size_t nb = (size_t)c->N * sizeof(double);
+    const bool vin = io && io->V_in, vout = io && io->V_out;
+    if (io && io->T_in && (e = cudaMemcpyAsync(c->T, io->T_in, nb, cudaMemcpyHostToDevice, S)) != cudaSuccess) return e;
+    if (vin) {
+        if ((e = cudaEventRecord(c->io_ev[0], S)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(I, c->io_ev[0], 0)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(c->V, io->V_in, nb, cudaMemcpyHostToDevice, I)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->io_ev[1], I)) != cudaSuccess) return e;
+    }
+    k_begin_step<<<1, 128, 0, S>>>(c->stats, c->istats, c->n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    if (vin && (e = cudaStreamWaitEvent(S, c->io_ev[1], 0)) != cudaSuccess) return e;
     if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
-    k_record<<<1, 128, 0, c->stream>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
+    k_record<<<1, 128, 0, S>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (vout) {
+        if ((e = cudaEventRecord(c->io_ev[2], S)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(I, c->io_ev[2], 0)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(io->V_out, c->V, nb, cudaMemcpyDeviceToHost, I)) != cudaSuccess) return e;
+    }
+    if (vin || vout) {
+        if ((e = cudaEventRecord(c->io_ev[3], I)) != cudaSuccess) return e;
+    }
     if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T)) != cudaSuccess) return e;
     if ((e = enqueue_predict(c, RAFEM_SYS_T)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T)) != cudaSuccess) return e;
-    k_record<<<1, 128, 0, c->stream>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 1);
-    return cudaGetLastError();
+    k_record<<<1, 128, 0, S>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (io && io->T_out && (e = cudaMemcpyAsync(io->T_out, c->T, nb, cudaMemcpyDeviceToHost, S)) != cudaSuccess)
+        return e;
+    if ((vin || vout) && (e = cudaStreamWaitEvent(S, c->io_ev[3], 0)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
+
+cudaError_t enqueue_step(rafem_ctx* c) { return enqueue_step_io(c, nullptr); }
 
 // Traced step: the same launches as enqueue_step with an event between regions (Assembly, Predict, Solve).
 cudaError_t enqueue_step_traced(rafem_ctx* c) {
@@ -811,10 +853,13 @@ cudaError_t launch_corrector_step(rafem_ctx* c) {
 void drop_graphs(rafem_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->corr_graph) cudaGraphExecDestroy(c->corr_graph);
+    if (c->io_graph) cudaGraphExecDestroy(c->io_graph);
     c->graph = nullptr;
     c->corr_graph = nullptr;
+    c->io_graph = nullptr;
     c->graph_failed = false;
     c->corr_graph_failed = false;
+    c->io_graph_failed = false;
 }
 
 // The step graph (captured once; direct launches if capture is not possible).
@@ -966,8 +1011,12 @@ void rafem_destroy(rafem_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->corr_graph) cudaGraphExecDestroy(c->corr_graph);
+    if (c->io_graph) cudaGraphExecDestroy(c->io_graph);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->io_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->io_stream) cudaStreamDestroy(c->io_stream);
     for (void* p : c->tile_allocs) cudaFree(p);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1554,6 +1603,56 @@ int rafem_solve_step(rafem_ctx* c, rafem_step_stats* stats) {
     // fixed-point corrector passes: sigma at the newest T iterate, mass term at T^n (device-side loop)
     CK(launch_corrector_step(c));
     return finish(c, stats, false);
+}
+
+int rafem_step_host(rafem_ctx* c, const double* T_in, const double* V_in, double* T_out, double* V_out,
+                    rafem_step_stats* stats) {
+    if (!c) return RAFEM_ERR_BAD_INPUT;
+    const size_t nb = (size_t)c->N * sizeof(double);
+    if (c->prm.n_corrector > 1 || c->mono || c->tracing) {
+        // corrector loop or traced step: the copies in sequence around the step
+        if (T_in) CK(cudaMemcpyAsync(c->T, T_in, nb, cudaMemcpyHostToDevice, c->stream));
+        if (V_in) CK(cudaMemcpyAsync(c->V, V_in, nb, cudaMemcpyHostToDevice, c->stream));
+        const int s = rafem_solve_step(c, stats);
+        if (s < 0) return s;
+        if (T_out) CK(cudaMemcpyAsync(T_out, c->T, nb, cudaMemcpyDeviceToHost, c->stream));
+        if (V_out) CK(cudaMemcpyAsync(V_out, c->V, nb, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return s;
+    }
+    if (!c->io_stream) {
+        CK(cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : c->io_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const StepIO io{T_in, V_in, T_out, V_out};
+    const void* key[4] = {T_in, V_in, T_out, V_out};
+    if (!std::equal(key, key + 4, c->io_key)) {
+        if (c->io_graph) cudaGraphExecDestroy(c->io_graph);
+        c->io_graph = nullptr;
+        c->io_graph_failed = false;
+        std::copy(key, key + 4, c->io_key);
+    }
+    if (!c->io_graph && !c->io_graph_failed) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t e1 = enqueue_step_io(c, &io);
+            const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || !g || cudaGraphInstantiate(&c->io_graph, g, 0) != cudaSuccess)
+                c->io_graph = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!c->io_graph) {
+            c->io_graph_failed = true;  // e.g. pageable host buffers: direct launches
+            cudaGetLastError();
+        }
+    }
+    if (c->io_graph)
+        CK(cudaGraphLaunch(c->io_graph, c->stream));
+    else
+        CK(enqueue_step_io(c, &io));
+    const int s = finish(c, stats, false);
+    const int t = tape_record(c, c->step);
+    return t != RAFEM_OK ? t : s;
 }
 
 int rafem_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* last) {

@@ -157,6 +157,7 @@ def lib() -> ctypes.CDLL:
         "rafem_precond_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_dt": (ctypes.c_int, [vp, ctypes.c_double]),
         "rafem_set_tol": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
+        "rafem_step_host": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(rafem_step_stats)]),
         "rafem_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
         "rafem_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(rafem_advance_stats)]),
@@ -417,6 +418,22 @@ class Context:
 
     def set_dt(self, dt: float):
         _check(lib().rafem_set_dt(self._ctx, float(dt)), "rafem_set_dt")
+
+    def step_host_ptr(self, T_in=None, V_in=None, T_out=None, V_out=None):
+        """rafem_step_host on raw host addresses (ints or None)."""
+        st = rafem_step_stats()
+        s = lib().rafem_step_host(self._ctx, T_in, V_in, T_out, V_out, ctypes.byref(st))
+        return _check(s, "rafem_step_host"), st
+
+    def step_host(self, T=None, V=None):
+        """One step from host state: numpy float64 arrays T, V (either may be None) are read before the step and
+        overwritten with the fields after it."""
+        Ta = None if T is None else np.ascontiguousarray(T, dtype=np.float64)
+        Va = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+        if Ta is not T and T is not None or Va is not V and V is not None:
+            raise ValueError("T and V must be contiguous float64 arrays")
+        return self.step_host_ptr(None if Ta is None else Ta.ctypes.data, None if Va is None else Va.ctypes.data,
+                                  None if Ta is None else Ta.ctypes.data, None if Va is None else Va.ctypes.data)
 
     def set_tol(self, tol: float, inner_tol: float = 0.0):
         _check(lib().rafem_set_tol(self._ctx, float(tol), float(inner_tol)), "rafem_set_tol")

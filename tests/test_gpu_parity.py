@@ -400,3 +400,34 @@ def test_larger_projection_basis_saves_iterations():
             ctx.run(25)
             iters[basis] = ctx.get_trace()["iters_V"]
     assert iters[8] < iters[4], iters
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_step_host_equals_device_steps(pinned):
+    """rafem_step_host (state in and out of host buffers, copies overlapped with the step on a second stream)
+    gives bitwise the fields and statistics of the same steps run on device-resident state."""
+    import torch
+    rafem = R()
+    m = mg.cube_mesh(12, jitter=0.1, seed=63, sigma0="lognormal")
+    with rafem.Context(m, precision=rafem.RAFEM_PRECISION_MIXED) as a, \
+            rafem.Context(m, precision=rafem.RAFEM_PRECISION_MIXED) as b:
+        a.run(2)
+        b.run(2)
+        if pinned:
+            T = torch.from_numpy(b.get_field(rafem.RAFEM_SYS_T)).pin_memory()
+            V = torch.from_numpy(b.get_field(rafem.RAFEM_SYS_V)).pin_memory()
+            ptr = lambda x: x.data_ptr()
+            tonp = lambda x: x.numpy()
+        else:
+            T, V = b.get_field(rafem.RAFEM_SYS_T), b.get_field(rafem.RAFEM_SYS_V)
+            ptr = lambda x: x.ctypes.data
+            tonp = lambda x: x
+        for _ in range(4):
+            sa, sta = a.solve_step()
+            sb, stb = b.step_host_ptr(ptr(T), ptr(V), ptr(T), ptr(V))
+            assert sa == sb == 0
+            assert sta.as_dict() == stb.as_dict()
+            np.testing.assert_array_equal(tonp(T), a.get_field(rafem.RAFEM_SYS_T))
+            np.testing.assert_array_equal(tonp(V), a.get_field(rafem.RAFEM_SYS_V))
+        if pinned:
+            assert b.graph_info()["step_graph"] in (-1, 0, 1)
