@@ -37,6 +37,37 @@ ORACLE_SAMPLE_N = 24          # oracle sample: the same workload family on a 24^
 ORACLE_SAMPLE_STEPS = 5
 
 
+def reduce_over_ranks(values, op, dist):
+    """All-reduce a few floats over the ranks ('max' or 'sum'), on the device the process group's backend uses
+    (CUDA tensors for NCCL, host tensors for gloo). Without a process group the values come back unchanged."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.cpu()]
+
+
+def aggregate_rate(units_per_rank, ms_per_rank_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (ms)."""
+    return units_per_rank / (ms_per_rank_max * 1e-3)
+
+
+def partition_instances(costs, world):
+    """Balanced split of independent instances over `world` ranks: longest processing time first (largest cost to
+    the least loaded rank, ties to the lower rank), deterministic on every rank. Returns one index list per rank,
+    each in increasing order."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -253,11 +284,7 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, preco
         clk.__exit__()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_over_ranks([ev0.elapsed_time(ev1)], "max", dist)[0]
     fields = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
     graph = ctx.graph_info()
     # region split and iteration counts of the same K steps: replayed from the initial state with tracing on (the
@@ -331,15 +358,22 @@ def roofline(res, mixed, peaks, peak_kind):
             "alg_bytes_per_launch": alg, **({"fp64_pipe": fp64_pipe} if fp64_pipe else {})}
 
 
-def measure_batch(rafem, torch, mg, args):
+def measure_batch(rafem, torch, mg, args, dist=None):
     """Batching form: the 96-instance workload (sizes 12^3..64^3 cells, electrode 10-40 V at 10-30 mm, sigma0
     0.25-0.45 S/m, seeded) in one context per precision, schedule from the autotuner, against one context per
-    instance run one after the other (FP64). Throughput in instance-steps per second."""
+    instance run one after the other (FP64). Throughput in instance-steps per second. Under several ranks the
+    instances are split by node count (partition_instances; no collective on the data path) and the rates are
+    aggregated over the slowest rank."""
     from paper_2409_13036_b300.autotune import autotune_schedule
-    meshes = [mg.batch_mesh(d) for d in mg.batch_draws()]
+    draws = mg.batch_draws()
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    mine = partition_instances([(d[0] + 1) ** 3 for d in draws], world)[rank]
+    meshes = [mg.batch_mesh(draws[i]) for i in mine]
     nodes = sum(m.n_nodes for m in meshes)
     kb = args.batch_steps
-    out = {"instances": len(meshes), "nodes": nodes, "steps": kb, "warmup": 3}
+    out = {"instances": len(draws), "instances_this_rank": len(meshes), "nodes_this_rank": nodes, "steps": kb,
+           "warmup": 3, "partition": "by instance, node-count balanced (largest first)" if world > 1 else "single"}
     stream = torch.cuda.Stream()
     for name, prec in (("mixed", rafem.RAFEM_PRECISION_MIXED), ("fp64", rafem.RAFEM_PRECISION_FP64)):
         ctx = rafem.Context.batch(meshes, stream=stream.cuda_stream, precision=prec)
@@ -353,9 +387,9 @@ def measure_batch(rafem, torch, mg, args):
         s, st = ctx.run(kb)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = reduce_over_ranks([e0.elapsed_time(e1)], "max", dist)[0]
         per = ctx.batch_stats()
-        out[name] = {"instance_steps_per_s": len(meshes) * kb / (ms * 1e-3), "ms_per_step": ms / kb,
+        out[name] = {"instance_steps_per_s": aggregate_rate(len(draws) * kb, ms), "ms_per_step": ms / kb,
                      "status": rafem.status_string(s), "rows_per_tile": tune["rows_per_tile"],
                      "tuned_from_cache": tune["cached"],
                      "iters_V_min_max": [min(q["iters_V"] for q in per), max(q["iters_V"] for q in per)]}
@@ -373,7 +407,8 @@ def measure_batch(rafem, torch, mg, args):
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         ctx.close()
-    out["sequential_fp64"] = {"instance_steps_per_s": len(meshes) * kb / (total_ms * 1e-3),
+    total_ms = reduce_over_ranks([total_ms], "max", dist)[0]
+    out["sequential_fp64"] = {"instance_steps_per_s": aggregate_rate(len(draws) * kb, total_ms),
                               "ms_per_step_all_instances": total_ms / kb}
     out["speedup_mixed_batch_vs_sequential_fp64"] = (out["mixed"]["instance_steps_per_s"] /
                                                      out["sequential_fp64"]["instance_steps_per_s"])
@@ -723,13 +758,13 @@ def main():
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         ctx.step_host_ptr(*ptrs)
-    t_e2e = time.perf_counter() - t0
+    t_e2e = reduce_over_ranks([time.perf_counter() - t0], "max", dist)[0]
     ctx.close()
 
     def summary(r):
         tr = r["trace"]
         k = r.get("steps", args.steps)
-        return {"value": world * k / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / k, "steps": k,
+        return {"value": aggregate_rate(world * k, r["ms"]), "unit": UNIT, "ms_per_step": r["ms"] / k, "steps": k,
                 "status": r["status"], "last_step": r["last"],
                 "iters_V_per_step": tr["iters_V"] / tr["steps"], "iters_T_per_step": tr["iters_T"] / tr["steps"],
                 "refine_V_per_step": tr["refine_V"] / tr["steps"],
@@ -756,7 +791,7 @@ def main():
             "refine_V_per_step": head_sum["refine_V_per_step"],
             "regions_ms_per_step": head_sum["regions_ms_per_step"],
             "roofline": head["roofline"],
-            "e2e": {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+            "e2e": {"value": aggregate_rate(world * e2e_steps, 1e3 * t_e2e), "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 16 * N, "steps": e2e_steps,
                     "note": "same steps as the device-timed region, replayed from the initial state; one "
                             "rafem_step_host call per step (state in, step, fields out)"},
@@ -786,7 +821,7 @@ def main():
         line["cpu_baseline"] = cpu
     if args.batch_steps > 0 and args.only is None and args.cells == 127:
         try:
-            line["batch"] = measure_batch(rafem, torch, mg, args)
+            line["batch"] = measure_batch(rafem, torch, mg, args, dist)
         except Exception as exc:  # the headline line must still be printed
             line["batch"] = {"error": repr(exc)[:300]}
     if args.small_steps > 0 and args.only in (None, "pipecg"):
