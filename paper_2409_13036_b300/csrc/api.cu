@@ -81,6 +81,8 @@ struct rafem_ctx {
     int32_t *proj_kin = nullptr, *proj_kout = nullptr;
     double* proj_D = nullptr;                      // [N][proj_stride(proj_k)] projection basis (its history)
     double* proj_Y = nullptr;                      // [N][proj_stride(proj_k)] A times the basis
+    double* proj_r0 = nullptr;                     // [N] residual of the projected guess
+    bool r0_fresh = false;                         // enqueue time: proj_r0 belongs to the next potential solve
     // solver workspace
     double *wr = nullptr, *wu = nullptr, *ww = nullptr, *wp = nullptr, *ws = nullptr, *wdinv = nullptr;
     float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr, *fd = nullptr, *fdinv = nullptr;
@@ -446,7 +448,16 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
     return cudaSuccess;
 }
 
+// The potential's initial guess comes from the projection predictor (it needs A SPD: the symmetric lift, any
+// solver).
+bool projected_V(const rafem_ctx* c) {
+    return c->prm.predictor == RAFEM_PREDICT_PROJECT && c->prm.lift == RAFEM_LIFT_SYMMETRIC;
+}
+
 cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
+    // the residual of the projected guess serves only the potential solve enqueued right after the projection
+    const bool r0_fresh = c->r0_fresh && which == RAFEM_SYS_V && b == c->bV && x == c->V;
+    if (which == RAFEM_SYS_V) c->r0_fresh = false;
     if (c->ilu) {
         IluSolveArgs s{};
         s.L = &c->il;
@@ -520,6 +531,11 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         return launch_bicgstab(g, c->bg_grid, c->stream);
     }
     SolveArgs a = make_args(c, which, b, x);
+    if (r0_fresh) {
+        // the projection predictor left the residual of its guess: no first residual SpMV
+        a.r0 = c->proj_r0;
+        a.r0_ok = c->proj_kout;
+    }
     return launch_krylov(a, c->lanes, c->prm.precision, c->prm.solver == RAFEM_SOLVER_PIPECG, c->grid, c->block,
                          c->stream);
 }
@@ -531,8 +547,7 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
 cudaError_t enqueue_predict(rafem_ctx* c, int which) {
     if (!c->prm.predictor) return cudaSuccess;
     const bool V = which == RAFEM_SYS_V;
-    const bool spd = c->prm.lift == RAFEM_LIFT_SYMMETRIC;  // the projection needs A SPD, whatever the solver
-    if (c->prm.predictor == RAFEM_PREDICT_PROJECT && spd && V) {
+    if (V && projected_V(c)) {
         ProjArgs a{};
         a.n_tiles = c->n_tiles;
         a.n_sub = c->proj_sub;
@@ -558,6 +573,8 @@ cudaError_t enqueue_predict(rafem_ctx* c, int which) {
         a.kout = c->proj_kout;
         a.D = c->proj_D;
         a.Y = c->proj_Y;
+        a.r0 = c->proj_r0;
+        c->r0_fresh = true;
         return launch_projection(a, &c->stats->hist, 1, c->stream);
     }
     const int order = c->prm.predictor == RAFEM_PREDICT_PROJECT ? 2 : c->prm.predictor;
@@ -586,6 +603,7 @@ cudaError_t enqueue_step_io(rafem_ctx* c, const StepIO* io) {
     cudaStream_t S = c->stream, I = c->io_stream;
     const size_t nb = (size_t)c->N * sizeof(double);
     const bool vin = io && io->V_in, vout = io && io->V_out;
+    c->r0_fresh = false;
     if (io && io->T_in && (e = cudaMemcpyAsync(c->T, io->T_in, nb, cudaMemcpyHostToDevice, S)) != cudaSuccess) return e;
     if (vin) {
         if ((e = cudaEventRecord(c->io_ev[0], S)) != cudaSuccess) return e;
@@ -1310,6 +1328,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         const size_t nd = (size_t)proj_stride(c->proj_k) * N;
         CK(dalloc(c, &c->proj_D, nd + 8));
         CK(dalloc(c, &c->proj_Y, nd + 8));
+        CK(dalloc(c, &c->proj_r0, N));
         CK(cudaMemsetAsync(c->proj_D, 0, nd * sizeof(double), c->stream));
     }
     CK(dalloc(c, &c->V_old, N));
@@ -1574,6 +1593,7 @@ int rafem_assemble(rafem_ctx* c, int which) {
 int rafem_solve(rafem_ctx* c, int which, rafem_step_stats* stats) {
     if (!c || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
     c->tape_every = 0;
+    c->r0_fresh = false;  // a standalone solve starts from its own residual
     k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     CK(cudaGetLastError());
     CK(enqueue_solve(c, which, which == RAFEM_SYS_V ? c->bV : c->bT, which == RAFEM_SYS_V ? c->V : c->T));

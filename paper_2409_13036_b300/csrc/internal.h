@@ -149,6 +149,8 @@ struct SolveArgs {
     // problem
     const double* b;
     double* x;
+    const double* r0;        // b - A x for the starting x, computed by the predictor, or null (CG kernels read it in
+    const int32_t* r0_ok;    // place of their first residual SpMV for instances i with r0_ok[i] > 0)
     // FP64 workspace
     double *r, *u, *w, *p, *s, *dinv;
     // FP32 workspace (mixed precision)
@@ -344,6 +346,7 @@ struct ProjArgs {
     double* D;                       // [N][proj_stride(kmax)] basis, 8-byte entries (FP64 or float pairs); the
                                      // previous call's basis on entry (the predictor's history)
     double* Y;                       // [N][proj_stride(kmax)] A D
+    double* r0;                      // [N] out: b - A x of the guess (b - Y c; 0 on Dirichlet rows) where kout > 0
     double* partial;                 // [kProjQ][n_tiles * n_sub]
     double* coef;                    // [kProjMax n_inst]
     int32_t *kin, *kout;             // [n_inst] solutions available / basis size used

@@ -665,12 +665,24 @@ struct EmInitResidual {
     const SolveArgs& a;
     double* v;
     __device__ __forceinline__ double pre(int row) const { return a.b[row]; }
-    __device__ __forceinline__ void fin(int row, double ax, double bi) const {
-        a.r[row] = bi - ax;
+    __device__ __forceinline__ void fin(int row, double ax, double bi) const { fin_res(row, bi - ax, bi); }
+    // the residual given (see given_residual)
+    __device__ __forceinline__ void fin_res(int row, double r, double bi) const {
+        a.r[row] = r;
         a.dinv[row] = 1.0 / a.A[a.diag[row]];
         v[0] = fma(bi, bi, v[0]);
     }
 };
+
+// Whether the starting residual b - A x of tile t's instance was computed by the predictor (SolveArgs::r0), so
+// that the first residual pass reads it instead of running an SpMV (block-uniform).
+__device__ __forceinline__ bool given_residual(const SolveArgs& a, int t) {
+    return a.r0 != nullptr && a.r0_ok[a.tile_inst[t]] > 0;
+}
+template <class Emit>
+__device__ __forceinline__ void given_residual_rows(const SolveArgs& a, int r0, int r1, const Emit& em) {
+    for (int row = r0 + threadIdx.x; row < r1; row += kBlock) em.fin_res(row, ldcg(a.r0 + row), em.pre(row));
+}
 
 // w = A u, partial delta += w u
 template <typename T>
@@ -709,11 +721,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
     unsigned target = 0;
     bool ok = true;
 
-    // init 1: r = b - A x, dinv, bb
+    // init 1: r = b - A x (or the predictor's residual), dinv, bb
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int r0 = a.tile_r0[t], r1 = a.tile_r1[t];
         double v[1] = {0.0};
-        ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmInitResidual{a, v}) && ok;
+        if (given_residual(a, t))
+            given_residual_rows(a, r0, r1, EmInitResidual{a, v});
+        else
+            ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmInitResidual{a, v}) && ok;
         block_sum<1>(v, sm);
         if (threadIdx.x == 0) a.partial[(size_t)Q_BB * nt + t] = v[0];
     }
@@ -1023,8 +1038,8 @@ struct EmOuter {
         float dinv;
     };
     __device__ __forceinline__ P pre(int row) const { return P{a.b[row], ldcg(a.dinv32 + row)}; }
-    __device__ __forceinline__ void fin(int row, double ax, const P& p) const {
-        const double r64 = p.b - ax;
+    __device__ __forceinline__ void fin(int row, double ax, const P& p) const { fin_res(row, p.b - ax, p); }
+    __device__ __forceinline__ void fin_res(int row, double r64, const P& p) const {
         const float r32 = (float)r64;
         const float u32 = p.dinv * r32;
         a.r32[row] = r32;
@@ -1126,7 +1141,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
             if (st.outer == ST_OUTER) {
                 double v[2] = {0.0, 0.0};
                 float f[2] = {0.0f, 0.0f};
-                ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmOuter{a, v, f}) && ok;
+                // the first residual of the solve may come from the predictor (no SpMV)
+                if (first_round && given_residual(a, t))
+                    given_residual_rows(a, r0, r1, EmOuter{a, v, f});
+                else
+                    ok = spmv_tile<L, double, double>(a, ring, a.A, a.x, r0, r1, EmOuter{a, v, f}) && ok;
                 block_sum<2>(v, sm);
                 double fd[2] = {(double)f[0], (double)f[1]};
                 block_sum<2>(fd, sm);

@@ -393,11 +393,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_proj_solve(ProjArgs a) {
     a.kout[inst] = k;
 }
 
-// One block per chunk: x = D c on free rows (when the instance has history).
+// One block per chunk: x = D c on free rows (when the instance has history), and the residual of that guess,
+// b - A x = b - Y c, for the solver's first residual (0 on Dirichlet rows, where x already holds the prescribed
+// value).
 template <class Ar, int K>
 __global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
     using T = typename Ar::T;
     const typename Ar::S* D = reinterpret_cast<const typename Ar::S*>(a.D);
+    const typename Ar::S* Y = reinterpret_cast<const typename Ar::S*>(a.Y);
     for (int ch = blockIdx.x; ch < a.n_tiles * a.n_sub; ch += gridDim.x) {
         int t, r0, r1;
         chunk_rows(a, ch, t, r0, r1);
@@ -408,15 +411,25 @@ __global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
         for (int i = 0; i < K; ++i) c[i] = Ar::from(a.coef[kProjMax * inst + i]);
         for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
             if (k > 0 && !a.bc[row]) {
-                T s = Ar::zero();
+                T s = Ar::zero(), ay = Ar::zero();
 #pragma unroll
                 for (int d = 0; d < K; d += 2) {
-                    T d0, d1;
+                    T d0, d1, y0, y1;
                     Ar::ldg2(D + (size_t)row * K + d, d0, d1);
-                    if (d < k) Ar::dot(s, c[d], d0);
-                    if (d + 1 < k) Ar::dot(s, c[d + 1], d1);
+                    Ar::ldg2(Y + (size_t)row * K + d, y0, y1);
+                    if (d < k) {
+                        Ar::dot(s, c[d], d0);
+                        Ar::dot(ay, c[d], y0);
+                    }
+                    if (d + 1 < k) {
+                        Ar::dot(s, c[d + 1], d1);
+                        Ar::dot(ay, c[d + 1], y1);
+                    }
                 }
                 a.x[row] = Ar::value(Ar::finish(s));
+                a.r0[row] = Ar::value(Ar::sub(Ar::from(a.b[row]), Ar::finish(ay)));
+            } else if (k > 0) {
+                a.r0[row] = 0.0;
             }
         }
     }
