@@ -399,23 +399,27 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     return a;
 }
 
-cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old);
+cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old, bool with_y);
 
-// Assembly of one system; with ILU(0) the potential matrix is refactored right after it is assembled.
-cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
-    cudaError_t e = enqueue_assemble_raw(c, which, T_sigma, T_old);
+// Assembly of one system; with ILU(0) the potential matrix is refactored right after it is assembled. with_y: the
+// potential's assembly also computes the projection predictor's Y = A D (double-word gather, basis of 4, basis
+// already built).
+cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, const double* T_old,
+                             bool with_y = false) {
+    cudaError_t e = enqueue_assemble_raw(c, which, T_sigma, T_old, with_y);
     if (e != cudaSuccess || !c->ilu || which != RAFEM_SYS_V) return e;
     return launch_ilu_refactor(c->il, c->valsV, c->ilu_AV, c->ilu_FV, c->ilu_DV, c->stream);
 }
 
-cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old) {
+cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old, bool with_y) {
     cudaError_t e;
     if (c->dw) {
         float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
         if (which == RAFEM_SYS_V)
             return launch_assemble_V_gather_dw(c->gd, c->gdw, c->N, c->rp, c->ci, c->diag, c->el, T_sigma,
                                                c->prm.alpha_sigma, c->bcV, c->gV, c->valsV, v32, c->bV, c->prm.lift,
-                                               c->stream);
+                                               with_y ? c->proj_D : nullptr, with_y ? c->proj_Y : nullptr,
+                                               with_y ? c->proj_kin : nullptr, c->stream);
         return launch_rhs_T_gather_dw(c->gd, c->gdw, c->N, c->el, T_sigma, T_old, c->V, c->bcT, c->gT, c->bTc,
                                       c->prm.alpha_sigma, c->bT, c->stream);
     }
@@ -452,6 +456,49 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
 // solver).
 bool projected_V(const rafem_ctx* c) {
     return c->prm.predictor == RAFEM_PREDICT_PROJECT && c->prm.lift == RAFEM_LIFT_SYMMETRIC;
+}
+
+// The projection's Y = A D comes from the potential's assembly: double-word gather assembly, basis of up to 4.
+bool fused_V(const rafem_ctx* c) { return c->dw && projected_V(c) && c->proj_D && proj_stride(c->proj_k) == 4; }
+
+ProjArgs proj_args(const rafem_ctx* c) {
+    ProjArgs a{};
+    a.n_tiles = c->n_tiles;
+    a.n_sub = c->proj_sub;
+    a.dw = c->dw ? 1 : 0;
+    a.tile_r0 = c->tile_r0;
+    a.tile_r1 = c->tile_r1;
+    a.tile_inst = c->tile_inst;
+    a.n_inst = c->n_inst;
+    a.inst_t0 = c->inst_t0;
+    a.inst_t1 = c->inst_t1;
+    a.sell = c->sell ? 1 : 0;
+    a.rp = c->rp;
+    a.ci = c->ci;
+    a.ci16 = c->ci16;
+    a.A = c->valsV;
+    a.bc = c->bcV;
+    a.b = c->bV;
+    a.x = c->V;
+    a.kmax = c->proj_k;
+    a.partial = c->proj_partial;
+    a.coef = c->proj_coef;
+    a.kin = c->proj_kin;
+    a.kout = c->proj_kout;
+    a.D = c->proj_D;
+    a.Y = c->proj_Y;
+    a.r0 = c->proj_r0;
+    return a;
+}
+
+// The step's potential assembly. fuse (fused_V, and V is final when it runs): the projection basis is built from
+// the previous solution first, and the assembly accumulates Y = A D along with the matrix.
+cudaError_t enqueue_assemble_V_step(rafem_ctx* c, bool fuse) {
+    if (fuse) {
+        const cudaError_t e = launch_projection_basis(proj_args(c), &c->stats->hist, 1, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T, fuse);
 }
 
 cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
@@ -544,38 +591,14 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
 // extrapolation of order 1..3, or (predictor 4) for the potential the A-orthogonal projection onto its last
 // proj_basis solutions, which needs an SPD system (the symmetric lift, any solver; order 2 otherwise, and for the
 // thermal system, whose few iterations would not repay the extra pass).
-cudaError_t enqueue_predict(rafem_ctx* c, int which) {
+// fused: the basis and Y were made with the assembly (enqueue_assemble_V_step).
+cudaError_t enqueue_predict(rafem_ctx* c, int which, bool fused = false) {
     if (!c->prm.predictor) return cudaSuccess;
     const bool V = which == RAFEM_SYS_V;
     if (V && projected_V(c)) {
-        ProjArgs a{};
-        a.n_tiles = c->n_tiles;
-        a.n_sub = c->proj_sub;
-        a.dw = c->dw ? 1 : 0;
-        a.tile_r0 = c->tile_r0;
-        a.tile_r1 = c->tile_r1;
-        a.tile_inst = c->tile_inst;
-        a.n_inst = c->n_inst;
-        a.inst_t0 = c->inst_t0;
-        a.inst_t1 = c->inst_t1;
-        a.sell = c->sell ? 1 : 0;
-        a.rp = c->rp;
-        a.ci = c->ci;
-        a.ci16 = c->ci16;
-        a.A = V ? c->valsV : c->valsT;
-        a.bc = V ? c->bcV : c->bcT;
-        a.b = V ? c->bV : c->bT;
-        a.x = V ? c->V : c->T;
-        a.kmax = c->proj_k;
-        a.partial = c->proj_partial;
-        a.coef = c->proj_coef;
-        a.kin = c->proj_kin;
-        a.kout = c->proj_kout;
-        a.D = c->proj_D;
-        a.Y = c->proj_Y;
-        a.r0 = c->proj_r0;
         c->r0_fresh = true;
-        return launch_projection(a, &c->stats->hist, 1, c->stream);
+        return fused ? launch_projection_rest(proj_args(c), false, c->stream)
+                     : launch_projection(proj_args(c), &c->stats->hist, 1, c->stream);
     }
     const int order = c->prm.predictor == RAFEM_PREDICT_PROJECT ? 2 : c->prm.predictor;
     if (V)
@@ -613,9 +636,10 @@ cudaError_t enqueue_step_io(rafem_ctx* c, const StepIO* io) {
     }
     k_begin_step<<<1, 128, 0, S>>>(c->stats, c->istats, c->n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    const bool fuse = fused_V(c) && !vin;  // the fused basis would have to wait for V before the assembly
+    if ((e = enqueue_assemble_V_step(c, fuse)) != cudaSuccess) return e;
     if (vin && (e = cudaStreamWaitEvent(S, c->io_ev[1], 0)) != cudaSuccess) return e;
-    if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
+    if ((e = enqueue_predict(c, RAFEM_SYS_V, fuse)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
     k_record<<<1, 128, 0, S>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -649,11 +673,11 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     nvtxRangePushA("Assembly");
     cudaEventRecord(c->ev[0], c->stream);
-    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_assemble_V_step(c, fused_V(c))) != cudaSuccess) return e;
     cudaEventRecord(c->ev[1], c->stream);
     nvtxRangePop();
     nvtxRangePushA("Predict");
-    if ((e = enqueue_predict(c, RAFEM_SYS_V)) != cudaSuccess) return e;
+    if ((e = enqueue_predict(c, RAFEM_SYS_V, fused_V(c))) != cudaSuccess) return e;
     cudaEventRecord(c->ev[6], c->stream);
     nvtxRangePop();
     nvtxRangePushA("Solve");

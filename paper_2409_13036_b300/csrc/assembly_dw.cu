@@ -53,12 +53,15 @@ __global__ void __launch_bounds__(kThreads) k_sigma_factor_dw(int E, const int32
 
 // Row i of A_V: off-diagonal a_ij = sum over the elements sharing edge (i, j) of sigma0_e G_e[ab] f_e, diagonal
 // = -(sum of the row's off-diagonals) (zero row sums of the stiffness), Dirichlet columns lifted into b_i.
+// kY: also (A D)_i for the projection predictor's basis D (4 float pairs per node, entries >= kin[0] zero), from
+// the same row of the lifted matrix (lifted columns excluded), so the predictor needs no pass over A.
+template <bool kY>
 __global__ void __launch_bounds__(kThreads) k_assemble_V_gather_dw(
     int N, const int32_t* __restrict__ sp, const int32_t* __restrict__ sc, const int32_t* __restrict__ diag,
     const int32_t* __restrict__ goff, const int32_t* __restrict__ gcnt, const float2* __restrict__ cval,
     const int32_t* __restrict__ celem, const float2* __restrict__ f, const uint8_t* __restrict__ bc,
     const double* __restrict__ g, double* __restrict__ vals, float* __restrict__ vals32, double* __restrict__ b,
-    int row_lift) {
+    int row_lift, const float4* __restrict__ D, float4* __restrict__ Y, const int32_t* __restrict__ kin) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= N) return;
     if (bc[row]) {
@@ -68,11 +71,19 @@ __global__ void __launch_bounds__(kThreads) k_assemble_V_gather_dw(
     const int s = row >> 5, lane = row & 31;
     const int base = __ldg(sp + s), w = (__ldg(sp + s + 1) - base) >> 5, q0 = base >> 5;
     const int dpos = __ldg(diag + row);
+    const bool wy = kY && *kin > 0;  // written by the previous launch
+    df y[4] = {dw::make(0.0f), dw::make(0.0f), dw::make(0.0f), dw::make(0.0f)};
     df dsum = dw::make(0.0f), lift = dw::make(0.0f);
     for (int k = 0; k < w; ++k) {
         const int pos = base + 32 * k + lane;
         const int P = __ldg(gcnt + q0 + k);
         if (P == 0 || pos == dpos) continue;
+        const int j = __ldg(sc + pos);
+        float4 dj0, dj1;
+        if (kY && wy) {  // the column's basis entries, loaded while its contributions are summed
+            dj0 = __ldg(D + 2 * j);
+            dj1 = __ldg(D + 2 * j + 1);
+        }
         const int off = __ldg(goff + q0 + k) + lane;
         df acc = dw::make(0.0f);
         // contributions in batches: coefficients and element ids, then the factor gathers, then the arithmetic,
@@ -94,17 +105,34 @@ __global__ void __launch_bounds__(kThreads) k_assemble_V_gather_dw(
                 if (ce[u] >= 0) acc = dw::add_fast(acc, dw::mul(dw::make(cv[u].x, cv[u].y), dw::make(fv[u].x, fv[u].y)));
         }
         dsum = dw::add(dsum, acc);
-        const int j = __ldg(sc + pos);
         if (j != row && bc[j] && !row_lift) {
             lift = dw::add(lift, dw::mul(acc, dw::split(g[j])));
         } else {
             vals[pos] = dw::to_double(acc);
             if (vals32) vals32[pos] = acc.h;
+            if (kY && wy) {
+                dw::dot_acc(y[0], acc, dw::make(dj0.x, dj0.y));
+                dw::dot_acc(y[1], acc, dw::make(dj0.z, dj0.w));
+                dw::dot_acc(y[2], acc, dw::make(dj1.x, dj1.y));
+                dw::dot_acc(y[3], acc, dw::make(dj1.z, dj1.w));
+            }
         }
     }
     vals[dpos] = -dw::to_double(dsum);
     if (vals32) vals32[dpos] = -dsum.h;
     b[row] = -dw::to_double(lift);
+    if (kY && wy) {
+        const df aii = dw::neg(dsum);
+        const float4 d0 = __ldg(D + 2 * row), d1 = __ldg(D + 2 * row + 1);
+        dw::dot_acc(y[0], aii, dw::make(d0.x, d0.y));
+        dw::dot_acc(y[1], aii, dw::make(d0.z, d0.w));
+        dw::dot_acc(y[2], aii, dw::make(d1.x, d1.y));
+        dw::dot_acc(y[3], aii, dw::make(d1.z, d1.w));
+#pragma unroll
+        for (int l = 0; l < 4; ++l) y[l] = dw::finish(y[l]);
+        Y[2 * row] = make_float4(y[0].h, y[0].l, y[1].h, y[1].l);
+        Y[2 * row + 1] = make_float4(y[2].h, y[2].l, y[3].h, y[3].l);
+    }
 }
 
 // Element pass of the thermal right-hand side: w_e = f_e sum_{a<b} q_ab (V_a - V_b)^2 + m_e sum_a T_old,a with
@@ -215,15 +243,22 @@ cudaError_t launch_fill_dw(const GatherDw& d, long long nc, const int32_t* celem
 cudaError_t launch_assemble_V_gather_dw(const GatherData& gd, const GatherDw& d, int N, const int32_t* sp,
                                         const int32_t* sc, const int32_t* diag, const ElemData& el, const double* T,
                                         double alpha, const uint8_t* bc, const double* g, double* vals, float* vals32,
-                                        double* b, int row_lift, cudaStream_t st) {
+                                        double* b, int row_lift, const double* D, double* Y, const int32_t* kin,
+                                        cudaStream_t st) {
     k_split_fields<<<blocks_for(N), kThreads, 0, st>>>(N, T, d.Ts, nullptr, nullptr, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     float2* f = reinterpret_cast<float2*>(gd.ework);
     k_sigma_factor_dw<<<blocks_for(el.E), kThreads, 0, st>>>(el.E, el.nodes, d.Ts, split_host(alpha), f);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_assemble_V_gather_dw<<<blocks_for(N), kThreads, 0, st>>>(N, sp, sc, diag, gd.goff, gd.gcnt, d.cval, gd.celem, f,
-                                                               bc, g, vals, vals32, b, row_lift);
+    if (D)
+        k_assemble_V_gather_dw<true><<<blocks_for(N), kThreads, 0, st>>>(
+            N, sp, sc, diag, gd.goff, gd.gcnt, d.cval, gd.celem, f, bc, g, vals, vals32, b, row_lift,
+            reinterpret_cast<const float4*>(D), reinterpret_cast<float4*>(Y), kin);
+    else
+        k_assemble_V_gather_dw<false><<<blocks_for(N), kThreads, 0, st>>>(
+            N, sp, sc, diag, gd.goff, gd.gcnt, d.cval, gd.celem, f, bc, g, vals, vals32, b, row_lift, nullptr, nullptr,
+            nullptr);
     return cudaGetLastError();
 }
 

@@ -48,10 +48,13 @@ struct GatherDw {
 };
 cudaError_t launch_fill_dw(const GatherDw& d, long long nc, const int32_t* celem, const uint8_t* cg,
                            const ElemData& el, double c_mass, cudaStream_t st);
+// With D non-null the assembly also accumulates Y = A D (the lifted matrix times the projection basis, 4
+// double-word entries per node) on free rows, when kin[0] > 0.
 cudaError_t launch_assemble_V_gather_dw(const GatherData& gd, const GatherDw& d, int N, const int32_t* sp,
                                         const int32_t* sc, const int32_t* diag, const ElemData& el, const double* T,
                                         double alpha, const uint8_t* bc, const double* g, double* vals, float* vals32,
-                                        double* b, int row_lift, cudaStream_t st);
+                                        double* b, int row_lift, const double* D, double* Y, const int32_t* kin,
+                                        cudaStream_t st);
 cudaError_t launch_rhs_T_gather_dw(const GatherData& gd, const GatherDw& d, int N, const ElemData& el,
                                    const double* T_sigma, const double* T_old, const double* V, const uint8_t* bc,
                                    const double* g, const double* bconst, double alpha, double* b, cudaStream_t st);
@@ -354,5 +357,9 @@ struct ProjArgs {
 };
 // hist: steps completed (device); lag: 1 when the initial field is not a solution (potential), 0 otherwise.
 cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);
+// The same in two parts: the basis sizes and the basis (before the assembly when the assembly computes Y = A D),
+// then [Y = A D if apply], the sums, the small solve and the guess with its residual.
+cudaError_t launch_projection_basis(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);
+cudaError_t launch_projection_rest(const ProjArgs& a, bool apply, cudaStream_t st);
 
 }  // namespace rafem

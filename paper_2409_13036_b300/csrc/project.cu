@@ -15,7 +15,8 @@
 // differentiation form's checkpoints) as the predictor's history: K - 1 subtractions per node.
 //
 // Launches per solve, per problem instance of a batch (the solver's work tiles never straddle instances), all
-// compiled for the context's basis limit K (2, 4, 6 or 8):
+// compiled for the context's basis limit K (2, 4, 6 or 8); with the double-word gather assembly and K = 4 the
+// basis is built before the potential's assembly, which accumulates Y = A D itself, and k_proj_apply is skipped:
 //   k_proj_count:   one thread: the basis size of every instance;
 //   k_proj_basis:   the basis D at every node from the solution and the previous basis (K 8-byte entries each);
 //   k_proj_apply:   Y = A D, one pass over A (SELL-32 or CSR), entries in batches;
@@ -436,12 +437,18 @@ __global__ void __launch_bounds__(kThreads) k_proj_combine(ProjArgs a) {
 }
 
 template <class Ar, int K>
-cudaError_t launch_passes(const ProjArgs& a, int grid, cudaStream_t st) {
-    cudaError_t e;
+cudaError_t launch_basis(const ProjArgs& a, int grid, cudaStream_t st) {
     k_proj_basis<Ar, K><<<grid, kThreads, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_proj_apply<Ar, K, K <= 4 ? 3 : 2><<<grid, kThreads, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <class Ar, int K>
+cudaError_t launch_rest(const ProjArgs& a, int grid, bool apply, cudaStream_t st) {
+    cudaError_t e;
+    if (apply) {
+        k_proj_apply<Ar, K, K <= 4 ? 3 : 2><<<grid, kThreads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_proj_gram<Ar, K><<<grid, kThreads, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_proj_solve<Ar, K><<<a.n_inst, kSolveThreads, 0, st>>>(a);
@@ -450,25 +457,50 @@ cudaError_t launch_passes(const ProjArgs& a, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+int grid_of(const ProjArgs& a) {
+    const long long nch = (long long)a.n_tiles * a.n_sub;
+    return (int)(nch < 148 * 32 ? nch : 148 * 32);
+}
+
 template <class Ar>
-cudaError_t launch_sized(const ProjArgs& a, int grid, cudaStream_t st) {
+cudaError_t sized_basis(const ProjArgs& a, cudaStream_t st) {
+    const int g = grid_of(a);
     switch (proj_stride(a.kmax)) {
-        case 2: return launch_passes<Ar, 2>(a, grid, st);
-        case 4: return launch_passes<Ar, 4>(a, grid, st);
-        case 6: return launch_passes<Ar, 6>(a, grid, st);
-        default: return launch_passes<Ar, 8>(a, grid, st);
+        case 2: return launch_basis<Ar, 2>(a, g, st);
+        case 4: return launch_basis<Ar, 4>(a, g, st);
+        case 6: return launch_basis<Ar, 6>(a, g, st);
+        default: return launch_basis<Ar, 8>(a, g, st);
+    }
+}
+
+template <class Ar>
+cudaError_t sized_rest(const ProjArgs& a, bool apply, cudaStream_t st) {
+    const int g = grid_of(a);
+    switch (proj_stride(a.kmax)) {
+        case 2: return launch_rest<Ar, 2>(a, g, apply, st);
+        case 4: return launch_rest<Ar, 4>(a, g, apply, st);
+        case 6: return launch_rest<Ar, 6>(a, g, apply, st);
+        default: return launch_rest<Ar, 8>(a, g, apply, st);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st) {
+cudaError_t launch_projection_basis(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st) {
     k_proj_count<<<1, 32, 0, st>>>(a, hist, lag);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long nch = (long long)a.n_tiles * a.n_sub;
-    const int grid = (int)(nch < 148 * 32 ? nch : 148 * 32);
-    return a.dw ? launch_sized<ArithDW>(a, grid, st) : launch_sized<ArithF64>(a, grid, st);
+    return a.dw ? sized_basis<ArithDW>(a, st) : sized_basis<ArithF64>(a, st);
+}
+
+cudaError_t launch_projection_rest(const ProjArgs& a, bool apply, cudaStream_t st) {
+    return a.dw ? sized_rest<ArithDW>(a, apply, st) : sized_rest<ArithF64>(a, apply, st);
+}
+
+cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st) {
+    cudaError_t e = launch_projection_basis(a, hist, lag, st);
+    if (e != cudaSuccess) return e;
+    return launch_projection_rest(a, true, st);
 }
 
 }  // namespace rafem
