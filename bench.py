@@ -174,13 +174,15 @@ def _ncu_traffic(kernel: str):
     return e
 
 
-def alg_bytes_cg64(N: int, nnz: int, iters: float, col_bytes: int) -> float:
+def alg_bytes_cg64(N: int, nnz: int, iters: float, col_bytes: int, given_r0: bool = True) -> float:
     """Algorithmic HBM bytes of one FP64 Chronopoulos-Gear Jacobi-PCG solve launch (stored format).
     Per iteration: SpMV w = A u streams (8 + col_bytes) B per nonzero (value + column index) and reads u once and
     writes w (16N); the vector phase reads u, w, p, s, x, r, dinv and writes p, s, x, r, u (96N). Start-up
-    (r = b - Ax, u, w = Au) and the final true-residual SpMV add two more iterations' worth."""
+    (r = b - Ax, u, w = Au) and the final true-residual SpMV add two more iterations' worth. given_r0: the
+    projection predictor handed over the starting residual (every step with history), so the start-up reads it
+    (8N, in place of the x gather) instead of streaming the matrix."""
     per_iter = (8 + col_bytes) * nnz + 16 * N + 96 * N
-    return (iters + 2) * per_iter
+    return (iters + 2) * per_iter - (given_r0 * (8 + col_bytes) * nnz)
 
 
 def alg_bytes_pipecg(N: int, nnz: int, iters: float, col_bytes: int) -> float:
@@ -192,15 +194,17 @@ def alg_bytes_pipecg(N: int, nnz: int, iters: float, col_bytes: int) -> float:
     return (iters + 3) * per_iter
 
 
-def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_bytes: int) -> float:
+def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_bytes: int,
+                    given_r0: bool = True) -> float:
     """Algorithmic HBM bytes of one mixed-precision solve launch (stored format).
     Inner FP32 iteration: SpMV (4 + col_bytes) B per nonzero + 8N (u read, w written); vector phase 12 x 4N.
     Each FP64 refinement: x64 += d32 (8N + 4N read, 8N written), the FP64 residual SpMV ((8 + col_bytes) B per
     nonzero + 8N x + 8N b) writing r32, u32, d32 (12N) and reading dinv32 (4N), and the FP32 start SpMV
-    ((4 + col_bytes) B per nonzero + 8N)."""
+    ((4 + col_bytes) B per nonzero + 8N). given_r0: the first residual was handed over by the projection
+    predictor (every step with history) and is read (8N, in place of the x gather) instead of computed."""
     inner = (4 + col_bytes) * nnz + 8 * N + 48 * N
     outer = (20 * N) + ((8 + col_bytes) * nnz + 16 * N + 16 * N) + ((4 + col_bytes) * nnz + 8 * N)
-    return iters * inner + (refinements + 1) * outer
+    return iters * inner + (refinements + 1) * outer - (given_r0 * (8 + col_bytes) * nnz)
 
 
 def alg_bytes_ilu(Np: int, nnz_p: int, iters: float) -> float:
