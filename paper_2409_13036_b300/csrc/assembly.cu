@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
     if (ep >= e1) return;
     const int e = list ? __ldg(list + ep) : ep;  // storage index of the element
     const size_t E = (size_t)el.E;
-    // round 1: element data
+    // load stage 1: element data
     int n[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) n[a] = __ldg(el.nodes + a * E + e);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
     for (int q = 0; q < 10; ++q) Ge[q] = __ldg(el.G + q * E + e);
     const double own = MODE == 0 ? __ldg(el.sigma0 + e) : __ldg(el.k + e);
     const double vol = MODE == 1 ? __ldg(el.vol + e) : 0.0;
-    // round 2: nodal gathers
+    // load stage 2: nodal gathers
     bool d[4];
     double tn[4] = {0.0, 0.0, 0.0, 0.0}, gn[4];
 #pragma unroll
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(ElemData el, int e0, int 
         mdiag = 2.0 * moff;
         rhs_const = coef_b * vol * 0.25;
     }
-    // round 3: previous values of the slots this element accumulates into
+    // load stage 3: previous values of the slots this element accumulates into
     double old[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {

@@ -1199,9 +1199,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
                     st.gprev32 = gamma;
                     st.aprev32 = st.alpha32;
                     // the inner solve stops at inner_tol, or once the predicted outer residual
-                    // ||r64|| * ||r32|| / ||r32_0|| is a quarter of the outer tolerance
+                    // ||r64|| * ||r32|| / ||r32_0|| reaches the outer tolerance (a stricter margin only adds
+                    // FP32 iterations: the next FP64 residual decides convergence either way)
                     const double bb = st.bb > 0.0 ? st.bb : 1.0;
-                    st.thr32 = (float)(fmax(itol2, 0.0625 * tol2 * bb / fmax(st.rr0, 1e-300)) * st.rr_in0);
+                    st.thr32 = (float)(fmax(itol2, tol2 * bb / fmax(st.rr0, 1e-300)) * st.rr_in0);
                     st.outer = ST_ITER;
                 }
             } else {
