@@ -283,6 +283,28 @@ def advance(model: "Model", duration, dt_min, T0=None):
 
 
 # ----------------------------------------------------------------------------------------------------------
+# Initial guess by projection (an extension of the predictor step of the main loop, Sec. II-A)
+# ----------------------------------------------------------------------------------------------------------
+
+def projection_guess(A, b, X, free):
+    """The element of span(X) closest to the solution of the SPD system A x = b in the A-norm, on the free rows.
+
+    Minimising (x - x*)^T A (x - x*) over x = X c gives the Galerkin condition X^T (b - A X c) = 0, solved here
+    with an orthonormal basis Q of span(X) from numpy's QR (the span, not the basis, defines the result):
+    (Q^T A Q) y = Q^T b, x = Q y. Rows outside `free` (the identity rows of the lifted system) keep the values
+    of the newest column X[:, 0]. A and b are the lifted system, X holds the past solutions as columns.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    free = np.asarray(free, dtype=bool)
+    Q, _ = np.linalg.qr(X[free])
+    Aff = sp.csr_matrix(A)[free][:, free]
+    y = np.linalg.solve(Q.T @ (Aff @ Q), Q.T @ np.asarray(b, dtype=np.float64)[free])
+    x0 = X[:, 0].copy()
+    x0[free] = Q @ y
+    return x0
+
+
+# ----------------------------------------------------------------------------------------------------------
 # Quality metrics (Sec. IV)
 # ----------------------------------------------------------------------------------------------------------
 

@@ -402,6 +402,33 @@ def test_larger_projection_basis_saves_iterations():
     assert iters[8] < iters[4], iters
 
 
+@pytest.mark.parametrize("basis", [2, 4])
+def test_projection_guess_matches_oracle(basis):
+    """The potential's initial guess equals the oracle's A-norm projection of the same system onto the same past
+    solutions (the oracle's own, from its direct solves) to 1e-8: a solve whose tolerance accepts any residual
+    returns the guess unchanged. Guesses from neighbouring basis sizes differ by 2e-6 (3 vs 4) to 4e-5 (2 vs 4) on
+    this run, so the bound also checks which solutions the basis holds: after six steps the last min(basis, 5)
+    (the first solve never enters the basis)."""
+    rafem = R()
+    m = mg.cube_mesh(10, jitter=0.1, seed=64, sigma0="lognormal")
+    model = O.Model(m, O.Params(dt=5.0))
+    T_ref, V_ref = model.run(6)
+    with rafem.Context(m, tol=1e-13, dt=5.0, proj_basis=basis, precision=rafem.RAFEM_PRECISION_FP64) as ctx:
+        s, _ = ctx.run(6)
+        assert s == 0
+        assert O.rel_err(ctx.get_field(rafem.RAFEM_SYS_T), T_ref[5]) <= 1e-9
+        ctx.set_tol(1e100)
+        s, st = ctx.solve_step()
+        assert s == 0 and st.iters_V == 0
+        guess = ctx.get_field(rafem.RAFEM_SYS_V)
+    k = min(basis, 5)
+    X = np.stack([V_ref[5 - j] for j in range(k)], axis=1)
+    A, b = model.system_V(T_ref[5])
+    x0 = O.projection_guess(A, b, X, ~m.bc_V.astype(bool))
+    assert O.rel_err(guess, x0) <= 1e-8
+    assert O.rel_err(guess, O.solve(A, b)) > 1e-8  # a guess, not the solution
+
+
 @pytest.mark.parametrize("pinned", [False, True])
 def test_step_host_equals_device_steps(pinned):
     """rafem_step_host (state in and out of host buffers, copies overlapped with the step on a second stream)

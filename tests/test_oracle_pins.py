@@ -439,3 +439,56 @@ def test_coupled_jacobian_matches_central_differences_and_newton_reaches_the_fix
     for a, b in zip(hist[1:-1], hist[2:]):
         if a < 1e-2:
             assert b <= 10.0 * a * a
+
+
+def _projection_case(seed=0):
+    m = mg.cube_mesh(6, jitter=0.1, seed=5, sigma0="lognormal")
+    model = O.Model(m)
+    rng = np.random.default_rng(seed)
+    T = np.where(m.bc_T.astype(bool), m.g_T, 37.0 + 10.0 * rng.random(m.n_nodes))
+    A, b = model.system_V(T)
+    free = ~m.bc_V.astype(bool)
+    xs = O.solve(A, b)
+    return m, A, b, free, xs, rng
+
+
+def _a_err(A, free, x, xs):
+    e = (x - xs)[free]
+    return float(e @ (sp.csr_matrix(A)[free][:, free] @ e))
+
+
+def test_projection_guess_exact_when_the_solution_is_in_the_span():
+    """With the exact solution among the columns, the projection returns it (the other columns get no weight)."""
+    m, A, b, free, xs, rng = _projection_case()
+    other = np.where(free, rng.standard_normal(m.n_nodes), xs)
+    for X in (np.stack([xs, other], axis=1), np.stack([xs, 0.5 * xs + other, other - xs], axis=1)):
+        np.testing.assert_allclose(O.projection_guess(A, b, X, free), xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+
+
+def test_projection_guess_minimises_the_energy_error():
+    """Brute force: no other combination of the columns is closer to the solution in the A-norm, and a single
+    column gives the closed form x = (x1^T b / x1^T A x1) x1 on the free rows."""
+    m, A, b, free, xs, rng = _projection_case(1)
+    X = np.stack([np.where(free, xs + 0.05 * rng.standard_normal(m.n_nodes) * np.abs(xs).max(), xs)
+                  for _ in range(3)], axis=1)
+    x0 = O.projection_guess(A, b, X, free)
+    e0 = _a_err(A, free, x0, xs)
+    c0 = np.linalg.lstsq(X[free], x0[free], rcond=None)[0]
+    for _ in range(300):
+        c = c0 + 1e-3 * rng.standard_normal(3) * np.abs(c0).max()
+        assert _a_err(A, free, np.where(free, X @ c, xs), xs) >= e0
+    x1 = X[:, :1]
+    Aff = sp.csr_matrix(A)[free][:, free]
+    alpha = (x1[free, 0] @ b[free]) / (x1[free, 0] @ (Aff @ x1[free, 0]))
+    np.testing.assert_allclose(O.projection_guess(A, b, x1, free)[free], alpha * x1[free, 0], rtol=1e-12)
+
+
+def test_projection_guess_depends_only_on_the_span():
+    """Raw past solutions and their backward differences (the same span) give the same guess on the free rows."""
+    m, A, b, free, xs, rng = _projection_case(2)
+    X = np.stack([np.where(free, xs * (1.0 + 0.02 * j) + 0.01 * rng.standard_normal(m.n_nodes), xs)
+                  for j in range(4)], axis=1)
+    D = np.stack([X[:, 0], X[:, 0] - X[:, 1], X[:, 0] - 2 * X[:, 1] + X[:, 2],
+                  X[:, 0] - 3 * X[:, 1] + 3 * X[:, 2] - X[:, 3]], axis=1)
+    np.testing.assert_allclose(O.projection_guess(A, b, D, free)[free], O.projection_guess(A, b, X, free)[free],
+                               rtol=0, atol=1e-11 * np.abs(xs).max())
