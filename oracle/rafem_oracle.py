@@ -22,6 +22,10 @@ with the consistent P1 mass matrix M. An optional fixed-point corrector re-evalu
 temperature iterate (the corrector passes of the main loop, Sec. II-A; at most 50 passes, Sec. IV).
 
 The PSNR quality metric follows Sec. IV, Eq. 1 and Eq. 2, read as 20*log10(MAX(A)/sqrt(MSE_i)).
+
+Beyond the paper's loop it also provides what the library's extensions are checked against: the A-norm
+projection that serves as the potential's initial guess (projection_guess), the tangent-linear step and a dense
+adjoint for the gradients, ILU(0), reverse Cuthill-McKee, the adaptive step rules and the coupled Newton step.
 """
 from __future__ import annotations
 
