@@ -1,0 +1,56 @@
+"""Host logic of bench.py (no GPU): the roofline object built from a launch's statistics, the traffic figure
+taken from the committed ncu summary only while the kernel's source is unchanged, and the byte formulas."""
+import json
+
+import pytest
+
+import bench
+
+
+def _res(iters=50.0, ms=3.0, refine=1.0):
+    N, nnz = 2_097_152, 31_065_598
+    return {"N": N, "nnz": nnz,
+            "trace": {"steps": 10, "ms_solve_V": 10 * ms, "iters_V": 10 * iters, "refine_V": 10 * refine},
+            "layout": {"column_bytes": 2, "kernel_code": 2, "nnz_stored": nnz}}
+
+
+def test_roofline_divides_algorithmic_bytes_by_the_launch_time():
+    peaks = {"hbm_gbs": 6500.0}
+    r = bench.roofline(_res(), True, peaks, "measured")
+    alg = bench.alg_bytes_mixed(2_097_152, 31_065_598, 50.0, 1.0, 2)
+    assert r["alg_bytes_per_launch"] == pytest.approx(alg)
+    assert r["achieved"] == pytest.approx(alg / 3.0e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6500.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and "of measured" in r["peak_kind"]
+    f = bench.roofline(_res(iters=40.0, ms=6.0, refine=0.0), False, peaks, "fallback")
+    assert f["kernel"].startswith("k_cg64") and "of fallback" in f["peak_kind"] and f["fp64_pipe"]["bound"] == "alu"
+
+
+def test_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The committed DRAM-per-algorithmic-byte ratio scales the launch's bytes while the source hash matches;
+    any other source gives null."""
+    src = tmp_path / "paper_2409_13036_b300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "krylov.cu").write_text("// kernel source\n")
+    (tmp_path / "profiles").mkdir()
+    entry = {"source": "krylov.cu", "source_sha256": bench._source_hash(str(src / "krylov.cu")),
+             "dram_per_alg_byte": 0.6}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"k_cg_mixed<2>": entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    r = bench.roofline(_res(), True, {"hbm_gbs": 6500.0}, "measured")
+    assert r["traffic"] == pytest.approx(0.6 * r["alg_bytes_per_launch"])
+    (src / "krylov.cu").write_text("// kernel source, changed\n")
+    assert bench.roofline(_res(), True, {"hbm_gbs": 6500.0}, "measured")["traffic"] is None
+
+
+def test_handed_over_residual_saves_one_matrix_stream():
+    """A residual handed over by the projection replaces the first FP64 residual SpMV: (8 + column bytes) per
+    nonzero less, in both CG byte counts."""
+    N, nnz = 1000, 15000
+    for cb in (2, 4):
+        assert (bench.alg_bytes_mixed(N, nnz, 30, 1, cb, given_r0=False) - bench.alg_bytes_mixed(N, nnz, 30, 1, cb)
+                == (8 + cb) * nnz)
+        assert (bench.alg_bytes_cg64(N, nnz, 30, cb, given_r0=False) - bench.alg_bytes_cg64(N, nnz, 30, cb)
+                == (8 + cb) * nnz)
+    # one more inner iteration streams the FP32 matrix once more
+    assert bench.alg_bytes_mixed(N, nnz, 31, 1, 2) - bench.alg_bytes_mixed(N, nnz, 30, 1, 2) == 6 * nnz + 56 * N
