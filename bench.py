@@ -92,6 +92,88 @@ def _oracle_sample(n: int, steps: int) -> dict:
     return {"n": n, "nodes": m.n_nodes, "times": times}
 
 
+def _host_info() -> dict:
+    """The host the CPU baseline ran on: logical CPUs and the CPU model (Linux /proc/cpuinfo)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "oracle_threads": 1}
+
+
+def _oracle_stream(which: str, steps: int) -> None:
+    """Time the FP64 oracle on one of the named workloads, printing one JSON line per phase as it completes (the
+    parent may stop the child after any line): the set-up (mesh-constant geometry, mass and thermal matrices),
+    then each time step (the first also factors the constant thermal matrix, kept for the later steps)."""
+    from oracle import rafem_oracle as O
+    from paper_2409_13036_b300 import meshgen as mg
+    import numpy as np
+    m = mg.workload_48() if which == "c2_48" else mg.workload_single_step_8()
+    t0 = time.perf_counter()
+    model = O.Model(m)
+    print(json.dumps({"phase": "setup", "s": time.perf_counter() - t0, "nodes": m.n_nodes}), flush=True)
+    T = np.full(m.n_nodes, 37.0)
+    for k in range(steps):
+        t0 = time.perf_counter()
+        T, V, _ = model.step(T)
+        print(json.dumps({"phase": "step", "k": k + 1, "s": time.perf_counter() - t0}), flush=True)
+
+
+class OracleTimer:
+    """The oracle timed in a child process (one thread, spawned by exec: no CUDA state is inherited) while the
+    parent runs its GPU legs; lines are collected by a reader thread."""
+
+    def __init__(self, which: str, steps: int):
+        import threading
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        code = ("import sys; sys.path.insert(0, %r); import bench; bench._oracle_stream(%r, %d)"
+                % (ROOT, which, steps))
+        self.which, self.steps = which, steps
+        self.t_start = time.perf_counter()
+        self.proc = subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                     stderr=subprocess.DEVNULL, text=True, env=env, cwd=ROOT)
+        self.lines = []
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            try:
+                self.lines.append(json.loads(line))
+            except ValueError:
+                pass
+
+    def finish(self, min_steps: int, max_wait_s: float) -> dict:
+        """Wait until min_steps steps are timed (or the child ends, or max_wait_s since the start), then stop it."""
+        while True:
+            done = sum(1 for x in self.lines if x.get("phase") == "step")
+            if done >= min_steps or self.proc.poll() is not None:
+                break
+            if time.perf_counter() - self.t_start > max_wait_s:
+                break
+            time.sleep(0.5)
+        if self.proc.poll() is None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.proc.wait()
+        self.reader.join(timeout=5)
+        setup = next((x for x in self.lines if x.get("phase") == "setup"), None)
+        steps = [x["s"] for x in self.lines if x.get("phase") == "step"]
+        return {"setup_s": setup["s"] if setup else None, "nodes": setup["nodes"] if setup else None,
+                "step_s": steps}
+
+
 def run_oracle_subprocess(n: int, steps: int) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -239,6 +321,32 @@ def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: in
     return steps * per_step + max(cycles, 1.0) * per_cycle
 
 
+def cpu_baseline_line(t: dict, c1: dict | None, small: dict | None) -> dict:
+    """The cpu_baseline object: the oracle's steps/s on the 48^3 workload (117,649 nodes, jitter 10%, 60 steps at
+    dt = 1 s to relative residual 1e-10 in its configuration) from the steps timed, with the 60-step run
+    extrapolated, the 8^3 single-step workload beside it, and the GPU's steps/s on the same 48^3 workload."""
+    steps = t["step_s"]
+    if not steps:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_info(),
+                "sample": "the 48^3 oracle timing did not complete a step within the wait", "c1_8": c1}
+    later = steps[1:] or steps
+    value = len(later) / sum(later)
+    run60 = (t["setup_s"] or 0.0) + steps[0] + 59 * (sum(later) / len(later))
+    out = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_info(),
+           "config": "48^3 cells, 117,649 nodes, 663,552 tets, jitter 10% (the 60-step FP64 workload)",
+           "sample": (f"FP64 oracle (own assembly + SuperLU direct solves, 1 thread) on the 48^3 workload: set-up "
+                      f"and the first {len(steps)} steps timed; value = steps/s over steps 2..{len(steps)} (step 1 "
+                      f"also factors the constant thermal matrix); the 60-step run extrapolated as set-up + step 1 "
+                      f"+ 59 x the mean later step"),
+           "setup_s": t["setup_s"], "step_s": steps, "extrapolated_60_step_run_s": run60}
+    if c1:
+        out["c1_8"] = c1
+    if small and "fp64_cg" in small:
+        out["gpu_same_config_steps_per_s"] = {k: small[k]["steps_per_s"] for k in ("fp64_cg", "mixed")
+                                              if k in small}
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -254,7 +362,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "oracle_sample_cells": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": _host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -351,11 +460,13 @@ def roofline(res, mixed, peaks, peak_kind):
     if nc:
         # DRAM bytes of one ncu capture (smaller case of the same workload), scaled by algorithmic bytes
         traffic = nc["dram_per_alg_byte"] * alg
+    dram = traffic / (solve_ms * 1e-3) / 1e9 if traffic else None
     return {"bound": "hbm", "kernel": f"{kern} (potential-system persistent solver, one launch per step)",
             "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "peak_kind": ("measured copy bandwidth, MEASURED_PEAKS.json hbm_gbs (of measured)"
                           if peak_kind == "measured" else "fallback 6.4 TB/s (of fallback)"),
             "traffic": traffic,
+            "dram_achieved": dram, "dram_frac": dram / peaks["hbm_gbs"] if dram else None,
             "traffic_note": ("ncu DRAM read+write of the 112^3 capture scaled by algorithmic bytes" if traffic else
                              "no ncu capture for the current source"),
             "launch_ms": solve_ms, "iters_per_launch": iters, "refinements_per_launch": ref,
@@ -499,17 +610,21 @@ def measure_adjoint(rafem, torch, mg, args):
 
 
 def measure_accuracy(rafem, torch, mesh, args):
-    """Tolerance sweep and long-run parity on the headline workload: the mixed path at relative residuals 1e-6,
-    1e-8, 1e-10 and 1e-12 against the FP64 path at 1e-12 over the first `accuracy_steps` steps of the run
-    (default 900, the paper's 15 simulated minutes), with the relative L2 differences of T and V and the PSNR of T
-    (Eq. 1-2: the peak over the whole run) every 100 steps."""
+    """Accuracy over the paper's run (Sec. IV: per-step error and PSNR, Eq. 1-2, against a reference run) on the
+    headline workload, every 100 steps of the first `accuracy_steps` (default 900, 15 simulated minutes). The
+    reference is the tightest run the library can make: FP64 Krylov, FP64 element and node passes, relative
+    residual 1e-13. Against it: the mixed path at relative residuals 1e-6 ... 1e-12 (the tolerance sweep), the
+    FP64 path (double-word element passes, the default) at 1e-10, the FP64 path with FP64 element passes at 1e-10,
+    and the double-word FP64 path at 1e-13 (which isolates the element-pass arithmetic from the solver tolerance).
+    Reported per arm: relative L2 differences of T and V, PSNR of T (peak over the reference run) and the arm's
+    steps/s over the run (host-synchronised every 100 steps)."""
     import numpy as np
     n = args.accuracy_steps
     marks = list(range(100, n, 100)) + [n]
     stream = torch.cuda.Stream()
 
     def trajectory(ctx):
-        Ts, Vs, done, t_run, iters = [], [], 0, 0.0, 0
+        Ts, Vs, done, t_run, worst = [], [], 0, 0.0, 0
         ctx.reset()
         for m in marks:
             torch.cuda.synchronize()
@@ -517,30 +632,60 @@ def measure_accuracy(rafem, torch, mesh, args):
             s, st = ctx.run(m - done)
             torch.cuda.synchronize()
             t_run += time.perf_counter() - t0
-            if s < 0:
-                raise RuntimeError(rafem.status_string(s))
+            worst = max(worst, s)
             done = m
             Ts.append(ctx.get_field(rafem.RAFEM_SYS_T))
             Vs.append(ctx.get_field(rafem.RAFEM_SYS_V))
-        return Ts, Vs, n / t_run
+        return Ts, Vs, n / t_run, rafem.status_string(worst)
 
-    ref = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_FP64, tol=1e-12)
-    Tr, Vr, ref_rate = trajectory(ref)
+    ref = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_FP64, tol=1e-13,
+                        arith=rafem.RAFEM_ARITH_FP64)
+    Tr, Vr, ref_rate, ref_status = trajectory(ref)
     ref.close()
     peak = max(float(T.max()) for T in Tr)
-    out = {"steps": n, "reference": {"precision": "fp64", "tol": 1e-12, "steps_per_s": ref_rate},
-           "marks": marks, "mixed": []}
+    out = {"steps": n, "marks": marks,
+           "reference": {"precision": "fp64", "element_arith": "fp64", "tol": 1e-13, "steps_per_s": ref_rate,
+                         "status": ref_status}}
+
+    def compare(Ta, Va):
+        eT = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Ta, Tr)]
+        eV = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Va, Vr)]
+        psnr = [float(20 * np.log10(peak / np.sqrt(max(float(np.mean((a - b) ** 2)), 1e-300))))
+                for a, b in zip(Ta, Tr)]
+        return {"rel_err_T_max": max(eT), "rel_err_V_max": max(eV), "psnr_T_db_min": min(psnr), "rel_err_T": eT,
+                "rel_err_V": eV}
+
+    out["mixed"] = []
     ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_MIXED)
     for tol in (1e-6, 1e-8, 1e-10, 1e-12):
         ctx.set_tol(tol)
-        Tm, Vm, rate = trajectory(ctx)
-        eT = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Tm, Tr)]
-        eV = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(Vm, Vr)]
-        psnr = [float(20 * np.log10(peak / np.sqrt(max(float(np.mean((a - b) ** 2)), 1e-300)))) for a, b in zip(Tm, Tr)]
-        out["mixed"].append({"tol": tol, "steps_per_s": rate, "rel_err_T_max": max(eT), "rel_err_V_max": max(eV),
-                             "psnr_T_db_min": min(psnr), "rel_err_T": eT, "rel_err_V": eV})
+        Tm, Vm, rate, status = trajectory(ctx)
+        out["mixed"].append({"tol": tol, "steps_per_s": rate, "status": status, **compare(Tm, Vm)})
     ctx.close()
+    out["fp64"] = []
+    for name, tol, arith in (("fp64 double-word elements", 1e-10, rafem.RAFEM_ARITH_DW),
+                             ("fp64 FP64 elements", 1e-10, rafem.RAFEM_ARITH_FP64),
+                             ("fp64 double-word elements", 1e-13, rafem.RAFEM_ARITH_DW)):
+        ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=rafem.RAFEM_PRECISION_FP64, tol=tol,
+                            arith=arith)
+        Tf, Vf, rate, status = trajectory(ctx)
+        ctx.close()
+        out["fp64"].append({"arm": name, "tol": tol, "steps_per_s": rate, "status": status, **compare(Tf, Vf)})
     return out
+
+
+def accuracy_headline(acc: dict) -> dict:
+    """The accuracy figures the headline is quoted beside: mixed and FP64 at the configured 1e-10, and the
+    double-word element passes against FP64 ones (both at 1e-13), each against the tight FP64 reference."""
+    keys = ("rel_err_T_max", "rel_err_V_max", "psnr_T_db_min", "steps_per_s", "status")
+    pick = lambda d: {k: d[k] for k in keys}
+    mixed = next(d for d in acc["mixed"] if d["tol"] == 1e-10)
+    fp64 = next(d for d in acc["fp64"] if d["tol"] == 1e-10 and d["arm"] == "fp64 double-word elements")
+    fp64a = next(d for d in acc["fp64"] if d["tol"] == 1e-10 and d["arm"] == "fp64 FP64 elements")
+    dw = next(d for d in acc["fp64"] if d["tol"] == 1e-13)
+    return {"reference": acc["reference"], "steps": acc["steps"],
+            "mixed_tol_1e-10": pick(mixed), "fp64_tol_1e-10": pick(fp64), "fp64_fp64_elements_tol_1e-10": pick(fp64a),
+            "double_word_vs_fp64_elements_tol_1e-13": pick(dw)}
 
 
 def measure_small(rafem, torch, mg, args):
@@ -635,6 +780,9 @@ def main():
     ap.add_argument("--cells", type=int, default=127)
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0 = the timed K steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps timed on the 48^3 workload")
+    ap.add_argument("--cpu-wait", type=float, default=900.0,
+                    help="seconds after its start at which the 48^3 oracle timing is stopped")
     ap.add_argument("--only", choices=["fp64", "mixed", "ilu0", "bicgstab", "gmres", "pipecg"], default=None,
                     help="run one solver configuration only")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batching form (0 = skip)")
@@ -659,15 +807,15 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
-    # CPU baseline first, in a child process (no CUDA context in this process yet)
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        res = run_oracle_subprocess(ORACLE_SAMPLE_N, ORACLE_SAMPLE_STEPS)
-        t = res["times"][1:]  # the first step also factors the constant thermal matrix
-        cpu = {"value": len(t) / sum(t), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"{len(t)} time steps of the FP64 oracle (own assembly + SuperLU, 1 thread) on the "
-                          f"{ORACLE_SAMPLE_N}^3-cell instance ({res['nodes']} nodes) of the same workload; "
-                          f"not extrapolated (direct LU cost grows superlinearly)")}
+    # CPU baseline: the FP64 oracle on the host, one thread. The 8^3 single-step workload is timed whole, first,
+    # in a child process (no CUDA context in this process yet); the 48^3 workload (configs' 60-step FP64 case)
+    # is timed in a child that runs while the GPU legs after the headline run, and is collected at the end.
+    cpu_c1 = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = OracleTimer("c1_8", 1).finish(1, 120.0)
+        if t["step_s"]:
+            cpu_c1 = {"steps_per_s": 1.0 / t["step_s"][0], "setup_s": t["setup_s"], "step_s": t["step_s"],
+                      "nodes": t["nodes"], "workload": "8^3 cells (729 nodes, 3,072 tets), no jitter, one step"}
 
     import numpy as np
     import torch
@@ -764,6 +912,11 @@ def main():
         ctx.step_host_ptr(*ptrs)
     t_e2e = reduce_over_ranks([time.perf_counter() - t0], "max", dist)[0]
     ctx.close()
+    # the 48^3 oracle timing runs on a host core from here on, beside the remaining GPU legs (the timed headline
+    # and end-to-end regions above are over)
+    c2_timer = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
+        c2_timer = OracleTimer("c2_48", args.cpu_steps)
 
     def summary(r):
         tr = r["trace"]
@@ -821,8 +974,6 @@ def main():
     if "fp64_ilu0" in runs:
         line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
         line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]
-    if cpu is not None:
-        line["cpu_baseline"] = cpu
     if args.batch_steps > 0 and args.only is None and args.cells == 127:
         try:
             line["batch"] = measure_batch(rafem, torch, mg, args, dist)
@@ -836,6 +987,7 @@ def main():
     if args.accuracy_steps > 0 and args.only is None:
         try:
             line["accuracy"] = measure_accuracy(rafem, torch, mesh, args)
+            line["accuracy_headline"] = accuracy_headline(line["accuracy"])
         except Exception as exc:
             line["accuracy"] = {"error": repr(exc)[:300]}
     if args.monolithic_steps > 0 and args.only is None:
@@ -853,6 +1005,9 @@ def main():
             line["adjoint"] = measure_adjoint(rafem, torch, mg, args)
         except Exception as exc:
             line["adjoint"] = {"error": repr(exc)[:300]}
+    if c2_timer is not None:
+        t = c2_timer.finish(args.cpu_steps, args.cpu_wait)
+        line["cpu_baseline"] = cpu_baseline_line(t, cpu_c1, line.get("small_48"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -42,7 +42,8 @@ extern "C" {
 #define RAFEM_ERR_BAD_MESH      -2   /* a tetrahedron with non-positive volume                                  */
 #define RAFEM_ERR_OOM           -3   /* device or host allocation failed                                       */
 #define RAFEM_ERR_NONFINITE     -4   /* NaN or Inf met in a residual, a coefficient or a field                  */
-#define RAFEM_ERR_TIMEOUT       -5   /* a device grid barrier waited past its limit (never expected)            */
+#define RAFEM_ERR_TIMEOUT       -5   /* a bounded device wait ran out (not expected in normal use; see
+                                        rafem_set_wait_limit)                                                  */
 #define RAFEM_ERR_CUDA          -6   /* a CUDA runtime call failed                                              */
 #define RAFEM_ERR_INTERNAL      -7   /* an internal consistency check failed                                   */
 #define RAFEM_ERR_BREAKDOWN     -8   /* Krylov breakdown: p^T A p <= 0 (matrix not SPD) or a zero denominator  */
@@ -253,6 +254,11 @@ int rafem_batch_info(rafem_ctx* ctx, int32_t* n_inst, int32_t* node_offsets);
 /* Statistics of the last step per instance, per_instance [n_inst] (host). The step statistics returned by
  * rafem_solve_step / rafem_run summarise all instances (worst status, largest iteration counts and residuals). */
 int rafem_batch_stats(rafem_ctx* ctx, rafem_step_stats* per_instance);
+/* n_steps time steps of every instance of a batch context (rafem_run on that context: one captured step graph per
+ * step, each system solved for all instances in one persistent launch), then the statistics of the last step per
+ * instance into per_instance [n_inst] (host, nullable) as rafem_batch_stats. Returns the worst status over all
+ * steps and instances (OK, NOT_CONVERGED or an error). Also valid on a single-instance context (n_inst = 1). */
+int rafem_batch_run(rafem_ctx* ctx, int32_t n_steps, rafem_step_stats* per_instance);
 
 /* Work schedule of the persistent solvers: rows per work tile (tiles never straddle batch instances; rounded up
  * to a multiple of 32 for SELL-32). 0 = automatic. Rebuilds only the tile arrays (cheap) and drops the captured
@@ -311,10 +317,10 @@ int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
 
 /* Solve A x = b with the library's persistent FP64 Jacobi-PCG for a CSR system the caller already holds on the
  * device, without allocating any memory. The paper has no counterpart: it exists for callers that cannot call
- * cudaMalloc when they need a solve, such as code running under CUDA stream capture (allocation is not allowed
- * there), code inside a framework whose caching allocator already owns the device memory, or a latency-bound
- * loop that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree. It calls no allocation
- * routine; the caller passes only its inputs and outputs.
+ * cudaMalloc when they need a solve, such as code inside a framework whose caching allocator already owns the
+ * device's memory (a cudaMalloc there can fail, or force the allocator to release its cache), or a latency-bound
+ * loop that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree. It calls no allocation routine;
+ * the caller passes only its inputs and outputs.
  *
  * Working memory comes from one fixed device array of RAFEM_NOALLOC_SCRATCH_BYTES (7 MiB) inside the library,
  * present on every device that loads the library until the process exits. Hence:
@@ -324,13 +330,18 @@ int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
  *     start at zero itself. Calls whose GPU work overlaps in time (different streams, or different host threads
  *     on the same device) race on the array and give wrong results: serialise them.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that device
- *     current) and keeps it; make that first call before any stream capture begins.
+ *     current) and keeps it for the life of the process; that first call should come before any stream capture
+ *     begins. After cudaDeviceReset the kept address is stale: do not call this entry point on a device after
+ *     resetting it.
+ * The call is synchronous: it waits on the stream twice (after the input check, and after the solve) and reads
+ * the check's result and the solver's statistics back into host memory before it returns.
  * Arguments (device pointers unless stated): row_ptr [n_rows+1] and col [row_ptr[n_rows]] int32 CSR pattern,
- * every row storing its diagonal entry (else RAFEM_ERR_BAD_INPUT); vals [row_ptr[n_rows]] FP64 values of a
- * symmetric positive-definite matrix; b [n_rows]; x [n_rows] initial guess on entry, solution on exit. tol:
- * relative residual ||b - A x|| / ||b||; max_iter: iteration cap. stream: cudaStream_t or NULL (legacy default
- * stream); the call synchronises it. stats (host, nullable): status, iters_V = iterations, relres_V = final
- * relative residual, other fields 0. Returns OK, NOT_CONVERGED, BAD_INPUT, BREAKDOWN, NONFINITE, TIMEOUT or CUDA. */
+ * every row storing its diagonal entry and every column in [0, n_rows) (else RAFEM_ERR_BAD_INPUT, with x left
+ * untouched); vals [row_ptr[n_rows]] FP64 values of a symmetric positive-definite matrix; b [n_rows]; x [n_rows]
+ * initial guess on entry, solution on exit. tol: relative residual ||b - A x|| / ||b||; max_iter: iteration cap.
+ * stream: cudaStream_t or NULL (legacy default stream). stats (host, nullable): status, iters_V = iterations,
+ * relres_V = final relative residual, other fields 0. Returns OK, NOT_CONVERGED, BAD_INPUT, BREAKDOWN, NONFINITE,
+ * TIMEOUT or CUDA. */
 #define RAFEM_NOALLOC_MAX_ROWS 131072
 #define RAFEM_NOALLOC_SCRATCH_BYTES 7340032
 int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* vals,
@@ -355,6 +366,16 @@ int rafem_set_dt(rafem_ctx* ctx, double dt);
  * relative residual to reach (> 0), and, when inner_tol > 0, the mixed solver's inner reduction (< 1); inner_tol
  * <= 0 keeps the current one. The captured step graphs are rebuilt at the next step. Errors: BAD_INPUT. */
 int rafem_set_tol(rafem_ctx* ctx, double tol, double inner_tol);
+
+/* Bounded device waits. Every wait inside a persistent solver kernel (the grid barriers between its phases and the
+ * shared-memory copy slots of the matrix stream) gives up after limit_ns nanoseconds of wall-clock time, records
+ * RAFEM_ERR_TIMEOUT and lets the kernel return, so a wait that cannot end costs at most that long and leaves the
+ * context usable (its fields hold whatever the interrupted solve left; rafem_reset or rafem_set_state restores a
+ * defined state). limit_ns <= 0 restores the default of 5 s. missing_arrivals (for testing the timeout path; 0 in
+ * normal use, at most 1024): the following solver launches start their grid-barrier counter that many arrivals
+ * short, so their first barrier cannot complete, its waits run out after limit_ns and the solve returns
+ * RAFEM_ERR_TIMEOUT, without a fault. The captured step graphs are rebuilt at the next step. Errors: BAD_INPUT. */
+int rafem_set_wait_limit(rafem_ctx* ctx, int64_t limit_ns, int32_t missing_arrivals);
 
 typedef struct rafem_advance_stats {
     int32_t status;                  /* worst status of the accepted steps                                     */
@@ -411,6 +432,10 @@ int rafem_reset(rafem_ctx* ctx);
  * the instances' elements one after the other). on_device: 0 = host pointers (checked for finite values),
  * 1 = device pointers (not checked). The constant thermal matrix is reassembled when k changes. Ends any tape. */
 int rafem_set_params(rafem_ctx* ctx, const double* sigma0, const double* k, int on_device);
+/* The same from FP32 device arrays (the usual storage of trainable per-element parameters, e.g. torch tensors):
+ * sigma0_dev [E] and/or k_dev [E] (either may be NULL to keep it), widened to FP64 by the library on its stream.
+ * Values are not checked for finiteness. Ends any tape. Errors: BAD_INPUT, OOM, CUDA. */
+int rafem_set_params_device(rafem_ctx* ctx, const float* sigma0_dev, const float* k_dev);
 
 /* Start recording: the current state is the tape's origin (checkpoint 0); every later time step taken by
  * rafem_run or rafem_solve_step stores a checkpoint of the state (fields, predictor history, statistics) each time
@@ -432,7 +457,9 @@ typedef struct rafem_adjoint_stats {
  * 1 = device): dL_dT = dL/dT at the current step (required), dL_dV = dL/dV at the current step (nullable; the
  * potential of the last step). Outputs (nullable; out_on_device as above): dL_dsigma0 [E] and dL_dk [E] in mesh
  * element order, dL_dT0 [N] = dL/dT at the tape origin with respect to every entry of that state vector (Dirichlet
- * entries included: they enter the first step through sigma(mean T) and the mass term). Entries of dL_dT and dL_dV
+ * entries included: they enter the first step through sigma(mean T) and the mass term); out_on_device = 2 writes
+ * dL_dsigma0 and dL_dk as FP32 device arrays (float* passed through the double* arguments; dL_dT0 stays FP64 on the
+ * device), the gradients of rafem_set_params_device's parameters. Entries of dL_dT and dL_dV
  * on Dirichlet nodes are ignored for steps after the origin (those values are fixed). The forward state of the
  * context is left exactly as it was. Returns the worse of the adjoint and recomputation statuses (OK or
  * NOT_CONVERGED), or BAD_INPUT (no tape), OOM, CUDA. stats: nullable. */

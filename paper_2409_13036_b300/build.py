@@ -1,7 +1,8 @@
 """Build librafem.so in-tree for sm_103a (B300) with nvcc.
 
 Usage: python -m paper_2409_13036_b300.build [--verbose]
-The library is written next to this file, so it travels with the source tree.
+The library is written next to this file, so it travels with the source tree, together with the SHA-256 of
+the sources it was built from (librafem.so.sha256): a library whose sources changed is rebuilt.
 """
 from __future__ import annotations
 
@@ -10,11 +11,13 @@ import shutil
 import subprocess
 import sys
 import concurrent.futures as cf
+import hashlib
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librafem.so")
+HASH = LIB + ".sha256"  # source hash of the build that produced LIB
 OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,14 +47,28 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def source_hash() -> str:
+    """SHA-256 over every input of the build: the sources, the headers, this script (flags included) and the nvcc
+    version. A library whose recorded hash differs (or is missing) is rebuilt, whatever the file times say."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    hdrs = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
     hdrs.append(os.path.join(INCLUDE, "rafem.h"))
-    if not force and os.path.exists(LIB):
-        newest = max(os.path.getmtime(p) for p in srcs + hdrs + [__file__])
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
+    h = hashlib.sha256()
+    for p in srcs + hdrs + [os.path.abspath(__file__)]:
+        h.update(os.path.basename(p).encode() + b"\0")
+        with open(p, "rb") as f:
+            h.update(f.read())
+    r = subprocess.run([nvcc(), "--version"], capture_output=True, text=True)
+    h.update(r.stdout.encode())
+    return h.hexdigest()
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    digest = source_hash()
+    if not force and os.path.exists(LIB) and os.path.exists(HASH):
+        with open(HASH) as f:
+            if f.read().strip() == digest:
+                return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
@@ -61,6 +78,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(HASH + ".tmp", "w") as f:
+        f.write(digest + "\n")
+    os.replace(HASH + ".tmp", HASH)
     return LIB
 
 

@@ -173,6 +173,9 @@ struct rafem_ctx {
     double *a_ew4 = nullptr, *a_w = nullptr, *a_gs = nullptr, *a_gk = nullptr;
     double *a_mu1 = nullptr, *a_mu2 = nullptr, *a_nu1 = nullptr, *a_nu2 = nullptr;  // backward-sweep histories
     int32_t* a_count = nullptr;      // [iters_V, iters_T, adjoint status, recomputation status]
+    // bounded device waits of the persistent solvers (rafem_set_wait_limit)
+    long long wait_ns = kDefaultWaitNs;
+    int wait_missing = 0;            // testing: grid-barrier arrivals the next solver launches start short of
 };
 
 namespace {
@@ -395,7 +398,8 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.inner_tol = c->prm.inner_tol;
     a.max_iter = c->prm.max_iter;
     a.max_refine = c->prm.max_refine;
-    a.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+    a.spin_limit_ns = c->wait_ns;
+    a.bar_missing = c->wait_missing;
     return a;
 }
 
@@ -524,7 +528,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         s.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
         s.tol = c->prm.tol;
         s.max_iter = c->prm.max_iter;
-        s.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        s.spin_limit_ns = c->wait_ns;
+        s.bar_missing = c->wait_missing;
         return launch_ilu_pcg(s, c->ilu_grid, c->stream);
     }
     if (c->prm.solver == RAFEM_SOLVER_GMRES) {
@@ -547,7 +552,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
         g.tol = c->prm.tol;
         g.max_iter = c->prm.max_iter;
-        g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        g.spin_limit_ns = c->wait_ns;
+        g.bar_missing = c->wait_missing;
         return launch_gmres(g, c->gm_grid, c->stream);
     }
     if (c->prm.solver == RAFEM_SOLVER_BICGSTAB) {
@@ -574,7 +580,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
         g.tol = c->prm.tol;
         g.max_iter = c->prm.max_iter;
-        g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+        g.spin_limit_ns = c->wait_ns;
+        g.bar_missing = c->wait_missing;
         return launch_bicgstab(g, c->bg_grid, c->stream);
     }
     SolveArgs a = make_args(c, which, b, x);
@@ -784,7 +791,8 @@ cudaError_t enqueue_newton(rafem_ctx* c) {
     g.inst = c->instV;
     g.tol = c->prm.tol;
     g.max_iter = c->prm.max_iter;
-    g.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+    g.spin_limit_ns = c->wait_ns;
+    g.bar_missing = c->wait_missing;
     if ((e = launch_bicgstab(g, c->mb_grid, st)) != cudaSuccess) return e;
     k_record<<<1, 128, 0, st>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1871,6 +1879,14 @@ int rafem_batch_stats(rafem_ctx* c, rafem_step_stats* per_instance) {
     return RAFEM_OK;
 }
 
+int rafem_batch_run(rafem_ctx* c, int32_t n_steps, rafem_step_stats* per_instance) {
+    if (!c || n_steps < 0) return RAFEM_ERR_BAD_INPUT;
+    const int s = rafem_run(c, n_steps, nullptr);
+    if (s < 0 || !per_instance) return s;
+    const int q = rafem_batch_stats(c, per_instance);
+    return q != RAFEM_OK ? q : s;
+}
+
 int rafem_reset(rafem_ctx* c) {
     if (!c) return RAFEM_ERR_BAD_INPUT;
     c->tape_every = 0;
@@ -1887,21 +1903,46 @@ int rafem_reset(rafem_ctx* c) {
     return RAFEM_OK;
 }
 
-int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on_device) {
+namespace {
+
+__global__ void k_widen(int n, const float* __restrict__ in, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
+__global__ void k_narrow(int n, const double* __restrict__ in, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+// Where a parameter array comes from: host FP64, device FP64 or device FP32.
+enum ParamSrc { SRC_HOST64 = 0, SRC_DEV64 = 1, SRC_DEV32 = 2 };
+
+// Stage one parameter array into p_tmpE (FP64, mesh element order).
+cudaError_t stage_param(rafem_ctx* c, const void* src, int kind) {
+    const int E = c->E;
+    if (kind == SRC_DEV32) {
+        k_widen<<<(E + 255) / 256, 256, 0, c->stream>>>(E, static_cast<const float*>(src), c->p_tmpE);
+        return cudaGetLastError();
+    }
+    return cudaMemcpyAsync(c->p_tmpE, src, E * sizeof(double),
+                           kind == SRC_DEV64 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+}
+
+int set_params_impl(rafem_ctx* c, const void* sigma0, const void* k, int kind) {
     if (!c || (!sigma0 && !k)) return RAFEM_ERR_BAD_INPUT;
     const int E = c->E;
-    if (!on_device) {
-        for (const double* q : {sigma0, k})
+    if (kind == SRC_HOST64) {
+        for (const void* q : {sigma0, k})
             if (q)
                 for (int e = 0; e < E; ++e)
-                    if (!std::isfinite(q[e])) return RAFEM_ERR_NONFINITE;
+                    if (!std::isfinite(static_cast<const double*>(q)[e])) return RAFEM_ERR_NONFINITE;
     }
     if (!c->p_tmpE) CK(dalloc(c, &c->p_tmpE, E));
     c->tape_every = 0;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaStream_t st = c->stream;
     if (sigma0) {
-        CK(cudaMemcpyAsync(c->p_tmpE, sigma0, E * sizeof(double), kind, st));
+        CK(stage_param(c, sigma0, kind));
         CK(launch_permute(E, c->e_order, c->p_tmpE, c->e_sig0, 0, st));
         if (c->dw)
             CK(launch_fill_dw(c->gdw, c->gather_nc, c->gd.celem, c->gather_cg, c->el, c->prm.rho_c / c->prm.dt, st));
@@ -1910,7 +1951,7 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
                                 const_cast<double*>(c->gd.cval), st));
     }
     if (k) {
-        CK(cudaMemcpyAsync(c->p_tmpE, k, E * sizeof(double), kind, st));
+        CK(stage_param(c, k, kind));
         CK(launch_permute(E, c->e_order, c->p_tmpE, c->e_k, 0, st));
         // constant thermal matrix and rhs part: every free slot is stored by its first writer, Dirichlet rows
         // keep the identity; the constant rhs accumulates and restarts from zero
@@ -1923,6 +1964,16 @@ int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on
     }
     CK(cudaStreamSynchronize(st));
     return RAFEM_OK;
+}
+
+}  // namespace
+
+int rafem_set_params(rafem_ctx* c, const double* sigma0, const double* k, int on_device) {
+    return set_params_impl(c, sigma0, k, on_device ? SRC_DEV64 : SRC_HOST64);
+}
+
+int rafem_set_params_device(rafem_ctx* c, const float* sigma0, const float* k) {
+    return set_params_impl(c, sigma0, k, SRC_DEV32);
 }
 
 int rafem_precond_info(rafem_ctx* c, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored, int32_t* order) {
@@ -1999,6 +2050,14 @@ int rafem_set_dt(rafem_ctx* c, double dt) {
     const int s = apply_dt(c, dt);
     if (s != RAFEM_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
+    return RAFEM_OK;
+}
+
+int rafem_set_wait_limit(rafem_ctx* c, int64_t limit_ns, int32_t missing_arrivals) {
+    if (!c || missing_arrivals < 0 || missing_arrivals > 1024) return RAFEM_ERR_BAD_INPUT;
+    c->wait_ns = limit_ns > 0 ? (long long)limit_ns : kDefaultWaitNs;
+    c->wait_missing = missing_arrivals;
+    drop_graphs(c);  // the solver launches carry both as arguments
     return RAFEM_OK;
 }
 
@@ -2145,7 +2204,7 @@ int merge_status(int a, int b) {
 
 int rafem_adjoint(rafem_ctx* c, const double* dL_dT, const double* dL_dV, int in_on_device, double* dL_dsigma0,
                   double* dL_dk, double* dL_dT0, int out_on_device, rafem_adjoint_stats* out) {
-    if (!c || !dL_dT || c->tape_every <= 0) return RAFEM_ERR_BAD_INPUT;
+    if (!c || !dL_dT || c->tape_every <= 0 || out_on_device < 0 || out_on_device > 2) return RAFEM_ERR_BAD_INPUT;
     const auto t_start = std::chrono::steady_clock::now();
     const int64_t nsteps = c->step - c->tape_origin;
     const int every = c->tape_every;
@@ -2217,18 +2276,24 @@ int rafem_adjoint(rafem_ctx* c, const double* dL_dT, const double* dL_dV, int in
         c->step = live_step;
         c->tape_every = saved_every;
     }
-    // outputs (gradients back in mesh element order)
+    // outputs (gradients back in mesh element order); out_on_device 2: element gradients as device floats
     const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (dL_dsigma0) {
-        double* dst = out_on_device ? dL_dsigma0 : c->p_tmpE;
-        CK(launch_permute(E, c->e_order, c->a_gs, dst, 1, st));
-        if (!out_on_device) CK(cudaMemcpyAsync(dL_dsigma0, c->p_tmpE, E * sizeof(double), out_kind, st));
-    }
-    if (dL_dk) {
-        if (!out_on_device) CK(cudaStreamSynchronize(st));  // p_tmpE is reused
-        double* dst = out_on_device ? dL_dk : c->p_tmpE;
-        CK(launch_permute(E, c->e_order, c->a_gk, dst, 1, st));
-        if (!out_on_device) CK(cudaMemcpyAsync(dL_dk, c->p_tmpE, E * sizeof(double), out_kind, st));
+    double* grads_dst[2] = {dL_dsigma0, dL_dk};
+    const double* grads_src[2] = {c->a_gs, c->a_gk};
+    for (int q = 0; q < 2; ++q) {
+        if (!grads_dst[q]) continue;
+        if (out_on_device == 1) {
+            CK(launch_permute(E, c->e_order, grads_src[q], grads_dst[q], 1, st));
+            continue;
+        }
+        CK(cudaStreamSynchronize(st));  // p_tmpE is reused
+        CK(launch_permute(E, c->e_order, grads_src[q], c->p_tmpE, 1, st));
+        if (out_on_device == 2) {
+            k_narrow<<<(E + 255) / 256, 256, 0, st>>>(E, c->p_tmpE, reinterpret_cast<float*>(grads_dst[q]));
+            CK(cudaGetLastError());
+        } else {
+            CK(cudaMemcpyAsync(grads_dst[q], c->p_tmpE, E * sizeof(double), out_kind, st));
+        }
     }
     if (dL_dT0) CK(cudaMemcpyAsync(dL_dT0, c->a_lam, nb, out_kind, st));
     int32_t cnt[4];

@@ -368,6 +368,7 @@ cudaError_t launch_bicgstab(const BicgArgs& s, int grid, cudaStream_t st) {
            s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
+    if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;
     void* params[] = {&a};
     const void* f = s.block == 2 ? (const void*)k_bicgstab<2> : (const void*)k_bicgstab<1>;
     return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(kBlock), params, 0, st);

@@ -327,6 +327,7 @@ cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
            s.inst, s.tol, s.max_iter, s.spin_limit_ns};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
+    if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;
     void* params[] = {&a};
     return cudaLaunchCooperativeKernel((const void*)k_gmres, dim3(grid), dim3(kBlock), params, smem_bytes(s.m), st);
 }

@@ -446,6 +446,7 @@ cudaError_t launch_ilu_pcg(const IluSolveArgs& s, int grid, cudaStream_t st) {
            s.tol, s.max_iter, s.spin_limit_ns};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
+    if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;
     void* params[] = {&a};
     return cudaLaunchCooperativeKernel((const void*)k_ilu_pcg, dim3(grid), dim3(kIluBlock), params, 0, st);
 }

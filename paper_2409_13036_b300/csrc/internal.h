@@ -132,6 +132,9 @@ struct InstState {
 // Number of per-tile partial sums a solver kernel writes (gamma, rr, delta, bb, rr64).
 constexpr int kPartialQ = 5;
 
+// Default wall-clock limit of every bounded device wait (grid barriers, copy slots): 5 s.
+constexpr long long kDefaultWaitNs = 5000000000LL;
+
 struct GridBarrier {
     unsigned int count;
     unsigned int gen;
@@ -139,6 +142,10 @@ struct GridBarrier {
     int n_active;       // instances still iterating (written by the last arriver)
     unsigned int pad[28];
 };
+
+// Enqueue the reset of a solver launch's barrier: counter at 0 - missing (missing > 0 only in tests: the first
+// barrier then cannot complete and its waits run out), no error recorded.
+cudaError_t launch_barrier_reset(GridBarrier* bar, int missing, cudaStream_t st);
 
 struct SolveArgs {
     // matrix (lifted, fixed pattern): CSR (rp, ci) or SELL-32 (rp = slice pointers, ci = slice columns)
@@ -174,6 +181,7 @@ struct SolveArgs {
     double tol, inner_tol;
     int max_iter, max_refine;
     long long spin_limit_ns;
+    int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 
 // Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 4/8/16/32 = CSR with that
@@ -242,6 +250,7 @@ struct IluSolveArgs {
     double tol;
     int max_iter;
     long long spin_limit_ns;
+    int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 
 // Ap = permuted values of `vals` (the system in its primary storage), F = ILU(0) factors of Ap, level by level,
@@ -280,6 +289,7 @@ struct BicgArgs {
     double tol;
     int max_iter;
     long long spin_limit_ns;
+    int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 int bicgstab_max_blocks(int block);
 int bicgstab_partial_slots();
@@ -309,6 +319,7 @@ struct GmresArgs {
     double tol;
     int max_iter;
     long long spin_limit_ns;
+    int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 int gmres_max_blocks(int m);
 cudaError_t launch_gmres(const GmresArgs& a, int grid, cudaStream_t st);

@@ -280,6 +280,7 @@ __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int
     constexpr int kTeamsG = kConsumerWarps / kG;
     const int ngroups = (s_end - s_begin + kG - 1) / kG;
     bool ok = true;
+    int issued = 0;  // producer lane: groups whose copies were issued in this call
     if (warp == kConsumerWarps) {
         if (lane == 0) {
             for (int j = 0; j < ngroups && ok; ++j) {
@@ -287,6 +288,7 @@ __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int
                 const int slot = (int)(J % kSlots);
                 if (J >= (unsigned)kSlots) ok = mbar_wait_bounded(&g.empty[slot], ((J / kSlots) - 1) & 1, a, g.abort);
                 if (!ok) break;
+                issued = j + 1;
                 const int s = s_begin + j * kG;
                 const int ns = min(kG, s_end - s);
                 const int base = __ldg(sp + s), endp = __ldg(sp + s + ns);
@@ -355,21 +357,26 @@ __device__ __forceinline__ bool sell_tile(const SolveArgs& a, Ring& g, const int
             if (lane == 0) mbar_arrive_n(&g.empty[slot], kConsumerWarps / kG);
         }
     }
+    const unsigned J0 = g.base;
     g.base += (unsigned)ngroups;
-    // On a failed wait the producer lane waits (bounded) for the copies it issued before the kernel exits.
-    if (!ok && warp == kConsumerWarps && lane == 0) {
-        const unsigned J0 = g.base - ngroups;
-        for (int j = 0; j < ngroups; ++j) {
+    if (__syncthreads_and(ok)) return true;
+    // A wait gave up somewhere in the block: before the kernel exits, the producer lane waits for the copies that
+    // may still be landing in shared memory. Only the last min(kSlots, issued) groups can be in flight (an
+    // earlier group's slot was refilled only after its consumers had waited for its bytes), and each of them is
+    // the newest user of its slot, so its full barrier's phase is unambiguous. Copies always complete, so one
+    // overall deadline (kDrainNs, independent of the configurable wait limit) bounds the drain.
+    if (warp == kConsumerWarps && lane == 0) {
+        constexpr long long kDrainNs = 2000000000LL;
+        const unsigned long long t0 = globaltimer();
+        for (int j = max(0, issued - kSlots); j < issued; ++j) {
             const unsigned J = J0 + j;
-            if (!mbar_try_wait(&g.full[J % kSlots], (J / kSlots) & 1)) {
-                const unsigned long long t0 = globaltimer();
-                while (!mbar_try_wait(&g.full[J % kSlots], (J / kSlots) & 1) &&
-                       (long long)(globaltimer() - t0) < a.spin_limit_ns) {
-                }
+            while (!mbar_try_wait(&g.full[J % kSlots], (J / kSlots) & 1) &&
+                   (long long)(globaltimer() - t0) < kDrainNs) {
             }
         }
     }
-    return __syncthreads_and(ok);
+    __syncthreads();
+    return false;
 }
 
 // CSR SpMV with L lanes per row; pre/fin run on lane 0 of the row's group.
@@ -1226,7 +1233,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
     publish_state(a, sst);
 }
 
-__global__ void k_reset(InstState* inst, int n_inst, GridBarrier* bar) {
+__global__ void k_reset(InstState* inst, int n_inst, GridBarrier* bar, int missing) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
         InstState z = {};
         z.active = 1;
@@ -1235,10 +1242,15 @@ __global__ void k_reset(InstState* inst, int n_inst, GridBarrier* bar) {
         inst[i] = z;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        bar->count = 0;
+        bar->count = 0u - (unsigned)missing;
         bar->err = 0;
         bar->n_active = n_inst;
     }
+}
+
+__global__ void k_barrier_reset(GridBarrier* bar, int missing) {
+    bar->count = 0u - (unsigned)missing;
+    bar->err = 0;
 }
 
 template <int L>
@@ -1261,6 +1273,11 @@ void* select_kernel(int lanes, int precision, bool pipelined) {
 
 }  // namespace
 
+cudaError_t launch_barrier_reset(GridBarrier* bar, int missing, cudaStream_t st) {
+    k_barrier_reset<<<1, 1, 0, st>>>(bar, missing);
+    return cudaGetLastError();
+}
+
 // Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32, none for CSR.
 static int dyn_smem(int lanes) { return lanes <= 2 ? kRingBytes : 0; }
 
@@ -1281,7 +1298,7 @@ cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, bool pip
                           cudaStream_t st) {
     void* k = select_kernel(lanes, precision, pipelined);
     if (!k) return cudaErrorInvalidValue;
-    k_reset<<<(a.n_inst + 255) / 256, 256, 0, st>>>(a.inst, a.n_inst, a.bar);
+    k_reset<<<(a.n_inst + 255) / 256, 256, 0, st>>>(a.inst, a.n_inst, a.bar, a.bar_missing);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

@@ -1,16 +1,18 @@
 // rafem_pcg_csr_noalloc: the persistent FP64 Jacobi-PCG solver applied to a caller-supplied CSR system, with
 // every piece of working memory taken from one fixed array that the library owns for the life of the process.
 //
-// Some callers cannot allocate device memory at the point where they need a solve: code that runs while a
-// stream is being captured into a CUDA graph (allocation calls are not allowed there), code inside a framework
-// whose caching allocator already holds the device's memory, or a time-critical loop that cannot afford the
-// implicit device synchronisation of cudaMalloc/cudaFree. This entry point serves them: it calls no allocation
-// routine of any kind, and the caller only passes its own inputs and outputs.
+// Some callers cannot allocate device memory at the point where they need a solve: code inside a framework whose
+// caching allocator already holds the device's memory (a cudaMalloc there may fail, or force the allocator to
+// give back its cache), or a time-critical loop that cannot afford the implicit device synchronisation of
+// cudaMalloc/cudaFree. This entry point serves them: it calls no allocation routine of any kind, and the caller
+// only passes its own inputs and outputs. The call is synchronous: it waits on its stream after checking the
+// input and again after the solve, and reads both results back into host variables.
 //
 // The working memory (Krylov vectors, diagonal positions, per-tile partial sums, work tiles, solver state and
 // the grid-barrier word) lives in the file-scope array g_noalloc_scratch below. Host code cannot use that name
 // as an address (it names a host-side stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress and then passed to the kernels.
+// cudaGetSymbolAddress, with that device current, and then passed to the kernels. The address is kept for the
+// life of the process, so it goes stale if the device is reset (cudaDeviceReset reloads the module).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -189,7 +191,7 @@ extern "C" int rafem_pcg_csr_noalloc(int32_t n_rows, const int32_t* row_ptr, con
     a.bar = c.bar;
     a.tol = tol;
     a.max_iter = max_iter;
-    a.spin_limit_ns = 5LL * 1000 * 1000 * 1000;
+    a.spin_limit_ns = kDefaultWaitNs;
     if ((e = launch_krylov(a, kLanes, RAFEM_PRECISION_FP64, false, std::min(n_tiles, maxb), block, st)) != cudaSuccess)
         return to_status(e);
     InstState s;

@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(rafem_params), vp, ctypes.POINTER(vp)]),
         "rafem_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), vp]),
         "rafem_batch_stats": (ctypes.c_int, [vp, vp]),
+        "rafem_batch_run": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
         "rafem_set_schedule": (ctypes.c_int, [vp, ctypes.c_int32]),
         "rafem_get_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]),
@@ -165,6 +166,8 @@ def lib() -> ctypes.CDLL:
         "rafem_get_coupled_system": (ctypes.c_int, [vp, vp, vp]),
         "rafem_reset": (ctypes.c_int, [vp]),
         "rafem_set_params": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "rafem_set_params_device": (ctypes.c_int, [vp, vp, vp]),
+        "rafem_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int32]),
         "rafem_tape_begin": (ctypes.c_int, [vp, ctypes.c_int32]),
         "rafem_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_int,
                                          ctypes.POINTER(rafem_adjoint_stats)]),
@@ -264,6 +267,13 @@ class Context:
         out = (rafem_step_stats * self.n_inst)()
         _check(lib().rafem_batch_stats(self._ctx, ctypes.cast(out, ctypes.c_void_p)), "rafem_batch_stats")
         return [o.as_dict() for o in out]
+
+    def batch_run(self, n_steps: int):
+        """rafem_batch_run: n_steps steps of every instance; returns (worst status, per-instance stats of the last
+        step)."""
+        out = (rafem_step_stats * self.n_inst)()
+        s = lib().rafem_batch_run(self._ctx, int(n_steps), ctypes.cast(out, ctypes.c_void_p))
+        return _check(s, "rafem_batch_run"), [o.as_dict() for o in out]
 
     def __init__(self, mesh, params: rafem_params | None = None, stream: int | None = None, **kw):
         self._keep = [np.ascontiguousarray(mesh.coords, dtype=np.float64),
@@ -478,6 +488,17 @@ class Context:
                                           None if kk is None else kk.ctypes.data, 0), "rafem_set_params")
         else:
             _check(lib().rafem_set_params(self._ctx, _dev(sigma0), _dev(k), 1), "rafem_set_params")
+
+    def set_params_device(self, sigma0=None, k=None):
+        """rafem_set_params_device: FP32 device tensors (or pointers) of E floats, mesh element order."""
+        if sigma0 is None and k is None:
+            raise ValueError("nothing to set")
+        _check(lib().rafem_set_params_device(self._ctx, _dev(sigma0), _dev(k)), "rafem_set_params_device")
+
+    def set_wait_limit(self, limit_ns: int = 0, missing_arrivals: int = 0):
+        """rafem_set_wait_limit: wall-clock limit of the solvers' device waits (0 = default 5 s); missing_arrivals
+        > 0 makes the next solves' first grid barrier incomplete (tests of the timeout path)."""
+        _check(lib().rafem_set_wait_limit(self._ctx, int(limit_ns), int(missing_arrivals)), "rafem_set_wait_limit")
 
     def tape_begin(self, checkpoint_every: int):
         _check(lib().rafem_tape_begin(self._ctx, int(checkpoint_every)), "rafem_tape_begin")

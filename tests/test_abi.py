@@ -27,6 +27,25 @@ def test_library_exports_every_header_symbol(built):
     assert rafem.lib() is not None
 
 
+# The calls of the boundary named for the hot path (mesh, tissue properties, boundary conditions, time stepping,
+# assemble and solve: the problem statement of Sec. II-A), each exported under its own name.
+BOUNDARY_CALLS = ["rafem_create", "rafem_assemble", "rafem_solve_step", "rafem_run", "rafem_get_field",
+                  "rafem_set_state", "rafem_set_params_device", "rafem_adjoint", "rafem_batch_create",
+                  "rafem_batch_run", "rafem_destroy", "rafem_status_string"]
+
+
+def test_boundary_calls_exported_and_bound(built):
+    from paper_2409_13036_b300 import rafem
+    names = rafem.header_symbols()
+    L = rafem.lib()
+    for n in BOUNDARY_CALLS:
+        assert n in names, n
+        assert hasattr(L, n), n
+    # every declared entry point has a ctypes signature in the binding (marshalling is typed, not guessed)
+    unbound = [n for n in names if getattr(L, n).argtypes is None and n != "rafem_status_string"]
+    assert not unbound, unbound
+
+
 def test_status_strings(built):
     from paper_2409_13036_b300 import rafem
     assert rafem.status_string(0) == "OK"

@@ -222,6 +222,27 @@ def test_set_params_equals_fresh_context():
         np.testing.assert_array_equal(a.get_field(rafem.RAFEM_SYS_V), b.get_field(rafem.RAFEM_SYS_V))
 
 
+def test_set_params_device_fp32_equals_fp64_of_rounded_values():
+    """rafem_set_params_device (FP32 device arrays, widened in the library) gives bitwise the fields of
+    rafem_set_params with the same FP32-rounded values as FP64 host arrays."""
+    import torch
+    rafem = R()
+    m = mg.cube_mesh(8, jitter=0.1, seed=8, sigma0="lognormal")
+    rng = np.random.default_rng(4)
+    s32 = (m.sigma0 * (1.0 + 0.3 * rng.random(m.n_tets))).astype(np.float32)
+    k32 = (m.k * (1.0 + 0.3 * rng.random(m.n_tets))).astype(np.float32)
+    with rafem.Context(m, dt=5.0) as a, rafem.Context(m, dt=5.0) as b:
+        ds = torch.tensor(s32, device="cuda")
+        dk = torch.tensor(k32, device="cuda")
+        torch.cuda.synchronize()
+        a.set_params_device(ds, dk)
+        b.set_params(s32.astype(np.float64), k32.astype(np.float64))
+        a.run(3)
+        b.run(3)
+        for which in (rafem.RAFEM_SYS_V, rafem.RAFEM_SYS_T):
+            np.testing.assert_array_equal(a.get_field(which), b.get_field(which))
+
+
 def test_adjoint_input_errors():
     """No tape, tape with corrector passes, bad spacing: BAD_INPUT; an empty tape returns dL/dT as dL/dT0."""
     rafem = R()

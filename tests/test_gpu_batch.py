@@ -28,17 +28,19 @@ def _instances():
 
 @pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-9), (1, 1e-11, 1e-8)])
 def test_batch_matches_single_instance_contexts(precision, tol, bound):
+    """Every instance of the batch (rafem_batch_run) against a single-instance context of its own and against the
+    oracle's direct solves."""
     from paper_2409_13036_b300 import rafem
     meshes = _instances()
     steps = 3
     with rafem.Context.batch(meshes, precision=precision, tol=tol, dt=5.0) as b:
-        s, st = b.run(steps)
-        assert s == rafem.RAFEM_OK, st.as_dict()
+        s, per = b.batch_run(steps)
+        assert s == rafem.RAFEM_OK, per
+        assert per == b.batch_stats()
         T = b.get_field(rafem.RAFEM_SYS_T)
         V = b.get_field(rafem.RAFEM_SYS_V)
-        per = b.batch_stats()
         off = b.offsets
-    assert len(per) == len(meshes) and all(p["status"] == 0 for p in per)
+    assert len(per) == len(meshes) and all(p["status"] == 0 and p["step"] == steps for p in per)
     assert len({p["iters_V"] for p in per}) > 1  # instances converge on their own schedules
     for i, m in enumerate(meshes):
         Ti, Vi = T[off[i]:off[i] + m.n_nodes], V[off[i]:off[i] + m.n_nodes]
@@ -49,11 +51,10 @@ def test_batch_matches_single_instance_contexts(precision, tol, bound):
         # the padding nodes between instances keep their boundary values
         pad = slice(off[i] + m.n_nodes, off[i + 1])
         assert np.all(V[pad] == 0.0)
-    # one instance against the oracle's direct solves
-    T_ref, V_ref = O.Model(meshes[2], O.Params(dt=5.0)).run(steps)
-    m = meshes[2]
-    assert O.rel_err(T[off[2]:off[2] + m.n_nodes], T_ref[-1]) <= bound
-    assert O.rel_err(V[off[2]:off[2] + m.n_nodes], V_ref[-1]) <= bound
+        # each instance against the oracle's direct solves
+        T_ref, V_ref = O.Model(m, O.Params(dt=5.0)).run(steps)
+        assert O.rel_err(Ti, T_ref[-1]) <= bound, i
+        assert O.rel_err(Vi, V_ref[-1]) <= bound, i
 
 
 def test_batch_limits():
