@@ -309,16 +309,18 @@ def alg_bytes_bicgstab(N: int, nnz: int, iters: float, col_bytes: int) -> float:
 
 
 def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: int, m: int = 30) -> float:
-    """Algorithmic HBM bytes of one GMRES(m) solve launch: per Arnoldi step j an SpMV ((8 + col_bytes) B per stored
-    entry, plus u and dinv gathered and v_j, w written: 32N) and three passes over the basis (j + 1 vectors read
-    by the dots, by the first and by the second orthogonalisation, with w read and written: 3 (j + 1) 8N + 32N);
-    per cycle the residual SpMV ((8 + col_bytes) nnz + 24N) and the update (k + 2 vectors). j averages about half
-    the steps per cycle."""
-    steps_per_cycle = steps / max(cycles, 1.0)
+    """Algorithmic HBM bytes of one GMRES(m) solve launch (single-pass Gram-Schmidt, the second pass being taken
+    only when the first cancels more than half of the vector's norm): per Arnoldi step j an SpMV ((8 + col_bytes) B
+    per stored entry, plus u and dinv gathered and v_j, w written: 32N), the dots pass (w and the j + 1 basis vectors
+    read) and the update pass (the j + 1 basis vectors read, w read and written); the last step of a cycle skips the
+    update. Per cycle the residual SpMV ((8 + col_bytes) nnz + 24N) and the update of x (k + 2 vectors). j averages
+    about half the steps per cycle."""
+    cycles = max(cycles, 1.0)
+    steps_per_cycle = steps / cycles
     j_avg = (steps_per_cycle - 1) / 2.0
-    per_step = (8 + col_bytes) * nnz + 32 * N + 3 * (j_avg + 1) * 8 * N + 32 * N
-    per_cycle = (8 + col_bytes) * nnz + 24 * N + (steps_per_cycle + 2) * 8 * N
-    return steps * per_step + max(cycles, 1.0) * per_cycle
+    per_step = (8 + col_bytes) * nnz + 32 * N + (j_avg + 2) * 8 * N + (j_avg + 3) * 8 * N
+    per_cycle = (8 + col_bytes) * nnz + 24 * N + (steps_per_cycle + 2) * 8 * N - (steps_per_cycle * 8 * N + 16 * N)
+    return steps * per_step + cycles * per_cycle
 
 
 def cpu_baseline_line(t: dict, c1: dict | None, small: dict | None) -> dict:
@@ -369,10 +371,11 @@ def reference_arm(args):
     return 0
 
 
-def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, precond=0, solver=0):
+def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, precond=0, solver=0, **extra):
     """Warm up, time K steps with CUDA events on the context's stream, then a few traced steps."""
     stream = torch.cuda.Stream()
-    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision, precond=precond, solver=solver)
+    ctx = rafem.Context(mesh, stream=stream.cuda_stream, precision=precision, precond=precond, solver=solver,
+                        **extra)
     N, nnz, n_colors = ctx.pattern_info()
     layout = ctx.layout_info()
     if precond == rafem.RAFEM_PRECOND_ILU0:
@@ -876,6 +879,15 @@ def main():
             r["ctx"].close()
             r["ctx"] = None
         runs["fp64_gmres30"] = r
+        # the adaptive cycle length (Sec. III-B): between 10 and 30 steps per cycle
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_FP64, g_args, local, dist, want_clocks=False,
+                    solver=rafem.RAFEM_SOLVER_GMRES, gmres_min_restart=10)
+        r["solver"] = "gmres"
+        r["roofline"] = roofline(r, False, peaks, peak_kind)
+        r["steps"] = args.gmres_steps
+        r["ctx"].close()
+        r["ctx"] = None
+        runs["fp64_gmres_adaptive"] = r
     if args.pipecg_steps > 0 and args.only in (None, "pipecg"):
         p_args = argparse.Namespace(**vars(args))
         p_args.steps = args.pipecg_steps
@@ -969,6 +981,9 @@ def main():
         line["fp64_bicgstab"] = summary(runs["fp64_bicgstab"])
     if "fp64_gmres30" in runs:
         line["fp64_gmres30"] = summary(runs["fp64_gmres30"])
+    if "fp64_gmres_adaptive" in runs:
+        line["fp64_gmres_adaptive"] = summary(runs["fp64_gmres_adaptive"])
+        line["fp64_gmres_adaptive"]["restart"] = "adaptive, 10..30 steps per cycle"
     if "fp64_pipecg" in runs and head_name != "fp64_pipecg":
         line["fp64_pipecg"] = summary(runs["fp64_pipecg"])
     if "fp64_ilu0" in runs:

@@ -66,8 +66,11 @@ extern "C" {
                                         single instance                                                        */
 
 #define RAFEM_SOLVER_GMRES    2      /* restarted GMRES(m), the paper's iterative method (Sec. III-B): FP64, right
-                                        Jacobi, classical Gram-Schmidt with reorthogonalisation, SELL-32 layout,
-                                        single instance; m = gmres_restart                                      */
+                                        Jacobi, classical Gram-Schmidt (repeated once when the first pass
+                                        cancels more than half of the vector's norm), SELL-32 layout, single
+                                        instance; m = gmres_restart, adaptive between gmres_min_restart and m
+                                        when that is set; two full-length cycles in a row that each reduce the
+                                        residual by less than 0.1% (stagnation) end the solve NOT_CONVERGED   */
 #define RAFEM_SOLVER_PIPECG   3      /* pipelined Jacobi-PCG (Ghysels-Vanroose): CG's iterates with one grid
                                         barrier per iteration instead of two, at the cost of 20 vector touches
                                         instead of 14; for small systems and batches of small instances. FP64,
@@ -153,6 +156,11 @@ typedef struct rafem_params {
     int32_t coupling;                /* RAFEM_COUPLING_STAGGERED (0) or RAFEM_COUPLING_MONOLITHIC               */
     int32_t arith;                   /* RAFEM_ARITH_AUTO (0), RAFEM_ARITH_FP64 or RAFEM_ARITH_DW                 */
     int32_t proj_basis;              /* RAFEM_PREDICT_PROJECT: solutions in the basis, 1..8 (0 = 4)             */
+    int32_t gmres_min_restart;       /* RAFEM_SOLVER_GMRES: 0 = every cycle has gmres_restart steps; 1..m = the
+                                        cycle length adapts between this and gmres_restart from each cycle's
+                                        residual reduction (shorter while convergence is moderate, back to the
+                                        full length on stagnation), and a solve starts with the length the
+                                        previous solve of the same system ended with                           */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */

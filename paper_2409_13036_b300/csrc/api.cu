@@ -148,6 +148,7 @@ struct rafem_ctx {
     int bg_grid = 0;
     // GMRES(m) (solver == RAFEM_SOLVER_GMRES)
     int gm_m = 0, gm_grid = 0;
+    int32_t* gm_mstate = nullptr;  // [2] adaptive restart length per system, carried from solve to solve
     // monolithic coupled step (coupling == RAFEM_COUPLING_MONOLITHIC): 2 x 2 block Jacobian on the node pattern,
     // interleaved residual and Newton correction, block-BiCGSTAB workspace (2N vectors)
     bool mono = false;
@@ -536,6 +537,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         GmresArgs g{};
         g.N = c->N;
         g.m = c->gm_m;
+        g.m_min = c->prm.gmres_min_restart;
+        g.m_state = c->gm_mstate + (which == RAFEM_SYS_V ? 0 : 1);
         g.sp = c->rp;
         g.sc = c->ci;
         g.sc16 = c->ci16;
@@ -1455,6 +1458,8 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         for (double** v : {&c->gm_w0, &c->gm_w1, &c->gm_dinv}) CK(dalloc(c, v, (size_t)N + SELL_C));
         c->gm_grid = gmres_max_blocks(c->gm_m);
         if (c->gm_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &c->gm_mstate, 2));  // per system; 0 = start at the full length
+
         CK(dalloc(c, &c->gm_partial, (size_t)(2 * (c->gm_m + 1) + 2) * c->gm_grid));
     }
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC) {
@@ -1572,6 +1577,9 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
          prm->coupling != RAFEM_COUPLING_STAGGERED))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->gmres_restart < 0 || prm->gmres_restart > 64) return RAFEM_ERR_BAD_INPUT;
+    if (prm->gmres_min_restart < 0 ||
+        prm->gmres_min_restart > (prm->gmres_restart > 0 ? prm->gmres_restart : 30))
+        return RAFEM_ERR_BAD_INPUT;
     if ((prm->solver == RAFEM_SOLVER_BICGSTAB || prm->solver == RAFEM_SOLVER_GMRES) &&
         (prm->precision != RAFEM_PRECISION_FP64 || prm->precond != RAFEM_PRECOND_JACOBI ||
          (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
@@ -1896,6 +1904,7 @@ int rafem_reset(rafem_ctx* c) {
     for (double* h : {c->T_hist, c->V_hist, c->T_hist2, c->V_hist2, c->T_hist3, c->V_hist3})
         CK(cudaMemsetAsync(h, 0, N * sizeof(double), c->stream));
     if (c->proj_D) CK(cudaMemsetAsync(c->proj_D, 0, (size_t)proj_stride(c->proj_k) * N * sizeof(double), c->stream));
+    if (c->gm_mstate) CK(cudaMemsetAsync(c->gm_mstate, 0, 2 * sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(c->istats, 0, c->n_inst * sizeof(rafem_step_stats), c->stream));
     CK(cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream));
     c->step = 0;

@@ -1,18 +1,34 @@
 // Persistent restarted GMRES(m) (FP64) with right Jacobi preconditioning on the SELL-32 layout.
 //
-// Sec. III-B solves every corrector pass's system with a restarted GMRES(m) to a 1e-10 residual, m tuned per mesh;
+// Sec. III-B solves every corrector pass's system with a restarted GMRES(m) to a 1e-10 residual, m tuned per mesh,
+// and notes that an m adapted during the simulation and for each solution would reduce the stagnation it observes;
 // Sec. II-B: GMRES suits general (nonsymmetric) systems. Here one cooperative launch runs all cycles:
 //   cycle start (SpMV):  r = b - A x, partial (r, r)                                   -- barrier: beta = ||r|| --
 //   Arnoldi step j, with u the unnormalised new basis vector and s its norm (r, beta for j = 0):
-//     S (SpMV):   v_j = u / s (own rows),  w = A M^-1 u / s,  partials h_ij = (w, v_i), i <= j       -- barrier --
-//     O1:         w -= sum_i h_ij v_i,  partials c_ij = (w, v_i)                                    -- barrier --
-//     O2:         w -= sum_i c_ij v_i,  h_ij += c_ij,  partial (w, w)      -- barrier: h_{j+1,j} = ||w|| --
-//   (classical Gram-Schmidt with one reorthogonalisation); every block applies the Givens rotations to column j
-//   of the Hessenberg matrix in shared memory (same inputs, same bits) and reads the residual estimate |g_{j+1}|.
+//     S (SpMV):   v_j = u / s (own rows),  w = A M^-1 u / s,
+//                 partials h_ij = (w, v_i), i <= j, and (w, w)                                       -- barrier --
+//     then, by Pythagoras, ||w - sum_i h_ij v_i||^2 = (w, w) - sum_i h_ij^2. While that keeps at least half of
+//     (w, w) the cancellation is mild and the norm is accurate, so one pass suffices:
+//     O:          w -= sum_i h_ij v_i                                    -- barrier (before the next SpMV) --
+//     otherwise classical Gram-Schmidt is repeated once ("twice is enough", Kahan-Parlett):
+//     O1:         w -= sum_i h_ij v_i,  partials c_ij = (w, v_i), (w, w)                            -- barrier --
+//     O2:         w -= sum_i c_ij v_i,  h_ij += c_ij,  ||w||^2 = (w, w) - sum_i c_ij^2            -- barrier --
+//   Every block applies the Givens rotations to column j of the Hessenberg matrix in shared memory (same inputs,
+//   same bits) and reads the residual estimate |g_{j+1}|; the step that reaches the tolerance or ends the cycle
+//   skips its O phase (w is not needed).
 //   cycle end:    y = R^-1 g (back substitution),  x += M^-1 sum_i y_i v_i (own rows)              -- barrier --
-// The cycle restarts until the true residual of a cycle start meets the tolerance. Dots are reduced per warp with
-// shuffles, per block in shared memory and across blocks in a fixed order (deterministic). Every barrier wait is
-// bounded.
+// The cycle restarts until the true residual of a cycle start meets the tolerance.
+//
+// Restart length. With m_min > 0 the length of each cycle adapts between m_min and m (the allocated basis) by the
+// rule of Baker, Jessup and Kolev, "A simple strategy for varying the restart parameter in GMRES(m)", J. Comput.
+// Appl. Math. 230 (2009): with cr the ratio of the true residual norms at the start of this cycle and the last,
+// cr > cos(8 deg) (stagnation) sets m; cr < cos(80 deg) (fast) keeps the length; otherwise the length drops by 3,
+// back to m once it would fall below m_min. The length a solve ends with starts the next solve of the same system
+// (the simulation's solves adapt too). Stagnation handling: cycles at the full length m that reduce the residual
+// by less than 0.1% are counted, and two in a row end the solve (RAFEM_NOT_CONVERGED) instead of burning the
+// iteration cap: at that rate a reduction of 1e-10 would take more than 23,000 cycles.
+// Dots are reduced per warp with shuffles, per block in shared memory and across blocks in a fixed order
+// (deterministic). Every barrier wait is bounded.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,7 +45,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kBatch = 8;
 
 struct Args {
-    int N, m;
+    int N, m, m_min;        // basis size (the longest cycle); shortest adaptive cycle (0: every cycle has m steps)
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
@@ -46,7 +62,15 @@ struct Args {
     double tol;
     int max_iter;
     long long spin_limit_ns;
+    int32_t* m_state;       // adaptive length the next solve starts with (read at launch, written at the end)
 };
+
+// Restart-length rule (Baker, Jessup, Kolev 2009): thresholds on the cycle's convergence ratio and the decrement.
+constexpr double kMaxCr = 0.99026806874157031;   // cos(8 deg)
+constexpr double kMinCr = 0.17364817766693041;   // cos(80 deg)
+constexpr int kDecrement = 3;
+constexpr double kStagnant = 0.999;              // a full-length cycle keeping 99.9% of the residual is stagnant
+constexpr int kStagnantStop = 2;                 // consecutive stagnant full-length cycles that end the solve
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
@@ -118,14 +142,17 @@ __device__ __forceinline__ void totals(const double* part, int n, double* tot) {
 // all its rows and the warp reduces them once per group of kDot basis vectors (a warp reduction per row and
 // vector would serialise the warp on shuffle latency). w holds values this thread wrote itself.
 constexpr int kDot = 8;
-__device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, int S) {
+// self: also (w, w) into acc[.][n], accumulated in the first group's pass over the rows.
+__device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, int S, bool self = false) {
     for (int i0 = 0; i0 < n; i0 += kDot) {
-        double sum[kDot];
+        double sum[kDot], ww = 0.0;
 #pragma unroll
         for (int t = 0; t < kDot; ++t) sum[t] = 0.0;
+        const bool with_self = self && i0 == 0;
         for_slices(S, [&](int, int row) {
             if (row >= a.N) return;
             const double wi = w[row];
+            if (with_self) ww = fma(wi, wi, ww);
 #pragma unroll
             for (int t = 0; t < kDot; ++t)
                 if (i0 + t < n) sum[t] = fma(wi, ldcg(a.Vb + (size_t)(i0 + t) * a.N + row), sum[t]);
@@ -133,6 +160,7 @@ __device__ __forceinline__ void dots(const Args& a, double* acc, const double* w
 #pragma unroll
         for (int t = 0; t < kDot; ++t)
             if (i0 + t < n) warp_add(acc, i0 + t, sum[t]);
+        if (with_self) warp_add(acc, n, ww);
     }
 }
 
@@ -176,6 +204,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         bb = tot[0];
     }
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
+    // restart length of the current cycle (adaptive: from the previous solve of this system)
+    int m_cur = m;
+    if (a.m_min > 0 && a.m_state) m_cur = min(max(*(volatile int32_t*)a.m_state, a.m_min), m);
+    double rr_prev = -1.0;
+    int stagnant = 0, reorths = 0;
     while (!err) {
         // cycle start: r = b - A x into w[0], (r, r)
         {
@@ -195,6 +228,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         if (!(rr == rr)) { status = RAFEM_ERR_NONFINITE; break; }
         if (rr <= thr) { status = RAFEM_OK; break; }
         if (iters >= a.max_iter) break;
+        if (rr_prev > 0.0) {
+            // the last cycle's convergence ratio decides this cycle's length (every block: same bits)
+            const double cr = sqrt(rr / rr_prev);
+            if (m_cur == m && cr > kStagnant) {
+                if (++stagnant >= kStagnantStop) break;  // stagnated at the full length: NOT_CONVERGED
+            } else {
+                stagnant = 0;
+            }
+            if (a.m_min > 0) {
+                if (cr > kMaxCr)
+                    m_cur = m;
+                else if (cr >= kMinCr)
+                    m_cur = m_cur - kDecrement >= a.m_min ? m_cur - kDecrement : m;
+            }
+        }
+        rr_prev = rr;
         ++cycles;
         if (threadIdx.x == 0) {
             g[0] = sqrt(rr);
@@ -203,77 +252,81 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         __syncthreads();
         double scale = sqrt(rr);  // norm of the unnormalised vector held in w[cur]
         int cur = 0, k = 0;
-        for (int j = 0; j < m; ++j) {
+        for (int j = 0; j < m_cur; ++j) {
             const double* u = a.w[cur];
             double* wn = a.w[cur ^ 1];
             double* vj = a.Vb + (size_t)j * N;
+            double* Hj = H + (size_t)j * (m + 1);
             const double inv = 1.0 / scale;
-            // S: v_j = u / s, w = A M^-1 u / s, then h_ij = (w, v_i) for i <= j
+            // S: v_j = u / s, w = A M^-1 u / s, then h_ij = (w, v_i) for i <= j and (w, w)
             for_slices(S, [&](int s, int row) {
                 if (row >= N) return;
                 wn[row] = spmv_row(a, u, a.dinv, s, row) * inv;
                 vj[row] = ldcg(u + row) * inv;
             });
-            dots(a, acc, wn, j + 1, S);
-            publish(acc, j + 1, PA);
+            dots(a, acc, wn, j + 1, S, true);
+            publish(acc, j + 2, PA);
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
-            totals(PA, j + 1, tot);
-            for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(size_t)j * (m + 1) + i] = tot[i];
+            totals(PA, j + 2, tot);
+            double proj = 0.0;  // sum_i h_ij^2 (same order in every block)
+            for (int i = 0; i <= j; ++i) proj = fma(tot[i], tot[i], proj);
+            const double ww = tot[j + 1];
+            double nh2 = ww - proj;
+            const bool reorth = !(nh2 >= 0.5 * ww);
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = tot[i];
             __syncthreads();
-            // O1: w -= sum_i h_ij v_i, then c_ij = (w, v_i)
-            for_slices(S, [&](int, int row) {
-                if (row >= N) return;
-                double wi = wn[row];
-                for (int i = 0; i <= j; ++i)
-                    wi = fma(-H[(size_t)j * (m + 1) + i], ldcg(a.Vb + (size_t)i * N + row), wi);
-                wn[row] = wi;
-            });
-            dots(a, acc, wn, j + 1, S);
-            publish(acc, j + 1, PB);
-            if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
-            totals(PB, j + 1, tot);
-            // O2: w -= sum_i c_ij v_i, h_ij += c_ij, (w, w)
-            {
-                double v = 0.0;
+            if (reorth) {
+                ++reorths;
+                // O1: w -= sum_i h_ij v_i, then c_ij = (w, v_i) and (w, w)
                 for_slices(S, [&](int, int row) {
                     if (row >= N) return;
                     double wi = wn[row];
-                    for (int i = 0; i <= j; ++i) wi = fma(-tot[i], ldcg(a.Vb + (size_t)i * N + row), wi);
+                    for (int i = 0; i <= j; ++i) wi = fma(-Hj[i], ldcg(a.Vb + (size_t)i * N + row), wi);
                     wn[row] = wi;
-                    v = fma(wi, wi, v);
                 });
-                __syncthreads();
-                for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(size_t)j * (m + 1) + i] += tot[i];
-                warp_add(acc, 0, v);
-                publish(acc, 1, PC);
+                dots(a, acc, wn, j + 1, S, true);
+                publish(acc, j + 2, PB);
                 if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
-                totals(PC, 1, tot);
+                totals(PB, j + 2, tot);
+                double c2 = 0.0;
+                for (int i = 0; i <= j; ++i) c2 = fma(tot[i], tot[i], c2);
+                nh2 = tot[j + 1] - c2;
+                for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] += tot[i];
+                __syncthreads();
             }
-            const double hn = sqrt(tot[0]);
+            const double hn = sqrt(fmax(nh2, 0.0));
             // Givens rotations on column j (thread 0; every block computes the same bits)
             if (threadIdx.x == 0) {
-                double* col = H + (size_t)j * (m + 1);
-                col[j + 1] = hn;
+                Hj[j + 1] = hn;
                 for (int i = 0; i < j; ++i) {
-                    const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
-                    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-                    col[i] = t0;
+                    const double t0 = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+                    Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+                    Hj[i] = t0;
                 }
-                const double den = hypot(col[j], col[j + 1]);
-                const double c = den > 0.0 ? col[j] / den : 1.0, sv = den > 0.0 ? col[j + 1] / den : 0.0;
+                const double den = hypot(Hj[j], Hj[j + 1]);
+                const double c = den > 0.0 ? Hj[j] / den : 1.0, sv = den > 0.0 ? Hj[j + 1] / den : 0.0;
                 cs[j] = c;
                 sn[j] = sv;
-                col[j] = den;
-                col[j + 1] = 0.0;
+                Hj[j] = den;
+                Hj[j + 1] = 0.0;
                 g[j + 1] = -sv * g[j];
                 g[j] = c * g[j];
             }
             __syncthreads();
             ++iters;
             k = j + 1;
+            if (g[j + 1] * g[j + 1] <= thr || !(hn > 0.0) || iters >= a.max_iter || j + 1 == m_cur) break;
+            // O (or O2): the next basis vector, unnormalised; its norm hn is already known. tot holds the h_ij of
+            // the single pass, or the c_ij of the second pass.
+            for_slices(S, [&](int, int row) {
+                if (row >= N) return;
+                double wi = wn[row];
+                for (int i = 0; i <= j; ++i) wi = fma(-tot[i], ldcg(a.Vb + (size_t)i * N + row), wi);
+                wn[row] = wi;
+            });
+            if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
             scale = hn;
             cur ^= 1;
-            if (g[j + 1] * g[j + 1] <= thr || !(hn > 0.0) || iters >= a.max_iter) break;
         }
         if (err) break;
         // y = R^-1 g, x += M^-1 sum_i y_i v_i
@@ -294,12 +347,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         });
         if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
     }
+    if (a.m_state && blockIdx.x == 0 && threadIdx.x == 0) *a.m_state = m_cur;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         InstState st = {};
         st.bb = bb;
         st.rr = rr;
         st.iters = iters;
         st.refine = cycles;
+        st.breakdowns = reorths;  // Arnoldi steps that needed the second Gram-Schmidt pass
+        st.outer = m_cur;         // restart length of the last cycle
         st.status = err ? (a.bar->err ? a.bar->err : RAFEM_ERR_TIMEOUT) : status;
         st.relres = sqrt(rr / (bb > 0.0 ? bb : 1.0));
         a.inst[0] = st;
@@ -323,8 +379,8 @@ int gmres_max_blocks(int m) {
 }
 
 cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
-    Args a{s.N, s.m, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.dinv, s.partial, s.bar,
-           s.inst, s.tol, s.max_iter, s.spin_limit_ns};
+    Args a{s.N, s.m, s.m_min, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.dinv, s.partial, s.bar,
+           s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.m_state};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;

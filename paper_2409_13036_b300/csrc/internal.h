@@ -303,7 +303,9 @@ namespace rafem {
 // Persistent restarted GMRES(m), FP64, right Jacobi preconditioning, SELL-32 primary storage (gmres.cu).
 // ------------------------------------------------------------------------------------------------------------
 struct GmresArgs {
-    int N, m;                        // rows, restart length (1..64)
+    int N, m;                        // rows, restart length (1..64): the longest cycle
+    int m_min;                       // 0: every cycle has m steps; else cycles adapt between m_min and m
+    int32_t* m_state;                // device: adaptive length the next solve starts with (nullable)
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;

@@ -70,7 +70,7 @@ class rafem_params(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
                 ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("coupling", ctypes.c_int32), ("arith", ctypes.c_int32),
-                ("proj_basis", ctypes.c_int32)]
+                ("proj_basis", ctypes.c_int32), ("gmres_min_restart", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):

@@ -123,3 +123,24 @@ def test_dw_run_matches_fp64_run():
     for k in (0, 1):
         a, b = fields[rafem.RAFEM_ARITH_FP64][k], fields[rafem.RAFEM_ARITH_DW][k]
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a), k
+
+
+def test_dw_matches_fp64_on_the_48_cube_after_ten_steps():
+    """The 48^3 workload (117,649 nodes, jitter 10%): ten FP64 steps with double-word element passes against ten
+    with FP64 element passes, both solved to a relative residual of 1e-13. The entries differ by at most
+    DW_REL (2.3e-13) of their row's magnitude and each solve leaves a residual of at most 1e-13, so the fields may
+    differ by about cond(A) x (2.3e-13 + 2e-13); cond(A_V) is ~1e3 at this size (the potential system's condition
+    number grows like the square of the cells per side: ~1e2 at 14^3, ~1e5 at 127^3), giving ~4e-10. The bound
+    1e-9 keeps a factor 2 for the ten steps' accumulation."""
+    rafem = R()
+    m = mg.workload_48()
+    fields = {}
+    for arith in (rafem.RAFEM_ARITH_FP64, rafem.RAFEM_ARITH_DW):
+        with rafem.Context(m, arith=arith, tol=1e-13) as ctx:
+            assert ctx.layout_info()["arith"] == arith
+            status, _ = ctx.run(10)
+            assert status == 0
+            fields[arith] = (ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V))
+    for k in (0, 1):
+        a, b = fields[rafem.RAFEM_ARITH_FP64][k], fields[rafem.RAFEM_ARITH_DW][k]
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a), (k, np.linalg.norm(a - b) / np.linalg.norm(a))
