@@ -157,6 +157,8 @@ struct rafem_ctx {
            *mb_sh = nullptr, *mb_t = nullptr, *mb_dinv = nullptr, *mb_partial = nullptr;
     int mb_grid = 0;
     double *gm_V = nullptr, *gm_w0 = nullptr, *gm_w1 = nullptr, *gm_dinv = nullptr, *gm_partial = nullptr;
+    double *gm_z = nullptr, *gm_H = nullptr;  // M^-1 of the next SpMV's input; per-block Hessenberg copies
+    int gm_ld = 0;                            // row stride of the basis
     // differentiation: element order map, tape of checkpoints, adjoint workspace
     int32_t* e_order = nullptr;      // [E] stored element -> mesh element
     int32_t* e_clist = nullptr;      // [E] stored elements in colour order (row-owner assembly), else null
@@ -546,10 +548,13 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.diag = c->diag;
         g.b = b;
         g.x = x;
+        g.ld = c->gm_ld;
         g.V = c->gm_V;
         g.w0 = c->gm_w0;
         g.w1 = c->gm_w1;
+        g.z = c->gm_z;
         g.dinv = c->gm_dinv;
+        g.H = c->gm_H;
         g.partial = c->gm_partial;
         g.bar = c->bar;
         g.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
@@ -1454,13 +1459,15 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     if (prm->solver == RAFEM_SOLVER_GMRES) {
         if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
         c->gm_m = prm->gmres_restart > 0 ? prm->gmres_restart : 30;
-        CK(dalloc(c, &c->gm_V, (size_t)c->gm_m * N + SELL_C));
-        for (double** v : {&c->gm_w0, &c->gm_w1, &c->gm_dinv}) CK(dalloc(c, v, (size_t)N + SELL_C));
+        c->gm_ld = (N + SELL_C - 1) / SELL_C * SELL_C;
+        CK(dalloc(c, &c->gm_V, (size_t)c->gm_m * c->gm_ld + SELL_C));
+        for (double** v : {&c->gm_w0, &c->gm_w1, &c->gm_z, &c->gm_dinv}) CK(dalloc(c, v, (size_t)N + SELL_C));
         c->gm_grid = gmres_max_blocks(c->gm_m);
         if (c->gm_grid <= 0) return RAFEM_ERR_CUDA;
+        c->gm_grid = std::min(c->gm_grid, (N + SELL_C - 1) / SELL_C);
         CK(dalloc(c, &c->gm_mstate, 2));  // per system; 0 = start at the full length
-
-        CK(dalloc(c, &c->gm_partial, (size_t)(2 * (c->gm_m + 1) + 2) * c->gm_grid));
+        CK(dalloc(c, &c->gm_partial, (size_t)gmres_partial_slots(c->gm_m) * c->gm_grid));
+        CK(dalloc(c, &c->gm_H, (size_t)c->gm_grid * (c->gm_m + 1) * c->gm_m));
     }
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC) {
         if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;

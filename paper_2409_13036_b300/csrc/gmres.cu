@@ -27,25 +27,34 @@
 // (the simulation's solves adapt too). Stagnation handling: cycles at the full length m that reduce the residual
 // by less than 0.1% are counted, and two in a row end the solve (RAFEM_NOT_CONVERGED) instead of burning the
 // iteration cap: at that rate a reduction of 1e-10 would take more than 23,000 cycles.
+//
+// Layout of the work: block b owns the rows [b R, (b + 1) R) (R a multiple of 32, one tile per block) in every
+// phase, so row-local vectors stay with their block. The SpMVs stream the matrix through the shared-memory ring of
+// the CG kernels (bulk copies by a producer warp, sell_ring.cuh) and gather z = M^-1 u, which the phase before
+// each SpMV writes for its own rows. The passes over the basis are row-local and vectorised: each thread takes
+// two consecutive rows (16-byte loads) and up to four basis vectors per batch, so every thread has five
+// independent loads in flight. The basis is stored with a row stride rounded up to a multiple of 32.
 // Dots are reduced per warp with shuffles, per block in shared memory and across blocks in a fixed order
-// (deterministic). Every barrier wait is bounded.
+// (deterministic). Every wait is bounded.
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "grid_sync.cuh"
 #include "internal.h"
+#include "sell_ring.cuh"
 
 namespace rafem {
 
 namespace {
 
-constexpr int kBlock = 512;
-constexpr int kWarps = kBlock / 32;
-constexpr int kBatch = 8;
+using namespace sell;
+
+constexpr int kAcc = 72;  // per-warp accumulator slots: up to 64 dots + (w, w)
 
 struct Args {
     int N, m, m_min;        // basis size (the longest cycle); shortest adaptive cycle (0: every cycle has m steps)
+    int ld;                 // row stride of the basis (N rounded up to a multiple of 32)
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
@@ -53,10 +62,12 @@ struct Args {
     const int32_t* diag;
     const double* b;
     double* x;
-    double* Vb;       // [m][N] basis
+    double* Vb;       // [m][ld] basis
     double* w[2];     // [N] alternating unnormalised vectors
+    double* z;        // [N] M^-1 of the vector the next SpMV multiplies
     double* dinv;     // [N]
-    double* partial;  // [2 (m + 1) + 2][grid]
+    double* H;        // [grid][(m + 1) m] Hessenberg matrix, one copy per block (column-major)
+    double* partial;  // [2 (m + 2) + 2][grid]
     GridBarrier* bar;
     InstState* inst;
     double tol;
@@ -72,60 +83,26 @@ constexpr int kDecrement = 3;
 constexpr double kStagnant = 0.999;              // a full-length cycle keeping 99.9% of the residual is stagnant
 constexpr int kStagnantStop = 2;                 // consecutive stagnant full-length cycles that end the solve
 
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-
-template <class Fn>
-__device__ __forceinline__ void for_slices(int S, const Fn& f) {
-    const int tw = gridDim.x * kWarps;
-    const int lane = threadIdx.x & 31;
-    for (int s = blockIdx.x * kWarps + (threadIdx.x >> 5); s < S; s += tw) f(s, s * 32 + lane);
-}
-
-// sum_k A_row,k dinv_k u_k (dinv = null: plain A u)
-__device__ __forceinline__ double spmv_row(const Args& a, const double* u, const double* dinv, int s, int row) {
-    const int lane = row & 31;
-    const int base = __ldg(a.sp + s), w = (__ldg(a.sp + s + 1) - base) >> 5;
-    double acc = 0.0;
-    for (int k = 0; k < w; k += kBatch) {
-        double m[kBatch], y[kBatch];
-        int c[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            const int pos = base + 32 * (k + t) + lane;
-            const bool ok = k + t < w;
-            m[t] = ok ? __ldg(a.A + pos) : 0.0;
-            c[t] = ok ? (a.sc16 ? row + (int)__ldg(a.sc16 + pos) : __ldg(a.sc + pos)) : -1;
-        }
-        // dinv is written in this launch, so it is read through L2 like the vectors
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t)
-            y[t] = c[t] >= 0 ? (dinv ? ldcg(u + c[t]) * ldcg(dinv + c[t]) : ldcg(u + c[t])) : 0.0;
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) acc = fma(m[t], y[t], acc);
-    }
-    return acc;
-}
-
-// Per-warp accumulation of up to n dot products into shared memory acc[warp][i] (lane 0 adds each warp sum).
+// Per-warp accumulation into shared memory acc[warp][i] (lane 0 adds the warp's sum).
 __device__ __forceinline__ void warp_add(double* acc, int i, double v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) acc[(threadIdx.x >> 5) * 72 + i] += v;
+    if ((threadIdx.x & 31) == 0) acc[(threadIdx.x >> 5) * kAcc + i] += v;
 }
 
-// Block sums of the n per-warp accumulators -> partial[i][blockIdx.x]; accumulators cleared for the next phase.
+// Block sums of the n per-warp accumulators -> part[i][blockIdx.x] (fixed order); accumulators cleared.
 __device__ __forceinline__ void publish(double* acc, int n, double* part) {
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += kBlock) {
         double s = 0.0;
-        for (int wp = 0; wp < kWarps; ++wp) s += acc[wp * 72 + i];
+        for (int wp = 0; wp < kWarps; ++wp) s += acc[wp * kAcc + i];
         part[(size_t)i * gridDim.x + blockIdx.x] = s;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kWarps * 72; i += blockDim.x) acc[i] = 0.0;
+    for (int i = threadIdx.x; i < kWarps * kAcc; i += kBlock) acc[i] = 0.0;
 }
 
-// After a barrier: tot[i] = sum over blocks of partial[i][.] (fixed order; warp per quantity).
+// After a barrier: tot[i] = sum over blocks of part[i][.] (fixed order; one warp per quantity).
 __device__ __forceinline__ void totals(const double* part, int n, double* tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < n; i += kWarps) {
@@ -138,67 +115,156 @@ __device__ __forceinline__ void totals(const double* part, int n, double* tot) {
     __syncthreads();
 }
 
-// acc[warp][i] += (w, v_i) over this warp's rows for i < n. Each lane keeps kDot running sums in registers over
-// all its rows and the warp reduces them once per group of kDot basis vectors (a warp reduction per row and
-// vector would serialise the warp on shuffle latency). w holds values this thread wrote itself.
-constexpr int kDot = 8;
-// self: also (w, w) into acc[.][n], accumulated in the first group's pass over the rows.
-__device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, int S, bool self = false) {
-    for (int i0 = 0; i0 < n; i0 += kDot) {
-        double sum[kDot], ww = 0.0;
+// The rows [r0, r1) of this block, two consecutive rows per thread (r0 even): f(i, 2) for a pair, f(i, 1) for a
+// single last row.
+template <class F>
+__device__ __forceinline__ void for_pairs(int r0, int r1, const F& f) {
+    for (int i = r0 + 2 * threadIdx.x; i < r1; i += 2 * kBlock) f(i, i + 1 < r1 ? 2 : 1);
+}
+
+// The same rows, two row pairs per call (i and i + 2 kBlock) so that the loads of both are in flight together:
+// f(i, ci, j, cj) with ci, cj in {0, 1, 2} rows (0: no such pair).
+template <class F>
+__device__ __forceinline__ void for_pairs2(int r0, int r1, const F& f) {
+    for (int i = r0 + 2 * threadIdx.x; i < r1; i += 4 * kBlock) {
+        const int j = i + 2 * kBlock;
+        f(i, i + 1 < r1 ? 2 : 1, j, j < r1 ? (j + 1 < r1 ? 2 : 1) : 0);
+    }
+}
+
+__device__ __forceinline__ double2 ld2(const double* p, int n) {
+    return n == 2 ? __ldcg(reinterpret_cast<const double2*>(p))
+                  : (n == 1 ? make_double2(__ldcg(p), 0.0) : make_double2(0.0, 0.0));
+}
+__device__ __forceinline__ void st2(double* p, double2 v, int n) {
+    if (n == 2)
+        *reinterpret_cast<double2*>(p) = v;
+    else if (n == 1)
+        p[0] = v.x;
+}
+
+constexpr int kVb = 4;  // basis vectors per batch of loads (more would spill: 17 warps cap a thread at 96 registers)
+
+// acc[warp][i] += (w, v_i) for i < n over the block's rows, and with self (w, w) into acc[warp][n].
+__device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, bool self, int r0, int r1) {
+    for (int i0 = 0; i0 < n; i0 += kVb) {
+        double sum[kVb], ww = 0.0;
 #pragma unroll
-        for (int t = 0; t < kDot; ++t) sum[t] = 0.0;
+        for (int t = 0; t < kVb; ++t) sum[t] = 0.0;
         const bool with_self = self && i0 == 0;
-        for_slices(S, [&](int, int row) {
-            if (row >= a.N) return;
-            const double wi = w[row];
-            if (with_self) ww = fma(wi, wi, ww);
+        for_pairs2(r0, r1, [&](int i, int ci, int j, int cj) {
+            const double2 wi = ld2(w + i, ci), wj = ld2(w + j, cj);
+            double2 v[kVb], u[kVb];
 #pragma unroll
-            for (int t = 0; t < kDot; ++t)
-                if (i0 + t < n) sum[t] = fma(wi, ldcg(a.Vb + (size_t)(i0 + t) * a.N + row), sum[t]);
+            for (int t = 0; t < kVb; ++t) {
+                const double* vt = a.Vb + (size_t)(i0 + t) * a.ld;
+                v[t] = ld2(vt + i, i0 + t < n ? ci : 0);
+                u[t] = ld2(vt + j, i0 + t < n ? cj : 0);
+            }
+#pragma unroll
+            for (int t = 0; t < kVb; ++t)
+                sum[t] = fma(wj.y, u[t].y, fma(wj.x, u[t].x, fma(wi.y, v[t].y, fma(wi.x, v[t].x, sum[t]))));
+            if (with_self) ww = fma(wj.y, wj.y, fma(wj.x, wj.x, fma(wi.y, wi.y, fma(wi.x, wi.x, ww))));
         });
 #pragma unroll
-        for (int t = 0; t < kDot; ++t)
+        for (int t = 0; t < kVb; ++t)
             if (i0 + t < n) warp_add(acc, i0 + t, sum[t]);
         if (with_self) warp_add(acc, n, ww);
     }
 }
 
+// w -= sum_{i < n} c_i v_i over the block's rows; with z, also z = dinv w (the next SpMV's input).
+__device__ __forceinline__ void subtract(const Args& a, double* w, const double* c_, int n, double* z, int r0, int r1) {
+    for_pairs2(r0, r1, [&](int i, int ci, int j, int cj) {
+        double2 wi = ld2(w + i, ci), wj = ld2(w + j, cj);
+        for (int i0 = 0; i0 < n; i0 += kVb) {
+            double2 v[kVb], u[kVb];
+#pragma unroll
+            for (int t = 0; t < kVb; ++t) {
+                const double* vt = a.Vb + (size_t)(i0 + t) * a.ld;
+                v[t] = ld2(vt + i, i0 + t < n ? ci : 0);
+                u[t] = ld2(vt + j, i0 + t < n ? cj : 0);
+            }
+#pragma unroll
+            for (int t = 0; t < kVb; ++t) {
+                const double ct = i0 + t < n ? c_[i0 + t] : 0.0;
+                wi.x = fma(-ct, v[t].x, wi.x);
+                wi.y = fma(-ct, v[t].y, wi.y);
+                wj.x = fma(-ct, u[t].x, wj.x);
+                wj.y = fma(-ct, u[t].y, wj.y);
+            }
+        }
+        st2(w + i, wi, ci);
+        st2(w + j, wj, cj);
+        if (z) {
+            const double2 di = ld2(a.dinv + i, ci), dj = ld2(a.dinv + j, cj);
+            st2(z + i, make_double2(di.x * wi.x, di.y * wi.y), ci);
+            st2(z + j, make_double2(dj.x * wj.x, dj.y * wj.y), cj);
+        }
+    });
+}
+
+// r = b - A x at the start of a cycle: w0 = r, z = M^-1 r, partial (r, r)
+struct EmStart {
+    const Args& a;
+    double* v;
+    __device__ __forceinline__ double pre(int row) const { return a.b[row]; }
+    __device__ __forceinline__ void fin(int row, double ax, double bi) const {
+        const double r = bi - ax;
+        a.w[0][row] = r;
+        a.z[row] = ldcg(a.dinv + row) * r;
+        v[0] = fma(r, r, v[0]);
+    }
+};
+
+// Arnoldi step: w = A M^-1 u / s, v_j = u / s
+struct EmArnoldi {
+    const double* u;
+    double* wn;
+    double* vj;
+    double inv;
+    __device__ __forceinline__ double pre(int row) const { return ldcg(u + row); }
+    __device__ __forceinline__ void fin(int row, double az, double ui) const {
+        wn[row] = az * inv;
+        vj[row] = ui * inv;
+    }
+};
+
+template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
-    extern __shared__ double smem[];
-    // layout: acc [kWarps][72] | H [(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | tot[72] | y[m]
-    const int m = a.m;
-    double* acc = smem;
-    double* H = acc + kWarps * 72;
-    double* cs = H + (size_t)(m + 1) * m;
-    double* sn = cs + m;
-    double* g = sn + m;
-    double* tot = g + (m + 1);
-    double* yv = tot + 72;
-    for (int i = threadIdx.x; i < kWarps * 72; i += blockDim.x) acc[i] = 0.0;
-    __syncthreads();
-    // partial-sum buffers of consecutive phases are disjoint: S -> PA, O1 -> PB, O2 -> PC, cycle start -> PD
+    RAFEM_RING_SETUP(L)
+    using CT = typename std::conditional<L == 2, int16_t, int32_t>::type;
+    const CT* sc = L == 2 ? reinterpret_cast<const CT*>(a.sc16) : reinterpret_cast<const CT*>(a.sc);
+    __shared__ double acc[kWarps * kAcc];
+    __shared__ double tot[kAcc];
+    __shared__ double cs[64], sn[64], g[65], yv[64];
+    __shared__ double sm[kSumMax * kBlock];
+    const int m = a.m, N = a.N;
+    double* H = a.H + (size_t)blockIdx.x * (m + 1) * m;
+    for (int i = threadIdx.x; i < kWarps * kAcc; i += kBlock) acc[i] = 0.0;
+    // this block's rows: whole slices [s0, s1); blocks past the last slice own no rows (block-uniform `own`)
+    const int S = (N + 31) / 32, spb = (S + gridDim.x - 1) / gridDim.x;
+    const int s0 = min((int)blockIdx.x * spb, S), s1 = min(s0 + spb, S);
+    const bool own = s0 < s1;
+    const int r0 = own ? s0 * 32 : N, r1 = own ? min(s1 * 32, N) : N;
+    // partial-sum buffers of consecutive phases are disjoint: S -> PA, O1 -> PB, cycle start and set-up -> PD
     const size_t G = gridDim.x;
     double* PA = a.partial;
-    double* PB = PA + (size_t)(m + 1) * G;
-    double* PC = PB + (size_t)(m + 1) * G;
-    double* PD = PC + G;
-    const int N = a.N, S = (N + 31) / 32;
+    double* PB = PA + (size_t)(m + 2) * G;
+    double* PD = PB + (size_t)(m + 2) * G;
     unsigned target = 0;
     bool err = false;
     int iters = 0, status = RAFEM_NOT_CONVERGED, cycles = 0;
     double bb = 0.0, rr = 0.0;
     // dinv = 1 / diag(A); (b, b)
     {
-        double v = 0.0;
-        for_slices(S, [&](int, int row) {
-            if (row < N) {
-                a.dinv[row] = 1.0 / __ldg(a.A + __ldg(a.diag + row));
-                v = fma(a.b[row], a.b[row], v);
-            }
-        });
-        warp_add(acc, 0, v);
-        publish(acc, 1, PD);
+        double v[1] = {0.0};
+        for (int row = r0 + threadIdx.x; row < r1; row += kBlock) {
+            a.dinv[row] = 1.0 / __ldg(a.A + __ldg(a.diag + row));
+            v[0] = fma(a.b[row], a.b[row], v[0]);
+        }
+        block_sum<1>(v, sm);
+        if (threadIdx.x == 0) PD[blockIdx.x] = v[0];
         err = grid_barrier(a.bar, a.spin_limit_ns, target);
         totals(PD, 1, tot);
         bb = tot[0];
@@ -210,19 +276,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     double rr_prev = -1.0;
     int stagnant = 0, reorths = 0;
     while (!err) {
-        // cycle start: r = b - A x into w[0], (r, r)
+        // cycle start: r = b - A x into w[0], z = M^-1 r, (r, r)
         {
-            double v = 0.0;
-            for_slices(S, [&](int s, int row) {
-                if (row >= N) return;
-                const double ri = a.b[row] - spmv_row(a, a.x, nullptr, s, row);
-                a.w[0][row] = ri;
-                v = fma(ri, ri, v);
-            });
-            warp_add(acc, 0, v);
-            publish(acc, 1, PD);
-            if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
-            totals(PD, 1, tot);
+            double v[1] = {0.0};
+            const bool ok = !own || sell_tile<double, double, CT>(a, ring, a.sp, sc, a.A, a.x, r0, r1, EmStart{a, v});
+            block_sum<1>(v, sm);
+            if (threadIdx.x == 0) PD[G + blockIdx.x] = v[0];
+            if (grid_barrier(a.bar, a.spin_limit_ns, target) || !ok) { err = true; break; }
+            totals(PD + G, 1, tot);
             rr = tot[0];
         }
         if (!(rr == rr)) { status = RAFEM_ERR_NONFINITE; break; }
@@ -255,44 +316,37 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         for (int j = 0; j < m_cur; ++j) {
             const double* u = a.w[cur];
             double* wn = a.w[cur ^ 1];
-            double* vj = a.Vb + (size_t)j * N;
+            double* vj = a.Vb + (size_t)j * a.ld;
             double* Hj = H + (size_t)j * (m + 1);
-            const double inv = 1.0 / scale;
-            // S: v_j = u / s, w = A M^-1 u / s, then h_ij = (w, v_i) for i <= j and (w, w)
-            for_slices(S, [&](int s, int row) {
-                if (row >= N) return;
-                wn[row] = spmv_row(a, u, a.dinv, s, row) * inv;
-                vj[row] = ldcg(u + row) * inv;
-            });
-            dots(a, acc, wn, j + 1, S, true);
+            // S: w = A M^-1 u / s and v_j = u / s (SpMV through the ring), then h_ij = (w, v_i), i <= j, and (w, w)
+            const bool ok = !own || sell_tile<double, double, CT>(a, ring, a.sp, sc, a.A, a.z, r0, r1,
+                                                                  EmArnoldi{u, wn, vj, 1.0 / scale});
+            dots(a, acc, wn, j + 1, true, r0, r1);
             publish(acc, j + 2, PA);
-            if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
+            if (grid_barrier(a.bar, a.spin_limit_ns, target) || !ok) { err = true; break; }
             totals(PA, j + 2, tot);
             double proj = 0.0;  // sum_i h_ij^2 (same order in every block)
             for (int i = 0; i <= j; ++i) proj = fma(tot[i], tot[i], proj);
             const double ww = tot[j + 1];
             double nh2 = ww - proj;
             const bool reorth = !(nh2 >= 0.5 * ww);
-            for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = tot[i];
-            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int i = 0; i <= j; ++i) Hj[i] = tot[i];
             if (reorth) {
                 ++reorths;
                 // O1: w -= sum_i h_ij v_i, then c_ij = (w, v_i) and (w, w)
-                for_slices(S, [&](int, int row) {
-                    if (row >= N) return;
-                    double wi = wn[row];
-                    for (int i = 0; i <= j; ++i) wi = fma(-Hj[i], ldcg(a.Vb + (size_t)i * N + row), wi);
-                    wn[row] = wi;
-                });
-                dots(a, acc, wn, j + 1, S, true);
+                __syncthreads();
+                subtract(a, wn, tot, j + 1, nullptr, r0, r1);
+                __syncthreads();  // tot is overwritten below; every thread has finished with it
+                dots(a, acc, wn, j + 1, true, r0, r1);
                 publish(acc, j + 2, PB);
                 if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
                 totals(PB, j + 2, tot);
                 double c2 = 0.0;
                 for (int i = 0; i <= j; ++i) c2 = fma(tot[i], tot[i], c2);
                 nh2 = tot[j + 1] - c2;
-                for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] += tot[i];
-                __syncthreads();
+                if (threadIdx.x == 0)
+                    for (int i = 0; i <= j; ++i) Hj[i] += tot[i];
             }
             const double hn = sqrt(fmax(nh2, 0.0));
             // Givens rotations on column j (thread 0; every block computes the same bits)
@@ -316,14 +370,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
             ++iters;
             k = j + 1;
             if (g[j + 1] * g[j + 1] <= thr || !(hn > 0.0) || iters >= a.max_iter || j + 1 == m_cur) break;
-            // O (or O2): the next basis vector, unnormalised; its norm hn is already known. tot holds the h_ij of
-            // the single pass, or the c_ij of the second pass.
-            for_slices(S, [&](int, int row) {
-                if (row >= N) return;
-                double wi = wn[row];
-                for (int i = 0; i <= j; ++i) wi = fma(-tot[i], ldcg(a.Vb + (size_t)i * N + row), wi);
-                wn[row] = wi;
-            });
+            // O (or O2): the next basis vector, unnormalised (its norm hn is known), and z = M^-1 of it. tot holds
+            // the h_ij of the single pass, or the c_ij of the second pass.
+            subtract(a, wn, tot, j + 1, a.z, r0, r1);
             if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
             scale = hn;
             cur ^= 1;
@@ -339,11 +388,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
             }
         }
         __syncthreads();
-        for_slices(S, [&](int, int row) {
-            if (row >= N) return;
-            double t = 0.0;
-            for (int i = 0; i < k; ++i) t = fma(yv[i], ldcg(a.Vb + (size_t)i * N + row), t);
-            a.x[row] = fma(a.dinv[row], t, a.x[row]);
+        for_pairs(r0, r1, [&](int i, int c) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int i0 = 0; i0 < k; i0 += kVb) {
+                double2 v[kVb];
+#pragma unroll
+                for (int q = 0; q < kVb; ++q)
+                    v[q] = i0 + q < k ? ld2(a.Vb + (size_t)(i0 + q) * a.ld + i, c) : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 0; q < kVb; ++q) {
+                    const double yq = i0 + q < k ? yv[i0 + q] : 0.0;
+                    t.x = fma(yq, v[q].x, t.x);
+                    t.y = fma(yq, v[q].y, t.y);
+                }
+            }
+            // x is the caller's buffer (no alignment beyond 8 bytes is assumed): scalar accesses
+            const double2 d = ld2(a.dinv + i, c);
+            a.x[i] = fma(d.x, t.x, a.x[i]);
+            if (c == 2) a.x[i + 1] = fma(d.y, t.y, a.x[i + 1]);
         });
         if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
     }
@@ -362,30 +424,32 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     }
 }
 
-size_t smem_bytes(int m) {
-    return sizeof(double) * ((size_t)kWarps * 72 + (size_t)(m + 1) * m + m + m + (m + 1) + 72 + m);
-}
+void* kernel_for(const GmresArgs& s) { return s.sc16 ? (void*)k_gmres<2> : (void*)k_gmres<1>; }
 
 }  // namespace
 
-int gmres_max_blocks(int m) {
-    int dev = 0, sms = 0, per = 0;
+int gmres_max_blocks(int /*m*/) {
+    int dev = 0, sms = 0, per1 = 0, per2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const size_t sh = smem_bytes(m);
-    if (cudaFuncSetAttribute(k_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres, kBlock, sh) != cudaSuccess) return 0;
+    for (void* k : {(void*)k_gmres<1>, (void*)k_gmres<2>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_gmres<1>, kBlock, kRingBytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_gmres<2>, kBlock, kRingBytes) != cudaSuccess) return 0;
+    const int per = per1 < per2 ? per1 : per2;
     return sms * (per < 1 ? per : 1);
 }
 
+int gmres_partial_slots(int m) { return 2 * (m + 2) + 2; }
+
 cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
-    Args a{s.N, s.m, s.m_min, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.dinv, s.partial, s.bar,
-           s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.m_state};
+    Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.z, s.dinv, s.H,
+           s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.m_state};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;
     void* params[] = {&a};
-    return cudaLaunchCooperativeKernel((const void*)k_gmres, dim3(grid), dim3(kBlock), params, smem_bytes(s.m), st);
+    return cudaLaunchCooperativeKernel(kernel_for(s), dim3(grid), dim3(kBlock), params, kRingBytes, st);
 }
 
 }  // namespace rafem

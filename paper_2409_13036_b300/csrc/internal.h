@@ -306,6 +306,7 @@ struct GmresArgs {
     int N, m;                        // rows, restart length (1..64): the longest cycle
     int m_min;                       // 0: every cycle has m steps; else cycles adapt between m_min and m
     int32_t* m_state;                // device: adaptive length the next solve starts with (nullable)
+    int ld;                          // row stride of the basis: N rounded up to a multiple of 32
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
@@ -313,9 +314,10 @@ struct GmresArgs {
     const int32_t* diag;
     const double* b;
     double* x;
-    double* V;                       // [m][N] basis
-    double *w0, *w1, *dinv;          // [N]
-    double* partial;                 // [2 (m + 1) + 2][grid]
+    double* V;                       // [m][ld] basis
+    double *w0, *w1, *z, *dinv;      // [N]
+    double* H;                       // [grid][(m + 1) m] Hessenberg matrix, one copy per block
+    double* partial;                 // [gmres_partial_slots(m)][grid]
     GridBarrier* bar;
     InstState* inst;                 // iters = Arnoldi steps, refine = restart cycles
     double tol;
@@ -324,6 +326,7 @@ struct GmresArgs {
     int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 int gmres_max_blocks(int m);
+int gmres_partial_slots(int m);
 cudaError_t launch_gmres(const GmresArgs& a, int grid, cudaStream_t st);
 
 }  // namespace rafem
