@@ -422,15 +422,17 @@ def roofline(res, mixed, peaks, peak_kind):
     steps = tr["steps"]
     solve_ms = tr["ms_solve_V"] / steps
     iters = tr["iters_V"] / steps
-    cb = res["layout"]["column_bytes"]
     code = res["layout"]["kernel_code"]
+    # kernel code 3: the CG-family solvers stream no per-entry columns (one column pattern per slice)
+    cb_cg = 0 if code == 3 else res["layout"]["column_bytes"]
+    cb = res["layout"]["column_bytes"]
     if res.get("solver") == "gmres":
         ref = tr["refine_V"] / steps
         alg = alg_bytes_gmres(N, nnz, iters, ref, cb)
         kern = "k_gmres"
     elif res.get("solver") == "pipecg":
         ref = 0.0
-        alg = alg_bytes_pipecg(N, nnz, iters, cb)
+        alg = alg_bytes_pipecg(N, nnz, iters, cb_cg)
         kern = f"k_pcg64<{code}>"
     elif res.get("solver") == "bicgstab":
         ref = 0.0
@@ -442,11 +444,11 @@ def roofline(res, mixed, peaks, peak_kind):
         kern = "k_ilu_pcg"
     elif mixed:
         ref = tr["refine_V"] / steps
-        alg = alg_bytes_mixed(N, nnz, iters, ref, cb)
+        alg = alg_bytes_mixed(N, nnz, iters, ref, cb_cg)
         kern = f"k_cg_mixed<{code}>"
     else:
         ref = 0.0
-        alg = alg_bytes_cg64(N, nnz, iters, cb)
+        alg = alg_bytes_cg64(N, nnz, iters, cb_cg)
         kern = f"k_cg64<{code}>"
     achieved = alg / (solve_ms * 1e-3) / 1e9
     fp64_pipe = None

@@ -53,6 +53,7 @@ struct rafem_ctx {
     // pattern and the CSR -> storage map stay on the host for inspection
     int32_t *rp = nullptr, *ci = nullptr, *diag = nullptr;
     int16_t* ci16 = nullptr;  // SELL column deltas (when they fit 16 bits)
+    int32_t *pat_off = nullptr, *pat_pool = nullptr;  // one column pattern per slice (kernel code 3)
     bool sell = true;
     int64_t nnz_store = 0;
     std::vector<int32_t> h_rp, h_col, h_map;
@@ -379,6 +380,8 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
     a.rp = c->rp;
     a.ci = c->ci;
     a.ci16 = c->ci16;
+    a.pat_off = c->pat_off;
+    a.pat_pool = c->pat_pool;
     a.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
     a.A32 = which == RAFEM_SYS_V ? c->valsV32 : c->valsT32;
     a.diag = c->diag;
@@ -1243,10 +1246,14 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     std::vector<int16_t> d16;
     std::vector<int32_t> g_off, g_cnt, g_elem, i_off, i_cnt, i_elem;
     std::vector<uint8_t> g_idx;
+    std::vector<int32_t> pat_off, pat_pool;
+    bool patterns = false;
     if (c->sell) {
         std::vector<int32_t> map;
-        build_sell(N, rp, col, dev_rp, dev_ci, map);
-        if (c->gather) build_gather(N, E, rp, col, slots, dev_rp, g_off, g_cnt, g_elem, g_idx);
+        // one column pattern per slice where that widens no slice (lattice-like numberings), else per-entry columns
+        patterns = build_sell_patterns(N, rp, col, dev_rp, dev_ci, map, pat_off, pat_pool);
+        if (!patterns) build_sell(N, rp, col, dev_rp, dev_ci, map);
+        if (c->gather) build_gather(N, E, rp, col, slots, dev_rp, map, g_off, g_cnt, g_elem, g_idx);
         if (want16) {
             bool fits = true;
             d16.resize(dev_ci.size());
@@ -1264,6 +1271,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
             if (fits) c->lanes = 2;
             else d16.clear();
         }
+        if (patterns) c->lanes = 3;
         c->nnz_store = (int64_t)dev_ci.size();
         if (c->nnz_store >= (int64_t)SLOT_MASK) return RAFEM_ERR_BAD_INPUT;
 #pragma omp parallel for schedule(static)
@@ -1385,6 +1393,13 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     if (!d16.empty()) {
         CK(dalloc(c, &c->ci16, d16.size()));
         CK(cudaMemcpyAsync(c->ci16, d16.data(), d16.size() * sizeof(int16_t), cudaMemcpyHostToDevice, st));
+    }
+    if (patterns) {
+        CK(dalloc(c, &c->pat_off, pat_off.size()));
+        CK(dalloc(c, &c->pat_pool, pat_pool.size()));
+        CK(cudaMemcpyAsync(c->pat_off, pat_off.data(), pat_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->pat_pool, pat_pool.data(), pat_pool.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           st));
     }
     CK(cudaMemcpyAsync(c->diag, diag.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->e_nodes, nodes_soa.data(), nodes_soa.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));

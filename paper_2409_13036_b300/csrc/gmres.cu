@@ -234,7 +234,7 @@ template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     RAFEM_RING_SETUP(L)
     using CT = typename std::conditional<L == 2, int16_t, int32_t>::type;
-    const CT* sc = L == 2 ? reinterpret_cast<const CT*>(a.sc16) : reinterpret_cast<const CT*>(a.sc);
+    const EntryCols<CT> sc{L == 2 ? reinterpret_cast<const CT*>(a.sc16) : reinterpret_cast<const CT*>(a.sc)};
     __shared__ double acc[kWarps * kAcc];
     __shared__ double tot[kAcc];
     __shared__ double cs[64], sn[64], g[65], yv[64];
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         // cycle start: r = b - A x into w[0], z = M^-1 r, (r, r)
         {
             double v[1] = {0.0};
-            const bool ok = !own || sell_tile<double, double, CT>(a, ring, a.sp, sc, a.A, a.x, r0, r1, EmStart{a, v});
+            const bool ok = !own || sell_tile<double, double>(a, ring, a.sp, sc, a.A, a.x, r0, r1, EmStart{a, v});
             block_sum<1>(v, sm);
             if (threadIdx.x == 0) PD[G + blockIdx.x] = v[0];
             if (grid_barrier(a.bar, a.spin_limit_ns, target) || !ok) { err = true; break; }
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
             double* vj = a.Vb + (size_t)j * a.ld;
             double* Hj = H + (size_t)j * (m + 1);
             // S: w = A M^-1 u / s and v_j = u / s (SpMV through the ring), then h_ij = (w, v_i), i <= j, and (w, w)
-            const bool ok = !own || sell_tile<double, double, CT>(a, ring, a.sp, sc, a.A, a.z, r0, r1,
+            const bool ok = !own || sell_tile<double, double>(a, ring, a.sp, sc, a.A, a.z, r0, r1,
                                                                   EmArnoldi{u, wn, vj, 1.0 / scale});
             dots(a, acc, wn, j + 1, true, r0, r1);
             publish(acc, j + 2, PA);

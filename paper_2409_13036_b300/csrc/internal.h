@@ -153,6 +153,8 @@ struct SolveArgs {
     const int32_t* rp;
     const int32_t* ci;
     const int16_t* ci16;  // SELL-32 column deltas col - row (kernel code 2), when every delta fits 16 bits
+    const int32_t* pat_off;   // kernel code 3: first offset of each slice's column pattern in pat_pool
+    const int32_t* pat_pool;  // kernel code 3: the distinct slice patterns (column - row per slot)
     const double* A;
     const float* A32;
     const int32_t* diag;  // slot of the diagonal entry of each row
@@ -184,8 +186,8 @@ struct SolveArgs {
     int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
 };
 
-// Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 4/8/16/32 = CSR with that
-// many lanes per row.
+// Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 3 = SELL-32 whose slices
+// share one column pattern (values streamed, no columns), 4/8/16/32 = CSR with that many lanes per row.
 int krylov_max_blocks(int lanes, int precision, bool pipelined, int* block_threads);
 cudaError_t launch_krylov(const SolveArgs& a, int lanes, int precision, bool pipelined, int grid, int block,
                           cudaStream_t st);

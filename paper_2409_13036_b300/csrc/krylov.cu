@@ -59,14 +59,16 @@ __device__ __forceinline__ bool grid_wait(const SolveArgs& a, unsigned& target) 
 }
 
 // SpMV over rows [r0, r1) of one tile in the context's storage: SELL-32 through the ring (L = 1: 32-bit columns,
-// L = 2: 16-bit column deltas) or CSR with L lanes per row.
+// L = 2: 16-bit column deltas, L = 3: one column pattern per slice, values only) or CSR with L lanes per row.
 template <int L, typename VT, typename AT, class Emit>
 __device__ __forceinline__ bool spmv_tile(const SolveArgs& a, Ring& g, const VT* A, const VT* xin, int r0, int r1,
                                           const Emit& em) {
     if constexpr (L == 1) {
-        return sell_tile<VT, AT, int32_t>(a, g, a.rp, a.ci, A, xin, r0, r1, em);
+        return sell_tile<VT, AT>(a, g, a.rp, EntryCols<int32_t>{a.ci}, A, xin, r0, r1, em);
     } else if constexpr (L == 2) {
-        return sell_tile<VT, AT, int16_t>(a, g, a.rp, a.ci16, A, xin, r0, r1, em);
+        return sell_tile<VT, AT>(a, g, a.rp, EntryCols<int16_t>{a.ci16}, A, xin, r0, r1, em);
+    } else if constexpr (L == 3) {
+        return sell_tile<VT, AT>(a, g, a.rp, SliceCols{a.pat_off, a.pat_pool, a.N}, A, xin, r0, r1, em);
     } else {
         csr_tile<L, VT, AT>(a.rp, a.ci, A, xin, r0, r1, em);
         return true;
@@ -908,6 +910,7 @@ void* select_kernel(int lanes, int precision, bool pipelined) {
     switch (lanes) {
         case 1: return kernel_ptr<1>(precision, pipelined);
         case 2: return kernel_ptr<2>(precision, pipelined);
+        case 3: return kernel_ptr<3>(precision, pipelined);
         case 4: return kernel_ptr<4>(precision, pipelined);
         case 8: return kernel_ptr<8>(precision, pipelined);
         case 16: return kernel_ptr<16>(precision, pipelined);
@@ -923,8 +926,8 @@ cudaError_t launch_barrier_reset(GridBarrier* bar, int missing, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32, none for CSR.
-static int dyn_smem(int lanes) { return lanes <= 2 ? kRingBytes : 0; }
+// Dynamic shared memory of a solver launch: the bulk-copy ring for SELL-32 (codes 1-3), none for CSR.
+static int dyn_smem(int lanes) { return lanes <= 3 ? kRingBytes : 0; }
 
 int krylov_max_blocks(int lanes, int precision, bool pipelined, int* block_threads) {
     void* k = select_kernel(lanes, precision, pipelined);

@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "grid_sync.cuh"
 #include "internal.h"
 
@@ -23,9 +25,37 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kSlots = 8;
 constexpr int kSlotBytes = 24576;
 constexpr int kRingBytes = kSlots * kSlotBytes;
-template <typename VT, typename CT>
+// Where a SELL entry's column comes from: a per-entry array streamed with the values through the ring (int32
+// columns, or int16 offsets to the row), or one offset pattern shared by the 32 rows of each slice (nothing
+// streamed: the column of slot k of row r is r + pattern[k], clamped to the rows; rows without that neighbour hold
+// a zero there).
+template <typename T>
+struct EntryCols {
+    const T* c;
+};
+struct SliceCols {
+    const int32_t* off;   // [slices] first offset of each slice's pattern in pool
+    const int32_t* pool;  // the distinct patterns
+    int n;                // rows (columns are clamped to [0, n))
+};
+template <class C>
+struct ColBytes;  // bytes streamed per entry
+template <>
+struct ColBytes<EntryCols<int32_t>> {
+    static constexpr int v = 4;
+};
+template <>
+struct ColBytes<EntryCols<int16_t>> {
+    static constexpr int v = 2;
+};
+template <>
+struct ColBytes<SliceCols> {
+    static constexpr int v = 0;
+};
+
+template <typename VT, class C>
 constexpr int group_slices() {
-    return kSlotBytes / (32 * 16 * (int)(sizeof(VT) + sizeof(CT))) >= 8 ? 8 : 4;
+    return kSlotBytes / (32 * 16 * (int)(sizeof(VT) + ColBytes<C>::v)) >= 8 ? 8 : 4;
 }
 
 // Loads of data written by other blocks during the kernel go through L2 (L1 is not coherent).
@@ -211,30 +241,40 @@ __device__ __forceinline__ int col_of(int16_t d, int row) { return row + (int)d;
 __device__ __forceinline__ int32_t ldm_col(const int32_t* p, unsigned long long pol) { return ldm(p, pol); }
 __device__ __forceinline__ int16_t ldm_col(const int16_t* p, unsigned long long) { return __ldg(p); }
 
-template <typename VT, typename AT, typename CT, class Emit>
-__device__ __forceinline__ void slice_direct(const int32_t* sp, const CT* sc, const VT* A, const VT* xin, int slice,
+__device__ __forceinline__ int pattern_col(const SliceCols& cs, const int32_t* pat, int q, int row) {
+    return min(max(row + __ldg(pat + q), 0), cs.n - 1);
+}
+
+template <typename VT, typename AT, class C, class Emit>
+__device__ __forceinline__ void slice_direct(const int32_t* sp, const C& cs, const VT* A, const VT* xin, int slice,
                                              int r1, const Emit& em, unsigned long long pol) {
     const int lane = threadIdx.x & 31;
     const int row = (slice << 5) + lane;
     const int base = __ldg(sp + slice), w = (__ldg(sp + slice + 1) - base) >> 5;
     AT acc = AT(0);
-    for (int k = 0; k < w; ++k)
-        acc = fma((AT)ldm(A + base + 32 * k + lane, pol),
-                  (AT)ldcg(xin + col_of(ldm_col(sc + base + 32 * k + lane, pol), row)), acc);
+    if constexpr (ColBytes<C>::v == 0) {
+        const int32_t* pat = cs.pool + __ldg(cs.off + slice);
+        for (int k = 0; k < w; ++k)
+            acc = fma((AT)ldm(A + base + 32 * k + lane, pol), (AT)ldcg(xin + pattern_col(cs, pat, k, row)), acc);
+    } else {
+        for (int k = 0; k < w; ++k)
+            acc = fma((AT)ldm(A + base + 32 * k + lane, pol),
+                      (AT)ldcg(xin + col_of(ldm_col(cs.c + base + 32 * k + lane, pol), row)), acc);
+    }
     if (row < r1) em.fin(row, acc, em.pre(row));
 }
 
 // SELL-32 SpMV over rows [r0, r1) of one tile (r0 a multiple of 32). The producer warp streams slice groups
 // into the ring; consumer warps take one slice each, team by team, and never synchronise the whole block.
 // Returns false when a wait gave up (the error is recorded in the barrier word).
-template <typename VT, typename AT, typename CT, class Emit, class Ctl>
-__device__ __forceinline__ bool sell_tile(const Ctl& a, Ring& g, const int32_t* __restrict__ sp,
-                                          const CT* __restrict__ sc, const VT* __restrict__ A, const VT* xin,
-                                          int r0, int r1, const Emit& em) {
+template <typename VT, typename AT, class C, class Emit, class Ctl>
+__device__ __forceinline__ bool sell_tile(const Ctl& a, Ring& g, const int32_t* __restrict__ sp, const C& cs,
+                                          const VT* __restrict__ A, const VT* xin, int r0, int r1, const Emit& em) {
+    constexpr int kCB = ColBytes<C>::v;
     const unsigned long long pol = policy_stream();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s_begin = r0 >> 5, s_end = (r1 + 31) >> 5;
-    constexpr int kG = group_slices<VT, CT>();
+    constexpr int kG = group_slices<VT, C>();
     constexpr int kCap = kG * 32 * 16;                 // entries per slot
     constexpr int kTeamsG = kConsumerWarps / kG;
     const int ngroups = (s_end - s_begin + kG - 1) / kG;
@@ -259,9 +299,10 @@ __device__ __forceinline__ bool sell_tile(const Ctl& a, Ring& g, const int32_t* 
                     g.st_n[slot] = ns;
                     unsigned char* dst = g.data + (size_t)slot * kSlotBytes;
                     fence_proxy_async();
-                    mbar_arrive_tx(&g.full[slot], nb * (unsigned)(sizeof(VT) + sizeof(CT)));
+                    mbar_arrive_tx(&g.full[slot], nb * (unsigned)(sizeof(VT) + kCB));
                     bulk_copy(dst, A + base, nb * (unsigned)sizeof(VT), &g.full[slot], pol);
-                    bulk_copy(dst + (size_t)kCap * sizeof(VT), sc + base, nb * (unsigned)sizeof(CT), &g.full[slot], pol);
+                    if constexpr (kCB > 0)
+                        bulk_copy(dst + (size_t)kCap * sizeof(VT), cs.c + base, nb * (unsigned)kCB, &g.full[slot], pol);
                 }
             }
         }
@@ -284,14 +325,25 @@ __device__ __forceinline__ bool sell_tile(const Ctl& a, Ring& g, const int32_t* 
                 const int w = (__ldg(sp + slice + 1) - __ldg(sp + slice)) >> 5;
                 const unsigned char* base = g.data + (size_t)slot * kSlotBytes;
                 const VT* av = reinterpret_cast<const VT*>(base) + off + lane;
-                const CT* cv = reinterpret_cast<const CT*>(base + (size_t)kCap * sizeof(VT)) + off + lane;
+                // column of slot q of this row: from the streamed entry columns, or from the slice's pattern
+                const int32_t* pat = nullptr;
+                if constexpr (kCB == 0) pat = cs.pool + __ldg(cs.off + slice);
+                auto colq = [&](int q) -> int {
+                    if constexpr (kCB == 0) {
+                        return pattern_col(cs, pat, q, row);
+                    } else {
+                        using T = typename std::remove_cv<typename std::remove_pointer<decltype(cs.c)>::type>::type;
+                        const T* cv = reinterpret_cast<const T*>(base + (size_t)kCap * sizeof(VT)) + off + lane;
+                        return col_of(cv[32 * q], row);
+                    }
+                };
                 const auto pre = em.pre(valid ? row : r0);
                 AT acc = AT(0);
                 if (w <= 16) {
                     // one batch of gathers for the whole row: a single L2 round trip per slice
                     VT x[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) x[q] = q < w ? ldcg(xin + col_of(cv[32 * q], row)) : VT(0);
+                    for (int q = 0; q < 16; ++q) x[q] = q < w ? ldcg(xin + colq(q)) : VT(0);
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
                         if (q < w) acc = fma((AT)av[32 * q], (AT)x[q], acc);
@@ -300,15 +352,15 @@ __device__ __forceinline__ bool sell_tile(const Ctl& a, Ring& g, const int32_t* 
                     for (; k + 8 <= w; k += 8) {
                         VT x[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + col_of(cv[32 * (k + q)], row));
+                        for (int q = 0; q < 8; ++q) x[q] = ldcg(xin + colq(k + q));
 #pragma unroll
                         for (int q = 0; q < 8; ++q) acc = fma((AT)av[32 * (k + q)], (AT)x[q], acc);
                     }
-                    for (; k < w; ++k) acc = fma((AT)av[32 * k], (AT)ldcg(xin + col_of(cv[32 * k], row)), acc);
+                    for (; k < w; ++k) acc = fma((AT)av[32 * k], (AT)ldcg(xin + colq(k)), acc);
                 }
                 if (valid) em.fin(row, acc, pre);
             } else if (n < 0 && member < -n) {
-                slice_direct<VT, AT, CT>(sp, sc, A, xin, slice, r1, em, pol);
+                slice_direct<VT, AT, C>(sp, cs, A, xin, slice, r1, em, pol);
             }
             __syncwarp();
             // the empty barrier expects kConsumerWarps arrivals per use: each of the kG warps of the team adds
@@ -362,7 +414,7 @@ __device__ __forceinline__ void csr_tile(const int32_t* __restrict__ rp, const i
     __shared__ unsigned long long ring_full[kSlots], ring_empty[kSlots];              \
     __shared__ int ring_n[kSlots], ring_abort;                                        \
     Ring ring{ring_data, ring_full, ring_empty, ring_n, &ring_abort, 0u};             \
-    if constexpr ((L_) <= 2) {                                                        \
+    if constexpr ((L_) <= 3) {                                                        \
         if (threadIdx.x == 0) {                                                       \
             for (int q = 0; q < kSlots; ++q) {                                        \
                 mbar_init(&ring_full[q], 1);                                          \

@@ -12,6 +12,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -193,6 +194,61 @@ void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<in
     }
 }
 
+bool build_sell_patterns(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                         std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col,
+                         std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& pat_off,
+                         std::vector<int32_t>& pat_pool) {
+    const int S = (N + SELL_C - 1) / SELL_C;
+    std::vector<std::vector<int32_t>> pats(S);
+    bool ok = true;
+#pragma omp parallel for schedule(static) reduction(&& : ok)
+    for (int s = 0; s < S; ++s) {
+        std::vector<int32_t>& u = pats[s];
+        int w = 0;
+        for (int r = s * SELL_C; r < std::min(N, (s + 1) * SELL_C); ++r) {
+            w = std::max(w, row_ptr[r + 1] - row_ptr[r]);
+            for (int32_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q) u.push_back(col[q] - r);
+        }
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        ok = ok && (int)u.size() == w;  // the shared pattern must not widen the slice
+    }
+    if (!ok) return false;
+    slice_ptr.assign(S + 1, 0);
+    for (int s = 0; s < S; ++s) slice_ptr[s + 1] = slice_ptr[s] + (int32_t)pats[s].size() * SELL_C;
+    // distinct patterns, each stored once in the pool
+    pat_off.assign(S, 0);
+    pat_pool.clear();
+    std::map<std::vector<int32_t>, int32_t> seen;
+    for (int s = 0; s < S; ++s) {
+        auto it = seen.find(pats[s]);
+        if (it == seen.end()) {
+            it = seen.emplace(pats[s], (int32_t)pat_pool.size()).first;
+            pat_pool.insert(pat_pool.end(), pats[s].begin(), pats[s].end());
+        }
+        pat_off[s] = it->second;
+    }
+    sell_col.assign(slice_ptr[S], 0);
+    csr_to_sell.assign(col.size(), 0);
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < S; ++s) {
+        const std::vector<int32_t>& u = pats[s];
+        const int w = (int)u.size();
+        for (int l = 0; l < SELL_C; ++l) {
+            const int r = s * SELL_C + l;
+            for (int k = 0; k < w; ++k) sell_col[slice_ptr[s] + k * SELL_C + l] = std::min(r, N - 1);
+            if (r >= N) continue;
+            for (int32_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
+                const int k = (int)(std::lower_bound(u.begin(), u.end(), col[q] - r) - u.begin());
+                const int pos = slice_ptr[s] + k * SELL_C + l;
+                sell_col[pos] = col[q];
+                csr_to_sell[q] = pos;
+            }
+        }
+    }
+    return true;
+}
+
 namespace {
 int local_gidx(int a, int b) {
     if (a == b) return a;
@@ -203,9 +259,13 @@ int local_gidx(int a, int b) {
 
 void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                   const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
-                  std::vector<int32_t>& gather_off, std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem,
-                  std::vector<uint8_t>& cgidx) {
+                  const std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& gather_off,
+                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx) {
+    (void)row_ptr;
+    (void)N;
     const int64_t nnz = (int64_t)col.size();
+    std::vector<int64_t> sell_to_csr(slice_ptr.back(), -1);  // CSR entry at each SELL position, -1 padding
+    for (int64_t q = 0; q < nnz; ++q) sell_to_csr[csr_to_sell[q]] = q;
     std::vector<int32_t> cnt(nnz, 0);
     for (int64_t ep = 0; ep < E; ++ep)
         for (int a = 0; a < 4; ++a)
@@ -223,14 +283,14 @@ void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::
         for (int k = 0; k < w; ++k) {
             int P = 0;
             for (int l = 0; l < SELL_C; ++l) {
-                const int r = s * SELL_C + l;
-                if (r < N && k < row_ptr[r + 1] - row_ptr[r]) P = std::max(P, cnt[row_ptr[r] + k]);
+                const int64_t e = sell_to_csr[slice_ptr[s] + (int64_t)k * SELL_C + l];
+                if (e >= 0) P = std::max(P, cnt[e]);
             }
             gather_off[q0 + k] = (int32_t)total;
             gather_cnt[q0 + k] = P;
             for (int l = 0; l < SELL_C; ++l) {
-                const int r = s * SELL_C + l;
-                if (r < N && k < row_ptr[r + 1] - row_ptr[r]) pos[row_ptr[r] + k] = total + l;
+                const int64_t e = sell_to_csr[slice_ptr[s] + (int64_t)k * SELL_C + l];
+                if (e >= 0) pos[e] = total + l;
             }
             total += (int64_t)P * SELL_C;
         }

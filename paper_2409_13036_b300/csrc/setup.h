@@ -31,16 +31,27 @@ constexpr int SELL_C = 32;
 void build_sell(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                 std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col, std::vector<int32_t>& csr_to_sell);
 
+// SELL-C layout whose slices share one column pattern per slice: the entries of slice s sit at the slots of the
+// sorted union of the column offsets (col - row) of its rows, slot k of every row holding offset pat[k] (rows
+// without that neighbour store a padding entry there, column min(row, N-1), never written). Used only when no slice
+// gets wider than its longest row, so the layout has the size of build_sell's. The patterns are stored once each
+// in pat_pool; pat_off[s] is slice s's first offset there. Returns false (outputs unspecified) otherwise.
+bool build_sell_patterns(int N, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                         std::vector<int32_t>& slice_ptr, std::vector<int32_t>& sell_col,
+                         std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& pat_off,
+                         std::vector<int32_t>& pat_pool);
+
 // Row-owner ("gather") assembly of the pure stiffness matrix sigma(T)-weighted sum_e sigma0_e G_e on the SELL-32
-// layout. For every off-diagonal SELL entry the elements sharing that edge are listed with the index of
+// layout (either SELL builder; csr_to_sell maps CSR positions to SELL positions). For every off-diagonal SELL entry
+// the elements sharing that edge are listed with the index of
 // G_e[a][b]; entries of one (slice, column) group are stored column-major with the group padded to the longest
 // list among its 32 rows: contribution m of lane l of group q lives at gather_off[q] + 32 m + l, and the group has
 // gather_cnt[q] contributions (0 for groups holding only diagonal or padding entries). Padding contributions
 // carry gidx = 255. csr_slots are the element->CSR slot codes (flags allowed) over the sorted element order.
 void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                   const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
-                  std::vector<int32_t>& gather_off, std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem,
-                  std::vector<uint8_t>& cgidx);
+                  const std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& gather_off,
+                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx);
 
 // Node -> element incidence (sorted element order) in the SELL-32 slice layout: entry m of row 32 s + l at
 // inc_off[s] + 32 m + l for m < inc_cnt[s] holds 4 e + a (element e, local vertex a); -1 marks padding.
