@@ -289,14 +289,26 @@ def alg_bytes_mixed(N: int, nnz: int, iters: float, refinements: float, col_byte
     return iters * inner + (refinements + 1) * outer - (given_r0 * (8 + col_bytes) * nnz)
 
 
-def alg_bytes_ilu(Np: int, nnz_p: int, iters: float) -> float:
-    """Algorithmic HBM bytes of one ILU(0)-PCG solve launch (level-ordered SELL-32, 32-bit columns).
-    Per iteration: phase A streams A (12 B per stored entry) and reads z, p, q and writes p, q (40 Np); phase B
-    reads x, p, q, r and writes x, r (48 Np, plus z on level-0 rows); the forward and backward level sweeps stream
-    the factors once (12 B per stored entry) and read r twice, write z twice and read it once (40 Np). Start-up
-    (gather, residual, first preconditioning) and the final true residual add about two iterations' worth."""
-    per_iter = 24 * nnz_p + 136 * Np
-    return (iters + 2) * per_iter
+def alg_bytes_ilu(Np: int, nnz_p: int, iters: float, nf: int | None = None, cb: int = 4, mixed: bool = False,
+                  refinements: float = 0.0) -> float:
+    """Algorithmic HBM bytes of one ILU(0)-PCG solve launch on the ring layouts: P A P^T (nnz_p stored entries) and
+    the strictly lower and upper factors (nf entries together; about nnz_p - Np when not given), each entry a value
+    plus cb column bytes (0 with shared slice patterns).
+    FP64: per iteration phase A streams A and reads z and p, q and writes p, q; phase B reads x, p, q, r and writes x,
+    r (and z on level-0 rows); the level sweeps stream L and U once and read r, z, 1/u_ii and write z: ~16 vector
+    accesses of 8 B per row. Start-up (gather, residual, first preconditioning) and the final true residual add about
+    two iterations' worth.
+    Mixed: the inner iteration the same in FP32 (values and vectors of 4 B: ~16 accesses of 4 B per row); each FP64
+    refinement streams A in FP64 ((8 + cb) nnz_p), reads b and gathers x and writes r, d, z in FP32 (~28 B per row),
+    then adds d to x (20 B per row)."""
+    if nf is None:
+        nf = max(nnz_p - Np, 0)
+    if not mixed:
+        per_iter = (8 + cb) * (nnz_p + nf) + 128 * Np
+        return (iters + 2) * per_iter
+    inner = (4 + cb) * (nnz_p + nf) + 64 * Np
+    outer = (8 + cb) * nnz_p + 28 * Np + 20 * Np
+    return iters * inner + (refinements + 1) * outer + (4 + cb) * nf + 32 * Np
 
 
 def alg_bytes_bicgstab(N: int, nnz: int, iters: float, col_bytes: int) -> float:
@@ -381,6 +393,7 @@ def measure(rafem, torch, mesh, precision, args, local, dist, want_clocks, preco
     if precond == rafem.RAFEM_PRECOND_ILU0:
         info = ctx.precond_info()
         layout["ilu"] = {"levels": info["n_levels"], "padded_rows": info["padded_rows"],
+                         "factor_stored": info["factor_stored"], "column_bytes": info["column_bytes"],
                          "nnz_stored": info["nnz_stored"]}
     s, st = ctx.run(args.warmup)
     if s < 0:
@@ -440,8 +453,11 @@ def roofline(res, mixed, peaks, peak_kind):
         kern = "k_bicgstab"
     elif "ilu" in res["layout"]:
         ref = 0.0
-        alg = alg_bytes_ilu(res["layout"]["ilu"]["padded_rows"], res["layout"]["ilu"]["nnz_stored"], iters)
-        kern = "k_ilu_pcg"
+        il = res["layout"]["ilu"]
+        ref = tr["refine_V"] / steps if mixed else 0.0
+        alg = alg_bytes_ilu(il["padded_rows"], il["nnz_stored"], iters, il["factor_stored"], il["column_bytes"], mixed,
+                            ref)
+        kern = "k_ilu_ring<mixed>" if mixed else "k_ilu_ring<fp64>"
     elif mixed:
         ref = tr["refine_V"] / steps
         alg = alg_bytes_mixed(N, nnz, iters, ref, cb_cg)
@@ -857,6 +873,14 @@ def main():
             r["ctx"].close()
             r["ctx"] = None
         runs["fp64_ilu0"] = r
+        # the same preconditioner in the precision form: FP32 factors, values and vectors in the inner iterations
+        r = measure(rafem, torch, mesh, rafem.RAFEM_PRECISION_MIXED, ilu_args, local, dist, want_clocks=False,
+                    precond=rafem.RAFEM_PRECOND_ILU0)
+        r["roofline"] = roofline(r, True, peaks, peak_kind)
+        r["steps"] = args.ilu_steps
+        r["ctx"].close()
+        r["ctx"] = None
+        runs["mixed_ilu0"] = r
     if args.bicgstab_steps > 0 and args.only in (None, "bicgstab"):
         b_args = argparse.Namespace(**vars(args))
         b_args.steps = args.bicgstab_steps
@@ -988,9 +1012,10 @@ def main():
         line["fp64_gmres_adaptive"]["restart"] = "adaptive, 10..30 steps per cycle"
     if "fp64_pipecg" in runs and head_name != "fp64_pipecg":
         line["fp64_pipecg"] = summary(runs["fp64_pipecg"])
-    if "fp64_ilu0" in runs:
-        line["fp64_ilu0"] = summary(runs["fp64_ilu0"])
-        line["fp64_ilu0"]["levels"] = runs["fp64_ilu0"]["layout"]["ilu"]["levels"]
+    for name in ("fp64_ilu0", "mixed_ilu0"):
+        if name in runs:
+            line[name] = summary(runs[name])
+            line[name]["levels"] = runs[name]["layout"]["ilu"]["levels"]
     if args.batch_steps > 0 and args.only is None and args.cells == 127:
         try:
             line["batch"] = measure_batch(rafem, torch, mg, args, dist)

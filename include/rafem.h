@@ -53,7 +53,7 @@ extern "C" {
 #define RAFEM_SYS_T 2                /* the thermal system                                                     */
 
 #define RAFEM_PRECOND_JACOBI 0       /* diagonal preconditioner                                               */
-#define RAFEM_PRECOND_ILU0   1       /* incomplete LU(0) on the fixed pattern (single instance, FP64 only)     */
+#define RAFEM_PRECOND_ILU0   1       /* incomplete LU(0) on the fixed pattern (single instance; FP64 or mixed)  */
 
 #define RAFEM_ILU_MULTICOLOR 0       /* ILU(0) ordering: greedy colours of the matrix graph, levels = colours  */
 #define RAFEM_ILU_NATURAL    1       /* ILU(0) ordering: the mesh numbering, levels = dependency levels        */
@@ -412,10 +412,13 @@ int rafem_advance(rafem_ctx* ctx, double duration, double dt_min, rafem_advance_
  * assembly, the constant thermal system once (and again when k changes). */
 
 /* n_levels, padded_rows (rows of the level-ordered layout, each level padded to a multiple of 32), nnz_stored
- * (entries of its SELL-32 storage, padding included) and order [N] (host): the original row of the k-th row in
- * factor order. Any out pointer may be NULL. Returns BAD_INPUT unless the context uses RAFEM_PRECOND_ILU0. */
+ * (entries of its SELL-32 storage of P A P^T, padding included), order [N] (host): the original row of the k-th
+ * row in factor order; factor_stored: entries of the solver's SELL-32 layouts of L and of the strictly upper part
+ * of U (padding included); column_bytes: column bytes the ILU(0) solver streams per stored entry, 0 when its
+ * layouts share one column pattern per 32-row slice, else 4. Any out pointer may be NULL. Returns BAD_INPUT unless
+ * the context uses RAFEM_PRECOND_ILU0. */
 int rafem_precond_info(rafem_ctx* ctx, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored,
-                       int32_t* order);
+                       int32_t* order, int64_t* factor_stored, int32_t* column_bytes);
 
 /* ILU(0) factors of system `which` mapped back onto the original CSR pattern (host, [nnz]): the entry of (i, j)
  * holds L_ij (below the diagonal of P A P^T, unit diagonal implied) or U_ij (diagonal and above), where "below"

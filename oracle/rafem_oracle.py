@@ -578,6 +578,35 @@ def ilu0_apply(F, r):
     return spla.spsolve_triangular(U, y, lower=False)
 
 
+def pcg(A, b, x0, apply_Minv, tol, max_iter=100000):
+    """Preconditioned conjugate gradients (Sec. II-B: CG for symmetric positive-definite systems, preconditioned to
+    speed up convergence), textbook Hestenes-Stiefel form: r = b - A x, z = M^-1 r, p = z; then alpha =
+    (r, z) / (p, A p), x += alpha p, r -= alpha A p, z = M^-1 r, beta = (r, z)_new / (r, z)_old, p = z + beta p,
+    until ||r|| <= tol ||b||. Returns (x, iterations). For iteration counts of a preconditioner, not for speed."""
+    A = sp.csr_matrix(A)
+    b = np.asarray(b, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64)
+    r = b - A @ x
+    bn = np.linalg.norm(b)
+    bn = bn if bn > 0 else 1.0
+    if np.linalg.norm(r) <= tol * bn:
+        return x, 0
+    z = apply_Minv(r)
+    p = z.copy()
+    rz = float(r @ z)
+    for it in range(1, max_iter + 1):
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        if np.linalg.norm(r) <= tol * bn:
+            return x, it
+        z = apply_Minv(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter
+
 
 # ----------------------------------------------------------------------------------------------------------
 # Node renumbering (locality of unstructured-like numberings): reverse Cuthill-McKee

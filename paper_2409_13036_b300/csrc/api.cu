@@ -140,9 +140,8 @@ struct rafem_ctx {
     std::vector<int32_t> ilu_perm;       // [Np] original row of each padded row (host), -1 dummy
     double *ilu_AV = nullptr, *ilu_FV = nullptr, *ilu_AT = nullptr, *ilu_FT = nullptr;
     double *ilu_DV = nullptr, *ilu_DT = nullptr;  // 1 / diag(U)
-    double *ilu_xv = nullptr, *ilu_bv = nullptr, *ilu_r = nullptr, *ilu_z = nullptr, *ilu_p = nullptr,
-           *ilu_q = nullptr, *ilu_partial = nullptr;
-    int ilu_grid = 0;
+    IluRingDev ir[2];                    // ring ILU solver: layouts and workspace shared, values per system (V, T)
+    int ir_grid = 0;
     // BiCGSTAB (solver == RAFEM_SOLVER_BICGSTAB)
     double *bg_r = nullptr, *bg_rh = nullptr, *bg_p = nullptr, *bg_ph = nullptr, *bg_v = nullptr, *bg_s = nullptr,
            *bg_sh = nullptr, *bg_t = nullptr, *bg_dinv = nullptr, *bg_partial = nullptr;
@@ -411,6 +410,17 @@ SolveArgs make_args(rafem_ctx* c, int which, const double* b, double* x) {
 
 cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old, bool with_y);
 
+// ILU(0) factors of system `which` after its matrix changed: the combined layout, then the ring solver's copies.
+cudaError_t ilu_refactor(rafem_ctx* c, int which, cudaStream_t st) {
+    const bool V = which == RAFEM_SYS_V;
+    double* Ap = V ? c->ilu_AV : c->ilu_AT;
+    double* F = V ? c->ilu_FV : c->ilu_FT;
+    double* D = V ? c->ilu_DV : c->ilu_DT;
+    const cudaError_t e = launch_ilu_refactor(c->il, V ? c->valsV : c->valsT, Ap, F, D, st);
+    if (e != cudaSuccess) return e;
+    return launch_ilu_ring_split(c->ir[V ? 0 : 1], Ap, F, D, c->prm.precision == RAFEM_PRECISION_MIXED, st);
+}
+
 // Assembly of one system; with ILU(0) the potential matrix is refactored right after it is assembled. with_y: the
 // potential's assembly also computes the projection predictor's Y = A D (double-word gather, basis of 4, basis
 // already built).
@@ -418,7 +428,7 @@ cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, con
                              bool with_y = false) {
     cudaError_t e = enqueue_assemble_raw(c, which, T_sigma, T_old, with_y);
     if (e != cudaSuccess || !c->ilu || which != RAFEM_SYS_V) return e;
-    return launch_ilu_refactor(c->il, c->valsV, c->ilu_AV, c->ilu_FV, c->ilu_DV, c->stream);
+    return ilu_refactor(c, RAFEM_SYS_V, c->stream);
 }
 
 cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old, bool with_y) {
@@ -516,27 +526,22 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
     const bool r0_fresh = c->r0_fresh && which == RAFEM_SYS_V && b == c->bV && x == c->V;
     if (which == RAFEM_SYS_V) c->r0_fresh = false;
     if (c->ilu) {
-        IluSolveArgs s{};
-        s.L = &c->il;
-        s.A = which == RAFEM_SYS_V ? c->ilu_AV : c->ilu_AT;
-        s.F = which == RAFEM_SYS_V ? c->ilu_FV : c->ilu_FT;
-        s.dinv = which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT;
+        IluRingSolve s{};
+        s.d = &c->ir[which == RAFEM_SYS_V ? 0 : 1];
+        s.mixed = c->prm.precision == RAFEM_PRECISION_MIXED;
+        s.N = c->N;
+        s.dinv64 = which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT;
         s.b = b;
         s.x = x;
-        s.xv = c->ilu_xv;
-        s.bv = c->ilu_bv;
-        s.r = c->ilu_r;
-        s.z = c->ilu_z;
-        s.p = c->ilu_p;
-        s.q = c->ilu_q;
-        s.partial = c->ilu_partial;
         s.bar = c->bar;
         s.inst = which == RAFEM_SYS_V ? c->instV : c->instT;
         s.tol = c->prm.tol;
+        s.inner_tol = c->prm.inner_tol;
         s.max_iter = c->prm.max_iter;
+        s.max_refine = c->prm.max_refine;
         s.spin_limit_ns = c->wait_ns;
         s.bar_missing = c->wait_missing;
-        return launch_ilu_pcg(s, c->ilu_grid, c->stream);
+        return launch_ilu_ring(s, c->ir_grid, c->stream);
     }
     if (c->prm.solver == RAFEM_SOLVER_GMRES) {
         GmresArgs g{};
@@ -1541,11 +1546,57 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         CK(dalloc(c, &c->ilu_FT, nz));
         CK(dalloc(c, &c->ilu_DV, Np));
         CK(dalloc(c, &c->ilu_DT, Np));
-        for (double** v : {&c->ilu_xv, &c->ilu_bv, &c->ilu_r, &c->ilu_z, &c->ilu_p, &c->ilu_q}) CK(dalloc(c, v, Np));
-        int bt = 0;
-        c->ilu_grid = ilu_max_blocks(&bt);
-        if (c->ilu_grid <= 0) return RAFEM_ERR_CUDA;
-        CK(dalloc(c, &c->ilu_partial, (size_t)kIluPartialSlots * c->ilu_grid));
+        // the ring solver's layouts of P A P^T, L and U (values split from the combined layout per refactorisation)
+        IluRingHost irh;
+        build_ilu_ring(ih, irh);
+        IluRingDev d;
+        d.Np = ih.Np;
+        d.n_levels = ih.n_levels;
+        d.patterns = irh.A.patterns && irh.L.patterns && irh.U.patterns;
+        d.lvl = lvl;
+        d.perm = pr;
+        auto upload = [&](const std::vector<int32_t>& v, const int32_t** dst) -> cudaError_t {
+            int32_t* q = nullptr;
+            cudaError_t e = dalloc(c, &q, v.size());
+            if (e == cudaSuccess && !v.empty())
+                e = cudaMemcpyAsync(q, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            *dst = q;
+            return e;
+        };
+        for (auto pr2 : {std::make_pair(&irh.A, &d.A), std::make_pair(&irh.L, &d.L), std::make_pair(&irh.U, &d.U)}) {
+            CK(upload(pr2.first->sp, &pr2.second->sp));
+            CK(upload(pr2.first->sc, &pr2.second->sc));
+            CK(upload(pr2.first->src, &pr2.second->src));
+            if (d.patterns) {
+                CK(upload(pr2.first->pat_off, &pr2.second->pat_off));
+                CK(upload(pr2.first->pat_pool, &pr2.second->pat_pool));
+            }
+        }
+        d.nA = (long long)irh.A.sc.size();
+        d.nL = (long long)irh.L.sc.size();
+        d.nU = (long long)irh.U.sc.size();
+        const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
+        for (double** v : {&d.xv, &d.bv, &d.r64, &d.z64, &d.p64, &d.q64}) CK(dalloc(c, v, Np));
+        if (mixed)
+            for (float** v : {&d.r32, &d.z32, &d.p32, &d.q32, &d.d32}) CK(dalloc(c, v, Np));
+        c->ir_grid = ilu_ring_max_blocks();
+        if (c->ir_grid <= 0) return RAFEM_ERR_CUDA;
+        CK(dalloc(c, &d.partial, (size_t)kIluRingSlots * c->ir_grid));
+        for (int sys = 0; sys < 2; ++sys) {
+            c->ir[sys] = d;
+            IluRingDev& e = c->ir[sys];
+            CK(dalloc(c, &e.A64, (size_t)d.nA));
+            if (mixed) {
+                CK(dalloc(c, &e.A32, (size_t)d.nA));
+                CK(dalloc(c, &e.L32, (size_t)d.nL));
+                CK(dalloc(c, &e.U32, (size_t)d.nU));
+                CK(dalloc(c, &e.dinv32, Np));
+            } else {
+                CK(dalloc(c, &e.L64, (size_t)d.nL));
+                CK(dalloc(c, &e.U64, (size_t)d.nU));
+            }
+        }
+        CK(cudaStreamSynchronize(st));  // host layouts go out of scope
     }
     // ---- device-side setup: geometry, constant thermal system, Dirichlet identity rows, initial fields
     CK(launch_geometry(c->el, c->xyz, c->e_G, c->e_vol, st));
@@ -1563,7 +1614,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     for (int q = 0; q < c->n_colors; ++q)
         CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                              prm->perf * prm->T_a, c->valsT, c->valsT32, c->bTc, prm->lift, c->e_clist, st));
-    if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
+    if (c->ilu) CK(ilu_refactor(c, RAFEM_SYS_T, st));
     k_init_fields<<<(N + 255) / 256, 256, 0, st>>>(N, prm->T_a, c->bcT, c->gT, c->bcV, c->gV, c->T, c->V);
     CK(cudaGetLastError());
     k_set_step<<<1, 1, 0, st>>>(c->stats, 0);
@@ -1588,8 +1639,7 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
     if (prm->precision == RAFEM_PRECISION_MIXED && !(prm->inner_tol > 0 && prm->inner_tol < 1)) return RAFEM_ERR_BAD_INPUT;
     if (prm->precond != RAFEM_PRECOND_JACOBI && prm->precond != RAFEM_PRECOND_ILU0) return RAFEM_ERR_BAD_INPUT;
     if (prm->precond == RAFEM_PRECOND_ILU0 &&
-        (prm->precision != RAFEM_PRECISION_FP64 ||
-         (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL)))
+        (prm->ilu_order != RAFEM_ILU_MULTICOLOR && prm->ilu_order != RAFEM_ILU_NATURAL))
         return RAFEM_ERR_BAD_INPUT;
     if (prm->solver != RAFEM_SOLVER_PCG && prm->solver != RAFEM_SOLVER_BICGSTAB && prm->solver != RAFEM_SOLVER_GMRES &&
         prm->solver != RAFEM_SOLVER_PIPECG)
@@ -1991,7 +2041,7 @@ int set_params_impl(rafem_ctx* c, const void* sigma0, const void* k, int kind) {
         for (int q = 0; q < c->n_colors; ++q)
             CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                                  c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
-        if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
+        if (c->ilu) CK(ilu_refactor(c, RAFEM_SYS_T, st));
     }
     CK(cudaStreamSynchronize(st));
     return RAFEM_OK;
@@ -2007,11 +2057,14 @@ int rafem_set_params_device(rafem_ctx* c, const float* sigma0, const float* k) {
     return set_params_impl(c, sigma0, k, SRC_DEV32);
 }
 
-int rafem_precond_info(rafem_ctx* c, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored, int32_t* order) {
+int rafem_precond_info(rafem_ctx* c, int32_t* n_levels, int32_t* padded_rows, int64_t* nnz_stored, int32_t* order,
+                       int64_t* factor_stored, int32_t* column_bytes) {
     if (!c || !c->ilu) return RAFEM_ERR_BAD_INPUT;
     if (n_levels) *n_levels = c->il.n_levels;
     if (padded_rows) *padded_rows = c->il.Np;
     if (nnz_stored) *nnz_stored = c->il.nnz;
+    if (factor_stored) *factor_stored = c->ir[0].nL + c->ir[0].nU;
+    if (column_bytes) *column_bytes = c->ir[0].patterns ? 0 : 4;
     if (order) {
         int k = 0;
         for (int32_t o : c->ilu_perm)
@@ -2035,7 +2088,7 @@ int rafem_precond_apply(rafem_ctx* c, int which, const double* r, double* z) {
     if (!c || !r || !z || r == z || (which != RAFEM_SYS_V && which != RAFEM_SYS_T)) return RAFEM_ERR_BAD_INPUT;
     if (c->ilu) {
         CK(launch_ilu_apply(c->il, which == RAFEM_SYS_V ? c->ilu_FV : c->ilu_FT,
-                            which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT, r, z, c->ilu_r, c->ilu_z, c->stream));
+                            which == RAFEM_SYS_V ? c->ilu_DV : c->ilu_DT, r, z, c->ir[0].r64, c->ir[0].z64, c->stream));
     } else {
         k_jacobi_apply<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->diag,
                                                                    which == RAFEM_SYS_V ? c->valsV : c->valsT, r, z);
@@ -2058,7 +2111,7 @@ int apply_dt(rafem_ctx* c, double dt) {
     for (int q = 0; q < c->n_colors; ++q)
         CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                              c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
-    if (c->ilu) CK(launch_ilu_refactor(c->il, c->valsT, c->ilu_AT, c->ilu_FT, c->ilu_DT, st));
+    if (c->ilu) CK(ilu_refactor(c, RAFEM_SYS_T, st));
     if (c->gd.mT) CK(launch_node_mass(c->gd, c->N, c->e_vol, c->prm.rho_c / dt, st));
     if (c->dw) CK(launch_fill_dw(c->gdw, 0, nullptr, nullptr, c->el, c->prm.rho_c / dt, st));
     drop_graphs(c);

@@ -236,32 +236,55 @@ struct IluLayout {
     std::vector<int32_t> h_lvl;      // host copy of lvl
 };
 
-constexpr int kIluPartialSlots = 5;  // partial-sum slots of the ILU solver, each [grid]
 
-struct IluSolveArgs {
-    const IluLayout* L;              // host pointer (fields copied into the kernel arguments)
-    const double* A;                 // [nnz] permuted system values
-    const double* F;                 // [nnz] factors
-    const double* dinv;              // [Np] 1 / u_ii
-    const double* b;                 // [N] original ordering
-    double* x;                       // [N] original ordering: initial guess in, solution out
-    double *xv, *bv, *r, *z, *p, *q; // [Np] padded ordering
-    double* partial;                 // [kIluPartialSlots][grid]
-    GridBarrier* bar;
-    InstState* inst;                 // [1]
-    double tol;
-    int max_iter;
-    long long spin_limit_ns;
-    int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
+// ILU(0)-PCG streaming its matrices through the shared-memory ring (ilu_ring.cu): layouts of P A P^T, L and U
+// (setup.h IluRingHost) on the device, the values of one system, and the solver workspace (shared by both
+// systems of a context).
+constexpr int kIluRingSlots = 8;  // partial-sum slots of the ring ILU solver, each [grid]
+struct IluRingPartDev {
+    const int32_t* sp = nullptr;
+    const int32_t* sc = nullptr;
+    const int32_t* pat_off = nullptr;
+    const int32_t* pat_pool = nullptr;
+    const int32_t* src = nullptr;   // position in the combined factor layout, -1 padding
 };
+struct IluRingDev {
+    int Np = 0, n_levels = 0;
+    bool patterns = false;          // all three layouts share one column pattern per slice
+    const int32_t* lvl = nullptr;   // [n_levels + 1]
+    const int32_t* perm = nullptr;  // [Np]
+    IluRingPartDev A, L, U;
+    long long nA = 0, nL = 0, nU = 0;
+    double *A64 = nullptr, *L64 = nullptr, *U64 = nullptr;           // FP64 values (L, U: FP64 Krylov only)
+    float *A32 = nullptr, *L32 = nullptr, *U32 = nullptr, *dinv32 = nullptr;  // mixed precision only
+    double *xv = nullptr, *bv = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+    double* partial = nullptr;      // [kIluRingSlots][grid]
+};
+struct IluRingSolve {
+    const IluRingDev* d;
+    bool mixed;
+    int N;
+    const double* dinv64;           // 1 / u_ii (FP64, padded level order)
+    const double* b;
+    double* x;
+    GridBarrier* bar;
+    InstState* inst;
+    double tol, inner_tol;
+    int max_iter, max_refine;
+    long long spin_limit_ns;
+    int bar_missing;
+};
+int ilu_ring_max_blocks();
+// Values of the ring layouts from the combined layout (Ap: the permuted system, F: its factors, dinv: 1 / u_ii).
+cudaError_t launch_ilu_ring_split(const IluRingDev& d, const double* Ap, const double* F, const double* dinv,
+                                  bool mixed, cudaStream_t st);
+cudaError_t launch_ilu_ring(const IluRingSolve& s, int grid, cudaStream_t st);
 
 // Ap = permuted values of `vals` (the system in its primary storage), F = ILU(0) factors of Ap, level by level,
 // dinv = 1 / diag(U).
 cudaError_t launch_ilu_refactor(const IluLayout& L, const double* vals, double* Ap, double* F, double* dinv,
                                 cudaStream_t st);
-// Persistent ILU(0)-preconditioned CG (FP64), one cooperative launch per solve.
-int ilu_max_blocks(int* block_threads);
-cudaError_t launch_ilu_pcg(const IluSolveArgs& a, int grid, cudaStream_t st);
 // z = U^-1 L^-1 r (original ordering; rv, zv: [Np] scratch).
 cudaError_t launch_ilu_apply(const IluLayout& L, const double* F, const double* dinv, const double* r, double* z,
                              double* rv, double* zv, cudaStream_t st);

@@ -451,6 +451,56 @@ int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>&
     return 0;
 }
 
+namespace {
+// SELL-32 layout of one row set of the padded ILU numbering (CSR rp/col over Np rows, sorted columns, src = the
+// combined-layout position of each entry): shared slice patterns where possible, else per-entry columns.
+void ilu_part_layout(int Np, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                     const std::vector<int32_t>& src, IluPart& out) {
+    std::vector<int32_t> map;
+    out.patterns = build_sell_patterns(Np, rp, col, out.sp, out.sc, map, out.pat_off, out.pat_pool);
+    if (!out.patterns) {
+        out.pat_off.clear();
+        out.pat_pool.clear();
+        build_sell(Np, rp, col, out.sp, out.sc, map);
+    }
+    out.src.assign(out.sc.size(), -1);
+    for (size_t q = 0; q < col.size(); ++q) out.src[map[q]] = src[q];
+}
+}  // namespace
+
+void build_ilu_ring(const IluHost& ih, IluRingHost& out) {
+    const int Np = ih.Np, S = Np / SELL_C;
+    // rows of P A P^T in the padded numbering: full, strictly lower, strictly upper (sorted columns)
+    std::vector<int32_t> rpA(Np + 1, 0), rpL(Np + 1, 0), rpU(Np + 1, 0);
+    for (int r = 0; r < Np; ++r) {
+        rpA[r + 1] = rpA[r] + ih.rlen[r];
+        rpL[r + 1] = rpL[r] + ih.dk[r];
+        rpU[r + 1] = rpU[r] + ih.rlen[r] - ih.dk[r] - 1;
+    }
+    std::vector<int32_t> cA(rpA[Np]), sA(rpA[Np]), cL(rpL[Np]), sL(rpL[Np]), cU(rpU[Np]), sU(rpU[Np]);
+#pragma omp parallel for schedule(static)
+    for (int sl = 0; sl < S; ++sl)
+        for (int l = 0; l < SELL_C; ++l) {
+            const int r = sl * SELL_C + l;
+            int a = rpA[r], lo = rpL[r], up = rpU[r];
+            for (int k = 0; k < ih.rlen[r]; ++k) {
+                const int32_t at = ih.sp[sl] + k * SELL_C + l;
+                cA[a] = ih.sc[at];
+                sA[a++] = at;
+                if (k < ih.dk[r]) {
+                    cL[lo] = ih.sc[at];
+                    sL[lo++] = at;
+                } else if (k > ih.dk[r]) {
+                    cU[up] = ih.sc[at];
+                    sU[up++] = at;
+                }
+            }
+        }
+    ilu_part_layout(Np, rpA, cA, sA, out.A);
+    ilu_part_layout(Np, rpL, cL, sL, out.L);
+    ilu_part_layout(Np, rpU, cU, sU, out.U);
+}
+
 }  // namespace rafem
 
 namespace rafem {

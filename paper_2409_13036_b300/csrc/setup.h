@@ -79,6 +79,19 @@ struct IluHost {
 // Returns 0, or -1 when a row has more than 255 entries or the padded size overflows.
 int build_ilu(int N, const std::vector<int32_t>& rp, const std::vector<int32_t>& col, int order, IluHost& out);
 
+// Layouts of the ILU(0) solver that streams its matrices through the shared-memory ring: P A P^T, the strictly
+// lower factor L and the strictly upper part of U, each a SELL-32 layout over the padded numbering of IluHost (one
+// column pattern per slice where that widens no slice, else per-entry columns). src maps every position to its
+// position in IluHost's combined layout (where the system and its factors are stored), -1 for padding.
+struct IluPart {
+    bool patterns = false;
+    std::vector<int32_t> sp, sc, pat_off, pat_pool, src;
+};
+struct IluRingHost {
+    IluPart A, L, U;
+};
+void build_ilu_ring(const IluHost& ih, IluRingHost& out);
+
 // Reverse Cuthill-McKee order of the node graph: perm[new] = old. Per connected component (taken in order of its
 // lowest node): start at the component's smallest-degree node (lowest index on ties), move to the smallest-degree
 // node of the last breadth-first level while that increases the eccentricity, then number breadth first with the

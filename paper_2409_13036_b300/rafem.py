@@ -153,7 +153,8 @@ def lib() -> ctypes.CDLL:
         "rafem_get_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]),
         "rafem_precond_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                              ctypes.POINTER(ctypes.c_int64), vp]),
+                                              ctypes.POINTER(ctypes.c_int64), vp, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int32)]),
         "rafem_get_precond": (ctypes.c_int, [vp, ctypes.c_int, vp]),
         "rafem_precond_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "rafem_set_dt": (ctypes.c_int, [vp, ctypes.c_double]),
@@ -457,9 +458,11 @@ class Context:
     def precond_info(self) -> dict:
         nl, npad, nz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         order = np.empty(self.N, np.int32)
+        nf, cb = ctypes.c_int64(), ctypes.c_int32()
         _check(lib().rafem_precond_info(self._ctx, ctypes.byref(nl), ctypes.byref(npad), ctypes.byref(nz),
-                                        order.ctypes.data), "rafem_precond_info")
-        return {"n_levels": nl.value, "padded_rows": npad.value, "nnz_stored": nz.value, "order": order}
+                                        order.ctypes.data, ctypes.byref(nf), ctypes.byref(cb)), "rafem_precond_info")
+        return {"n_levels": nl.value, "padded_rows": npad.value, "nnz_stored": nz.value, "order": order,
+                "factor_stored": nf.value, "column_bytes": cb.value}
 
     def get_precond(self, which: int) -> np.ndarray:
         _, nnz, _ = self.pattern_info()

@@ -66,3 +66,32 @@ def test_batch_limits():
     with rafem.Context.batch([m]) as b:
         s, st = b.run(1)
         assert s == rafem.RAFEM_OK and b.n_inst == 1
+
+
+def test_autotuner_caches_its_choice_and_keeps_the_fields(tmp_path, monkeypatch):
+    """The schedule autotuner times the candidate tile sizes on a live batch, keeps the fastest and stores it in
+    its cache file; a second context of the same shape takes the cached choice without timing. The tile size only
+    changes the work split: a batch run with the tuned schedule gives the same fields as the default schedule up to
+    the solver tolerance (both solved to 1e-12; cond(A) ~1e2 on these instances, bound 1e-9)."""
+    from paper_2409_13036_b300 import rafem
+    from paper_2409_13036_b300.autotune import autotune_schedule, cache_path
+    monkeypatch.setenv("RAFEM_CACHE_DIR", str(tmp_path))
+    meshes = _instances()
+    with rafem.Context.batch(meshes, tol=1e-12, dt=5.0) as b:
+        rep = autotune_schedule(b, candidates=(0, 1024, 4096), steps=1)
+        assert not rep["cached"] and len(rep["trials"]) == 3
+        assert rep["rows_per_tile"] == min(rep["trials"], key=lambda t: t["ms_per_iteration"])["rows_per_tile"]
+        assert b.get_schedule()["rows_per_tile"] == rep["rows_per_tile"]
+    import json
+    with open(cache_path()) as f:
+        assert len(json.load(f)) == 1
+    with rafem.Context.batch(meshes, tol=1e-12, dt=5.0) as tuned, rafem.Context.batch(meshes, tol=1e-12, dt=5.0) as ref:
+        rep2 = autotune_schedule(tuned, candidates=(0, 1024, 4096), steps=1)
+        assert rep2["cached"] and rep2["rows_per_tile"] == rep["rows_per_tile"]
+        assert tuned.get_schedule()["rows_per_tile"] == rep["rows_per_tile"]
+        s1, _ = tuned.run(3)
+        s2, _ = ref.run(3)
+        assert s1 == 0 and s2 == 0
+        for which in (rafem.RAFEM_SYS_T, rafem.RAFEM_SYS_V):
+            a, c = tuned.get_field(which), ref.get_field(which)
+            assert np.linalg.norm(a - c) <= 1e-9 * np.linalg.norm(c)

@@ -492,3 +492,35 @@ def test_projection_guess_depends_only_on_the_span():
                   X[:, 0] - 3 * X[:, 1] + 3 * X[:, 2] - X[:, 3]], axis=1)
     np.testing.assert_allclose(O.projection_guess(A, b, D, free)[free], O.projection_guess(A, b, X, free)[free],
                                rtol=0, atol=1e-11 * np.abs(xs).max())
+
+
+def test_pcg_finite_termination_and_preconditioning():
+    """The oracle's PCG: on an SPD matrix with k distinct eigenvalues CG ends in at most k iterations (the Krylov
+    space then holds the solution exactly); the exact inverse as preconditioner ends in one; Jacobi on a diagonal
+    matrix ends in one; and on a Poisson-like system the ILU(0) preconditioner needs fewer iterations than Jacobi,
+    each reaching the direct solve."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lam = np.repeat([1.0, 3.0, 7.0], 4)
+    A = sp.csr_matrix(Q @ np.diag(lam) @ Q.T)
+    b = rng.standard_normal(12)
+    x, it = O.pcg(A, b, np.zeros(12), lambda r: r, 1e-10)
+    assert it <= 3 and np.allclose(A @ x, b, atol=1e-9)
+    Ainv = np.linalg.inv(A.toarray())
+    _, it1 = O.pcg(A, b, np.zeros(12), lambda r: Ainv @ r, 1e-10)
+    assert it1 == 1
+    D = sp.diags(rng.uniform(1, 5, 20)).tocsr()
+    bd = rng.standard_normal(20)
+    xd, itd = O.pcg(D, bd, np.zeros(20), lambda r: r / D.diagonal(), 1e-12)
+    assert itd == 1 and np.allclose(xd, bd / D.diagonal())
+    m = mg.cube_mesh(8, jitter=0.1, seed=12, sigma0="lognormal")
+    AV, bV = O.Model(m).system_V(np.full(m.n_nodes, 37.0))
+    x_ref = O.solve(AV, bV)
+    perm, _ = O.ilu_permutation(AV, "multicolor")
+    Ap = O.permute_symmetric(AV, perm)
+    F = O.ilu0(Ap)
+    _, it_j = O.pcg(Ap, bV[perm], np.zeros(m.n_nodes), lambda r: r / Ap.diagonal(), 1e-10)
+    xi, it_i = O.pcg(Ap, bV[perm], np.zeros(m.n_nodes), lambda r: O.ilu0_apply(F, r), 1e-10)
+    assert it_i < it_j
+    assert np.linalg.norm(xi - x_ref[perm]) <= 1e-7 * np.linalg.norm(x_ref)
