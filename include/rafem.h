@@ -88,8 +88,10 @@ extern "C" {
                                         method (Jacobian with the sigma(T) and Joule couplings, unknowns
                                         interleaved per node, 2 x 2 blocks on the node pattern, block-Jacobi
                                         BiCGSTAB, row-only Dirichlet rows) until max |dT| < corrector_tol or
-                                        n_corrector iterations; FP64, SELL-32 layout, single instance; the
-                                        iterations run on the device like corrector passes                    */
+                                        n_corrector iterations, starting from the lagged staggered step; each
+                                        linear solve is inexact (forcing terms of Eisenstat and Walker, within
+                                        [tol, 1e-2]); FP64, SELL-32 layout, single instance; the iterations run
+                                        on the device like corrector passes                                    */
 
 #define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known
                                         values moved to the right-hand side: the systems stay SPD              */

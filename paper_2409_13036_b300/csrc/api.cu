@@ -34,6 +34,7 @@ struct CorrDev {
     int32_t pass;           // corrector passes done in the current step
     int32_t converged;      // 1 once max |T^{k+1} - T^k| < corrector_tol
     double change;          // max |T^{k+1} - T^k| of the last pass
+    double newton_rr;       // monolithic step: ||R||^2 of the last Newton linear solve (0 before the first)
 };
 
 }  // namespace
@@ -318,6 +319,7 @@ __global__ void k_corr_init(CorrDev* c) {
     c->pass = 0;
     c->converged = 0;
     c->change = 0.0;
+    c->newton_rr = 0.0;
 }
 
 // After a corrector pass: count it, read max |T^{k+1} - T^k| (non-negative double stored as its bit pattern) and
@@ -758,12 +760,20 @@ cudaError_t enqueue_step_traced(rafem_ctx* c) {
 
 // ---- corrector passes on the device --------------------------------------------------------------------------
 // Prologue: T_old = T (the mass term keeps T^n), statistics and pass counter cleared.
+// Monolithic step: Newton starts from the lagged staggered step (V, then T, each an SPD solve with sigma(T^n)),
+// which differs from the coupled solution only through the step's own temperature change, so the first Newton
+// residual is already small. The start's own solves are not counted in the step statistics.
 cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return e;
     k_begin_step<<<1, 128, 0, c->stream>>>(c->stats, c->istats, c->n_inst);
     k_corr_init<<<1, 1, 0, c->stream>>>(c->corr);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess || !c->mono) return e;
+    c->r0_fresh = false;
+    if ((e = enqueue_assemble(c, RAFEM_SYS_V, c->T, c->T)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c, RAFEM_SYS_V, c->bV, c->V)) != cudaSuccess) return e;
+    if ((e = enqueue_assemble(c, RAFEM_SYS_T, c->T, c->T_old)) != cudaSuccess) return e;
+    return enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T);
 }
 
 // One Newton iteration of the monolithic coupled step: assemble the 2N x 2N Jacobian and residual at the current
@@ -809,6 +819,7 @@ cudaError_t enqueue_newton(rafem_ctx* c) {
     g.max_iter = c->prm.max_iter;
     g.spin_limit_ns = c->wait_ns;
     g.bar_missing = c->wait_missing;
+    g.newton = &c->corr->newton_rr;  // inexact Newton: each linear solve only as accurate as the iteration needs
     if ((e = launch_bicgstab(g, c->mb_grid, st)) != cudaSuccess) return e;
     k_record<<<1, 128, 0, st>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -44,7 +44,16 @@ struct Args {
     double tol;
     int max_iter;
     long long spin_limit_ns;
+    double* newton;       // inexact Newton: ||R||^2 of the previous linear solve of this step (0: the first), or null
 };
+
+// Forcing terms of the inexact Newton iteration of the monolithic step (Eisenstat and Walker, "Choosing the forcing
+// terms in an inexact Newton method", SIAM J. Sci. Comput. 17 (1996), their second choice): the linear solve of
+// Newton iteration k stops at ||r|| <= eta_k ||R_k|| with eta_k = gamma (||R_k|| / ||R_{k-1}||)^alpha, gamma = 0.9,
+// alpha = 2, kept within [tol, kEtaMax]; the first iteration of a step uses kEta0.
+constexpr double kEtaGamma = 0.9;
+constexpr double kEta0 = 1e-3;
+constexpr double kEtaMax = 1e-2;
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ double* slot(const Args& a, int k) { return a.partial + (size_t)k * gridDim.x; }
@@ -177,7 +186,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
         rr = s_tot[1];
         rho = rr;  // (rh, r) with rh = r
     }
-    const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
+    double tol = a.tol;
+    if (a.newton) {
+        const double prev = *(volatile double*)a.newton;
+        const double eta = prev > 0.0 ? kEtaGamma * (bb / prev) : kEta0;  // (||R_k|| / ||R_{k-1}||)^2 = bb / prev
+        tol = fmin(fmax(eta, a.tol), kEtaMax);
+    }
+    const double thr = tol * tol * (bb > 0.0 ? bb : 1.0);
     bool done = err || !(rr > thr);
     if (!err && !(rr == rr)) status = RAFEM_ERR_NONFINITE;
     else if (done) status = RAFEM_OK;
@@ -347,6 +362,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
         st.status = err ? (a.bar->err ? a.bar->err : RAFEM_ERR_TIMEOUT) : status;
         st.relres = relres;
         a.inst[0] = st;
+        if (a.newton) *a.newton = bb;
     }
 }
 
@@ -365,7 +381,7 @@ int bicgstab_partial_slots() { return kSlots; }
 
 cudaError_t launch_bicgstab(const BicgArgs& s, int grid, cudaStream_t st) {
     Args a{s.N, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.r, s.rh, s.p, s.ph, s.v, s.s, s.sh, s.t, s.dinv,
-           s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns};
+           s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.newton};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;

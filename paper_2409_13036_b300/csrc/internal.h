@@ -315,6 +315,7 @@ struct BicgArgs {
     int max_iter;
     long long spin_limit_ns;
     int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
+    double* newton = nullptr;  // monolithic step: inexact-Newton forcing state (bicgstab.cu), else null
 };
 int bicgstab_max_blocks(int block);
 int bicgstab_partial_slots();
