@@ -436,12 +436,13 @@ def roofline(res, mixed, peaks, peak_kind):
     solve_ms = tr["ms_solve_V"] / steps
     iters = tr["iters_V"] / steps
     code = res["layout"]["kernel_code"]
-    # kernel code 3: the CG-family solvers stream no per-entry columns (one column pattern per slice)
+    # kernel code 3: the ring solvers (CG family, BiCGSTAB, GMRES) stream no per-entry columns (one column pattern
+    # per slice)
     cb_cg = 0 if code == 3 else res["layout"]["column_bytes"]
     cb = res["layout"]["column_bytes"]
     if res.get("solver") == "gmres":
         ref = tr["refine_V"] / steps
-        alg = alg_bytes_gmres(N, nnz, iters, ref, cb)
+        alg = alg_bytes_gmres(N, nnz, iters, ref, cb_cg)
         kern = "k_gmres"
     elif res.get("solver") == "pipecg":
         ref = 0.0
@@ -449,7 +450,7 @@ def roofline(res, mixed, peaks, peak_kind):
         kern = f"k_pcg64<{code}>"
     elif res.get("solver") == "bicgstab":
         ref = 0.0
-        alg = alg_bytes_bicgstab(N, nnz, iters, cb)
+        alg = alg_bytes_bicgstab(N, nnz, iters, cb_cg)
         kern = "k_bicgstab"
     elif "ilu" in res["layout"]:
         ref = 0.0

@@ -554,6 +554,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.sp = c->rp;
         g.sc = c->ci;
         g.sc16 = c->ci16;
+        g.pat_off = c->pat_off;
+        g.pat_pool = c->pat_pool;
         g.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
         g.diag = c->diag;
         g.b = b;
@@ -580,6 +582,8 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.sp = c->rp;
         g.sc = c->ci;
         g.sc16 = c->ci16;
+        g.pat_off = c->pat_off;
+        g.pat_pool = c->pat_pool;
         g.A = which == RAFEM_SYS_V ? c->valsV : c->valsT;
         g.diag = c->diag;
         g.b = b;

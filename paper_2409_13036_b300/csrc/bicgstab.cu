@@ -369,24 +369,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab(Args a) {
 }  // namespace
 
 int bicgstab_max_blocks(int block) {
+    if (block == 1) return bicgstab_ring_max_blocks();
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const void* f = block == 2 ? (const void*)k_bicgstab<2> : (const void*)k_bicgstab<1>;
+    const void* f = (const void*)k_bicgstab<2>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, kBlock, 0) != cudaSuccess) return 0;
     return sms * (per < 1 ? per : 1);
 }
 
-int bicgstab_partial_slots() { return kSlots; }
+int bicgstab_partial_slots() { return kSlots > bicgstab_ring_partial_slots() ? kSlots : bicgstab_ring_partial_slots(); }
 
 cudaError_t launch_bicgstab(const BicgArgs& s, int grid, cudaStream_t st) {
+    if (s.block == 1) return launch_bicgstab_ring(s, grid, st);
     Args a{s.N, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.r, s.rh, s.p, s.ph, s.v, s.s, s.sh, s.t, s.dinv,
            s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.newton};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;
     void* params[] = {&a};
-    const void* f = s.block == 2 ? (const void*)k_bicgstab<2> : (const void*)k_bicgstab<1>;
+    const void* f = (const void*)k_bicgstab<2>;
     return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(kBlock), params, 0, st);
 }
 

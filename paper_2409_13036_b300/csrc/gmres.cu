@@ -58,6 +58,8 @@ struct Args {
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
+    const int32_t* pat_off;   // one column pattern per slice (kernel code 3), or null
+    const int32_t* pat_pool;
     const double* A;
     const int32_t* diag;
     const double* b;
@@ -233,8 +235,16 @@ struct EmArnoldi {
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     RAFEM_RING_SETUP(L)
-    using CT = typename std::conditional<L == 2, int16_t, int32_t>::type;
-    const EntryCols<CT> sc{L == 2 ? reinterpret_cast<const CT*>(a.sc16) : reinterpret_cast<const CT*>(a.sc)};
+    // columns: 32-bit (L = 1), 16-bit offsets (L = 2) or one pattern per slice (L = 3, values only)
+    using Cols = typename std::conditional<
+        L == 3, SliceCols, EntryCols<typename std::conditional<L == 2, int16_t, int32_t>::type>>::type;
+    Cols sc;
+    if constexpr (L == 3)
+        sc = SliceCols{a.pat_off, a.pat_pool, a.N};
+    else if constexpr (L == 2)
+        sc = Cols{a.sc16};
+    else
+        sc = Cols{a.sc};
     __shared__ double acc[kWarps * kAcc];
     __shared__ double tot[kAcc];
     __shared__ double cs[64], sn[64], g[65], yv[64];
@@ -424,7 +434,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     }
 }
 
-void* kernel_for(const GmresArgs& s) { return s.sc16 ? (void*)k_gmres<2> : (void*)k_gmres<1>; }
+void* kernel_for(const GmresArgs& s) {
+    return s.pat_off ? (void*)k_gmres<3> : (s.sc16 ? (void*)k_gmres<2> : (void*)k_gmres<1>);
+}
 
 }  // namespace
 
@@ -432,18 +444,20 @@ int gmres_max_blocks(int /*m*/) {
     int dev = 0, sms = 0, per1 = 0, per2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    for (void* k : {(void*)k_gmres<1>, (void*)k_gmres<2>})
+    int per = 1;
+    for (void* k : {(void*)k_gmres<1>, (void*)k_gmres<2>, (void*)k_gmres<3>}) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_gmres<1>, kBlock, kRingBytes) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_gmres<2>, kBlock, kRingBytes) != cudaSuccess) return 0;
-    const int per = per1 < per2 ? per1 : per2;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k, kBlock, kRingBytes) != cudaSuccess) return 0;
+        per = per1 < per ? per1 : per;
+    }
+    (void)per2;
     return sms * (per < 1 ? per : 1);
 }
 
 int gmres_partial_slots(int m) { return 2 * (m + 2) + 2; }
 
 cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
-    Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.z, s.dinv, s.H,
+    Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.pat_off, s.pat_pool, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.z, s.dinv, s.H,
            s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.m_state};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;

@@ -303,6 +303,8 @@ struct BicgArgs {
     const int32_t* sp;               // slice pointers
     const int32_t* sc;               // 32-bit columns (used when sc16 is null)
     const int16_t* sc16;             // 16-bit column deltas or null
+    const int32_t* pat_off = nullptr;   // scalar rows: one column pattern per slice (kernel code 3), or null
+    const int32_t* pat_pool = nullptr;
     const double* A;
     const int32_t* diag;             // storage position of each row's diagonal
     const double* b;
@@ -317,9 +319,13 @@ struct BicgArgs {
     int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
     double* newton = nullptr;  // monolithic step: inexact-Newton forcing state (bicgstab.cu), else null
 };
+// block = 1 runs the ring kernel of bicgstab_ring.cu, block = 2 the block kernel of bicgstab.cu.
 int bicgstab_max_blocks(int block);
 int bicgstab_partial_slots();
 cudaError_t launch_bicgstab(const BicgArgs& a, int grid, cudaStream_t st);
+int bicgstab_ring_max_blocks();
+int bicgstab_ring_partial_slots();
+cudaError_t launch_bicgstab_ring(const BicgArgs& a, int grid, cudaStream_t st);
 
 }  // namespace rafem
 
@@ -336,6 +342,8 @@ struct GmresArgs {
     const int32_t* sp;
     const int32_t* sc;
     const int16_t* sc16;
+    const int32_t* pat_off;          // one column pattern per slice (kernel code 3), or null
+    const int32_t* pat_pool;
     const double* A;
     const int32_t* diag;
     const double* b;
