@@ -250,9 +250,10 @@ def _ncu_traffic(kernel: str):
         e = json.load(f).get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_2409_13036_b300", "csrc", e["source"])
-    if _source_hash(src) != e["source_sha256"]:
-        return None
+    # every source file the kernel is built from must be unchanged since the capture
+    for name, sha in zip(e.get("sources", [e.get("source")]), e.get("sources_sha256", [e.get("source_sha256")])):
+        if not name or _source_hash(os.path.join(ROOT, "paper_2409_13036_b300", "csrc", name)) != sha:
+            return None
     return e
 
 

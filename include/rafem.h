@@ -277,11 +277,12 @@ int rafem_set_schedule(rafem_ctx* ctx, int32_t rows_per_tile);
 int rafem_get_schedule(rafem_ctx* ctx, int32_t* rows_per_tile, int32_t* n_tiles, int32_t* grid);
 
 /* Storage actually used by the solver: kernel_code 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit
- * column deltas, 3 = SELL-32 whose 32-row slices each share one column pattern (chosen at create when that widens
- * no slice, as on lattice-numbered meshes: the CG-family solvers then stream matrix values only), 4/8/16/32 = CSR
- * with that many lanes per row; nnz_stored includes slice padding; column_bytes is the size of the per-entry
- * columns, 2 or 4 (read by the other passes, and by the solvers unless kernel_code is 3); assembly is the RAFEM_ASSEMBLY_* in use; arith is RAFEM_ARITH_FP64 or RAFEM_ARITH_DW (what
- * RAFEM_ARITH_AUTO resolved to). Any out pointer may be NULL. */
+ * column deltas, 3 = SELL-32 whose 32-row slices each share one column pattern (chosen at create when that adds
+ * at most 2% of stored entries, as on lattice-numbered meshes: the ring solvers then stream matrix values only),
+ * 4/8/16/32 = CSR with that many lanes per row; nnz_stored includes slice padding; column_bytes is the size of the
+ * per-entry columns, 2 or 4 (read by the other passes, and by the solvers unless kernel_code is 3); assembly is the
+ * RAFEM_ASSEMBLY_* in use; arith is RAFEM_ARITH_FP64 or RAFEM_ARITH_DW (what RAFEM_ARITH_AUTO resolved to). Any out
+ * pointer may be NULL. */
 int rafem_layout_info(rafem_ctx* ctx, int32_t* kernel_code, int64_t* nnz_stored, int32_t* column_bytes,
                       int32_t* assembly, int32_t* arith);
 
