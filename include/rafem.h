@@ -161,8 +161,7 @@ typedef struct rafem_params {
     int32_t gmres_min_restart;       /* RAFEM_SOLVER_GMRES: 0 = every cycle has gmres_restart steps; 1..m = the
                                         cycle length adapts between this and gmres_restart from each cycle's
                                         residual reduction (shorter while convergence is moderate, back to the
-                                        full length on stagnation), and a solve starts with the length the
-                                        previous solve of the same system ended with                           */
+                                        full length on stagnation); every solve starts at the full length      */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */

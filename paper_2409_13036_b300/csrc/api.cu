@@ -149,7 +149,6 @@ struct rafem_ctx {
     int bg_grid = 0;
     // GMRES(m) (solver == RAFEM_SOLVER_GMRES)
     int gm_m = 0, gm_grid = 0;
-    int32_t* gm_mstate = nullptr;  // [2] adaptive restart length per system, carried from solve to solve
     // monolithic coupled step (coupling == RAFEM_COUPLING_MONOLITHIC): 2 x 2 block Jacobian on the node pattern,
     // interleaved residual and Newton correction, block-BiCGSTAB workspace (2N vectors)
     bool mono = false;
@@ -550,7 +549,6 @@ cudaError_t enqueue_solve(rafem_ctx* c, int which, const double* b, double* x) {
         g.N = c->N;
         g.m = c->gm_m;
         g.m_min = c->prm.gmres_min_restart;
-        g.m_state = c->gm_mstate + (which == RAFEM_SYS_V ? 0 : 1);
         g.sp = c->rp;
         g.sc = c->ci;
         g.sc16 = c->ci16;
@@ -1500,7 +1498,6 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         c->gm_grid = gmres_max_blocks(c->gm_m);
         if (c->gm_grid <= 0) return RAFEM_ERR_CUDA;
         c->gm_grid = std::min(c->gm_grid, (N + SELL_C - 1) / SELL_C);
-        CK(dalloc(c, &c->gm_mstate, 2));  // per system; 0 = start at the full length
         CK(dalloc(c, &c->gm_partial, (size_t)gmres_partial_slots(c->gm_m) * c->gm_grid));
         CK(dalloc(c, &c->gm_H, (size_t)c->gm_grid * (c->gm_m + 1) * c->gm_m));
     }
@@ -1991,7 +1988,6 @@ int rafem_reset(rafem_ctx* c) {
     for (double* h : {c->T_hist, c->V_hist, c->T_hist2, c->V_hist2, c->T_hist3, c->V_hist3})
         CK(cudaMemsetAsync(h, 0, N * sizeof(double), c->stream));
     if (c->proj_D) CK(cudaMemsetAsync(c->proj_D, 0, (size_t)proj_stride(c->proj_k) * N * sizeof(double), c->stream));
-    if (c->gm_mstate) CK(cudaMemsetAsync(c->gm_mstate, 0, 2 * sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(c->istats, 0, c->n_inst * sizeof(rafem_step_stats), c->stream));
     CK(cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream));
     c->step = 0;

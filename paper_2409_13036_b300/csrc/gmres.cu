@@ -23,8 +23,8 @@
 // rule of Baker, Jessup and Kolev, "A simple strategy for varying the restart parameter in GMRES(m)", J. Comput.
 // Appl. Math. 230 (2009): with cr the ratio of the true residual norms at the start of this cycle and the last,
 // cr > cos(8 deg) (stagnation) sets m; cr < cos(80 deg) (fast) keeps the length; otherwise the length drops by 3,
-// back to m once it would fall below m_min. The length a solve ends with starts the next solve of the same system
-// (the simulation's solves adapt too). Stagnation handling: cycles at the full length m that reduce the residual
+// back to m once it would fall below m_min; every solve starts at m (carrying a short length over to the next
+// solve of the simulation cost more cycles on the measured workloads than it saved). Stagnation handling: cycles at the full length m that reduce the residual
 // by less than 0.1% are counted, and two in a row end the solve (RAFEM_NOT_CONVERGED) instead of burning the
 // iteration cap: at that rate a reduction of 1e-10 would take more than 23,000 cycles.
 //
@@ -75,7 +75,6 @@ struct Args {
     double tol;
     int max_iter;
     long long spin_limit_ns;
-    int32_t* m_state;       // adaptive length the next solve starts with (read at launch, written at the end)
 };
 
 // Restart-length rule (Baker, Jessup, Kolev 2009): thresholds on the cycle's convergence ratio and the decrement.
@@ -280,9 +279,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         bb = tot[0];
     }
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
-    // restart length of the current cycle (adaptive: from the previous solve of this system)
+    // restart length of the current cycle: every solve starts at the full length m
     int m_cur = m;
-    if (a.m_min > 0 && a.m_state) m_cur = min(max(*(volatile int32_t*)a.m_state, a.m_min), m);
     double rr_prev = -1.0;
     int stagnant = 0, reorths = 0;
     while (!err) {
@@ -419,7 +417,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         });
         if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
     }
-    if (a.m_state && blockIdx.x == 0 && threadIdx.x == 0) *a.m_state = m_cur;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         InstState st = {};
         st.bb = bb;
@@ -458,7 +455,7 @@ int gmres_partial_slots(int m) { return 2 * (m + 2) + 2; }
 
 cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
     Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.pat_off, s.pat_pool, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.z, s.dinv, s.H,
-           s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns, s.m_state};
+           s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     if (s.bar_missing > 0 && (e = launch_barrier_reset(s.bar, s.bar_missing, st)) != cudaSuccess) return e;

@@ -337,7 +337,6 @@ namespace rafem {
 struct GmresArgs {
     int N, m;                        // rows, restart length (1..64): the longest cycle
     int m_min;                       // 0: every cycle has m steps; else cycles adapt between m_min and m
-    int32_t* m_state;                // device: adaptive length the next solve starts with (nullable)
     int ld;                          // row stride of the basis: N rounded up to a multiple of 32
     const int32_t* sp;
     const int32_t* sc;
