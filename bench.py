@@ -336,6 +336,28 @@ def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: in
     return steps * per_step + cycles * per_cycle
 
 
+def alg_fma_gmres(N: int, nnz: int, steps: float, cycles: float) -> float:
+    """FP64 fused multiply-adds of one GMRES(m) solve launch: per Arnoldi step j one per stored entry (SpMV), j + 1
+    per row for the dots against the basis, j + 1 for the update, and ~3 for the norm, the Jacobi scaling and the
+    new basis vector; per cycle the residual SpMV and the update of x (one per row and basis vector). j averages
+    about half the steps per cycle (as in alg_bytes_gmres)."""
+    cycles = max(cycles, 1.0)
+    steps_per_cycle = steps / cycles
+    j_avg = (steps_per_cycle - 1) / 2.0
+    per_step = nnz + (2 * (j_avg + 1) + 3) * N
+    per_cycle = nnz + (steps_per_cycle + 2) * N
+    return steps * per_step + cycles * per_cycle
+
+
+def fp64_pipe_line(fma: float, solve_ms: float) -> dict:
+    """FP64 FMA rate of a launch against the FP64 pipe: B300 retires 2 FP64 FMAs per clock per SM (148 SMs at
+    2.032 GHz: 0.60 TFMA/s)."""
+    peak_fma = 148 * 2 * 2.032e9
+    return {"bound": "alu", "achieved": fma / (solve_ms * 1e-3) / 1e12, "peak": peak_fma / 1e12,
+            "unit": "TFMA/s (FP64)", "frac": fma / (solve_ms * 1e-3) / peak_fma,
+            "peak_kind": "2 FP64 FMA/clk/SM x 148 SMs x 2.032 GHz (unit count and clock)"}
+
+
 def cpu_baseline_line(t: dict, c1: dict | None, small: dict | None) -> dict:
     """The cpu_baseline object: the oracle's steps/s on the 48^3 workload (117,649 nodes, jitter 10%, 60 steps at
     dt = 1 s to relative residual 1e-10 in its configuration) from the steps timed, with the 60-step run
@@ -471,13 +493,12 @@ def roofline(res, mixed, peaks, peak_kind):
     achieved = alg / (solve_ms * 1e-3) / 1e9
     fp64_pipe = None
     if kern.startswith("k_cg64"):
-        # the FP64 solver is co-limited by the FP64 pipe: B300 retires 2 FP64 FMAs per clock per SM (148 SMs at
-        # 2.032 GHz: 0.60 TFMA/s); per iteration one FMA per stored entry (SpMV) and ~10 per row (vector phase)
-        fma = (iters + 2) * (res["layout"]["nnz_stored"] + 10 * N)
-        peak_fma = 148 * 2 * 2.032e9
-        fp64_pipe = {"bound": "alu", "achieved": fma / (solve_ms * 1e-3) / 1e12, "peak": peak_fma / 1e12,
-                     "unit": "TFMA/s (FP64)", "frac": fma / (solve_ms * 1e-3) / peak_fma,
-                     "peak_kind": "2 FP64 FMA/clk/SM x 148 SMs x 2.032 GHz (unit count and clock)"}
+        # the FP64 solver is co-limited by the FP64 pipe: per iteration one FMA per stored entry (SpMV) and ~10 per
+        # row (vector phase)
+        fp64_pipe = fp64_pipe_line((iters + 2) * (res["layout"]["nnz_stored"] + 10 * N), solve_ms)
+    elif kern == "k_gmres":
+        # GMRES is bound by the FP64 pipe (its Gram-Schmidt dots and updates)
+        fp64_pipe = fp64_pipe_line(alg_fma_gmres(N, res["layout"]["nnz_stored"], iters, ref), solve_ms)
     nc = _ncu_traffic(kern)
     traffic = None
     if nc:

@@ -226,7 +226,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
         if ((++spins & 63) == 0) {
             if (*(volatile int*)abort) return false;
             if ((long long)(globaltimer() - t0) > a.spin_limit_ns || spins > (1LL << 34)) {
-                atomicExch(&a.bar->err, RAFEM_ERR_TIMEOUT);
+                raise_barrier_error(a.bar, RAFEM_ERR_TIMEOUT);
                 atomicExch(abort, 1);
                 return false;
             }
