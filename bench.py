@@ -337,16 +337,12 @@ def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: in
 
 
 def alg_fma_gmres(N: int, nnz: int, steps: float, cycles: float) -> float:
-    """FP64 fused multiply-adds of one GMRES(m) solve launch: per Arnoldi step j one per stored entry (SpMV), j + 1
-    per row for the dots against the basis, j + 1 for the update, and ~3 for the norm, the Jacobi scaling and the
-    new basis vector; per cycle the residual SpMV and the update of x (one per row and basis vector). j averages
-    about half the steps per cycle (as in alg_bytes_gmres)."""
+    """FP64 operations of one GMRES(m) solve launch. The Gram-Schmidt dots and updates and the update of x run in
+    double-word arithmetic on the FP32 pipes (the basis is stored as float pairs), so the FP64 pipe carries per
+    Arnoldi step one FMA per stored entry (SpMV) and ~5 per row (scaling of w and of the new basis vector, (w, w),
+    the double-word to FP64 rounding of w, the Jacobi scaling), and per cycle the residual SpMV and ~2 per row."""
     cycles = max(cycles, 1.0)
-    steps_per_cycle = steps / cycles
-    j_avg = (steps_per_cycle - 1) / 2.0
-    per_step = nnz + (2 * (j_avg + 1) + 3) * N
-    per_cycle = nnz + (steps_per_cycle + 2) * N
-    return steps * per_step + cycles * per_cycle
+    return steps * (nnz + 5 * N) + cycles * (nnz + 2 * N)
 
 
 def fp64_pipe_line(fma: float, solve_ms: float) -> dict:
@@ -497,7 +493,7 @@ def roofline(res, mixed, peaks, peak_kind):
         # row (vector phase)
         fp64_pipe = fp64_pipe_line((iters + 2) * (res["layout"]["nnz_stored"] + 10 * N), solve_ms)
     elif kern == "k_gmres":
-        # GMRES is bound by the FP64 pipe (its Gram-Schmidt dots and updates)
+        # GMRES's FP64 work: its SpMVs and a few operations per row (Gram-Schmidt runs on the FP32 pipes)
         fp64_pipe = fp64_pipe_line(alg_fma_gmres(N, res["layout"]["nnz_stored"], iters, ref), solve_ms)
     nc = _ncu_traffic(kern)
     traffic = None

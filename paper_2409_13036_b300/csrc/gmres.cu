@@ -42,6 +42,7 @@
 
 #include "grid_sync.cuh"
 #include "internal.h"
+#include "dw.cuh"
 #include "sell_ring.cuh"
 
 namespace rafem {
@@ -64,7 +65,7 @@ struct Args {
     const int32_t* diag;
     const double* b;
     double* x;
-    double* Vb;       // [m][ld] basis
+    float2* Vb;       // [m][ld] basis, double-word (float pairs, 8 bytes per entry like the double it replaces)
     double* w[2];     // [N] alternating unnormalised vectors
     double* z;        // [N] M^-1 of the vector the next SpMV multiplies
     double* dinv;     // [N]
@@ -144,63 +145,93 @@ __device__ __forceinline__ void st2(double* p, double2 v, int n) {
         p[0] = v.x;
 }
 
-constexpr int kVb = 4;  // basis vectors per batch of loads (more would spill: 17 warps cap a thread at 96 registers)
+constexpr int kVb = 3;  // basis vectors per batch of loads (more would spill: 17 warps cap a thread at 96 registers)
+
+// The Gram-Schmidt dots and updates and the update of x run in double-word arithmetic on the FP32 pipes: B300
+// retires 2 FP64 FMAs per clock per SM, and with FP64 basis vectors these passes, 2 (j + 1) FMAs per row in
+// Arnoldi step j, held the kernel to the FP64 pipe. The basis is stored as float pairs (48 significant bits, no
+// conversion when read); each basis term is one compensated product-accumulate (dw::dot_acc, Ogita-Rump-Oishi
+// Dot2), whose result is as accurate as an FP64 dot of the same 48-bit inputs. The Arnoldi vector w, the SpMV and
+// the Hessenberg arithmetic stay FP64.
+
+// rows i, i + 1 (n of them present) of a double-word vector as one 16-byte load
+__device__ __forceinline__ float4 ldw2(const float2* p, int n) {
+    if (n == 2) return __ldcg(reinterpret_cast<const float4*>(p));
+    if (n == 1) {
+        const float2 v = __ldcg(p);
+        return make_float4(v.x, v.y, 0.0f, 0.0f);
+    }
+    return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
 
 // acc[warp][i] += (w, v_i) for i < n over the block's rows, and with self (w, w) into acc[warp][n].
 __device__ __forceinline__ void dots(const Args& a, double* acc, const double* w, int n, bool self, int r0, int r1) {
     for (int i0 = 0; i0 < n; i0 += kVb) {
-        double sum[kVb], ww = 0.0;
+        dw::df sum[kVb];
+        double ww = 0.0;
 #pragma unroll
-        for (int t = 0; t < kVb; ++t) sum[t] = 0.0;
+        for (int t = 0; t < kVb; ++t) sum[t] = dw::make(0.0f);
         const bool with_self = self && i0 == 0;
         for_pairs2(r0, r1, [&](int i, int ci, int j, int cj) {
             const double2 wi = ld2(w + i, ci), wj = ld2(w + j, cj);
-            double2 v[kVb], u[kVb];
+            const dw::df w0 = dw::split(wi.x), w1 = dw::split(wi.y), w2 = dw::split(wj.x), w3 = dw::split(wj.y);
+            float4 v[kVb], u[kVb];
 #pragma unroll
             for (int t = 0; t < kVb; ++t) {
-                const double* vt = a.Vb + (size_t)(i0 + t) * a.ld;
-                v[t] = ld2(vt + i, i0 + t < n ? ci : 0);
-                u[t] = ld2(vt + j, i0 + t < n ? cj : 0);
+                const float2* vt = a.Vb + (size_t)(i0 + t) * a.ld;
+                v[t] = ldw2(vt + i, i0 + t < n ? ci : 0);
+                u[t] = ldw2(vt + j, i0 + t < n ? cj : 0);
             }
 #pragma unroll
-            for (int t = 0; t < kVb; ++t)
-                sum[t] = fma(wj.y, u[t].y, fma(wj.x, u[t].x, fma(wi.y, v[t].y, fma(wi.x, v[t].x, sum[t]))));
+            for (int t = 0; t < kVb; ++t) {
+                dw::dot_acc(sum[t], w0, dw::make(v[t].x, v[t].y));
+                dw::dot_acc(sum[t], w1, dw::make(v[t].z, v[t].w));
+                dw::dot_acc(sum[t], w2, dw::make(u[t].x, u[t].y));
+                dw::dot_acc(sum[t], w3, dw::make(u[t].z, u[t].w));
+            }
             if (with_self) ww = fma(wj.y, wj.y, fma(wj.x, wj.x, fma(wi.y, wi.y, fma(wi.x, wi.x, ww))));
         });
 #pragma unroll
         for (int t = 0; t < kVb; ++t)
-            if (i0 + t < n) warp_add(acc, i0 + t, sum[t]);
+            if (i0 + t < n) warp_add(acc, i0 + t, dw::to_double(dw::finish(sum[t])));
         if (with_self) warp_add(acc, n, ww);
     }
 }
 
 // w -= sum_{i < n} c_i v_i over the block's rows; with z, also z = dinv w (the next SpMV's input).
 __device__ __forceinline__ void subtract(const Args& a, double* w, const double* c_, int n, double* z, int r0, int r1) {
+    __shared__ float2 cn[64];  // -c_i as double-word
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += kBlock) dw::store(cn + t, dw::split(-c_[t]));
+    __syncthreads();
     for_pairs2(r0, r1, [&](int i, int ci, int j, int cj) {
-        double2 wi = ld2(w + i, ci), wj = ld2(w + j, cj);
+        const double2 wi = ld2(w + i, ci), wj = ld2(w + j, cj);
+        dw::df y0 = dw::split(wi.x), y1 = dw::split(wi.y), y2 = dw::split(wj.x), y3 = dw::split(wj.y);
         for (int i0 = 0; i0 < n; i0 += kVb) {
-            double2 v[kVb], u[kVb];
+            float4 v[kVb], u[kVb];
 #pragma unroll
             for (int t = 0; t < kVb; ++t) {
-                const double* vt = a.Vb + (size_t)(i0 + t) * a.ld;
-                v[t] = ld2(vt + i, i0 + t < n ? ci : 0);
-                u[t] = ld2(vt + j, i0 + t < n ? cj : 0);
+                const float2* vt = a.Vb + (size_t)(i0 + t) * a.ld;
+                v[t] = ldw2(vt + i, i0 + t < n ? ci : 0);
+                u[t] = ldw2(vt + j, i0 + t < n ? cj : 0);
             }
 #pragma unroll
             for (int t = 0; t < kVb; ++t) {
-                const double ct = i0 + t < n ? c_[i0 + t] : 0.0;
-                wi.x = fma(-ct, v[t].x, wi.x);
-                wi.y = fma(-ct, v[t].y, wi.y);
-                wj.x = fma(-ct, u[t].x, wj.x);
-                wj.y = fma(-ct, u[t].y, wj.y);
+                const dw::df ct = i0 + t < n ? dw::load(cn + i0 + t) : dw::make(0.0f);
+                dw::dot_acc(y0, ct, dw::make(v[t].x, v[t].y));
+                dw::dot_acc(y1, ct, dw::make(v[t].z, v[t].w));
+                dw::dot_acc(y2, ct, dw::make(u[t].x, u[t].y));
+                dw::dot_acc(y3, ct, dw::make(u[t].z, u[t].w));
             }
         }
-        st2(w + i, wi, ci);
-        st2(w + j, wj, cj);
+        const double2 ni = make_double2(dw::to_double(dw::finish(y0)), dw::to_double(dw::finish(y1)));
+        const double2 nj = make_double2(dw::to_double(dw::finish(y2)), dw::to_double(dw::finish(y3)));
+        st2(w + i, ni, ci);
+        st2(w + j, nj, cj);
         if (z) {
             const double2 di = ld2(a.dinv + i, ci), dj = ld2(a.dinv + j, cj);
-            st2(z + i, make_double2(di.x * wi.x, di.y * wi.y), ci);
-            st2(z + j, make_double2(dj.x * wj.x, dj.y * wj.y), cj);
+            st2(z + i, make_double2(di.x * ni.x, di.y * ni.y), ci);
+            st2(z + j, make_double2(dj.x * nj.x, dj.y * nj.y), cj);
         }
     });
 }
@@ -222,12 +253,12 @@ struct EmStart {
 struct EmArnoldi {
     const double* u;
     double* wn;
-    double* vj;
+    float2* vj;
     double inv;
     __device__ __forceinline__ double pre(int row) const { return ldcg(u + row); }
     __device__ __forceinline__ void fin(int row, double az, double ui) const {
         wn[row] = az * inv;
-        vj[row] = ui * inv;
+        dw::store(vj + row, dw::split(ui * inv));
     }
 };
 
@@ -247,6 +278,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
     __shared__ double acc[kWarps * kAcc];
     __shared__ double tot[kAcc];
     __shared__ double cs[64], sn[64], g[65], yv[64];
+    __shared__ float2 yd[64];  // y as double-word
     __shared__ double sm[kSumMax * kBlock];
     const int m = a.m, N = a.N;
     double* H = a.H + (size_t)blockIdx.x * (m + 1) * m;
@@ -324,7 +356,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
         for (int j = 0; j < m_cur; ++j) {
             const double* u = a.w[cur];
             double* wn = a.w[cur ^ 1];
-            double* vj = a.Vb + (size_t)j * a.ld;
+            float2* vj = a.Vb + (size_t)j * a.ld;
             double* Hj = H + (size_t)j * (m + 1);
             // S: w = A M^-1 u / s and v_j = u / s (SpMV through the ring), then h_ij = (w, v_i), i <= j, and (w, w)
             const bool ok = !own || sell_tile<double, double>(a, ring, a.sp, sc, a.A, a.z, r0, r1,
@@ -396,24 +428,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_gmres(Args a) {
             }
         }
         __syncthreads();
+        for (int i = threadIdx.x; i < k; i += kBlock) dw::store(yd + i, dw::split(yv[i]));
+        __syncthreads();
         for_pairs(r0, r1, [&](int i, int c) {
-            double2 t = make_double2(0.0, 0.0);
+            dw::df t0 = dw::make(0.0f), t1 = dw::make(0.0f);
             for (int i0 = 0; i0 < k; i0 += kVb) {
-                double2 v[kVb];
+                float4 v[kVb];
 #pragma unroll
-                for (int q = 0; q < kVb; ++q)
-                    v[q] = i0 + q < k ? ld2(a.Vb + (size_t)(i0 + q) * a.ld + i, c) : make_double2(0.0, 0.0);
+                for (int q = 0; q < kVb; ++q) v[q] = ldw2(a.Vb + (size_t)(i0 + q) * a.ld + i, i0 + q < k ? c : 0);
 #pragma unroll
                 for (int q = 0; q < kVb; ++q) {
-                    const double yq = i0 + q < k ? yv[i0 + q] : 0.0;
-                    t.x = fma(yq, v[q].x, t.x);
-                    t.y = fma(yq, v[q].y, t.y);
+                    const dw::df yq = i0 + q < k ? dw::load(yd + i0 + q) : dw::make(0.0f);
+                    dw::dot_acc(t0, yq, dw::make(v[q].x, v[q].y));
+                    dw::dot_acc(t1, yq, dw::make(v[q].z, v[q].w));
                 }
             }
+            const double tx = dw::to_double(dw::finish(t0)), ty = dw::to_double(dw::finish(t1));
             // x is the caller's buffer (no alignment beyond 8 bytes is assumed): scalar accesses
             const double2 d = ld2(a.dinv + i, c);
-            a.x[i] = fma(d.x, t.x, a.x[i]);
-            if (c == 2) a.x[i + 1] = fma(d.y, t.y, a.x[i + 1]);
+            a.x[i] = fma(d.x, tx, a.x[i]);
+            if (c == 2) a.x[i + 1] = fma(d.y, ty, a.x[i + 1]);
         });
         if (grid_barrier(a.bar, a.spin_limit_ns, target)) { err = true; break; }
     }
@@ -438,7 +472,7 @@ void* kernel_for(const GmresArgs& s) {
 }  // namespace
 
 int gmres_max_blocks(int /*m*/) {
-    int dev = 0, sms = 0, per1 = 0, per2 = 0;
+    int dev = 0, sms = 0, per1 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     int per = 1;
@@ -447,14 +481,13 @@ int gmres_max_blocks(int /*m*/) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k, kBlock, kRingBytes) != cudaSuccess) return 0;
         per = per1 < per ? per1 : per;
     }
-    (void)per2;
     return sms * (per < 1 ? per : 1);
 }
 
 int gmres_partial_slots(int m) { return 2 * (m + 2) + 2; }
 
 cudaError_t launch_gmres(const GmresArgs& s, int grid, cudaStream_t st) {
-    Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.pat_off, s.pat_pool, s.A, s.diag, s.b, s.x, s.V, {s.w0, s.w1}, s.z, s.dinv, s.H,
+    Args a{s.N, s.m, s.m_min, s.ld, s.sp, s.sc, s.sc16, s.pat_off, s.pat_pool, s.A, s.diag, s.b, s.x, reinterpret_cast<float2*>(s.V), {s.w0, s.w1}, s.z, s.dinv, s.H,
            s.partial, s.bar, s.inst, s.tol, s.max_iter, s.spin_limit_ns};
     cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
