@@ -86,12 +86,19 @@ extern "C" {
 #define RAFEM_COUPLING_STAGGERED   0 /* V then T per pass (lagged sigma; corrector passes when n_corrector > 1) */
 #define RAFEM_COUPLING_MONOLITHIC  1 /* the paper's 2N x 2N system: V and T of a step solved together by Newton's
                                         method (Jacobian with the sigma(T) and Joule couplings, unknowns
-                                        interleaved per node, 2 x 2 blocks on the node pattern, block-Jacobi
-                                        BiCGSTAB, row-only Dirichlet rows) until max |dT| < corrector_tol or
-                                        n_corrector iterations, starting from the lagged staggered step; each
-                                        linear solve is inexact (forcing terms of Eisenstat and Walker, within
-                                        [tol, 1e-2]); FP64, SELL-32 layout, single instance; the iterations run
-                                        on the device like corrector passes                                    */
+                                        interleaved per node, 2 x 2 blocks on the node pattern, row-only
+                                        Dirichlet rows; linear solver: coupled_solver) until max |dT| <
+                                        corrector_tol or n_corrector iterations, starting from the lagged
+                                        staggered step; each linear solve is inexact (forcing terms of Eisenstat
+                                        and Walker, within [tol, 1e-2]); FP64, SELL-32 layout, single instance;
+                                        the iterations run on the device like corrector passes                 */
+
+/* Linear solver of the monolithic step's Newton iterations (rafem_params.coupled_solver). */
+#define RAFEM_COUPLED_FGMRES   0     /* flexible GMRES, at most 8 iterations per Newton iteration, right-
+                                        preconditioned by one block Gauss-Seidel sweep (potential block, then
+                                        thermal block with the coupling term) whose block solves are Jacobi-PCG
+                                        solves of the split systems to a relative residual of 0.1 (default)    */
+#define RAFEM_COUPLED_BICGSTAB 1     /* BiCGSTAB with 2 x 2 block-Jacobi preconditioning                        */
 
 #define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known
                                         values moved to the right-hand side: the systems stay SPD              */
@@ -162,17 +169,23 @@ typedef struct rafem_params {
                                         cycle length adapts between this and gmres_restart from each cycle's
                                         residual reduction (shorter while convergence is moderate, back to the
                                         full length on stagnation); every solve starts at the full length      */
+    int32_t coupled_solver;          /* RAFEM_COUPLING_MONOLITHIC: RAFEM_COUPLED_FGMRES (0) or
+                                        RAFEM_COUPLED_BICGSTAB                                                 */
 } rafem_params;
 
 /* Per-step statistics, filled on the device and copied back when requested. */
 typedef struct rafem_step_stats {
     int32_t status;                  /* RAFEM_OK, RAFEM_NOT_CONVERGED or a negative error                     */
-    int32_t iters_V;                 /* Krylov iterations of the potential solve (all refinements)             */
-    int32_t iters_T;                 /* Krylov iterations of the thermal solve                                  */
+    int32_t iters_V;                 /* Krylov iterations of the potential solve (all refinements); monolithic
+                                        step: BiCGSTAB iterations, or with RAFEM_COUPLED_FGMRES the inner CG
+                                        iterations on the potential block, over all Newton iterations          */
+    int32_t iters_T;                 /* Krylov iterations of the thermal solve (monolithic step with
+                                        RAFEM_COUPLED_FGMRES: inner CG iterations on the thermal block)        */
     int32_t refine_V;                /* FP64 refinements of the potential solve (mixed precision), restart
-                                        cycles (GMRES), else 0                                                 */
+                                        cycles (GMRES), outer flexible-GMRES iterations (monolithic step with
+                                        RAFEM_COUPLED_FGMRES), else 0                                          */
     int32_t refine_T;                /* FP64 refinements of the thermal solve                                  */
-    int32_t correctors;              /* corrector passes taken in this step                                    */
+    int32_t correctors;              /* corrector passes (monolithic step: Newton iterations) in this step     */
     double  relres_V;                /* final relative residual of the potential solve (FP64)                 */
     double  relres_T;                /* final relative residual of the thermal solve (FP64)                   */
     int64_t step;                    /* steps completed by the context                                         */

@@ -156,6 +156,13 @@ struct rafem_ctx {
     double *mb_r = nullptr, *mb_rh = nullptr, *mb_p = nullptr, *mb_ph = nullptr, *mb_v = nullptr, *mb_s = nullptr,
            *mb_sh = nullptr, *mb_t = nullptr, *mb_dinv = nullptr, *mb_partial = nullptr;
     int mb_grid = 0;
+    // flexible GMRES of the monolithic step (coupled_solver = RAFEM_COUPLED_FGMRES): basis V (kFgMax + 1 vectors
+    // of 2N) and preconditioned vectors Z (kFgMax), the Arnoldi vector, the split preconditioner's vectors
+    double *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr, *fg_partial = nullptr;
+    double *fg_rV = nullptr, *fg_rT = nullptr, *fg_zV = nullptr, *fg_zT = nullptr;
+    FgState* fg_st = nullptr;
+    size_t fg_ld = 0;
+    int fg_G = 0;
     double *gm_V = nullptr, *gm_w0 = nullptr, *gm_w1 = nullptr, *gm_dinv = nullptr, *gm_partial = nullptr;
     double *gm_z = nullptr, *gm_H = nullptr;  // M^-1 of the next SpMV's input; per-block Hessenberg copies
     int gm_ld = 0;                            // row stride of the basis
@@ -435,7 +442,7 @@ cudaError_t enqueue_assemble(rafem_ctx* c, int which, const double* T_sigma, con
 cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma, const double* T_old, bool with_y) {
     cudaError_t e;
     if (c->dw) {
-        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        float* v32 = c->valsV32;  // FP32 copy, when the context keeps one
         if (which == RAFEM_SYS_V)
             return launch_assemble_V_gather_dw(c->gd, c->gdw, c->N, c->rp, c->ci, c->diag, c->el, T_sigma,
                                                c->prm.alpha_sigma, c->bcV, c->gV, c->valsV, v32, c->bV, c->prm.lift,
@@ -445,7 +452,7 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
                                       c->prm.alpha_sigma, c->bT, c->stream);
     }
     if (c->gather) {
-        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        float* v32 = c->valsV32;  // FP32 copy, when the context keeps one
         if (which == RAFEM_SYS_V)
             return launch_assemble_V_gather(c->gd, c->N, c->rp, c->ci, c->diag, c->el, T_sigma, c->prm.alpha_sigma,
                                             c->bcV, c->gV, c->valsV, v32, c->bV, c->prm.lift, c->stream);
@@ -455,7 +462,7 @@ cudaError_t enqueue_assemble_raw(rafem_ctx* c, int which, const double* T_sigma,
     if (which == RAFEM_SYS_V) {
         e = launch_init_rhs(c->N, c->bcV, c->gV, nullptr, c->bV, c->stream);
         if (e != cudaSuccess) return e;
-        float* v32 = c->prm.precision == RAFEM_PRECISION_MIXED ? c->valsV32 : nullptr;
+        float* v32 = c->valsV32;  // FP32 copy, when the context keeps one
         for (int col = 0; col < c->n_colors; ++col) {
             e = launch_assemble_V(c->el, c->color_off[col], c->color_off[col + 1], T_sigma, c->bcV, c->gV,
                                   c->prm.alpha_sigma, c->valsV, v32, c->bV, c->prm.lift, c->stream);
@@ -778,6 +785,56 @@ cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
     return enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T);
 }
 
+// The Newton linear solve J delta = R by flexible GMRES with the split-system preconditioner (mono_fgmres.cu): a
+// fixed sequence of kFgMax outer iterations whose launches return at once after convergence, then delta and
+// (V, T) -= delta. The inner solves are mixed-precision Jacobi-PCG launches (FP32 iterations, FP64 residual) on
+// the assembled split matrices (A_V with sigma at T^n from the step's staggered start, the constant A_T), each to
+// a relative residual of kFgInnerTol.
+constexpr double kFgInnerTol = 0.1;
+cudaError_t enqueue_newton_fgmres(rafem_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int N = c->N, n2 = 2 * N, G = c->fg_G;
+    const size_t ld = c->fg_ld;
+    FgState* fs = c->fg_st;
+    cudaError_t e = cudaMemsetAsync(&fs->done, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_fg_dots(n2, c->m_R, c->fg_V, ld, 0, fs, c->fg_partial, G, st)) != cudaSuccess) return e;
+    if ((e = launch_fg_init(fs, c->fg_partial, G, &c->corr->newton_rr, c->prm.tol, st)) != cudaSuccess) return e;
+    if ((e = launch_fg_scale(n2, c->m_R, c->fg_V, fs, st)) != cudaSuccess) return e;
+    for (int j = 0; j < kFgMax; ++j) {
+        const double* Vj = c->fg_V + (size_t)j * ld;
+        if ((e = launch_fg_split(N, Vj, c->fg_rV, c->fg_rT, c->fg_zV, c->fg_zT, fs, st)) != cudaSuccess) return e;
+        for (int which : {RAFEM_SYS_V, RAFEM_SYS_T}) {
+            const bool V = which == RAFEM_SYS_V;
+            if (!V && (e = launch_fg_couple(N, c->rp, c->ci, c->ci16, c->m_vals4, c->fg_zV, c->fg_rT, fs, st)) !=
+                          cudaSuccess)
+                return e;
+            SolveArgs a = make_args(c, which, V ? c->fg_rV : c->fg_rT, V ? c->fg_zV : c->fg_zT);
+            a.tol = kFgInnerTol;
+            a.skip = &fs->done;
+            if ((e = launch_krylov(a, c->lanes, c->valsV32 ? RAFEM_PRECISION_MIXED : RAFEM_PRECISION_FP64, false,
+                                   c->grid, c->block, st)) != cudaSuccess)
+                return e;
+            if ((e = launch_fg_count(fs, V ? c->instV : c->instT, which, st)) != cudaSuccess) return e;
+        }
+        double* Zj = c->fg_Z + (size_t)j * ld;
+        if ((e = launch_fg_spmv(N, c->rp, c->ci, c->ci16, c->m_vals4, c->fg_zV, c->fg_zT, c->fg_w, Zj, fs, st)) !=
+            cudaSuccess)
+            return e;
+        for (int pass = 1; pass <= 2; ++pass) {
+            if ((e = launch_fg_dots(n2, c->fg_w, c->fg_V, ld, j + 1, fs, c->fg_partial, G, st)) != cudaSuccess) return e;
+            if ((e = launch_fg_gs(fs, c->fg_partial, G, j, pass, st)) != cudaSuccess) return e;
+            double* next = pass == 2 ? c->fg_V + (size_t)(j + 1) * ld : nullptr;
+            if ((e = launch_fg_sub(n2, c->fg_w, c->fg_V, ld, j, fs, next, st)) != cudaSuccess) return e;
+        }
+    }
+    if ((e = launch_fg_finish(n2, c->fg_Z, ld, fs, c->m_D, c->instV, c->instT, st)) != cudaSuccess) return e;
+    k_record<<<1, 128, 0, st>>>(c->instV, c->n_inst, c->bar, RAFEM_SYS_V, c->stats, c->istats, 0);
+    k_record<<<1, 128, 0, st>>>(c->instT, c->n_inst, c->bar, RAFEM_SYS_T, c->stats, c->istats, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_newton_update(N, c->m_D, c->V, c->T, st);
+}
+
 // One Newton iteration of the monolithic coupled step: assemble the 2N x 2N Jacobian and residual at the current
 // (V, T), solve J delta = R with block-Jacobi BiCGSTAB, (V, T) -= delta.
 cudaError_t enqueue_newton(rafem_ctx* c) {
@@ -794,6 +851,7 @@ cudaError_t enqueue_newton(rafem_ctx* c) {
     e = launch_coupled_dirichlet(N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
                                  c->m_vals4, c->m_R, st);
     if (e != cudaSuccess) return e;
+    if (c->fg_st) return enqueue_newton_fgmres(c);
     if ((e = cudaMemsetAsync(c->m_D, 0, 2 * (size_t)N * sizeof(double), st)) != cudaSuccess) return e;
     BicgArgs g{};
     g.block = 2;
@@ -1327,7 +1385,10 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     std::vector<int32_t> order32(order.begin(), order.end());
     // ---- device buffers
     const size_t nnz = (size_t)c->nnz_store;
-    const bool mixed = prm->precision == RAFEM_PRECISION_MIXED;
+    // FP32 copies of the matrices and the FP32 Krylov vectors: the mixed-precision solves, and the monolithic
+    // step's flexible GMRES, whose preconditioner solves run in mixed precision
+    const bool mixed = prm->precision == RAFEM_PRECISION_MIXED ||
+                       (prm->coupling == RAFEM_COUPLING_MONOLITHIC && prm->coupled_solver == RAFEM_COUPLED_FGMRES);
     CK(dalloc(c, &c->rp, dev_rp.size()));
     CK(dalloc(c, &c->ci, nnz));
     CK(dalloc(c, &c->diag, N));
@@ -1483,6 +1544,13 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     int block = 0;
     int maxb = krylov_max_blocks(c->lanes, prm->precision, prm->solver == RAFEM_SOLVER_PIPECG, &block);
     if (maxb <= 0) return RAFEM_ERR_BAD_INPUT;
+    if (prm->coupling == RAFEM_COUPLING_MONOLITHIC && prm->coupled_solver == RAFEM_COUPLED_FGMRES) {
+        // the preconditioner's inner solves launch the mixed-precision kernel as well: prepare it (its dynamic
+        // shared memory) and keep the schedule within what both kernels hold co-resident
+        const int mb2 = krylov_max_blocks(c->lanes, RAFEM_PRECISION_MIXED, false, nullptr);
+        if (mb2 <= 0) return RAFEM_ERR_BAD_INPUT;
+        maxb = std::min(maxb, mb2);
+    }
     c->block = block;
     c->maxb = maxb;
     {
@@ -1513,6 +1581,20 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         c->mb_grid = bicgstab_max_blocks(2);
         if (c->mb_grid <= 0) return RAFEM_ERR_CUDA;
         CK(dalloc(c, &c->mb_partial, (size_t)bicgstab_partial_slots() * c->mb_grid));
+        if (prm->coupled_solver == RAFEM_COUPLED_FGMRES) {
+            c->fg_ld = (2 * (size_t)N + 63) / 64 * 64;
+            c->fg_G = fg_grid();
+            if (c->fg_G <= 0) return RAFEM_ERR_CUDA;
+            CK(dalloc(c, &c->fg_V, (size_t)(kFgMax + 1) * c->fg_ld));
+            CK(dalloc(c, &c->fg_Z, (size_t)kFgMax * c->fg_ld));
+            CK(dalloc(c, &c->fg_w, c->fg_ld));
+            for (double** v : {&c->fg_rV, &c->fg_rT, &c->fg_zV, &c->fg_zT}) CK(dalloc(c, v, (size_t)N + SELL_C));
+            CK(dalloc(c, &c->fg_partial, (size_t)(kFgMax + 2) * c->fg_G));
+            void* stp = nullptr;
+            CK(cudaMalloc(&stp, sizeof(FgState)));
+            c->allocs.push_back(stp);
+            c->fg_st = static_cast<FgState*>(stp);
+        }
     }
     if (prm->solver == RAFEM_SOLVER_BICGSTAB) {
         if (n_inst != 1 || !c->sell) return RAFEM_ERR_BAD_INPUT;
@@ -1675,6 +1757,8 @@ static int validate_params(const rafem_mesh* m, const rafem_params* prm) {
         return RAFEM_ERR_BAD_INPUT;
     if (prm->coupling == RAFEM_COUPLING_MONOLITHIC &&
         (prm->precision != RAFEM_PRECISION_FP64 || (prm->lanes_per_row != 0 && prm->lanes_per_row != 1)))
+        return RAFEM_ERR_BAD_INPUT;
+    if (prm->coupled_solver != RAFEM_COUPLED_FGMRES && prm->coupled_solver != RAFEM_COUPLED_BICGSTAB)
         return RAFEM_ERR_BAD_INPUT;
     if (prm->lift == RAFEM_LIFT_ROW && (prm->solver == RAFEM_SOLVER_PCG || prm->solver == RAFEM_SOLVER_PIPECG))
         return RAFEM_ERR_BAD_INPUT;

@@ -184,6 +184,7 @@ struct SolveArgs {
     int max_iter, max_refine;
     long long spin_limit_ns;
     int bar_missing;         // testing: the barrier counter starts this many arrivals short (0 in normal use)
+    const int* skip;         // when set and nonzero at launch, the solve does nothing (a finished outer iteration)
 };
 
 // Kernel code: 1 = SELL-32 with 32-bit columns, 2 = SELL-32 with 16-bit column deltas, 3 = SELL-32 whose slices
@@ -410,5 +411,40 @@ cudaError_t launch_projection(const ProjArgs& a, const int32_t* hist, int lag, c
 // then [Y = A D if apply], the sums, the small solve and the guess with its residual.
 cudaError_t launch_projection_basis(const ProjArgs& a, const int32_t* hist, int lag, cudaStream_t st);
 cudaError_t launch_projection_rest(const ProjArgs& a, bool apply, cudaStream_t st);
+
+// ---- monolithic step: flexible GMRES on the coupled Jacobian (mono_fgmres.cu) ---------------------------------
+// Outer iterations of one Newton linear solve at most; the state lives in device memory so that every kernel of an
+// outer iteration (and the inner persistent solves, through SolveArgs::skip) returns at once after convergence.
+constexpr int kFgMax = 8;
+struct FgState {
+    int32_t done;                     // 1: converged, out of iterations, or broken down (the rest is skipped)
+    int32_t k;                        // basis columns in the correction
+    int32_t outer;                    // outer iterations taken
+    int32_t status;                   // worst status of the inner solves (or RAFEM_ERR_NONFINITE)
+    int32_t itV, itT;                 // inner Krylov iterations of the two systems
+    double beta, eta, scale, ww;      // ||R||; forcing (relative); 1 / norm of the next basis vector; (w, w)
+    double h[(kFgMax + 1) * kFgMax];  // Hessenberg, column j at h + j (kFgMax + 1), Givens-rotated
+    double g[kFgMax + 1], cs[kFgMax], sn[kFgMax], y[kFgMax];
+    double coef[kFgMax + 1];          // coefficients of the current Gram-Schmidt pass
+};
+// 2N-vector kernels of the solve: n2 = 2 N interleaved (V, T) entries; ld the stride of the basis arrays.
+cudaError_t launch_fg_dots(int n2, const double* w, const double* V, size_t ld, int nv, const FgState* st,
+                           double* partial, int G, cudaStream_t s);
+cudaError_t launch_fg_init(FgState* st, const double* partial, int G, double* newton_rr, double tol, cudaStream_t s);
+cudaError_t launch_fg_scale(int n2, const double* src, double* dst, const FgState* st, cudaStream_t s);
+cudaError_t launch_fg_split(int N, const double* v, double* rV, double* rT, double* zV, double* zT,
+                            const FgState* st, cudaStream_t s);
+cudaError_t launch_fg_count(FgState* st, const InstState* inst, int which, cudaStream_t s);
+cudaError_t launch_fg_couple(int N, const int32_t* sp, const int32_t* sc, const int16_t* sc16, const double* vals4,
+                             const double* zV, double* rT, const FgState* st, cudaStream_t s);
+cudaError_t launch_fg_spmv(int N, const int32_t* sp, const int32_t* sc, const int16_t* sc16, const double* vals4,
+                           const double* zV, const double* zT, double* w, double* Zj, const FgState* st,
+                           cudaStream_t s);
+cudaError_t launch_fg_gs(FgState* st, const double* partial, int G, int j, int pass, cudaStream_t s);
+cudaError_t launch_fg_sub(int n2, double* w, const double* V, size_t ld, int j, const FgState* st, double* next,
+                          cudaStream_t s);
+cudaError_t launch_fg_finish(int n2, const double* Z, size_t ld, FgState* st, double* delta, InstState* instV,
+                             InstState* instT, cudaStream_t s);
+int fg_grid();
 
 }  // namespace rafem

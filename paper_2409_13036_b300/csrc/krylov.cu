@@ -366,6 +366,7 @@ struct EmTrueResidual {
 
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_cg64(SolveArgs a) {
+    if (a.skip && *(volatile const int*)a.skip) return;  // an outer iteration that is not needed
     RAFEM_RING_SETUP(L)
     __shared__ double sm[kSumMax * kBlock];
     __shared__ InstState sst[kMaxInst];
@@ -557,6 +558,7 @@ struct EmPipe {
 
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_pcg64(SolveArgs a) {
+    if (a.skip && *(volatile const int*)a.skip) return;  // an outer iteration that is not needed
     RAFEM_RING_SETUP(L)
     __shared__ double sm[kSumMax * kBlock];
     __shared__ InstState sst[kMaxInst];
@@ -734,6 +736,7 @@ struct AddCorrection {
 
 template <int L>
 __global__ void __launch_bounds__(kBlock, 1) k_cg_mixed(SolveArgs a) {
+    if (a.skip && *(volatile const int*)a.skip) return;  // an outer iteration that is not needed
     RAFEM_RING_SETUP(L)
     __shared__ double sm[kSumMax * kBlock];
     __shared__ InstState sst[kMaxInst];

@@ -41,6 +41,8 @@ RAFEM_SOLVER_PIPECG = 3
 RAFEM_PREDICT_PROJECT = 4
 RAFEM_COUPLING_STAGGERED = 0
 RAFEM_COUPLING_MONOLITHIC = 1
+RAFEM_COUPLED_FGMRES = 0
+RAFEM_COUPLED_BICGSTAB = 1
 RAFEM_LIFT_SYMMETRIC = 0
 RAFEM_LIFT_ROW = 1
 RAFEM_ILU_MULTICOLOR = 0
@@ -70,7 +72,8 @@ class rafem_params(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32), ("assembly", ctypes.c_int32),
                 ("predictor", ctypes.c_int32), ("ilu_order", ctypes.c_int32), ("lift", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("coupling", ctypes.c_int32), ("arith", ctypes.c_int32),
-                ("proj_basis", ctypes.c_int32), ("gmres_min_restart", ctypes.c_int32)]
+                ("proj_basis", ctypes.c_int32), ("gmres_min_restart", ctypes.c_int32),
+                ("coupled_solver", ctypes.c_int32)]
 
 
 class rafem_step_stats(ctypes.Structure):

@@ -49,19 +49,25 @@ def test_coupled_jacobian_and_residual_match_oracle(assembly):
     np.testing.assert_allclose(res.ravel(), Rref, rtol=1e-11, atol=1e-12 * np.abs(Rref).max())
 
 
-def test_monolithic_steps_match_oracle_fixed_point():
+@pytest.mark.parametrize("solver", [0, 1], ids=["fgmres", "bicgstab"])
+def test_monolithic_steps_match_oracle_fixed_point(solver):
     """Two monolithic steps (dt = 30 s, 40 V, Newton to max |dT| < 1e-9) agree with the oracle's Newton step and
-    with the corrector's fixed point (1e-9), in a few Newton iterations, through the device-side loop."""
+    with the corrector's fixed point (1e-9), in a few Newton iterations, through the device-side loop; with either
+    linear solver (flexible GMRES with the split-system preconditioner: at most 8 outer iterations per Newton
+    iteration, reported as refine_V; block-Jacobi BiCGSTAB)."""
     rafem = R()
     m = mg.cube_mesh(10, jitter=0.1, seed=82, sigma0="lognormal", V_electrode=40.0)
     model = O.Model(m, O.Params(dt=30.0, n_corrector=50, corrector_tol=1e-11))
     T = np.full(m.n_nodes, 37.0)
-    with rafem.Context(m, dt=30.0, coupling=1, n_corrector=20, corrector_tol=1e-9, tol=1e-13) as ctx:
+    with rafem.Context(m, dt=30.0, coupling=1, n_corrector=20, corrector_tol=1e-9, tol=1e-13,
+                       coupled_solver=solver) as ctx:
         for k in range(2):
             Tn, Vn, it, _ = O.step_newton(model, T, tol=1e-11)
             Tp, Vp, _ = model.step(T)
             s, st = ctx.solve_step()
             assert s == 0 and 2 <= st.correctors <= 8
+            if solver == 0:
+                assert 1 <= st.refine_V <= 8 * st.correctors and st.iters_V > 0 and st.iters_T > 0
             Tg, Vg = ctx.get_field(rafem.RAFEM_SYS_T), ctx.get_field(rafem.RAFEM_SYS_V)
             for ref_T, ref_V in ((Tn, Vn), (Tp, Vp)):
                 assert O.rel_err(Tg, ref_T) <= 1e-9
@@ -74,7 +80,8 @@ def test_monolithic_rejections():
     """Monolithic coupling needs FP64, the SELL-32 layout and a single instance; it has no adjoint."""
     rafem = R()
     m = mg.cube_mesh(6, jitter=0.1, seed=83)
-    for kw in (dict(coupling=1, precision=1), dict(coupling=1, lanes_per_row=8), dict(coupling=2)):
+    for kw in (dict(coupling=1, precision=1), dict(coupling=1, lanes_per_row=8), dict(coupling=2),
+               dict(coupling=1, coupled_solver=2)):
         with pytest.raises(rafem.RafemError):
             rafem.Context(m, **kw)
     with pytest.raises(rafem.RafemError):
@@ -82,3 +89,23 @@ def test_monolithic_rejections():
     with rafem.Context(m, coupling=1) as ctx:
         with pytest.raises(rafem.RafemError):
             ctx.tape_begin(2)
+
+
+def test_monolithic_fresh_process():
+    """A monolithic context with the flexible-GMRES solver in a process where no other context ever ran: its inner
+    mixed-precision solves must find their kernel prepared by the context itself (not by an earlier mixed context
+    of the same process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2409_13036_b300 import meshgen as mg, rafem\n"
+            "m = mg.cube_mesh(12, jitter=0.1, seed=84, V_electrode=40.0)\n"
+            "with rafem.Context(m, dt=30.0, coupling=1, n_corrector=20, corrector_tol=1e-9) as ctx:\n"
+            "    s, st = ctx.run(2)\n"
+            "    print(s, st.correctors, st.refine_V)\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    s, corr, outer = (int(x) for x in r.stdout.split()[-3:])
+    assert s == 0 and corr >= 1 and outer >= 1
