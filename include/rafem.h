@@ -96,8 +96,9 @@ extern "C" {
 /* Linear solver of the monolithic step's Newton iterations (rafem_params.coupled_solver). */
 #define RAFEM_COUPLED_FGMRES   0     /* flexible GMRES, at most 8 iterations per Newton iteration, right-
                                         preconditioned by one block Gauss-Seidel sweep (potential block, then
-                                        thermal block with the coupling term) whose block solves are Jacobi-PCG
-                                        solves of the split systems to a relative residual of 0.1 (default)    */
+                                        thermal block with the coupling term) whose block solves are mixed-
+                                        precision Jacobi-PCG solves of the split systems to a relative residual
+                                        of 0.4; forcing terms within [max(tol, 1e-6), 1e-2] (default)           */
 #define RAFEM_COUPLED_BICGSTAB 1     /* BiCGSTAB with 2 x 2 block-Jacobi preconditioning                        */
 
 #define RAFEM_LIFT_SYMMETRIC  0      /* Dirichlet rows and columns of the matrix zeroed, unit diagonal, known

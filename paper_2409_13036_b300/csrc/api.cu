@@ -790,7 +790,8 @@ cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
 // (V, T) -= delta. The inner solves are mixed-precision Jacobi-PCG launches (FP32 iterations, FP64 residual) on
 // the assembled split matrices (A_V with sigma at T^n from the step's staggered start, the constant A_T), each to
 // a relative residual of kFgInnerTol.
-constexpr double kFgInnerTol = 0.1;
+// Looser inner solves trade inner iterations for outer ones: of 0.05 to 0.6, 0.4 was the fastest at 127^3.
+constexpr double kFgInnerTol = 0.4;
 cudaError_t enqueue_newton_fgmres(rafem_ctx* c) {
     cudaStream_t st = c->stream;
     const int N = c->N, n2 = 2 * N, G = c->fg_G;

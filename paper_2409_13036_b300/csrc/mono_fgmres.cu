@@ -1,7 +1,7 @@
 // Newton linear solve of the monolithic step (the 2N x 2N coupled system of Table II) by flexible GMRES, right-
 // preconditioned by one block Gauss-Seidel sweep over the (V, T) blocks whose diagonal-block solves are loose
 // Jacobi-PCG solves of the split systems:
-//   z_V = A_V^-1 r_V   (persistent CG on the assembled potential matrix, relative residual 0.1, from zero)
+//   z_V = A_V^-1 r_V   (persistent CG on the assembled potential matrix, relative residual 0.4, from zero)
 //   z_T = A_T^-1 (r_T - J_TV z_V)
 // A_V (sigma at T^n, from the staggered start of the step) and A_T (constant) stand in for the Jacobian's
 // diagonal blocks, which differ from them only by the step's own temperature change and the Joule term's
@@ -29,10 +29,14 @@ constexpr int kDots = kFgMax + 2;  // at most kFgMax + 1 basis vectors and (w, w
 inline int blocks_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
 // Forcing terms of the inexact Newton iteration (Eisenstat and Walker, "Choosing the forcing terms in an inexact
-// Newton method", SIAM J. Sci. Comput. 17(1), 1996, choice 2 with gamma = 0.9, alpha = 2), within [tol, kEtaMax];
-// the first Newton iteration of a step uses kEta0.
+// Newton method", SIAM J. Sci. Comput. 17(1), 1996, choice 2 with gamma = 0.9, alpha = 2), within
+// [max(tol, kEtaMin), kEtaMax]; the first Newton iteration of a step uses kEta0. The floor kEtaMin: once the
+// Newton iteration converges quadratically, choice 2 asks for reductions far below what the step's stopping test
+// (max |dT| < corrector_tol) needs, and each further decade costs outer iterations while another Newton
+// iteration (a new residual from the exact assembly) costs one assembly.
 constexpr double kEtaGamma = 0.9;
 constexpr double kEta0 = 1e-3;
+constexpr double kEtaMin = 1e-6;
 constexpr double kEtaMax = 1e-2;
 
 __device__ __forceinline__ bool skipped(const FgState* st) { return *(volatile const int*)&st->done != 0; }
@@ -87,7 +91,7 @@ __global__ void k_fg_init(FgState* st, const double* partial, int G, double* new
     *newton_rr = bb;
     FgState s{};
     s.beta = sqrt(bb);
-    s.eta = fmin(fmax(eta, tol), kEtaMax);
+    s.eta = fmin(fmax(eta, fmax(tol, kEtaMin)), kEtaMax);
     s.g[0] = s.beta;
     s.scale = s.beta > 0.0 ? 1.0 / s.beta : 0.0;
     s.status = RAFEM_OK;
