@@ -619,7 +619,7 @@ def measure_adjoint(rafem, torch, mg, args):
     ctx.close()
     ctx = rafem.Context(mesh, tol=1e-13, predictor=0, arith=rafem.RAFEM_ARITH_FP64)
 
-    def fd_at(eps):
+    def fd_at(eps, ctx=ctx):
         # Two forms of the same quotient. "loss difference" subtracts the two losses (each ~1e5, so their
         # difference of ~1e-6 loses everything below the rounding of a 274,625-term FP64 sum, ~1e-10);
         # "field difference" forms L+ - L- = sum_i (T+_i - T-_i)(T+_i + T-_i - 2 T*_i) node by node, which is
@@ -649,6 +649,12 @@ def measure_adjoint(rafem, torch, mg, args):
 
     t3 = time.perf_counter()
     checks = [fd_at(1e-6), fd_at(1e-3)]
+    # the noise floor at eps = 1e-6: the same differences with the forward solved 10x less tightly; an error that
+    # grows with the solver tolerance is the solves' termination noise in T+ - T-, divided by 2h
+    ctx12 = rafem.Context(mesh, tol=1e-12, predictor=0, arith=rafem.RAFEM_ARITH_FP64)
+    noise = fd_at(1e-6, ctx12)
+    noise["forward_tol"] = 1e-12
+    ctx12.close()
     t4 = time.perf_counter()
     ctx.close()
     return {"workload": "64^3 cells (274,625 nodes, 1,572,864 tets), jitter +-10%, tumour-sigma0 target",
@@ -657,7 +663,8 @@ def measure_adjoint(rafem, torch, mg, args):
             "fd_quotient": "(L+ - L-)/(2h) with L+ - L- summed node by node from the two temperature fields",
             "loss": float(loss.item()), "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
             "backward_over_forward": (t2 - t1) / (t1 - t0), "adjoint": adj,
-            "fd_check": {"elements": n_fd, "relative_steps": checks, "seconds": t4 - t3}}
+            "fd_check": {"elements": n_fd, "relative_steps": checks, "forward_tol_1e-12_at_eps_1e-6": noise,
+                         "seconds": t4 - t3}}
 
 
 def measure_accuracy(rafem, torch, mesh, args):
