@@ -102,3 +102,14 @@ def test_dram_fraction_from_traffic(tmp_path, monkeypatch):
     r = bench.roofline(_res(ms=3.0), True, {"hbm_gbs": 6500.0}, "measured")
     assert r["dram_achieved"] == pytest.approx(r["traffic"] / 3.0e-3 / 1e9)
     assert r["dram_frac"] == pytest.approx(0.5 * r["frac"])
+
+
+def test_gmres_fp64_accounting():
+    """GMRES's FP64 work counts its SpMVs and a few operations per row (the Gram-Schmidt runs on the FP32 pipes);
+    the FP64-pipe line divides by 2 FMA/clk/SM x 148 SMs x 2.032 GHz."""
+    import bench
+    N, nnz = 1000, 15000
+    assert bench.alg_fma_gmres(N, nnz, 10, 1) == 10 * (nnz + 5 * N) + (nnz + 2 * N)
+    assert bench.alg_fma_gmres(N, nnz, 10, 0) == bench.alg_fma_gmres(N, nnz, 10, 1)  # at least one cycle
+    line = bench.fp64_pipe_line(148 * 2 * 2.032e9 * 1e-3, 1.0)  # one millisecond at the peak rate
+    assert abs(line["frac"] - 1.0) < 1e-12 and line["bound"] == "alu"
