@@ -161,6 +161,7 @@ struct rafem_ctx {
     double *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr, *fg_partial = nullptr;
     double *fg_rV = nullptr, *fg_rT = nullptr, *fg_zV = nullptr, *fg_zT = nullptr;
     FgState* fg_st = nullptr;
+    int32_t* fg_one = nullptr;  // [1] = 1: the inner solves' starting residual is given (x0 = 0, r0 = b)
     size_t fg_ld = 0;
     int fg_G = 0;
     double *gm_V = nullptr, *gm_w0 = nullptr, *gm_w1 = nullptr, *gm_dinv = nullptr, *gm_partial = nullptr;
@@ -813,6 +814,8 @@ cudaError_t enqueue_newton_fgmres(rafem_ctx* c) {
             SolveArgs a = make_args(c, which, V ? c->fg_rV : c->fg_rT, V ? c->fg_zV : c->fg_zT);
             a.tol = kFgInnerTol;
             a.skip = &fs->done;
+            a.r0 = a.b;  // x0 = 0: the starting residual is the right-hand side (no first SpMV)
+            a.r0_ok = c->fg_one;
             if ((e = launch_krylov(a, c->lanes, c->valsV32 ? RAFEM_PRECISION_MIXED : RAFEM_PRECISION_FP64, false,
                                    c->grid, c->block, st)) != cudaSuccess)
                 return e;
@@ -1595,6 +1598,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
             CK(cudaMalloc(&stp, sizeof(FgState)));
             c->allocs.push_back(stp);
             c->fg_st = static_cast<FgState*>(stp);
+            const int32_t one = 1;
+            CK(dalloc(c, &c->fg_one, 1));
+            CK(cudaMemcpyAsync(c->fg_one, &one, sizeof(one), cudaMemcpyHostToDevice, st));
         }
     }
     if (prm->solver == RAFEM_SOLVER_BICGSTAB) {

@@ -76,16 +76,15 @@ __global__ void __launch_bounds__(kThreads) k_fg_dots(int n2, const double* __re
     }
 }
 
-// sum over the G block partials of quantity q (one thread; fixed order)
-__device__ __forceinline__ double total(const double* partial, int G, int q) {
-    double s = 0.0;
-    for (int b = 0; b < G; ++b) s += partial[(size_t)q * G + b];
-    return s;
-}
-
 // start of a Newton linear solve: beta = ||R|| (partial slot 0 of a dots launch with nv = 0), forcing term, state
 __global__ void k_fg_init(FgState* st, const double* partial, int G, double* newton_rr, double tol) {
-    const double bb = total(partial, G, 0);
+    // one warp: lanes take every 32nd block partial, then a fixed shuffle tree
+    double v = 0.0;
+    for (int b = threadIdx.x; b < G; b += 32) v += partial[b];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x != 0) return;
+    const double bb = v;
     const double prev = *newton_rr;
     const double eta = prev > 0.0 ? kEtaGamma * (bb / prev) : kEta0;  // (||R_k|| / ||R_{k-1}||)^2 = bb / prev
     *newton_rr = bb;
@@ -187,13 +186,25 @@ namespace {
 // Gram-Schmidt coefficients of outer iteration j from a dots launch over V_0..V_j (slot j + 1: (w, w)). Pass 1:
 // h_ij = (w, v_i). Pass 2 (after w -= sum h_ij v_i): the corrections c_i = (w, v_i) are added to h_ij, the new
 // vector's norm is sqrt((w, w) - sum c_i^2), then the Givens rotations, the residual estimate |g_{j+1}| and the
-// stopping test |g_{j+1}| <= eta beta. One thread; every quantity in a fixed order.
+// stopping test |g_{j+1}| <= eta beta. The sums in a fixed order, the rest on one thread.
 __global__ void k_fg_gs(FgState* st, const double* partial, int G, int j, int pass) {
     if (skipped(st)) return;
+    // the j + 2 block-partial sums, one warp per quantity (lanes take every 32nd block, then a fixed shuffle tree)
+    __shared__ double tot[kDots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp <= j + 1) {
+        double v = 0.0;
+        for (int b = lane; b < G; b += 32) v += partial[(size_t)warp * G + b];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double* hj = st->h + (size_t)j * (kFgMax + 1);
     if (pass == 1) {
         for (int i = 0; i <= j; ++i) {
-            const double c = total(partial, G, i);
+            const double c = tot[i];
             st->coef[i] = c;
             hj[i] = c;
         }
@@ -201,12 +212,12 @@ __global__ void k_fg_gs(FgState* st, const double* partial, int G, int j, int pa
     }
     double c2 = 0.0;
     for (int i = 0; i <= j; ++i) {
-        const double c = total(partial, G, i);
+        const double c = tot[i];
         st->coef[i] = c;
         hj[i] += c;
         c2 = fma(c, c, c2);
     }
-    const double ww = total(partial, G, j + 1);
+    const double ww = tot[j + 1];
     const double hn = sqrt(fmax(ww - c2, 0.0));
     if (!isfinite(ww)) {
         st->status = RAFEM_ERR_NONFINITE;
@@ -314,7 +325,7 @@ cudaError_t launch_fg_dots(int n2, const double* w, const double* V, size_t ld, 
 }
 
 cudaError_t launch_fg_init(FgState* st, const double* partial, int G, double* newton_rr, double tol, cudaStream_t s) {
-    k_fg_init<<<1, 1, 0, s>>>(st, partial, G, newton_rr, tol);
+    k_fg_init<<<1, 32, 0, s>>>(st, partial, G, newton_rr, tol);
     return cudaGetLastError();
 }
 
@@ -349,7 +360,7 @@ cudaError_t launch_fg_spmv(int N, const int32_t* sp, const int32_t* sc, const in
 
 cudaError_t launch_fg_gs(FgState* st, const double* partial, int G, int j, int pass, cudaStream_t s) {
     if (j < 0 || j >= kFgMax) return cudaErrorInvalidValue;
-    k_fg_gs<<<1, 1, 0, s>>>(st, partial, G, j, pass);
+    k_fg_gs<<<1, 32 * kDots, 0, s>>>(st, partial, G, j, pass);
     return cudaGetLastError();
 }
 
