@@ -323,7 +323,7 @@ def alg_bytes_bicgstab(N: int, nnz: int, iters: float, col_bytes: int) -> float:
 
 def alg_bytes_gmres(N: int, nnz: int, steps: float, cycles: float, col_bytes: int, m: int = 30) -> float:
     """Algorithmic HBM bytes of one GMRES(m) solve launch (single-pass Gram-Schmidt, the second pass being taken
-    only when the first cancels more than half of the vector's norm): per Arnoldi step j an SpMV ((8 + col_bytes) B
+    only when the first cancels more than 99% of the vector's squared norm, which on these systems never happens): per Arnoldi step j an SpMV ((8 + col_bytes) B
     per stored entry, plus u and dinv gathered and v_j, w written: 32N), the dots pass (w and the j + 1 basis vectors
     read) and the update pass (the j + 1 basis vectors read, w read and written); the last step of a cycle skips the
     update. Per cycle the residual SpMV ((8 + col_bytes) nnz + 24N) and the update of x (k + 2 vectors). j averages

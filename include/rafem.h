@@ -67,7 +67,7 @@ extern "C" {
 
 #define RAFEM_SOLVER_GMRES    2      /* restarted GMRES(m), the paper's iterative method (Sec. III-B): FP64, right
                                         Jacobi, classical Gram-Schmidt (repeated once when the first pass
-                                        cancels more than half of the vector's norm), SELL-32 layout, single
+                                        cancels more than 99% of the vector's squared norm), SELL-32 layout, single
                                         instance; m = gmres_restart, adaptive between gmres_min_restart and m
                                         when that is set; two full-length cycles in a row that each reduce the
                                         residual by less than 0.1% (stagnation) end the solve NOT_CONVERGED   */
