@@ -825,11 +825,14 @@ cudaError_t enqueue_newton_fgmres(rafem_ctx* c) {
         if ((e = launch_fg_spmv(N, c->rp, c->ci, c->ci16, c->m_vals4, c->fg_zV, c->fg_zT, c->fg_w, Zj, fs, st)) !=
             cudaSuccess)
             return e;
+        // Gram-Schmidt: the second pass's launches return at once when the first pass was enough
         for (int pass = 1; pass <= 2; ++pass) {
-            if ((e = launch_fg_dots(n2, c->fg_w, c->fg_V, ld, j + 1, fs, c->fg_partial, G, st)) != cudaSuccess) return e;
+            if ((e = launch_fg_dots(n2, c->fg_w, c->fg_V, ld, j + 1, fs, c->fg_partial, G, st, pass)) != cudaSuccess)
+                return e;
             if ((e = launch_fg_gs(fs, c->fg_partial, G, j, pass, st)) != cudaSuccess) return e;
-            double* next = pass == 2 ? c->fg_V + (size_t)(j + 1) * ld : nullptr;
-            if ((e = launch_fg_sub(n2, c->fg_w, c->fg_V, ld, j, fs, next, st)) != cudaSuccess) return e;
+            if ((e = launch_fg_sub(n2, c->fg_w, c->fg_V, ld, j, fs, c->fg_V + (size_t)(j + 1) * ld, pass, st)) !=
+                cudaSuccess)
+                return e;
         }
     }
     if ((e = launch_fg_finish(n2, c->fg_Z, ld, fs, c->m_D, c->instV, c->instT, st)) != cudaSuccess) return e;

@@ -422,6 +422,8 @@ struct FgState {
     int32_t outer;                    // outer iterations taken
     int32_t status;                   // worst status of the inner solves (or RAFEM_ERR_NONFINITE)
     int32_t itV, itT;                 // inner Krylov iterations of the two systems
+    int32_t single;                   // 1: the current column needed one Gram-Schmidt pass (the second is skipped)
+    int32_t pad;
     double beta, eta, scale, ww;      // ||R||; forcing (relative); 1 / norm of the next basis vector; (w, w)
     double h[(kFgMax + 1) * kFgMax];  // Hessenberg, column j at h + j (kFgMax + 1), Givens-rotated
     double g[kFgMax + 1], cs[kFgMax], sn[kFgMax], y[kFgMax];
@@ -429,7 +431,7 @@ struct FgState {
 };
 // 2N-vector kernels of the solve: n2 = 2 N interleaved (V, T) entries; ld the stride of the basis arrays.
 cudaError_t launch_fg_dots(int n2, const double* w, const double* V, size_t ld, int nv, const FgState* st,
-                           double* partial, int G, cudaStream_t s);
+                           double* partial, int G, cudaStream_t s, int pass = 1);
 cudaError_t launch_fg_init(FgState* st, const double* partial, int G, double* newton_rr, double tol, cudaStream_t s);
 cudaError_t launch_fg_scale(int n2, const double* src, double* dst, const FgState* st, cudaStream_t s);
 cudaError_t launch_fg_split(int N, const double* v, double* rV, double* rT, double* zV, double* zT,
@@ -442,7 +444,7 @@ cudaError_t launch_fg_spmv(int N, const int32_t* sp, const int32_t* sc, const in
                            cudaStream_t s);
 cudaError_t launch_fg_gs(FgState* st, const double* partial, int G, int j, int pass, cudaStream_t s);
 cudaError_t launch_fg_sub(int n2, double* w, const double* V, size_t ld, int j, const FgState* st, double* next,
-                          cudaStream_t s);
+                          int pass, cudaStream_t s);
 cudaError_t launch_fg_finish(int n2, const double* Z, size_t ld, FgState* st, double* delta, InstState* instV,
                              InstState* instT, cudaStream_t s);
 int fg_grid();

@@ -10,9 +10,9 @@
 // Sci. Comput. 14(2), 1993): the preconditioned vectors z_j are kept and the correction is sum_j y_j z_j. Each outer
 // iteration is a fixed sequence of launches; once the state's done flag is set (converged to the Newton forcing
 // term, out of iterations, or broken down) every later kernel and inner solve returns at once, so the sequence can
-// sit in the step's captured graph without a conditional node. Gram-Schmidt is classical with a second pass
-// (CGS2), the norm from the second pass's Pythagorean identity. Reductions are two-pass and in a fixed order:
-// repeated runs give the same bits.
+// sit in the step's captured graph without a conditional node. Gram-Schmidt is classical, with a second pass only
+// when the first keeps less than 1% of (w, w), the norm from the Pythagorean identity of the last pass. Reductions
+// are two-pass and in a fixed order: repeated runs give the same bits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,8 +44,8 @@ __device__ __forceinline__ bool skipped(const FgState* st) { return *(volatile c
 // partial[q][block] = sum over the block's entries of w * V_q (q < nv) and w * w (q = nv); fixed order
 __global__ void __launch_bounds__(kThreads) k_fg_dots(int n2, const double* __restrict__ w,
                                                       const double* __restrict__ V, size_t ld, int nv,
-                                                      const FgState* st, double* __restrict__ partial) {
-    if (skipped(st)) return;
+                                                      const FgState* st, double* __restrict__ partial, int pass) {
+    if (skipped(st) || (pass == 2 && st->single)) return;
     __shared__ double sm[kDots][kThreads / 32];
     double acc[kDots];
 #pragma unroll
@@ -183,48 +183,9 @@ __global__ void __launch_bounds__(kThreads) k_fg_spmv(int N, const int32_t* __re
 
 namespace {
 
-// Gram-Schmidt coefficients of outer iteration j from a dots launch over V_0..V_j (slot j + 1: (w, w)). Pass 1:
-// h_ij = (w, v_i). Pass 2 (after w -= sum h_ij v_i): the corrections c_i = (w, v_i) are added to h_ij, the new
-// vector's norm is sqrt((w, w) - sum c_i^2), then the Givens rotations, the residual estimate |g_{j+1}| and the
-// stopping test |g_{j+1}| <= eta beta. The sums in a fixed order, the rest on one thread.
-__global__ void k_fg_gs(FgState* st, const double* partial, int G, int j, int pass) {
-    if (skipped(st)) return;
-    // the j + 2 block-partial sums, one warp per quantity (lanes take every 32nd block, then a fixed shuffle tree)
-    __shared__ double tot[kDots];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp <= j + 1) {
-        double v = 0.0;
-        for (int b = lane; b < G; b += 32) v += partial[(size_t)warp * G + b];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) tot[warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double* hj = st->h + (size_t)j * (kFgMax + 1);
-    if (pass == 1) {
-        for (int i = 0; i <= j; ++i) {
-            const double c = tot[i];
-            st->coef[i] = c;
-            hj[i] = c;
-        }
-        return;
-    }
-    double c2 = 0.0;
-    for (int i = 0; i <= j; ++i) {
-        const double c = tot[i];
-        st->coef[i] = c;
-        hj[i] += c;
-        c2 = fma(c, c, c2);
-    }
-    const double ww = tot[j + 1];
-    const double hn = sqrt(fmax(ww - c2, 0.0));
-    if (!isfinite(ww)) {
-        st->status = RAFEM_ERR_NONFINITE;
-        st->done = 1;
-        st->k = 0;
-        return;
-    }
+// Givens rotations on column j (its new subdiagonal entry hn), the residual estimate |g_{j+1}| and the stopping
+// test |g_{j+1}| <= eta beta (one thread)
+__device__ void finish_column(FgState* st, double* hj, int j, double hn) {
     for (int i = 0; i < j; ++i) {
         const double t = st->cs[i] * hj[i] + st->sn[i] * hj[i + 1];
         hj[i + 1] = -st->sn[i] * hj[i] + st->cs[i] * hj[i + 1];
@@ -248,11 +209,57 @@ __global__ void k_fg_gs(FgState* st, const double* partial, int G, int j, int pa
     }
 }
 
-// w -= sum_{i <= j} coef_i V_i; with next, the result scaled by 1 / its norm goes to next (the basis vector j + 1)
-// and w is left as it was
+// Gram-Schmidt coefficients of outer iteration j from a dots launch over V_0..V_j (slot j + 1: (w, w)). Pass 1:
+// h_ij = (w, v_i); when (w, w) - sum h_ij^2 keeps at least kReorth of (w, w) that is the new vector's squared
+// norm and the column is finished (single pass). Otherwise pass 2 (after w -= sum h_ij v_i): the corrections
+// c_i = (w, v_i) are added to h_ij and the norm is sqrt((w, w) - sum c_i^2). The sums in a fixed order, the rest
+// on one thread.
+constexpr double kReorth = 0.01;
+__global__ void k_fg_gs(FgState* st, const double* partial, int G, int j, int pass) {
+    if (skipped(st) || (pass == 2 && st->single)) return;
+    // the j + 2 block-partial sums, one warp per quantity (lanes take every 32nd block, then a fixed shuffle tree)
+    __shared__ double tot[kDots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp <= j + 1) {
+        double v = 0.0;
+        for (int b = lane; b < G; b += 32) v += partial[(size_t)warp * G + b];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double* hj = st->h + (size_t)j * (kFgMax + 1);
+    const double ww = tot[j + 1];
+    if (!isfinite(ww)) {
+        st->status = RAFEM_ERR_NONFINITE;
+        st->done = 1;
+        st->k = 0;
+        return;
+    }
+    double c2 = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        const double c = tot[i];
+        st->coef[i] = c;
+        hj[i] = pass == 1 ? c : hj[i] + c;
+        c2 = fma(c, c, c2);
+    }
+    const double nh2 = ww - c2;
+    if (pass == 1) {
+        st->single = nh2 >= kReorth * ww;
+        if (!st->single) return;
+    }
+    finish_column(st, hj, j, sqrt(fmax(nh2, 0.0)));
+}
+
+// w -= sum_{i <= j} coef_i V_i. The result scaled by 1 / its norm goes to next (the basis vector j + 1) after the
+// column's last pass (pass 1 when it was the only one, else pass 2); after a first pass that needs a second, w is
+// updated in place.
 __global__ void __launch_bounds__(kThreads) k_fg_sub(int n2, double* __restrict__ w, const double* __restrict__ V,
-                                                     size_t ld, int j, const FgState* st, double* __restrict__ next) {
-    if (skipped(st)) return;
+                                                     size_t ld, int j, const FgState* st, double* __restrict__ next,
+                                                     int pass) {
+    if (skipped(st) || (pass == 2 && st->single)) return;
+    const bool last = pass == 2 || st->single;
     double c[kFgMax + 1];
 #pragma unroll
     for (int i = 0; i <= kFgMax; ++i) c[i] = i <= j ? st->coef[i] : 0.0;
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_fg_sub(int n2, double* __restrict_
 #pragma unroll
         for (int i = 0; i <= kFgMax; ++i)
             if (i <= j) v = fma(-c[i], V[i * ld + k], v);
-        if (next)
+        if (last)
             next[k] = v * sc;
         else
             w[k] = v;
@@ -318,9 +325,9 @@ int fg_grid() {
 }
 
 cudaError_t launch_fg_dots(int n2, const double* w, const double* V, size_t ld, int nv, const FgState* st,
-                           double* partial, int G, cudaStream_t s) {
+                           double* partial, int G, cudaStream_t s, int pass) {
     if (nv < 0 || nv > kFgMax + 1) return cudaErrorInvalidValue;
-    k_fg_dots<<<G, kThreads, 0, s>>>(n2, w, V, ld, nv, st, partial);
+    k_fg_dots<<<G, kThreads, 0, s>>>(n2, w, V, ld, nv, st, partial, pass);
     return cudaGetLastError();
 }
 
@@ -365,9 +372,9 @@ cudaError_t launch_fg_gs(FgState* st, const double* partial, int G, int j, int p
 }
 
 cudaError_t launch_fg_sub(int n2, double* w, const double* V, size_t ld, int j, const FgState* st, double* next,
-                          cudaStream_t s) {
-    if (j < 0 || j >= kFgMax) return cudaErrorInvalidValue;
-    k_fg_sub<<<fg_grid(), kThreads, 0, s>>>(n2, w, V, ld, j, st, next);
+                          int pass, cudaStream_t s) {
+    if (j < 0 || j >= kFgMax || !next) return cudaErrorInvalidValue;
+    k_fg_sub<<<fg_grid(), kThreads, 0, s>>>(n2, w, V, ld, j, st, next, pass);
     return cudaGetLastError();
 }
 
