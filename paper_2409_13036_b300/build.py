@@ -23,7 +23,7 @@ OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O2", "-I" + INCLUDE,
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
-SOURCES = ["api.cu", "adjoint.cu", "assembly.cu", "assembly_dw.cu", "bicgstab.cu", "bicgstab_ring.cu", "gmres.cu", "ilu.cu", "ilu_ring.cu", "krylov.cu", "mono_fgmres.cu", "noalloc.cu", "project.cu", "setup.cpp"]
+SOURCES = ["api.cu", "adjoint.cu", "assembly.cu", "assembly_dw.cu", "bicgstab.cu", "bicgstab_ring.cu", "gmres.cu", "ilu.cu", "ilu_ring.cu", "krylov.cu", "mono_fgmres.cu", "coupled_gather.cu", "noalloc.cu", "project.cu", "setup.cpp"]
 
 
 def nvcc() -> str:

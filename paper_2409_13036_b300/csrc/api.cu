@@ -109,6 +109,7 @@ struct rafem_ctx {
     GatherData gd;
     bool dw = false;  // double-word element and node passes (RAFEM_ARITH_DW resolved at create)
     GatherDw gdw;
+    CoupledGather mg;  // coupled Jacobian by rows (monolithic contexts with the gather assembly)
     uint8_t* gather_cg = nullptr;
     long long gather_nc = 0;
     // graph
@@ -786,6 +787,27 @@ cudaError_t enqueue_corr_prologue(rafem_ctx* c) {
     return enqueue_solve(c, RAFEM_SYS_T, c->bT, c->T);
 }
 
+// The coupled Jacobian (2 x 2 blocks on the node pattern) and residual at the current (V, T): by rows on the
+// gather lists when the context has them, else by the colour scatter followed by the Dirichlet rows.
+cudaError_t enqueue_coupled_assembly(rafem_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int N = c->N;
+    const double c_dt = c->prm.rho_c / c->prm.dt;
+    if (c->mg.cab)
+        return launch_coupled_gather(c->mg, c->gd, N, c->rp, c->diag, c->el, c->V, c->T, c->T_old, c->prm.alpha_sigma,
+                                     c_dt, c->prm.perf, c->prm.T_a, c->bcV, c->bcT, c->gV, c->gT, c->m_vals4, c->m_R,
+                                     st);
+    cudaError_t e = cudaMemsetAsync(c->m_R, 0, 2 * (size_t)N * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    for (int q = 0; q < c->n_colors; ++q) {
+        e = launch_coupled(c->el, c->color_off[q], c->color_off[q + 1], c->e_clist, c->V, c->T, c->T_old,
+                           c->prm.alpha_sigma, c_dt, c->prm.perf, c->prm.T_a, c->m_vals4, c->m_R, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_coupled_dirichlet(N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
+                                    c->m_vals4, c->m_R, st);
+}
+
 // The Newton linear solve J delta = R by flexible GMRES with the split-system preconditioner (mono_fgmres.cu): a
 // fixed sequence of kFgMax outer iterations whose launches return at once after convergence, then delta and
 // (V, T) -= delta. The inner solves are mixed-precision Jacobi-PCG launches (FP32 iterations, FP64 residual) on
@@ -847,16 +869,7 @@ cudaError_t enqueue_newton_fgmres(rafem_ctx* c) {
 cudaError_t enqueue_newton(rafem_ctx* c) {
     cudaStream_t st = c->stream;
     const int N = c->N;
-    cudaError_t e = cudaMemsetAsync(c->m_R, 0, 2 * (size_t)N * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    for (int q = 0; q < c->n_colors; ++q) {
-        e = launch_coupled(c->el, c->color_off[q], c->color_off[q + 1], c->e_clist, c->V, c->T, c->T_old,
-                           c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->prm.perf, c->prm.T_a, c->m_vals4, c->m_R,
-                           st);
-        if (e != cudaSuccess) return e;
-    }
-    e = launch_coupled_dirichlet(N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
-                                 c->m_vals4, c->m_R, st);
+    cudaError_t e = enqueue_coupled_assembly(c);
     if (e != cudaSuccess) return e;
     if (c->fg_st) return enqueue_newton_fgmres(c);
     if ((e = cudaMemsetAsync(c->m_D, 0, 2 * (size_t)N * sizeof(double), st)) != cudaSuccess) return e;
@@ -1328,7 +1341,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
     std::vector<int32_t> dev_rp, dev_ci;
     std::vector<int16_t> d16;
     std::vector<int32_t> g_off, g_cnt, g_elem, i_off, i_cnt, i_elem;
-    std::vector<uint8_t> g_idx;
+    std::vector<uint8_t> g_idx, g_cab;
     std::vector<int32_t> pat_off, pat_pool;
     bool patterns = false;
     if (c->sell) {
@@ -1336,7 +1349,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         // one column pattern per slice where that widens no slice (lattice-like numberings), else per-entry columns
         patterns = build_sell_patterns(N, rp, col, dev_rp, dev_ci, map, pat_off, pat_pool);
         if (!patterns) build_sell(N, rp, col, dev_rp, dev_ci, map);
-        if (c->gather) build_gather(N, E, rp, col, slots, dev_rp, map, g_off, g_cnt, g_elem, g_idx);
+        if (c->gather)
+            build_gather(N, E, rp, col, slots, dev_rp, map, g_off, g_cnt, g_elem, g_idx,
+                         prm->coupling == RAFEM_COUPLING_MONOLITHIC ? &g_cab : nullptr);
         if (want16) {
             bool fits = true;
             d16.resize(dev_ci.size());
@@ -1539,6 +1554,14 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
         c->gd.mT = mT;
         c->gather_cg = cg;
         c->gather_nc = (long long)g_elem.size();
+        if (!g_cab.empty()) {
+            CK(dalloc(c, &c->mg.cab, g_cab.size()));
+            CK(dalloc(c, &c->mg.Gc, g_cab.size()));
+            CK(dalloc(c, &c->mg.tc, (size_t)dev_rp.back()));
+            CK(dalloc(c, &c->mg.q, 8 * (size_t)E));
+            CK(dalloc(c, &c->mg.rt, 4 * (size_t)E));
+            CK(cudaMemcpyAsync(c->mg.cab, g_cab.data(), g_cab.size(), cudaMemcpyHostToDevice, st));
+        }
     }
     c->el.E = E;
     c->el.nodes = c->e_nodes;
@@ -1712,6 +1735,9 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
                             st));
         CK(launch_node_mass(c->gd, N, c->e_vol, prm->rho_c / prm->dt, st));
     }
+    if (c->mg.cab)
+        CK(launch_coupled_fill(c->mg, c->gd, c->gather_nc, N, c->rp, c->diag, c->el, prm->rho_c / prm->dt + prm->perf,
+                               true, st));
     CK(launch_set_dirichlet_identity(N, c->bcV, c->diag, c->valsV, c->valsV32, st));
     CK(launch_set_dirichlet_identity(N, c->bcT, c->diag, c->valsT, c->valsT32, st));
     const double c_matrix = prm->rho_c / prm->dt + prm->perf;
@@ -2147,6 +2173,7 @@ int set_params_impl(rafem_ctx* c, const void* sigma0, const void* k, int kind) {
             CK(launch_assemble_T(c->el, c->color_off[q], c->color_off[q + 1], c->bcT, c->gT, c_matrix,
                                  c->prm.perf * c->prm.T_a, c->valsT, c->valsT32, c->bTc, c->prm.lift, c->e_clist, st));
         if (c->ilu) CK(ilu_refactor(c, RAFEM_SYS_T, st));
+        if (c->mg.cab) CK(launch_coupled_fill(c->mg, c->gd, c->gather_nc, c->N, c->rp, c->diag, c->el, c_matrix, false, st));
     }
     CK(cudaStreamSynchronize(st));
     return RAFEM_OK;
@@ -2219,6 +2246,7 @@ int apply_dt(rafem_ctx* c, double dt) {
     if (c->ilu) CK(ilu_refactor(c, RAFEM_SYS_T, st));
     if (c->gd.mT) CK(launch_node_mass(c->gd, c->N, c->e_vol, c->prm.rho_c / dt, st));
     if (c->dw) CK(launch_fill_dw(c->gdw, 0, nullptr, nullptr, c->el, c->prm.rho_c / dt, st));
+    if (c->mg.cab) CK(launch_coupled_fill(c->mg, c->gd, c->gather_nc, c->N, c->rp, c->diag, c->el, c_matrix, false, st));
     drop_graphs(c);
     return RAFEM_OK;
 }
@@ -2554,13 +2582,7 @@ int rafem_get_coupled_system(rafem_ctx* c, double* blocks, double* residual) {
     if (!c || !c->mono) return RAFEM_ERR_BAD_INPUT;
     CK(cudaMemcpyAsync(c->T_old, c->T, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     cudaStream_t st = c->stream;
-    CK(cudaMemsetAsync(c->m_R, 0, 2 * (size_t)c->N * sizeof(double), st));
-    for (int q = 0; q < c->n_colors; ++q)
-        CK(launch_coupled(c->el, c->color_off[q], c->color_off[q + 1], c->e_clist, c->V, c->T, c->T_old,
-                          c->prm.alpha_sigma, c->prm.rho_c / c->prm.dt, c->prm.perf, c->prm.T_a, c->m_vals4, c->m_R,
-                          st));
-    CK(launch_coupled_dirichlet(c->N, c->sell ? 1 : 0, c->rp, c->diag, c->bcV, c->bcT, c->gV, c->gT, c->V, c->T,
-                                c->m_vals4, c->m_R, st));
+    CK(enqueue_coupled_assembly(c));
     std::vector<double> v4(4 * (size_t)c->nnz_store);
     CK(cudaMemcpyAsync(v4.data(), c->m_vals4, v4.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (residual) CK(cudaMemcpyAsync(residual, c->m_R, 2 * (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost, st));

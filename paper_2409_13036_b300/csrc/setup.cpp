@@ -261,7 +261,8 @@ int local_gidx(int a, int b) {
 void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                   const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
                   const std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& gather_off,
-                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx) {
+                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx,
+                  std::vector<uint8_t>* cab) {
     (void)row_ptr;
     (void)N;
     const int64_t nnz = (int64_t)col.size();
@@ -298,6 +299,7 @@ void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::
     }
     celem.assign(total, 0);
     cgidx.assign(total, 255);
+    if (cab) cab->assign(total, 255);
     std::vector<int32_t> fill(nnz, 0);
     for (int64_t ep = 0; ep < E; ++ep)
         for (int a = 0; a < 4; ++a)
@@ -307,6 +309,7 @@ void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::
                 const int64_t at = pos[p] + (int64_t)SELL_C * fill[p]++;
                 celem[at] = (int32_t)ep;
                 cgidx[at] = (uint8_t)local_gidx(a, b);
+                if (cab) (*cab)[at] = (uint8_t)(4 * a + b);
             }
 }
 

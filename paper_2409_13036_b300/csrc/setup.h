@@ -50,10 +50,13 @@ bool build_sell_patterns(int N, const std::vector<int32_t>& row_ptr, const std::
 // list among its 32 rows: contribution m of lane l of group q lives at gather_off[q] + 32 m + l, and the group has
 // gather_cnt[q] contributions (0 for groups holding only diagonal or padding entries). Padding contributions
 // carry gidx = 255. csr_slots are the element->CSR slot codes (flags allowed) over the sorted element order.
+// With cab non-null it also receives, per contribution, the local vertices of the row (a) and of the column (b) as
+// 4 a + b (255 for padding), which the coupled Jacobian needs because its blocks are not symmetric in (a, b).
 void build_gather(int N, int E, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
                   const std::vector<int32_t>& csr_slots, const std::vector<int32_t>& slice_ptr,
                   const std::vector<int32_t>& csr_to_sell, std::vector<int32_t>& gather_off,
-                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx);
+                  std::vector<int32_t>& gather_cnt, std::vector<int32_t>& celem, std::vector<uint8_t>& cgidx,
+                  std::vector<uint8_t>* cab = nullptr);
 
 // Node -> element incidence (sorted element order) in the SELL-32 slice layout: entry m of row 32 s + l at
 // inc_off[s] + 32 m + l for m < inc_cnt[s] holds 4 e + a (element e, local vertex a); -1 marks padding.

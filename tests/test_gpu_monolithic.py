@@ -49,6 +49,35 @@ def test_coupled_jacobian_and_residual_match_oracle(assembly):
     np.testing.assert_allclose(res.ravel(), Rref, rtol=1e-11, atol=1e-12 * np.abs(Rref).max())
 
 
+@pytest.mark.parametrize("assembly", [0, 1], ids=["gather", "colour"])
+def test_coupled_system_after_k_and_dt_change(assembly):
+    """The coupled Jacobian and residual after rafem_set_params (new thermal conductivities) and rafem_set_dt: the
+    constant thermal block (k G + (rho_c/dt + perf) M) follows both changes, entry by entry against the oracle."""
+    import dataclasses
+    rafem = R()
+    m = mg.cube_mesh(7, jitter=0.1, seed=85, sigma0="lognormal", V_electrode=30.0)
+    rng = np.random.default_rng(2)
+    V = np.where(m.bc_V.astype(bool), m.g_V, 15.0 * rng.random(m.n_nodes))
+    T = np.where(m.bc_T.astype(bool), m.g_T, 37.0 + 10.0 * rng.random(m.n_nodes))
+    k2 = m.k * (0.5 + rng.random(m.n_tets))
+    m2 = dataclasses.replace(m, k=k2)
+    model = O.Model(m2, O.Params(dt=12.0))
+    with rafem.Context(m, dt=30.0, coupling=1, assembly=assembly) as ctx:
+        ctx.set_params(k=k2)
+        ctx.set_dt(12.0)
+        ctx.set_state(T=T, V=V)
+        blocks, res = ctx.get_coupled_system()
+        rp, col, _, _ = ctx.get_system(rafem.RAFEM_SYS_V)
+    J = O.coupled_jacobian(model, V, T).tocsr()
+    Rref = O.coupled_residual(model, V, T, T)
+    rows = np.repeat(np.arange(m.n_nodes), np.diff(rp))
+    for a in range(2):
+        for b in range(2):
+            ref = np.asarray(J[2 * rows + a, 2 * col + b]).ravel()
+            np.testing.assert_allclose(blocks[:, a, b], ref, rtol=1e-12, atol=1e-13 * np.abs(J.data).max())
+    np.testing.assert_allclose(res.ravel(), Rref, rtol=1e-11, atol=1e-12 * np.abs(Rref).max())
+
+
 @pytest.mark.parametrize("solver", [0, 1], ids=["fgmres", "bicgstab"])
 def test_monolithic_steps_match_oracle_fixed_point(solver):
     """Two monolithic steps (dt = 30 s, 40 V, Newton to max |dT| < 1e-9) agree with the oracle's Newton step and
