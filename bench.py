@@ -781,8 +781,9 @@ def measure_monolithic(rafem, torch, mesh, args):
     """The paper's 2N x 2N system shape: V and T of each step solved together by Newton's method (corrector_tol
     1e-6 degC on max |dT|, at most 20 iterations, inexact linear solves) on the 127^3 workload, with each Newton
     linear solver: flexible GMRES preconditioned by split-system solves (the default) and block-Jacobi BiCGSTAB.
-    K steps after W warm-up, CUDA events on the context's stream. Reported beside the staggered (lagged) step; the
-    two compute different time discretisations (implicit vs lagged coupling)."""
+    K steps after W warm-up, CUDA events on the context's stream, then (flexible GMRES) one untimed step as direct
+    launches for per-kernel profilers. Reported beside the staggered (lagged) step; the two compute different time
+    discretisations (implicit vs lagged coupling)."""
     out = {"steps": args.monolithic_steps}
     for name, solver in (("fgmres_split_precond", rafem.RAFEM_COUPLED_FGMRES),
                          ("bicgstab_block_jacobi", rafem.RAFEM_COUPLED_BICGSTAB)):
@@ -804,6 +805,12 @@ def measure_monolithic(rafem, torch, mesh, args):
         if solver == rafem.RAFEM_COUPLED_FGMRES:
             r.update({"outer_iterations_last_step": st.refine_V, "inner_potential_cg_iterations_last_step": st.iters_V,
                       "inner_thermal_cg_iterations_last_step": st.iters_T})
+            # one more step as direct launches (untimed): per-kernel profilers list these one by one
+            ctx.set_tracing(True)
+            s2, st2 = ctx.run(1)
+            ctx.set_tracing(False)
+            r["traced_step"] = {"newton_iterations": st2.correctors, "outer_iterations": st2.refine_V,
+                                "status": rafem.status_string(s2)}
         else:
             r["bicgstab_iterations_last_step"] = st.iters_V
         out[name] = r

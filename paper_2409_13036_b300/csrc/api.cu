@@ -794,7 +794,7 @@ cudaError_t enqueue_coupled_assembly(rafem_ctx* c) {
     const int N = c->N;
     const double c_dt = c->prm.rho_c / c->prm.dt;
     if (c->mg.cab)
-        return launch_coupled_gather(c->mg, c->gd, N, c->rp, c->diag, c->el, c->V, c->T, c->T_old, c->prm.alpha_sigma,
+        return launch_coupled_gather(c->mg, c->gd, N, c->rp, c->ci, c->diag, c->el, c->V, c->T, c->T_old, c->prm.alpha_sigma,
                                      c_dt, c->prm.perf, c->prm.T_a, c->bcV, c->bcT, c->gV, c->gT, c->m_vals4, c->m_R,
                                      st);
     cudaError_t e = cudaMemsetAsync(c->m_R, 0, 2 * (size_t)N * sizeof(double), st);
@@ -1558,7 +1558,7 @@ static int create_impl(const rafem_mesh* m, const rafem_params* prm, void* strea
             CK(dalloc(c, &c->mg.cab, g_cab.size()));
             CK(dalloc(c, &c->mg.Gc, g_cab.size()));
             CK(dalloc(c, &c->mg.tc, (size_t)dev_rp.back()));
-            CK(dalloc(c, &c->mg.q, 8 * (size_t)E));
+            CK(dalloc(c, &c->mg.rec, 4 * (size_t)E));
             CK(dalloc(c, &c->mg.rt, 4 * (size_t)E));
             CK(cudaMemcpyAsync(c->mg.cab, g_cab.data(), g_cab.size(), cudaMemcpyHostToDevice, st));
         }

@@ -109,15 +109,15 @@ struct CoupledGather {
     uint8_t* cab = nullptr;  // per contribution: 4 a + b (row vertex a, column vertex b of the element), 255 padding
     double* Gc = nullptr;    // per contribution: G_e[a][b] (0 for padding)
     double* tc = nullptr;    // [nnz_store] constant thermal block, unlifted: k G + (rho_c/dt + perf) M
-    double2* q = nullptr;    // [4 E][2] per (element, vertex a): {ds (G V)_a, -sigma (G V)_a / 2}, {sigma, -ds quad / 4}
-    double* rt = nullptr;    // [4 E] thermal residual contribution per (element, vertex)
+    double2* rec = nullptr;  // [E][4] per element: {sigma, ds}, {-ds quad / 4, 0}, {(G V)_0, (G V)_1}, {(G V)_2, (G V)_3}
+    double* rt = nullptr;    // [4 E] thermal residual contribution per (element, vertex), less tc T
 };
 // Gc (when geometry is set: once per context) and tc (again whenever k or rho_c/dt + perf = cm changes).
 cudaError_t launch_coupled_fill(const CoupledGather& cg, const GatherData& gd, long long nc, int N, const int32_t* sp,
                                 const int32_t* diag, const ElemData& el, double cm, bool geometry, cudaStream_t st);
 // Every entry of vals4 (padding as zero) and of R is written: no clearing needed.
 cudaError_t launch_coupled_gather(const CoupledGather& cg, const GatherData& gd, int N, const int32_t* sp,
-                                  const int32_t* diag, const ElemData& el, const double* V, const double* T,
+                                  const int32_t* sc, const int32_t* diag, const ElemData& el, const double* V, const double* T,
                                   const double* T_old, double alpha, double c_dt, double perf, double T_a,
                                   const uint8_t* bcV, const uint8_t* bcT, const double* gV, const double* gT,
                                   double* vals4, double* R, cudaStream_t st);
