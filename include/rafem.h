@@ -356,9 +356,8 @@ int rafem_get_trace(rafem_ctx* ctx, rafem_trace* out);
  *     start at zero itself. Calls whose GPU work overlaps in time (different streams, or different host threads
  *     on the same device) race on the array and give wrong results: serialise them.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that device
- *     current) and keeps it for the life of the process; that first call should come before any stream capture
- *     begins. After cudaDeviceReset the kept address is stale: do not call this entry point on a device after
- *     resetting it.
+ *     current) and keeps it for the life of the process. After cudaDeviceReset the kept address is stale: do not
+ *     call this entry point on a device after resetting it.
  * The call is synchronous: it waits on the stream twice (after the input check, and after the solve) and reads
  * the check's result and the solver's statistics back into host memory before it returns.
  * Arguments (device pointers unless stated): row_ptr [n_rows+1] and col [row_ptr[n_rows]] int32 CSR pattern,
