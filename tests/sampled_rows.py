@@ -63,3 +63,36 @@ def rows_adjacent_to(mesh, nodes):
     """All nodes sharing an element with any of `nodes` (including them)."""
     els = elements_touching(mesh.tets, nodes)
     return np.unique(np.asarray(mesh.tets)[els].ravel())
+
+
+def coupled_rows(mesh, rows, V, T, params=None):
+    """Rows of the monolithic Newton system (the oracle's coupled_jacobian and coupled_residual with T_old = T)
+    for the sampled nodes, from the oracle applied to the sub-mesh of the elements that touch them: a node's rows
+    depend only on its incident elements, its own boundary flags and the fields at their vertices.
+    Returns (rows, {row: {(a, col, b): value}}, {row: (R_V, R_T)}) with a, b in {0: V, 1: T}."""
+    import types
+    rows = np.unique(np.asarray(rows, dtype=np.int64))
+    els = elements_touching(mesh.tets, rows)
+    tets = np.asarray(mesh.tets, dtype=np.int64)[els]
+    nodes = np.unique(tets.ravel())
+    local = {int(n): k for k, n in enumerate(nodes)}
+    sub = types.SimpleNamespace(
+        coords=np.asarray(mesh.coords)[nodes], tets=np.searchsorted(nodes, tets),
+        bc_V=np.asarray(mesh.bc_V)[nodes], g_V=np.asarray(mesh.g_V)[nodes],
+        bc_T=np.asarray(mesh.bc_T)[nodes], g_T=np.asarray(mesh.g_T)[nodes],
+        sigma0=np.asarray(mesh.sigma0)[els], k=np.asarray(mesh.k)[els])
+    model = O.Model(sub, params or O.Params())
+    Vs, Ts = np.asarray(V, dtype=np.float64)[nodes], np.asarray(T, dtype=np.float64)[nodes]
+    J = O.coupled_jacobian(model, Vs, Ts).tocsr()
+    R = O.coupled_residual(model, Vs, Ts, Ts)
+    out, res = {}, {}
+    for i in rows:
+        li = local[int(i)]
+        ent = {}
+        for a in range(2):
+            lo, hi = J.indptr[2 * li + a], J.indptr[2 * li + a + 1]
+            for c, v in zip(J.indices[lo:hi], J.data[lo:hi]):
+                ent[(a, int(nodes[c // 2]), int(c % 2))] = float(v)
+        out[int(i)] = ent
+        res[int(i)] = (float(R[2 * li]), float(R[2 * li + 1]))
+    return rows, out, res

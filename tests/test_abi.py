@@ -75,6 +75,31 @@ def test_sampled_rows_helper_matches_full_oracle():
             np.testing.assert_allclose(got, A.data[lo:hi], rtol=1e-12, atol=1e-14 * np.abs(A.data).max())
 
 
+def test_coupled_rows_helper_matches_full_oracle():
+    """The sub-mesh rows of the monolithic system (tests/sampled_rows.coupled_rows) equal the rows of the oracle's
+    coupled_jacobian and coupled_residual on the whole mesh, Dirichlet rows of both fields included."""
+    from tests.sampled_rows import coupled_rows
+    m = mg.cube_mesh(7, jitter=0.1, seed=85, sigma0="lognormal", V_electrode=30.0)
+    rng = np.random.default_rng(2)
+    V = np.where(m.bc_V.astype(bool), m.g_V, 15.0 * rng.random(m.n_nodes))
+    T = np.where(m.bc_T.astype(bool), m.g_T, 37.0 + 10.0 * rng.random(m.n_nodes))
+    model = O.Model(m)
+    J = O.coupled_jacobian(model, V, T).tocsr()
+    R = O.coupled_residual(model, V, T, T)
+    rows = np.concatenate([rng.choice(m.n_nodes, 40, replace=False), np.flatnonzero(m.bc_V)[:3],
+                           np.flatnonzero(m.bc_T)[:3], [m.n_nodes - 1]])
+    r, ref, res = coupled_rows(m, rows, V, T)
+    for i in r:
+        full = {}
+        for a in range(2):
+            lo, hi = J.indptr[2 * i + a], J.indptr[2 * i + a + 1]
+            full.update({(a, int(c // 2), int(c % 2)): v for c, v in zip(J.indices[lo:hi], J.data[lo:hi])})
+        assert set(full) == set(ref[int(i)])
+        for k, v in full.items():
+            assert abs(ref[int(i)][k] - v) <= 1e-13 * abs(v) + 1e-15
+        assert res[int(i)] == pytest.approx((R[2 * i], R[2 * i + 1]), rel=1e-13, abs=1e-12 * np.abs(R).max())
+
+
 def test_mesh_generator_counts():
     for n, N, E, el in ((8, 729, 3072, 3), (48, 117649, 663552, 13)):
         m = mg.cube_mesh(n, jitter=0.1, seed=1)

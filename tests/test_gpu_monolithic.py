@@ -78,6 +78,40 @@ def test_coupled_system_after_k_and_dt_change(assembly):
     np.testing.assert_allclose(res.ravel(), Rref, rtol=1e-11, atol=1e-12 * np.abs(Rref).max())
 
 
+def test_coupled_system_full_size_sampled_rows():
+    """At the 127^3 bench workload (2,097,152 nodes, launch configuration of the bench's monolithic leg), the
+    coupled Jacobian and residual of the row-owner assembly on sampled rows (2,000 random rows, 200 Dirichlet rows
+    of each field and the last row) against the oracle applied to the elements around them."""
+    from tests.sampled_rows import coupled_rows
+    rafem = R()
+    m = mg.workload_127()
+    rng = np.random.default_rng(3)
+    V = np.where(m.bc_V.astype(bool), m.g_V, 30.0 * rng.random(m.n_nodes))
+    T = np.where(m.bc_T.astype(bool), m.g_T, 37.0 + 15.0 * rng.random(m.n_nodes))
+    with rafem.Context(m, coupling=1, n_corrector=20, corrector_tol=1e-6) as ctx:
+        ctx.set_state(T=T, V=V)
+        blocks, res = ctx.get_coupled_system()
+        rp, col, _, _ = ctx.get_system(rafem.RAFEM_SYS_V)
+    sample = np.concatenate([rng.choice(m.n_nodes, 2000, replace=False),
+                             rng.choice(np.flatnonzero(m.bc_V), 200, replace=False),
+                             rng.choice(np.flatnonzero(m.bc_T), 200, replace=False), [m.n_nodes - 1]])
+    rows, ref, ref_res = coupled_rows(m, sample, V, T)
+    scale = max(abs(v) for e in ref.values() for v in e.values())
+    rscale = max(max(abs(a), abs(b)) for a, b in ref_res.values())
+    for i in rows:
+        got = {}
+        for q in range(rp[i], rp[i + 1]):
+            for a in range(2):
+                for b in range(2):
+                    got[(a, int(col[q]), b)] = blocks[q, a, b]
+        want = ref[int(i)]
+        for key in set(got) | set(want):
+            g, w = got.get(key, 0.0), want.get(key, 0.0)
+            assert abs(g - w) <= 1e-12 * abs(w) + 1e-13 * scale, (int(i), key, g, w)
+        for a in range(2):
+            assert abs(res[i, a] - ref_res[int(i)][a]) <= 1e-11 * abs(ref_res[int(i)][a]) + 1e-12 * rscale
+
+
 @pytest.mark.parametrize("solver", [0, 1], ids=["fgmres", "bicgstab"])
 def test_monolithic_steps_match_oracle_fixed_point(solver):
     """Two monolithic steps (dt = 30 s, 40 V, Newton to max |dT| < 1e-9) agree with the oracle's Newton step and
