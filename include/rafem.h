@@ -107,7 +107,9 @@ extern "C" {
                                         from a nonsymmetric system (BiCGSTAB or GMRES; no adjoint)              */
 
 #define RAFEM_ASSEMBLY_GATHER 0      /* row-owner assembly: one thread per matrix row sums the element
-                                        contributions of its entries (SELL-32 layout only)                    */
+                                        contributions of its entries (SELL-32 layout only); for the monolithic
+                                        step's 2 x 2 block Jacobian as well (an element pass writes per-element
+                                        records, a row pass sums them per entry)                              */
 #define RAFEM_ASSEMBLY_COLOR  1      /* element-owner scatter, one launch per element colour, no atomics     */
 
 #define RAFEM_ARITH_AUTO      0      /* element and node passes of the gather assembly in double-word arithmetic
